@@ -1,0 +1,1036 @@
+// CPU FP64 oracle for the fully-implicit black-oil Newton step.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, sequential
+// reference that the CUDA library is checked against.  Only the test suite,
+// the smoke check and the benchmark's CPU-baseline leg may build, load or call
+// it; the product path never does.  It shares no code with the CUDA library.
+//
+// What it computes, with the paper's notation (arXiv 1910.06059):
+//   * Discrete residual, Eq. (materialbalance), Section 2.1.1:
+//       R_a,i = phi_ref,i V_i / dt (A_a,i - A0_a,i) + sum_j u_a,ij + q_a,i
+//     with the accumulation terms of Eq. (acc) for dry gas (r_og = 0):
+//       A_w = m_phi b_w s_w, A_o = m_phi b_o s_o, A_g = m_phi (b_g s_g + r_go b_o s_o).
+//   * TPFA fluxes, Eqs. (flux1), (flux2), (head): upwinded b lambda times
+//     T_ij times the potential difference, with the arithmetic-mean density
+//     and the upwind cell chosen on the sign of the potential (>= 0: cell i).
+//   * Transmissibility, Appendix B: harmonic combination of the two
+//     half-transmissibilities t = |F| k / (distance centre to face).
+//   * Three-phase oil relative permeability by segregation, Eq. (gwseg).
+//   * Standard-well inflow, Eq. (wellinflow), in the reduced one-unknown
+//     form (BHP only) and the Schur complement of Eq. (wellequation).
+//   * Jacobian by forward-mode automatic differentiation (Section 2.4):
+//     a value carried together with its derivatives; products by the
+//     product rule.
+//   * Newton iteration, Eq. (linsystem), with Appleyard chop, variable
+//     switching with a threshold, time-step cutting (Section 2.3), and the
+//     MB / CNV convergence measures of Section 2.3.
+//   * ILU0 preconditioned BiCGStab (Section 2.3.1): textbook block ILU(0)
+//     on the matrix pattern in natural order, right-preconditioned
+//     BiCGStab of van der Vorst.
+//
+// Parity: the functions are pinned by the CPU test suite against finite
+// differences, mass conservation, hydrostatic equilibrium, the 1-D
+// incompressible closed form, the ILU(0) identity and dense LU on tiny grids.
+// Full three-phase trajectories are pinned only through those invariants.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+namespace orc {
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual number: value plus N first derivatives.
+// ---------------------------------------------------------------------------
+template <int N>
+struct Dual {
+    double v;
+    double d[N];
+    Dual() : v(0.0) { for (int k = 0; k < N; ++k) d[k] = 0.0; }
+    Dual(double c) : v(c) { for (int k = 0; k < N; ++k) d[k] = 0.0; }  // NOLINT
+    static Dual var(double val, int slot) { Dual r(val); r.d[slot] = 1.0; return r; }
+};
+
+template <int N> Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v + b.v; for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + b.d[k]; return r;
+}
+template <int N> Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v - b.v; for (int k = 0; k < N; ++k) r.d[k] = a.d[k] - b.d[k]; return r;
+}
+template <int N> Dual<N> operator-(const Dual<N>& a) {
+    Dual<N> r; r.v = -a.v; for (int k = 0; k < N; ++k) r.d[k] = -a.d[k]; return r;
+}
+template <int N> Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v * b.v;
+    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+template <int N> Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v / b.v;
+    for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+    return r;
+}
+template <int N> Dual<N> operator*(double s, const Dual<N>& a) { return Dual<N>(s) * a; }
+template <int N> Dual<N> operator*(const Dual<N>& a, double s) { return a * Dual<N>(s); }
+template <int N> Dual<N> operator+(double s, const Dual<N>& a) { return Dual<N>(s) + a; }
+template <int N> Dual<N> operator-(double s, const Dual<N>& a) { return Dual<N>(s) - a; }
+template <int N> Dual<N> operator-(const Dual<N>& a, double s) { return a - Dual<N>(s); }
+template <int N> Dual<N> operator/(const Dual<N>& a, double s) { return a / Dual<N>(s); }
+template <int N> Dual<N> operator/(double s, const Dual<N>& a) { return Dual<N>(s) / a; }
+
+template <int N> Dual<N> dexp(const Dual<N>& a) {
+    Dual<N> r; r.v = std::exp(a.v);
+    for (int k = 0; k < N; ++k) r.d[k] = r.v * a.d[k];
+    return r;
+}
+// a^n for a >= 0 (n > 1), derivative n a^(n-1).
+template <int N> Dual<N> dpow(const Dual<N>& a, double n) {
+    Dual<N> r; r.v = std::pow(a.v, n);
+    double dd = n * std::pow(a.v, n - 1.0);
+    for (int k = 0; k < N; ++k) r.d[k] = dd * a.d[k];
+    return r;
+}
+// clamp to [0, 1]; derivative zero where the clamp is active.
+template <int N> Dual<N> clamp01(const Dual<N>& a) {
+    if (a.v <= 0.0) return Dual<N>(0.0);
+    if (a.v >= 1.0) return Dual<N>(1.0);
+    return a;
+}
+// Re-seat a 3-derivative cell dual into slots [off, off+3) of an M-dual.
+template <int M> Dual<M> lift(const Dual<3>& a, int off) {
+    Dual<M> r(a.v); for (int k = 0; k < 3; ++k) r.d[off + k] = a.d[k]; return r;
+}
+
+// ---------------------------------------------------------------------------
+// Parameters.  The order of the flat array matches synth.fluid_params().
+// ---------------------------------------------------------------------------
+struct Fluid {
+    double g, rho_s[3], p_ref, bw_ref, c_w, mu_w, R_sb, p_b, Bo_slope, c_o, mu_o0, mu_o_r,
+        c_mu, p_sc, Z, mu_g0, mu_g_p, c_r, s_wco, s_orw, s_org, n_corey;
+};
+static Fluid fluid_from(const double* f) {
+    Fluid F;
+    F.g = f[0]; F.rho_s[0] = f[1]; F.rho_s[1] = f[2]; F.rho_s[2] = f[3];
+    F.p_ref = f[4]; F.bw_ref = f[5]; F.c_w = f[6]; F.mu_w = f[7]; F.R_sb = f[8]; F.p_b = f[9];
+    F.Bo_slope = f[10]; F.c_o = f[11]; F.mu_o0 = f[12]; F.mu_o_r = f[13]; F.c_mu = f[14];
+    F.p_sc = f[15]; F.Z = f[16]; F.mu_g0 = f[17]; F.mu_g_p = f[18]; F.c_r = f[19];
+    F.s_wco = f[20]; F.s_orw = f[21]; F.s_org = f[22]; F.n_corey = f[23];
+    return F;
+}
+
+enum { W = 0, O = 1, G = 2 };
+enum { SAT = 0, USAT = 1 };
+
+// Cell quantities with derivatives with respect to the cell's own primary
+// variables (p_o, s_w, x) -- Section 2.1.2 primary-variable choice.
+struct CellProps {
+    Dual<3> b[3], lam[3], rho[3], mphi, rgo, s[3];
+    Dual<3> A[3];  // accumulation terms (Eq. acc)
+};
+
+// Dissolution limit r_s(p): linear up to the bubble point (reading of the
+// configuration "Rs(p) linear to bubble point").
+static Dual<3> rs_of(const Fluid& F, const Dual<3>& p) { return p * (F.R_sb / F.p_b); }
+
+static CellProps cell_props(const Fluid& F, double p_, double sw_, double x_, int flag) {
+    CellProps c;
+    Dual<3> p = Dual<3>::var(p_, 0), sw = Dual<3>::var(sw_, 1), x = Dual<3>::var(x_, 2);
+    Dual<3> sg, rgo;
+    if (flag == SAT) { sg = x; rgo = rs_of(F, p); }      // gas present: x = s_g, oil saturated
+    else             { sg = Dual<3>(0.0); rgo = x; }     // no gas: x = r_go
+    Dual<3> so = 1.0 - sw - sg;
+    c.s[W] = sw; c.s[O] = so; c.s[G] = sg; c.rgo = rgo;
+
+    // Water: b_w(p; c_w, p_ref, b_ref), constant viscosity (Section 2.1.6).
+    c.b[W] = F.bw_ref * dexp(F.c_w * (p - F.p_ref));
+    Dual<3> mu_w(F.mu_w);
+    // Live oil: saturated FVF B_o,sat(r) and undersaturated compressibility
+    // about the saturation pressure p_sat(r) of the dissolved gas ratio.
+    Dual<3> psat = rgo * (F.p_b / F.R_sb);
+    Dual<3> Bsat = 1.0 + F.Bo_slope * rgo;
+    c.b[O] = dexp(F.c_o * (p - psat)) / Bsat;
+    Dual<3> mu_o = (F.mu_o0 / (1.0 + F.mu_o_r * rgo)) * dexp(F.c_mu * (p - psat));
+    // Dry gas.
+    c.b[G] = p / (F.p_sc * F.Z);
+    Dual<3> mu_g = F.mu_g0 * (1.0 + p / F.mu_g_p);
+    // Rock: phi = m_phi(p) phi_ref (Section 2.1.4).
+    c.mphi = dexp(F.c_r * (p - F.p_ref));
+    // Densities (nomenclature): rho_w = b_w rho_Sw, rho_o = b_o (rho_So + r_go rho_Sg), rho_g = b_g rho_Sg.
+    c.rho[W] = c.b[W] * F.rho_s[W];
+    c.rho[O] = c.b[O] * (F.rho_s[O] + rgo * F.rho_s[G]);
+    c.rho[G] = c.b[G] * F.rho_s[G];
+
+    // Relative permeabilities: Corey two-phase curves combined by Eq. (gwseg).
+    double n = F.n_corey;
+    Dual<3> krw = dpow(clamp01((sw - F.s_wco) / (1.0 - F.s_wco - F.s_orw)), n);
+    Dual<3> krg = dpow(clamp01(sg / (1.0 - F.s_wco - F.s_org)), n);
+    Dual<3> krow = dpow(clamp01((so - F.s_orw) / (1.0 - F.s_wco - F.s_orw)), n);
+    Dual<3> krog = dpow(clamp01((so - F.s_org) / (1.0 - F.s_wco - F.s_org)), n);
+    Dual<3> ww = sw - F.s_wco;
+    if (ww.v < 0.0) ww = Dual<3>(0.0);
+    Dual<3> den = ww + sg;
+    Dual<3> kro = (den.v <= 1e-14) ? krow : (ww * krow + sg * krog) / den;
+    c.lam[W] = krw / mu_w;
+    c.lam[O] = kro / mu_o;
+    c.lam[G] = krg / mu_g;
+
+    c.A[W] = c.mphi * c.b[W] * sw;
+    c.A[O] = c.mphi * c.b[O] * so;
+    c.A[G] = c.mphi * (c.b[G] * sg + rgo * c.b[O] * so);
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Model
+// ---------------------------------------------------------------------------
+struct Well {
+    int kind;      // 0 injector, 1 producer
+    int phase;     // injected phase (W or G) for injectors
+    int control0;  // 0 rate, 1 bhp (as given)
+    int control;   // current control within a step
+    double target, bhp_limit, rw, skin;
+    std::vector<int> cells;
+    std::vector<double> WI;
+    double z_datum = 0.0, rho_well = 0.0;
+    double bhp = 0.0;
+    // Linearisation of the well (rate-controlled wells only).
+    double Rw = 0.0, Dw = 0.0;
+    std::vector<double> B;  // 3 per connection: dR_w/dy_cell
+    std::vector<double> C;  // 3 per connection: dR_cell/dbhp
+};
+
+struct Model {
+    int nx, ny, nz, n;
+    double top_depth = 0.0;
+    Fluid F;
+    std::vector<double> dx, dy, dz;
+    std::vector<double> perm, poro, pv, depth, vol;
+    // Transmissibility of the +x, +y, +z face of each cell (0 at the boundary).
+    std::vector<double> Tx, Ty, Tz;
+    std::vector<Well> wells;
+    // State
+    std::vector<double> p, sw, x;
+    std::vector<uint8_t> flag;
+    // Step-start data
+    std::vector<double> A0;  // 3n
+    std::vector<double> bk_p, bk_sw, bk_x, bk_bhp;
+    std::vector<uint8_t> bk_flag;
+    // Linear system (BCSR, 3x3 row-major blocks) and residual
+    std::vector<int> rowptr, colind, diagpos;
+    std::vector<double> vals, R;
+    // ILU(0) factors in the same pattern (strict L blocks and U blocks incl. diagonal)
+    std::vector<double> lu;
+    std::vector<double> Uinv;  // inverse of U diagonal blocks, 9n
+    double dt_last = 0.0;
+};
+
+static inline int cidx(const Model& m, int i, int j, int k) { return i + m.nx * (j + m.ny * k); }
+
+static void build_pattern(Model& m) {
+    int n = m.n;
+    m.rowptr.assign(n + 1, 0);
+    m.colind.clear();
+    m.diagpos.assign(n, 0);
+    for (int k = 0; k < m.nz; ++k)
+        for (int j = 0; j < m.ny; ++j)
+            for (int i = 0; i < m.nx; ++i) {
+                int c = cidx(m, i, j, k);
+                std::vector<int> cols;
+                if (k > 0) cols.push_back(c - m.nx * m.ny);
+                if (j > 0) cols.push_back(c - m.nx);
+                if (i > 0) cols.push_back(c - 1);
+                cols.push_back(c);
+                if (i < m.nx - 1) cols.push_back(c + 1);
+                if (j < m.ny - 1) cols.push_back(c + m.nx);
+                if (k < m.nz - 1) cols.push_back(c + m.nx * m.ny);
+                for (int q : cols) {
+                    if (q == c) m.diagpos[c] = (int)m.colind.size();
+                    m.colind.push_back(q);
+                }
+                m.rowptr[c + 1] = (int)m.colind.size();
+            }
+    m.vals.assign(9 * m.colind.size(), 0.0);
+}
+
+static int find_block(const Model& m, int row, int col) {
+    for (int q = m.rowptr[row]; q < m.rowptr[row + 1]; ++q)
+        if (m.colind[q] == col) return q;
+    return -1;
+}
+
+// Appendix B: half-transmissibility of a box cell towards a face normal to
+// axis d is |F| k / (h_d / 2); T_ij = t_ij t_ji / (t_ij + t_ji).
+static void compute_static(Model& m) {
+    int n = m.n;
+    m.pv.assign(n, 0); m.depth.assign(n, 0); m.vol.assign(n, 0);
+    m.Tx.assign(n, 0); m.Ty.assign(n, 0); m.Tz.assign(n, 0);
+    std::vector<double> ztop(m.nz + 1, m.top_depth);
+    for (int k = 0; k < m.nz; ++k) ztop[k + 1] = ztop[k] + m.dz[k];
+    for (int k = 0; k < m.nz; ++k)
+        for (int j = 0; j < m.ny; ++j)
+            for (int i = 0; i < m.nx; ++i) {
+                int c = cidx(m, i, j, k);
+                m.vol[c] = m.dx[i] * m.dy[j] * m.dz[k];
+                m.pv[c] = m.poro[c] * m.vol[c];
+            }
+    for (int k = 0; k < m.nz; ++k)
+        for (int j = 0; j < m.ny; ++j)
+            for (int i = 0; i < m.nx; ++i)
+                m.depth[cidx(m, i, j, k)] = ztop[k] + 0.5 * m.dz[k];
+    for (int k = 0; k < m.nz; ++k)
+        for (int j = 0; j < m.ny; ++j)
+            for (int i = 0; i < m.nx; ++i) {
+                int c = cidx(m, i, j, k);
+                if (i + 1 < m.nx) {
+                    int e = c + 1;
+                    double area = m.dy[j] * m.dz[k];
+                    double t1 = area * m.perm[c] / (0.5 * m.dx[i]);
+                    double t2 = area * m.perm[e] / (0.5 * m.dx[i + 1]);
+                    m.Tx[c] = t1 * t2 / (t1 + t2);
+                }
+                if (j + 1 < m.ny) {
+                    int e = c + m.nx;
+                    double area = m.dx[i] * m.dz[k];
+                    double t1 = area * m.perm[c] / (0.5 * m.dy[j]);
+                    double t2 = area * m.perm[e] / (0.5 * m.dy[j + 1]);
+                    m.Ty[c] = t1 * t2 / (t1 + t2);
+                }
+                if (k + 1 < m.nz) {
+                    int e = c + m.nx * m.ny;
+                    double area = m.dx[i] * m.dy[j];
+                    double t1 = area * m.perm[c] / (0.5 * m.dz[k]);
+                    double t2 = area * m.perm[e] / (0.5 * m.dz[k + 1]);
+                    m.Tz[c] = t1 * t2 / (t1 + t2);
+                }
+            }
+}
+
+// Peaceman well index for a vertical connection in a box cell:
+// WI = 2 pi k h / (ln(r_o / r_w) + skin), r_o = 0.14 sqrt(dx^2 + dy^2).
+static double peaceman(double k, double dx, double dy, double h, double rw, double skin) {
+    double ro = 0.14 * std::sqrt(dx * dx + dy * dy);
+    return 2.0 * M_PI * k * h / (std::log(ro / rw) + skin);
+}
+
+// ---------------------------------------------------------------------------
+// Well terms.  Connection inflow (Eq. wellinflow) in surface volumes, with
+// derivatives with respect to the cell's (p, s_w, x) (slots 0..2) and the
+// well BHP (slot 3).  Reading of the paper's M_{a,j}: producing connections
+// carry each phase at its own mobility; injecting connections carry the
+// injected phase at the total mobility; reverse flow is set to zero.
+// ---------------------------------------------------------------------------
+static void connection_rates(const Model& m, const Well& w, int con, Dual<4> q[3]) {
+    const Fluid& F = m.F;
+    int c = w.cells[con];
+    CellProps cp = cell_props(F, m.p[c], m.sw[c], m.x[c], m.flag[c]);
+    Dual<4> pc = lift<4>(Dual<3>::var(m.p[c], 0), 0);
+    Dual<4> bhp = (w.control == 0) ? Dual<4>::var(w.bhp, 3) : Dual<4>(w.bhp);
+    double h = F.g * w.rho_well * (m.depth[c] - w.z_datum);
+    Dual<4> dp = pc - bhp - h;
+    for (int a = 0; a < 3; ++a) q[a] = Dual<4>(0.0);
+    double WI = w.WI[con];
+    if (w.kind == 1) {  // producer
+        if (dp.v > 0.0) {
+            for (int a = 0; a < 3; ++a) q[a] = WI * lift<4>(cp.b[a] * cp.lam[a], 0) * dp;
+            q[G] = q[G] + WI * lift<4>(cp.rgo * cp.b[O] * cp.lam[O], 0) * dp;
+        }
+    } else {            // injector
+        if (dp.v < 0.0) {
+            Dual<3> lt = cp.lam[W] + cp.lam[O] + cp.lam[G];
+            q[w.phase] = WI * lift<4>(lt * cp.b[w.phase], 0) * dp;
+        }
+    }
+}
+
+// Surface rate that a rate control acts on: the injected component for an
+// injector (positive when injecting), the oil rate for a producer.
+static Dual<4> controlled_rate(const Well& w, const Dual<4> q[3]) {
+    if (w.kind == 0) return -q[w.phase];
+    return q[O];
+}
+
+// ---------------------------------------------------------------------------
+// Assembly
+// ---------------------------------------------------------------------------
+static void add_block(Model& m, int q, const double blk[9], double sgn) {
+    for (int e = 0; e < 9; ++e) m.vals[9 * q + e] += sgn * blk[e];
+}
+
+static void begin_step(Model& m) {
+    int n = m.n;
+    m.A0.assign(3 * n, 0.0);
+    for (int c = 0; c < n; ++c) {
+        CellProps cp = cell_props(m.F, m.p[c], m.sw[c], m.x[c], m.flag[c]);
+        for (int a = 0; a < 3; ++a) m.A0[3 * c + a] = cp.A[a].v;
+    }
+    // Well datum and wellbore density, explicit over the step (Section 2.2.1).
+    for (Well& w : m.wells) {
+        w.control = w.control0;
+        if (w.control == 1) w.bhp = w.target;
+        int c0 = w.cells[0];
+        w.z_datum = m.depth[c0];
+        if (w.kind == 0) {
+            CellProps cp = cell_props(m.F, m.p[c0], m.sw[c0], m.x[c0], m.flag[c0]);
+            w.rho_well = cp.rho[w.phase].v;
+        } else {
+            double num = 0.0, den = 0.0;
+            for (int c : w.cells) {
+                CellProps cp = cell_props(m.F, m.p[c], m.sw[c], m.x[c], m.flag[c]);
+                for (int a = 0; a < 3; ++a) { num += cp.lam[a].v * cp.rho[a].v; den += cp.lam[a].v; }
+            }
+            w.rho_well = den > 0.0 ? num / den : 0.0;
+        }
+    }
+    m.bk_p = m.p; m.bk_sw = m.sw; m.bk_x = m.x; m.bk_flag = m.flag;
+    m.bk_bhp.clear();
+    for (Well& w : m.wells) m.bk_bhp.push_back(w.bhp);
+}
+
+static void assemble(Model& m, double dt) {
+    const Fluid& F = m.F;
+    int n = m.n;
+    std::fill(m.vals.begin(), m.vals.end(), 0.0);
+    m.R.assign(3 * n, 0.0);
+    m.dt_last = dt;
+    std::vector<CellProps> props(n);
+    for (int c = 0; c < n; ++c) props[c] = cell_props(F, m.p[c], m.sw[c], m.x[c], m.flag[c]);
+
+    // Accumulation: (phi_ref V / dt) (A - A0) into R and the diagonal block.
+    for (int c = 0; c < n; ++c) {
+        double s = m.pv[c] / dt;
+        double blk[9];
+        for (int a = 0; a < 3; ++a) {
+            m.R[3 * c + a] += s * (props[c].A[a].v - m.A0[3 * c + a]);
+            for (int v = 0; v < 3; ++v) blk[3 * a + v] = s * props[c].A[a].d[v];
+        }
+        add_block(m, m.diagpos[c], blk, 1.0);
+    }
+
+    // Faces: each connection once, oriented from the lower to the higher index.
+    auto face = [&](int i, int j, double T) {
+        const CellProps& ci = props[i];
+        const CellProps& cj = props[j];
+        Dual<6> pi = lift<6>(Dual<3>::var(m.p[i], 0), 0);
+        Dual<6> pj = lift<6>(Dual<3>::var(m.p[j], 0), 3);
+        double dz = m.depth[i] - m.depth[j];
+        Dual<6> u[3];
+        Dual<6> dphi[3];
+        bool up_i[3];
+        for (int a = 0; a < 3; ++a) {
+            Dual<6> rho_ij = 0.5 * (lift<6>(ci.rho[a], 0) + lift<6>(cj.rho[a], 3));
+            dphi[a] = pi - pj - F.g * rho_ij * dz;
+            up_i[a] = dphi[a].v >= 0.0;
+            Dual<6> mob = up_i[a] ? lift<6>(ci.b[a] * ci.lam[a], 0) : lift<6>(cj.b[a] * cj.lam[a], 3);
+            u[a] = mob * T * dphi[a];
+        }
+        // Dissolved gas travels with the oil phase (Eq. flux2).
+        Dual<6> rmob = up_i[O] ? lift<6>(ci.rgo * ci.b[O] * ci.lam[O], 0)
+                               : lift<6>(cj.rgo * cj.b[O] * cj.lam[O], 3);
+        u[G] = u[G] + rmob * T * dphi[O];
+        double bi[9], bj[9];
+        for (int a = 0; a < 3; ++a) {
+            m.R[3 * i + a] += u[a].v;
+            m.R[3 * j + a] -= u[a].v;
+            for (int v = 0; v < 3; ++v) { bi[3 * a + v] = u[a].d[v]; bj[3 * a + v] = u[a].d[3 + v]; }
+        }
+        add_block(m, m.diagpos[i], bi, 1.0);
+        add_block(m, find_block(m, i, j), bj, 1.0);
+        add_block(m, find_block(m, j, i), bi, -1.0);
+        add_block(m, m.diagpos[j], bj, -1.0);
+    };
+    for (int k = 0; k < m.nz; ++k)
+        for (int jj = 0; jj < m.ny; ++jj)
+            for (int ii = 0; ii < m.nx; ++ii) {
+                int c = cidx(m, ii, jj, k);
+                if (ii + 1 < m.nx) face(c, c + 1, m.Tx[c]);
+                if (jj + 1 < m.ny) face(c, c + m.nx, m.Ty[c]);
+                if (k + 1 < m.nz) face(c, c + m.nx * m.ny, m.Tz[c]);
+            }
+
+    // Wells: q_a,i adds to R_a,i; rate-controlled wells add an equation.
+    for (Well& w : m.wells) {
+        int nc = (int)w.cells.size();
+        w.B.assign(3 * nc, 0.0); w.C.assign(3 * nc, 0.0);
+        Dual<4> rate(0.0);
+        for (int con = 0; con < nc; ++con) {
+            int c = w.cells[con];
+            Dual<4> q[3];
+            connection_rates(m, w, con, q);
+            double blk[9];
+            for (int a = 0; a < 3; ++a) {
+                m.R[3 * c + a] += q[a].v;
+                for (int v = 0; v < 3; ++v) blk[3 * a + v] = q[a].d[v];
+                w.C[3 * con + a] = q[a].d[3];
+            }
+            add_block(m, m.diagpos[c], blk, 1.0);
+            Dual<4> r = controlled_rate(w, q);
+            for (int v = 0; v < 3; ++v) w.B[3 * con + v] = r.d[v];
+            rate = rate + r;
+        }
+        if (w.control == 0) {
+            // Eq. (well-control-rate): R_c = Q - Q_target.
+            w.Rw = rate.v - w.target;
+            w.Dw = rate.d[3];
+        } else {
+            w.Rw = 0.0; w.Dw = 1.0;
+            std::fill(w.B.begin(), w.B.end(), 0.0);
+            std::fill(w.C.begin(), w.C.end(), 0.0);
+        }
+    }
+}
+
+// Section 2.3 convergence measures (per component a):
+//   MB_a  = dt * Bavg_a * |sum_i R_a,i| / sum_i PV_i
+//   CNV_a = dt * Bavg_a * max_i |R_a,i| / PV_i,   Bavg_a = mean_i 1 / b_a,i
+// out[0..2] = MB, out[3..5] = CNV, out[6] = max relative well-equation residual.
+static void norms(const Model& m, double dt, double* out) {
+    int n = m.n;
+    double sumR[3] = {0, 0, 0}, maxR[3] = {0, 0, 0}, sumB[3] = {0, 0, 0}, pvt = 0.0;
+    for (int c = 0; c < n; ++c) {
+        CellProps cp = cell_props(m.F, m.p[c], m.sw[c], m.x[c], m.flag[c]);
+        pvt += m.pv[c];
+        for (int a = 0; a < 3; ++a) {
+            sumR[a] += m.R[3 * c + a];
+            maxR[a] = std::max(maxR[a], std::fabs(m.R[3 * c + a]) / m.pv[c]);
+            sumB[a] += 1.0 / cp.b[a].v;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        double Bavg = sumB[a] / n;
+        out[a] = dt * Bavg * std::fabs(sumR[a]) / pvt;
+        out[3 + a] = dt * Bavg * maxR[a];
+    }
+    double wr = 0.0;
+    for (const Well& w : m.wells)
+        if (w.control == 0) wr = std::max(wr, std::fabs(w.Rw) / std::max(std::fabs(w.target), 1e-300));
+    out[6] = wr;
+}
+
+// ---------------------------------------------------------------------------
+// Linear algebra on 3x3 blocks (row-major)
+// ---------------------------------------------------------------------------
+static void mm3(const double* a, const double* b, double* c) {
+    for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += a[3 * r + k] * b[3 * k + s];
+            c[3 * r + s] = acc;
+        }
+}
+static void mv3(const double* a, const double* x, double* y) {
+    for (int r = 0; r < 3; ++r) y[r] = a[3 * r] * x[0] + a[3 * r + 1] * x[1] + a[3 * r + 2] * x[2];
+}
+// Inverse by Gaussian elimination with partial pivoting.
+static bool inv3(const double* a, double* out) {
+    double m[3][6];
+    for (int r = 0; r < 3; ++r) {
+        for (int s = 0; s < 3; ++s) { m[r][s] = a[3 * r + s]; m[r][3 + s] = (r == s) ? 1.0 : 0.0; }
+    }
+    for (int col = 0; col < 3; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 3; ++r) if (std::fabs(m[r][col]) > std::fabs(m[piv][col])) piv = r;
+        if (m[piv][col] == 0.0) return false;
+        if (piv != col) for (int s = 0; s < 6; ++s) std::swap(m[col][s], m[piv][s]);
+        double d = m[col][col];
+        for (int s = 0; s < 6; ++s) m[col][s] /= d;
+        for (int r = 0; r < 3; ++r) {
+            if (r == col) continue;
+            double f = m[r][col];
+            for (int s = 0; s < 6; ++s) m[r][s] -= f * m[col][s];
+        }
+    }
+    for (int r = 0; r < 3; ++r) for (int s = 0; s < 3; ++s) out[3 * r + s] = m[r][3 + s];
+    return true;
+}
+
+// Textbook block ILU(0) in natural row order, restricted to the pattern of A:
+// for each row i and each k < i in the pattern: L_ik = A_ik U_kk^-1, then
+// A_ij -= L_ik U_kj for every j > k present in both row i and row k.
+static bool ilu0(Model& m) {
+    int n = m.n;
+    m.lu = m.vals;
+    m.Uinv.assign(9 * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        for (int q = m.rowptr[i]; q < m.rowptr[i + 1]; ++q) {
+            int k = m.colind[q];
+            if (k >= i) break;
+            double L[9];
+            mm3(&m.lu[9 * q], &m.Uinv[9 * k], L);
+            std::memcpy(&m.lu[9 * q], L, sizeof(L));
+            for (int qk = m.rowptr[k]; qk < m.rowptr[k + 1]; ++qk) {
+                int j = m.colind[qk];
+                if (j <= k) continue;
+                int qi = find_block(m, i, j);
+                if (qi < 0) continue;
+                double P[9];
+                mm3(L, &m.lu[9 * qk], P);
+                for (int e = 0; e < 9; ++e) m.lu[9 * qi + e] -= P[e];
+            }
+        }
+        if (!inv3(&m.lu[9 * m.diagpos[i]], &m.Uinv[9 * i])) return false;
+    }
+    return true;
+}
+
+// z = (LU)^-1 r: forward substitution with unit-lower L, back substitution with U.
+static void ilu_apply(const Model& m, const double* r, double* z) {
+    int n = m.n;
+    std::vector<double> y(3 * n);
+    for (int i = 0; i < n; ++i) {
+        double acc[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
+        for (int q = m.rowptr[i]; q < m.diagpos[i]; ++q) {
+            double t[3];
+            mv3(&m.lu[9 * q], &y[3 * m.colind[q]], t);
+            for (int e = 0; e < 3; ++e) acc[e] -= t[e];
+        }
+        for (int e = 0; e < 3; ++e) y[3 * i + e] = acc[e];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double acc[3] = {y[3 * i], y[3 * i + 1], y[3 * i + 2]};
+        for (int q = m.diagpos[i] + 1; q < m.rowptr[i + 1]; ++q) {
+            double t[3];
+            mv3(&m.lu[9 * q], &z[3 * m.colind[q]], t);
+            for (int e = 0; e < 3; ++e) acc[e] -= t[e];
+        }
+        mv3(&m.Uinv[9 * i], acc, &z[3 * i]);
+    }
+}
+
+// Reduced operator of Eq. (wellequation): y = A x - sum_w C_w D_w^-1 (B_w x).
+static void apply_op(const Model& m, const double* x, double* y) {
+    int n = m.n;
+    for (int i = 0; i < n; ++i) {
+        double acc[3] = {0, 0, 0};
+        for (int q = m.rowptr[i]; q < m.rowptr[i + 1]; ++q) {
+            double t[3];
+            mv3(&m.vals[9 * q], &x[3 * m.colind[q]], t);
+            for (int e = 0; e < 3; ++e) acc[e] += t[e];
+        }
+        for (int e = 0; e < 3; ++e) y[3 * i + e] = acc[e];
+    }
+    for (const Well& w : m.wells) {
+        if (w.control != 0) continue;
+        double bx = 0.0;
+        for (size_t con = 0; con < w.cells.size(); ++con)
+            for (int v = 0; v < 3; ++v) bx += w.B[3 * con + v] * x[3 * w.cells[con] + v];
+        double s = bx / w.Dw;
+        for (size_t con = 0; con < w.cells.size(); ++con)
+            for (int e = 0; e < 3; ++e) y[3 * w.cells[con] + e] -= w.C[3 * con + e] * s;
+    }
+}
+
+static double dot(const std::vector<double>& a, const std::vector<double>& b) {
+    double s = 0.0;
+    for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+    return s;
+}
+
+enum { LIN_OK = 0, LIN_NOT_CONVERGED = 1, LIN_BREAKDOWN = 2, LIN_FACTOR_FAIL = 3 };
+
+// Right-preconditioned BiCGStab (van der Vorst) on the reduced system
+// S x = b, b = R_r - sum_w C_w D_w^-1 R_w; then x_w = D_w^-1 (R_w - B_w x_r).
+// Output sol has 3n reservoir entries followed by one entry per well
+// (zero for wells without an unknown).  Stops when ||r|| <= tol ||r0||.
+static int solve(Model& m, double tol, int maxit, double* sol, int* its_out) {
+    int n = m.n, N = 3 * n;
+    *its_out = 0;
+    if (!ilu0(m)) return LIN_FACTOR_FAIL;
+    std::vector<double> b(m.R);
+    for (const Well& w : m.wells) {
+        if (w.control != 0) continue;
+        double s = w.Rw / w.Dw;
+        for (size_t con = 0; con < w.cells.size(); ++con)
+            for (int e = 0; e < 3; ++e) b[3 * w.cells[con] + e] -= w.C[3 * con + e] * s;
+    }
+    std::vector<double> x(N, 0.0), r(b), rh(b), p(N, 0.0), v(N, 0.0), ph(N), s(N), sh(N), t(N);
+    double nr0 = std::sqrt(dot(r, r));
+    int status = LIN_NOT_CONVERGED;
+    int it = 0;
+    if (nr0 == 0.0) status = LIN_OK;
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    for (it = 1; status == LIN_NOT_CONVERGED && it <= maxit; ++it) {
+        double rho = dot(rh, r);
+        if (rho == 0.0 || !std::isfinite(rho)) { status = LIN_BREAKDOWN; break; }
+        double beta = (rho / rho_old) * (alpha / omega);
+        for (int i = 0; i < N; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        ilu_apply(m, p.data(), ph.data());
+        apply_op(m, ph.data(), v.data());
+        double rv = dot(rh, v);
+        if (rv == 0.0 || !std::isfinite(rv)) { status = LIN_BREAKDOWN; break; }
+        alpha = rho / rv;
+        for (int i = 0; i < N; ++i) s[i] = r[i] - alpha * v[i];
+        double ns = std::sqrt(dot(s, s));
+        if (ns <= tol * nr0) {
+            for (int i = 0; i < N; ++i) x[i] += alpha * ph[i];
+            status = LIN_OK;
+            *its_out = it;
+            break;
+        }
+        ilu_apply(m, s.data(), sh.data());
+        apply_op(m, sh.data(), t.data());
+        double tt = dot(t, t);
+        if (tt == 0.0 || !std::isfinite(tt)) { status = LIN_BREAKDOWN; break; }
+        omega = dot(t, s) / tt;
+        if (omega == 0.0 || !std::isfinite(omega)) { status = LIN_BREAKDOWN; break; }
+        for (int i = 0; i < N; ++i) { x[i] += alpha * ph[i] + omega * sh[i]; r[i] = s[i] - omega * t[i]; }
+        double nr = std::sqrt(dot(r, r));
+        *its_out = it;
+        if (nr <= tol * nr0) { status = LIN_OK; break; }
+        rho_old = rho;
+    }
+    if (status == LIN_NOT_CONVERGED) *its_out = maxit;
+    for (int i = 0; i < N; ++i) sol[i] = x[i];
+    int wi = 0;
+    for (const Well& w : m.wells) {
+        double xw = 0.0;
+        if (w.control == 0) {
+            double bx = 0.0;
+            for (size_t con = 0; con < w.cells.size(); ++con)
+                for (int v2 = 0; v2 < 3; ++v2) bx += w.B[3 * con + v2] * x[3 * w.cells[con] + v2];
+            xw = (w.Rw - bx) / w.Dw;
+        }
+        sol[N + wi] = xw;
+        ++wi;
+    }
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// Newton update (Section 2.3): dy = -sol; Appleyard chop; variable switching.
+// ---------------------------------------------------------------------------
+struct Opts {
+    double tol_mb, tol_cnv, tol_well;
+    int max_newton;
+    double tol_lin;
+    int max_lin, max_cuts;
+    double ds_max, dp_rel_max, drs_rel_max, eps_switch;
+};
+static Opts opts_from(const double* o) {
+    Opts r;
+    r.tol_mb = o[0]; r.tol_cnv = o[1]; r.tol_well = o[2]; r.max_newton = (int)o[3];
+    r.tol_lin = o[4]; r.max_lin = (int)o[5]; r.max_cuts = (int)o[6];
+    r.ds_max = o[7]; r.dp_rel_max = o[8]; r.drs_rel_max = o[9]; r.eps_switch = o[10];
+    return r;
+}
+
+static void newton_update(Model& m, const Opts& o, const double* sol) {
+    const Fluid& F = m.F;
+    int n = m.n;
+    for (int c = 0; c < n; ++c) {
+        double dp = -sol[3 * c], dsw = -sol[3 * c + 1], dx = -sol[3 * c + 2];
+        double p = m.p[c];
+        double dpmax = o.dp_rel_max * p;
+        if (std::fabs(dp) > dpmax) dp = (dp > 0 ? dpmax : -dpmax);
+        if (m.flag[c] == SAT) {
+            double mx = std::max(std::fabs(dsw), std::fabs(dx));
+            if (mx > o.ds_max) { double f = o.ds_max / mx; dsw *= f; dx *= f; }
+        } else {
+            if (std::fabs(dsw) > o.ds_max) { double f = o.ds_max / std::fabs(dsw); dsw *= f; }
+            double drmax = o.drs_rel_max * F.R_sb;
+            if (std::fabs(dx) > drmax) dx = (dx > 0 ? drmax : -drmax);
+        }
+        double pn = p + dp, swn = m.sw[c] + dsw, xn = m.x[c] + dx;
+        swn = std::min(std::max(swn, 0.0), 1.0);
+        uint8_t fl = m.flag[c];
+        if (fl == SAT) {
+            if (xn > 1.0 - swn) xn = 1.0 - swn;
+            if (xn < 0.0) { fl = USAT; xn = pn * (F.R_sb / F.p_b); }
+        } else {
+            double rs = pn * (F.R_sb / F.p_b);
+            if (xn > rs * (1.0 + o.eps_switch)) { fl = SAT; xn = 0.0; }
+        }
+        m.p[c] = pn; m.sw[c] = swn; m.x[c] = xn; m.flag[c] = fl;
+    }
+    int wi = 0;
+    for (Well& w : m.wells) {
+        if (w.control == 0) {
+            double d = -sol[3 * n + wi];
+            double dmax = o.dp_rel_max * w.bhp;
+            if (std::fabs(d) > dmax) d = (d > 0 ? dmax : -dmax);
+            w.bhp += d;
+            bool viol = (w.kind == 0) ? (w.bhp > w.bhp_limit) : (w.bhp < w.bhp_limit);
+            if (viol) { w.control = 1; w.bhp = w.bhp_limit; }
+        }
+        ++wi;
+    }
+}
+
+// After assembly: a rate-controlled well with no flowing connection (D_w = 0)
+// cannot meet its target at the current BHP; it is put on its BHP limit for
+// the rest of the step, and the system is assembled again.
+static bool fix_dead_wells(Model& m) {
+    bool changed = false;
+    for (Well& w : m.wells)
+        if (w.control == 0 && w.Dw == 0.0) { w.control = 1; w.bhp = w.bhp_limit; changed = true; }
+    return changed;
+}
+
+static void restore(Model& m) {
+    m.p = m.bk_p; m.sw = m.bk_sw; m.x = m.bk_x; m.flag = m.bk_flag;
+    for (size_t i = 0; i < m.wells.size(); ++i) m.wells[i].bhp = m.bk_bhp[i];
+}
+
+// One Newton solve of a (sub)step of length dt; returns 0 when converged.
+// rep: [newton_its, lin_its]
+static int newton(Model& m, double dt, const Opts& o, int* nits, int* lits) {
+    begin_step(m);
+    std::vector<double> sol(3 * m.n + m.wells.size());
+    double nrm[7];
+    for (int it = 0;; ++it) {
+        assemble(m, dt);
+        if (fix_dead_wells(m)) assemble(m, dt);
+        norms(m, dt, nrm);
+        bool finite = true;
+        for (double v : nrm) if (!std::isfinite(v)) finite = false;
+        if (!finite) return 2;
+        bool conv = true;
+        for (int a = 0; a < 3; ++a) if (nrm[a] > o.tol_mb || nrm[3 + a] > o.tol_cnv) conv = false;
+        if (nrm[6] > o.tol_well) conv = false;
+        if (conv) { *nits = it; return 0; }
+        if (it == o.max_newton) { *nits = it; return 1; }
+        int li = 0;
+        int st = solve(m, o.tol_lin, o.max_lin, sol.data(), &li);
+        *lits += li;
+        if (st == LIN_BREAKDOWN || st == LIN_FACTOR_FAIL) { *nits = it + 1; return 3; }
+        newton_update(m, o, sol.data());
+    }
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+// fluid: 24 values in the order of synth.fluid_params(); wells: per well
+// wint[4*w] = {kind, phase, control, ncon}, wdbl[4*w] = {target, bhp_limit, rw, skin},
+// wcells = concatenated connection cell indices.
+void* orc_create(int nx, int ny, int nz, const double* dx, const double* dy, const double* dz,
+                 double top_depth, const double* perm, const double* poro, const double* fluid, int nwells,
+                 const int* wint, const double* wdbl, const int* wcells) {
+    Model* m = new Model();
+    m->nx = nx; m->ny = ny; m->nz = nz; m->n = nx * ny * nz;
+    m->F = fluid_from(fluid);
+    m->dx.assign(dx, dx + nx); m->dy.assign(dy, dy + ny); m->dz.assign(dz, dz + nz);
+    m->perm.assign(perm, perm + m->n); m->poro.assign(poro, poro + m->n);
+    m->top_depth = top_depth;
+    compute_static(*m);
+    build_pattern(*m);
+    int off = 0;
+    for (int w = 0; w < nwells; ++w) {
+        Well wl;
+        wl.kind = wint[4 * w]; wl.phase = wint[4 * w + 1]; wl.control0 = wl.control = wint[4 * w + 2];
+        int ncon = wint[4 * w + 3];
+        wl.target = wdbl[4 * w]; wl.bhp_limit = wdbl[4 * w + 1]; wl.rw = wdbl[4 * w + 2]; wl.skin = wdbl[4 * w + 3];
+        for (int q = 0; q < ncon; ++q) {
+            int c = wcells[off + q];
+            wl.cells.push_back(c);
+            int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+            wl.WI.push_back(peaceman(m->perm[c], m->dx[i], m->dy[j], m->dz[k], wl.rw, wl.skin));
+        }
+        off += ncon;
+        wl.bhp = (wl.control == 1) ? wl.target : wl.bhp_limit;
+        m->wells.push_back(wl);
+    }
+    m->p.assign(m->n, 0.0); m->sw.assign(m->n, 0.0); m->x.assign(m->n, 0.0); m->flag.assign(m->n, 0);
+    m->A0.assign(3 * m->n, 0.0);
+    m->R.assign(3 * m->n, 0.0);
+    return m;
+}
+
+void orc_destroy(void* h) { delete static_cast<Model*>(h); }
+int orc_nnzb(void* h) { return (int)static_cast<Model*>(h)->colind.size(); }
+
+void orc_static(void* h, double* Tx, double* Ty, double* Tz, double* pv, double* depth, double* wi) {
+    Model* m = static_cast<Model*>(h);
+    std::memcpy(Tx, m->Tx.data(), sizeof(double) * m->n);
+    std::memcpy(Ty, m->Ty.data(), sizeof(double) * m->n);
+    std::memcpy(Tz, m->Tz.data(), sizeof(double) * m->n);
+    std::memcpy(pv, m->pv.data(), sizeof(double) * m->n);
+    std::memcpy(depth, m->depth.data(), sizeof(double) * m->n);
+    int q = 0;
+    for (const Well& w : m->wells) for (double v : w.WI) wi[q++] = v;
+}
+
+void orc_set_state(void* h, const double* p, const double* sw, const double* x,
+                   const uint8_t* flag, const double* bhp) {
+    Model* m = static_cast<Model*>(h);
+    m->p.assign(p, p + m->n); m->sw.assign(sw, sw + m->n); m->x.assign(x, x + m->n);
+    m->flag.assign(flag, flag + m->n);
+    for (size_t w = 0; w < m->wells.size(); ++w) m->wells[w].bhp = bhp[w];
+}
+
+void orc_get_state(void* h, double* p, double* sw, double* x, uint8_t* flag, double* bhp) {
+    Model* m = static_cast<Model*>(h);
+    std::memcpy(p, m->p.data(), sizeof(double) * m->n);
+    std::memcpy(sw, m->sw.data(), sizeof(double) * m->n);
+    std::memcpy(x, m->x.data(), sizeof(double) * m->n);
+    std::memcpy(flag, m->flag.data(), m->n);
+    for (size_t w = 0; w < m->wells.size(); ++w) bhp[w] = m->wells[w].bhp;
+}
+
+// Initial state: undersaturated oil at dissolved ratio rgo, water saturation
+// sw, and pressure in discrete hydrostatic equilibrium of the oil phase in
+// every column, p = p_top at the centre of the top layer:
+//   p_{k+1} = p_k + g (rho_o(p_k) + rho_o(p_{k+1}))/2 (z_{k+1} - z_k)
+// (the equilibrium equation dp/dz = rho g of Section 2.1.3 written with the
+// face density of Eq. (head)), solved by fixed-point iteration.
+void orc_init_hydrostatic(void* h, double p_top, double sw, double rgo) {
+    Model* m = static_cast<Model*>(h);
+    const Fluid& F = m->F;
+    for (int j = 0; j < m->ny; ++j)
+        for (int i = 0; i < m->nx; ++i) {
+            double pk = p_top;
+            for (int k = 0; k < m->nz; ++k) {
+                int c = cidx(*m, i, j, k);
+                if (k > 0) {
+                    int cu = cidx(*m, i, j, k - 1);
+                    double dzz = m->depth[c] - m->depth[cu];
+                    double rho_u = cell_props(F, pk, sw, rgo, USAT).rho[O].v;
+                    double pn = pk;
+                    for (int it = 0; it < 200; ++it) {
+                        double rho_n = cell_props(F, pn, sw, rgo, USAT).rho[O].v;
+                        double nxt = pk + F.g * 0.5 * (rho_u + rho_n) * dzz;
+                        bool done = std::fabs(nxt - pn) <= 1e-15 * std::fabs(nxt);
+                        pn = nxt;
+                        if (done) break;
+                    }
+                    pk = pn;
+                }
+                m->p[c] = pk; m->sw[c] = sw; m->x[c] = rgo; m->flag[c] = USAT;
+            }
+        }
+    for (Well& w : m->wells) w.bhp = (w.control0 == 1) ? w.target : w.bhp_limit;
+}
+
+void orc_begin_step(void* h) { begin_step(*static_cast<Model*>(h)); }
+
+void orc_assemble(void* h, double dt) {
+    Model* m = static_cast<Model*>(h);
+    assemble(*m, dt);
+}
+
+void orc_get_system(void* h, int* rowptr, int* colind, double* vals, double* res) {
+    Model* m = static_cast<Model*>(h);
+    std::memcpy(rowptr, m->rowptr.data(), sizeof(int) * (m->n + 1));
+    std::memcpy(colind, m->colind.data(), sizeof(int) * m->colind.size());
+    std::memcpy(vals, m->vals.data(), sizeof(double) * m->vals.size());
+    std::memcpy(res, m->R.data(), sizeof(double) * 3 * m->n);
+}
+
+// Per well: Rw, Dw, then B (3 per connection) and C (3 per connection),
+// packed well after well; control[w] is the current control.
+void orc_get_wells(void* h, double* rw, double* dw, double* B, double* C, int* control) {
+    Model* m = static_cast<Model*>(h);
+    int q = 0;
+    for (size_t w = 0; w < m->wells.size(); ++w) {
+        const Well& wl = m->wells[w];
+        rw[w] = wl.Rw; dw[w] = wl.Dw; control[w] = wl.control;
+        for (size_t k = 0; k < wl.B.size(); ++k) { B[q + k] = wl.B[k]; C[q + k] = wl.C[k]; }
+        q += (int)wl.B.size();
+    }
+}
+
+void orc_set_well_control(void* h, int w, int control, double bhp) {
+    Model* m = static_cast<Model*>(h);
+    m->wells[w].control = control;
+    m->wells[w].bhp = bhp;
+}
+
+void orc_norms(void* h, double dt, double* out) { norms(*static_cast<Model*>(h), dt, out); }
+
+// Residual of the full (reservoir + well) system at a given solution vector,
+// computed with the unreduced blocks: out = J sol - [R; R_w].
+void orc_residual_check(void* h, const double* sol, double* out) {
+    Model* m = static_cast<Model*>(h);
+    int n = m->n;
+    for (int i = 0; i < n; ++i) {
+        double acc[3] = {0, 0, 0};
+        for (int q = m->rowptr[i]; q < m->rowptr[i + 1]; ++q) {
+            double t[3];
+            mv3(&m->vals[9 * q], &sol[3 * m->colind[q]], t);
+            for (int e = 0; e < 3; ++e) acc[e] += t[e];
+        }
+        for (int e = 0; e < 3; ++e) out[3 * i + e] = acc[e] - m->R[3 * i + e];
+    }
+    int wi = 0;
+    for (const Well& w : m->wells) {
+        double xw = sol[3 * n + wi];
+        double r = 0.0;
+        if (w.control == 0) {
+            for (size_t con = 0; con < w.cells.size(); ++con) {
+                int c = w.cells[con];
+                for (int e = 0; e < 3; ++e) out[3 * c + e] += w.C[3 * con + e] * xw;
+                for (int v = 0; v < 3; ++v) r += w.B[3 * con + v] * sol[3 * c + v];
+            }
+            r += w.Dw * xw - w.Rw;
+        }
+        out[3 * n + wi] = r;
+        ++wi;
+    }
+}
+
+int orc_ilu0(void* h, double* lu_vals, double* uinv) {
+    Model* m = static_cast<Model*>(h);
+    if (!ilu0(*m)) return 1;
+    std::memcpy(lu_vals, m->lu.data(), sizeof(double) * m->lu.size());
+    std::memcpy(uinv, m->Uinv.data(), sizeof(double) * 9 * m->n);
+    return 0;
+}
+
+// z = M^-1 r with M the ILU(0) factors from the last orc_ilu0 call.
+void orc_ilu_apply(void* h, const double* r, double* z) { ilu_apply(*static_cast<Model*>(h), r, z); }
+
+// y = reduced operator applied to x (after orc_assemble).
+void orc_apply_op(void* h, const double* x, double* y) { apply_op(*static_cast<Model*>(h), x, y); }
+
+int orc_solve(void* h, double tol, int maxit, double* sol, int* its) {
+    return solve(*static_cast<Model*>(h), tol, maxit, sol, its);
+}
+
+void orc_newton_update(void* h, const double* opts, const double* sol) {
+    newton_update(*static_cast<Model*>(h), opts_from(opts), sol);
+}
+
+// One report step of length dt with time-step cutting: a failed Newton solve
+// restores the state, halves the sub-step, and retries (at most max_cuts
+// times).  report: [newton_its, lin_its, cuts, substeps, status(0 ok)].
+int orc_step(void* h, double dt, const double* opts, double* report) {
+    Model* m = static_cast<Model*>(h);
+    Opts o = opts_from(opts);
+    double t = 0.0, dtry = dt;
+    int nits_tot = 0, lits_tot = 0, cuts = 0, subs = 0;
+    int status = 0;
+    while (t < dt * (1.0 - 1e-12)) {
+        double dts = std::min(dtry, dt - t);
+        int nits = 0, lits = 0;
+        int st = newton(*m, dts, o, &nits, &lits);
+        nits_tot += nits; lits_tot += lits;
+        if (st == 0) { t += dts; ++subs; continue; }
+        restore(*m);
+        ++cuts;
+        if (cuts > o.max_cuts) { status = 1; break; }
+        dtry = 0.5 * dts;
+    }
+    report[0] = nits_tot; report[1] = lits_tot; report[2] = cuts; report[3] = subs; report[4] = status;
+    return status;
+}
+
+// Single-cell property evaluation with derivatives (for pin tests).
+// out: for each quantity value then d/dp, d/dsw, d/dx; quantities in order
+// b_w b_o b_g lam_w lam_o lam_g rho_w rho_o rho_g m_phi r_go A_w A_o A_g  (14 x 4)
+void orc_cell_props(const double* fluid, double p, double sw, double x, int flag, double* out) {
+    Fluid F = fluid_from(fluid);
+    CellProps c = cell_props(F, p, sw, x, flag);
+    const Dual<3>* q[14] = {&c.b[0], &c.b[1], &c.b[2], &c.lam[0], &c.lam[1], &c.lam[2],
+                            &c.rho[0], &c.rho[1], &c.rho[2], &c.mphi, &c.rgo,
+                            &c.A[0], &c.A[1], &c.A[2]};
+    for (int k = 0; k < 14; ++k) {
+        out[4 * k] = q[k]->v;
+        for (int v = 0; v < 3; ++v) out[4 * k + 1 + v] = q[k]->d[v];
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,511 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each test ties one part of the oracle to something fixed independently:
+finite differences, closed-form solutions of the continuous equations,
+conservation, equilibrium, textbook linear-algebra identities, dense LU, and
+a published well-index value.  A dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails at least one of them.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import bcsr_to_dense, entrywise_rel_ok, make_model, _well
+
+PSI = synth.PSI
+MD = synth.MD
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Transmissibility (Appendix B): T_ij must reproduce steady Darcy flow through
+# two homogeneous half-cells in series (exact for piecewise-constant k).
+# ---------------------------------------------------------------------------
+def test_transmissibility_series_darcy():
+    k1, k2 = 50 * MD, 800 * MD
+    dx = np.array([12.0, 30.0])
+    dy, dz = 7.0, 3.0
+    m = make_model(2, 1, 1, [k1, k2], 0.2, [], dx=dx, dy=dy, dz=dz)
+    o = oracle.Oracle(m)
+    st = o.static()
+    area = dy * dz
+    # Series resistance of the continuous problem v = -k grad p between the
+    # two cell centres: (dx1/2)/(k1 A) + (dx2/2)/(k2 A).
+    resistance = (dx[0] / 2) / (k1 * area) + (dx[1] / 2) / (k2 * area)
+    assert st["Tx"][0] == pytest.approx(1.0 / resistance, rel=1e-14)
+    assert st["Tx"][1] == 0.0  # boundary face: no flow (Section 2.1.3)
+    # Pore volume and cell-centre depth.
+    assert st["pv"][1] == pytest.approx(0.2 * dx[1] * dy * dz, rel=1e-15)
+    assert st["depth"][0] == pytest.approx(2500.0 + dz / 2, rel=1e-15)
+
+
+def test_transmissibility_vertical_uses_layer_thickness():
+    m = make_model(1, 1, 3, [100 * MD, 100 * MD, 400 * MD], 0.2, [], dx=5.0, dy=8.0,
+                   dz=np.array([1.0, 2.0, 4.0]))
+    st = oracle.Oracle(m).static()
+    area = 5.0 * 8.0
+    for k, (h1, h2, k1, k2) in enumerate([(1.0, 2.0, 100, 100), (2.0, 4.0, 100, 400)]):
+        res = (h1 / 2) / (k1 * MD * area) + (h2 / 2) / (k2 * MD * area)
+        assert st["Tz"][k] == pytest.approx(1 / res, rel=1e-14)
+    assert np.allclose(st["depth"], 2500.0 + np.array([0.5, 2.0, 5.0]))
+
+
+# ---------------------------------------------------------------------------
+# Peaceman well index against the published equivalent radius.
+# ---------------------------------------------------------------------------
+def test_peaceman_equivalent_radius_square_block():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "peaceman_1978.txt"))
+            if l.strip() and not l.startswith("#")]
+    ref = {r[0]: (float(r[1]), float(r[2])) for r in rows}
+    val, tol = ref["ro_over_dx_square"]
+    k, h, dx, rw = 150 * MD, 6.0, 40.0, 0.1
+    w = _well(0, 0, [0], "prod", "bhp", 3000 * PSI, 3000 * PSI, rw=rw)
+    m = make_model(1, 1, 1, k, 0.2, [w], dx=dx, dy=dx, dz=h)
+    wi = oracle.Oracle(m).static()["wi"][0]
+    # Steady radial flow q = 2 pi k h dp / (mu ln(r_o/r_w)) defines r_o from WI.
+    ro = rw * math.exp(2 * math.pi * k * h / wi)
+    assert abs(ro / dx - val) <= tol
+
+
+# ---------------------------------------------------------------------------
+# Cell properties: AD derivatives against central differences; end points of
+# the relative permeability curves; continuity at the bubble point.
+# ---------------------------------------------------------------------------
+def _fd_props(fluid, y, flag, h):
+    base = oracle.cell_props(fluid, *y, flag)
+    out = {}
+    for v in range(3):
+        yp = list(y); ym = list(y)
+        yp[v] += h[v]; ym[v] -= h[v]
+        fp = oracle.cell_props(fluid, *yp, flag)
+        fm = oracle.cell_props(fluid, *ym, flag)
+        for k in base:
+            out.setdefault(k, np.zeros(3))[v] = (fp[k][0] - fm[k][0]) / (2 * h[v])
+    return base, out
+
+
+@pytest.mark.parametrize("flag", [0, 1])
+def test_cell_props_ad_vs_fd(flag):
+    fluid = synth.fluid_params()
+    rng = np.random.default_rng(1)
+    for _ in range(25):
+        sw = rng.uniform(0.15, 0.55)
+        if flag == 0:
+            y = (rng.uniform(2500, 6000) * PSI, sw, rng.uniform(0.05, 0.8 - sw))
+        else:
+            y = (rng.uniform(4100, 6000) * PSI, sw, rng.uniform(50, 170))
+        h = (1e-6 * y[0], 1e-7, 1e-7 if flag == 0 else 1e-5)
+        base, fd = _fd_props(fluid, y, flag, h)
+        for k in base:
+            ad = base[k][1:]
+            scale = max(np.abs(ad).max(), np.abs(fd[k]).max(), 1e-300)
+            # derivatives of a smooth function: per-quantity relative agreement
+            assert np.abs(ad - fd[k]).max() <= 1e-7 * scale + 1e-300, (k, ad, fd[k])
+
+
+def test_relperm_end_points():
+    f = synth.fluid_params()
+    swco, sorw, sorg = f["s_wco"], f["s_orw"], f["s_org"]
+    p = 5000 * PSI
+    # connate water, no gas: water immobile, oil at its end point k_ro = 1
+    c = oracle.cell_props(f, p, swco, 100.0, 1)
+    assert c["lam_w"][0] == 0.0
+    assert c["lam_o"][0] * f["mu_o0"] > 0
+    mu_o = f["mu_o0"]  # oil mobility times viscosity gives k_ro; recover mu from a zero-krw state
+    # residual oil in the water system: oil immobile (k_ro = k_row(s_orw) = 0 with s_g = 0)
+    c = oracle.cell_props(f, p, 1.0 - sorw, 100.0, 1)
+    assert c["lam_o"][0] == 0.0
+    # maximum water saturation 1 - s_orw gives k_rw = 1: lam_w = 1/mu_w
+    assert c["lam_w"][0] == pytest.approx(1.0 / f["mu_w"], rel=1e-15)
+    # no gas saturation: gas immobile
+    c = oracle.cell_props(f, 3000 * PSI, 0.3, 0.0, 0)
+    assert c["lam_g"][0] == 0.0
+    # gas at 1 - s_wco - s_org in the gas system: k_rg = 1
+    c = oracle.cell_props(f, 3000 * PSI, swco, 1 - swco - sorg, 0)
+    assert c["lam_g"][0] * (f["mu_g0"] * (1 + 3000 * PSI / f["mu_g_p"])) == pytest.approx(1.0, rel=1e-14)
+    # ... and the oil in that state is at its residual: k_rog = 0, and with
+    # s_w = s_wco the segregation weights put all weight on k_rog (Eq. gwseg)
+    assert c["lam_o"][0] == 0.0
+    del mu_o
+
+
+def test_segregation_model_weights():
+    """Eq. (gwseg) is a weighted mean: with s_w = s_wco the oil relperm equals
+    the gas-oil curve, with s_g = 0 it equals the water-oil curve, and in
+    between it lies between the two."""
+    f = synth.fluid_params()
+    f["s_org"] = 0.2  # make the water-oil and gas-oil curves differ
+    p = 3000 * PSI
+    so = 0.55
+    # pure gas-oil (s_w = s_wco): k_ro = k_rog(s_o)
+    a = oracle.cell_props(f, p, f["s_wco"], 1 - f["s_wco"] - so, 0)
+    # pure water-oil (s_g = 0): k_ro = k_row(s_o)
+    b = oracle.cell_props(f, p, 1 - so, 0.0, 0)
+    mixed = oracle.cell_props(f, p, 0.25, 1 - 0.25 - so, 0)
+    lo, hi = sorted([a["lam_o"][0], b["lam_o"][0]])
+    assert lo <= mixed["lam_o"][0] <= hi
+    # equal weights give the arithmetic mean of the two curves
+    sg = (1 - so - f["s_wco"]) / 2
+    eq = oracle.cell_props(f, p, f["s_wco"] + sg, sg, 0)
+    assert eq["lam_o"][0] == pytest.approx(0.5 * (a["lam_o"][0] + b["lam_o"][0]), rel=1e-13)
+
+
+def test_properties_continuous_at_saturation_boundary():
+    """At r_go = r_s(p) the saturated (x = s_g = 0) and undersaturated
+    (x = r_go) descriptions are the same fluid (Section 2.1.2, 2.1.6)."""
+    f = synth.fluid_params()
+    for p in (1500 * PSI, 3000 * PSI, 4000 * PSI):
+        sat = oracle.cell_props(f, p, 0.3, 0.0, 0)
+        rs = sat["r_go"][0]
+        usat = oracle.cell_props(f, p, 0.3, rs, 1)
+        for k in ("b_o", "rho_o", "lam_o", "A_o", "A_g", "A_w", "b_w", "b_g"):
+            assert usat[k][0] == pytest.approx(sat[k][0], rel=1e-13), k
+        # the saturated dissolved ratio grows with pressure
+        assert sat["r_go"][1] > 0
+
+
+# ---------------------------------------------------------------------------
+# Full Jacobian (cells, faces, wells) against central finite differences.
+# ---------------------------------------------------------------------------
+def _residual_vector(o, state, dt):
+    o.set_state(*state)
+    o.assemble(dt)
+    _, _, _, R = o.system()
+    wl = o.wells()
+    return R.reshape(-1).copy(), np.array([w["Rw"] for w in wl])
+
+
+@pytest.mark.parametrize("frac_sat", [0.0, 0.5, 1.0])
+def test_jacobian_ad_vs_fd(frac_sat):
+    m = synth.small_model(4, 3, 3, wells="5spot", dz=4.0)
+    o = oracle.Oracle(m)
+    st = synth.random_state(m, seed_member=int(frac_sat * 10), frac_sat=frac_sat)
+    o.set_state(*st)
+    o.begin_step()
+    # perturb the state away from the step start so accumulation is active
+    p, sw, x, fl, bhp = [a.copy() for a in st]
+    p *= 1.01
+    sw += 0.01
+    state = (p, sw, x, fl, bhp)
+    dt = 5 * synth.DAY
+    o.set_state(*state)
+    o.assemble(dt)
+    rp, ci, vals, R0 = o.system()
+    J = bcsr_to_dense(rp, ci, vals, o.n)
+    wl = o.wells()
+    n = o.n
+    rng = np.random.default_rng(3)
+    cells = rng.choice(n, size=8, replace=False)
+    wcells = [c for cs in o.well_cells for c in cs]
+    cells = np.unique(np.concatenate([cells, wcells[:4]]))
+    def fd_column(c, v, h):
+        def central(hh):
+            yp = [a.copy() for a in (p, sw, x)]
+            ym = [a.copy() for a in (p, sw, x)]
+            yp[v][c] += hh
+            ym[v][c] -= hh
+            Rp, Wp = _residual_vector(o, (*yp, fl, bhp), dt)
+            Rm, Wm = _residual_vector(o, (*ym, fl, bhp), dt)
+            return (Rp - Rm) / (2 * hh), (Wp - Wm) / (2 * hh)
+        # Richardson extrapolation of the central difference: O(h^4) error
+        r1, w1 = central(h)
+        r2, w2 = central(h / 2)
+        return (4 * r2 - r1) / 3, (4 * w2 - w1) / 3
+
+    for c in cells:
+        for v in range(3):
+            y = [p, sw, x][v]
+            h = 1e-4 * abs(y[c]) if v == 0 or (v == 2 and fl[c] == 1) else 1e-4
+            col_fd, wfd = fd_column(c, v, h)
+            col_ad = J[:, 3 * c + v]
+            # each entry against its own size, floored by the largest entry of
+            # the same unknown family in its row (pressure columns are per Pa)
+            fam = np.abs(J[:, v::3]).max(axis=1)
+            scale = np.maximum(np.abs(col_ad), 1e-3 * fam)
+            nz = scale > 0
+            err = np.abs(col_fd - col_ad)[nz] / scale[nz]
+            assert err.max() <= 1e-7, (c, v, err.max())
+            # well equations: B entries
+            for q, w in enumerate(wl):
+                if w["control"] != 0 or c not in o.well_cells[q]:
+                    continue
+                con = o.well_cells[q].index(c)
+                assert wfd[q] == pytest.approx(w["B"][con, v], rel=1e-7,
+                                               abs=1e-7 * np.abs(w["B"][:, v]).max())
+    # BHP column: C and D of the rate-controlled wells
+    for q, w in enumerate(wl):
+        if w["control"] != 0:
+            continue
+        def central(hh):
+            bp = bhp.copy(); bm = bhp.copy()
+            bp[q] += hh; bm[q] -= hh
+            Rp, Wp = _residual_vector(o, (p, sw, x, fl, bp), dt)
+            Rm, Wm = _residual_vector(o, (p, sw, x, fl, bm), dt)
+            return (Rp - Rm) / (2 * hh), (Wp[q] - Wm[q]) / (2 * hh)
+        h = 1e-4 * bhp[q]
+        r1, d1 = central(h)
+        r2, d2 = central(h / 2)
+        fdC = ((4 * r2 - r1) / 3).reshape(-1, 3)[o.well_cells[q]]
+        assert np.allclose(fdC, w["C"], rtol=1e-7, atol=1e-7 * np.abs(w["C"]).max())
+        assert (4 * d2 - d1) / 3 == pytest.approx(w["Dw"], rel=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# Conservation: in a closed reservoir the fluxes cancel and every Newton step
+# conserves each component's surface volume.
+# ---------------------------------------------------------------------------
+def _component_masses(o):
+    f = o.model["fluid"]
+    pv = o.static()["pv"]
+    p, sw, x, fl, _ = o.get_state()
+    M = np.zeros(3)
+    for c in range(o.n):
+        cp = oracle.cell_props(f, p[c], sw[c], x[c], fl[c])
+        M += pv[c] * np.array([cp["A_w"][0], cp["A_o"][0], cp["A_g"][0]])
+    return M
+
+
+def test_flux_terms_cancel_in_closed_reservoir():
+    m = synth.small_model(5, 4, 3, wells="none", dz=6.0)
+    o = oracle.Oracle(m)
+    st = synth.random_state(m, seed_member=4)
+    o.set_state(*st)
+    o.begin_step()
+    o.assemble(synth.DAY)
+    _, _, _, R = o.system()
+    # state == step start: accumulation is zero, so the residual is flux only
+    flux_scale = np.abs(R).max()
+    assert flux_scale > 0
+    assert np.all(np.abs(R.sum(axis=0)) <= 1e-12 * flux_scale * o.n)
+
+
+def test_mass_conservation_per_step():
+    m = synth.small_model(5, 4, 3, wells="none", dz=6.0)
+    o = oracle.Oracle(m)
+    st = synth.random_state(m, seed_member=5)
+    o.set_state(*st)
+    M0 = _component_masses(o)
+    for _ in range(3):
+        status, rep = o.step(2 * synth.DAY, tol_mb=1e-13, tol_cnv=1e-11, tol_lin=1e-12)
+        assert status == 0, rep
+        M1 = _component_masses(o)
+        assert np.all(np.abs(M1 - M0) <= 1e-10 * M0), (M1 - M0) / M0
+        M0 = M1
+
+
+# ---------------------------------------------------------------------------
+# Hydrostatic equilibrium (Section 2.1.3, Eq. head): the initial column
+# matches the continuous ODE dp/dz = rho(p) g, and a closed reservoir with
+# immobile water and no gas stays at rest.
+# ---------------------------------------------------------------------------
+def test_hydrostatic_column_matches_ode():
+    from scipy.integrate import solve_ivp
+    nz, dz = 60, 5.0
+    m = make_model(1, 1, nz, 100 * MD, 0.2, [], dz=dz)
+    o = oracle.Oracle(m)
+    o.init_hydrostatic()
+    p, *_ = o.get_state()
+    f = m["fluid"]
+    r = m["init"]["rgo"]
+    sw = m["init"]["sw"]
+    rho = lambda pp: oracle.cell_props(f, pp, sw, r, 1)["rho_o"][0]
+    sol = solve_ivp(lambda z, y: [f["g"] * rho(y[0])], (0, dz * (nz - 1)), [p[0]],
+                    rtol=1e-13, atol=1e-6, dense_output=True)
+    z = dz * np.arange(nz)
+    ref = sol.sol(z)[0]
+    # trapezoidal discretisation error is O(dz^2 rho'') -- negligible here
+    assert np.max(np.abs(p - ref) / ref) < 1e-10
+    assert p[0] == m["init"]["p_top"]
+    assert np.all(np.diff(p) > 0)  # pressure increases with depth
+
+
+def test_closed_reservoir_at_rest_stays_at_rest():
+    m = synth.small_model(4, 3, 6, wells="none", dz=3.0)
+    m["init"]["sw"] = m["fluid"]["s_wco"]  # immobile water, no free gas
+    o = oracle.Oracle(m)
+    o.init_hydrostatic()
+    s0 = o.get_state()
+    for _ in range(10):
+        # rounding leaves CNV near 1e-12, four orders below the 1e-6 tolerance
+        status, rep = o.step(30 * synth.DAY, tol_mb=1e-10, tol_cnv=1e-10)
+        assert status == 0
+        assert rep["newton_its"] == 0 and rep["lin_its"] == 0
+    s1 = o.get_state()
+    assert np.allclose(s1[0], s0[0], rtol=1e-12, atol=0)
+    assert np.array_equal(s1[3], s0[3])
+    o.begin_step()
+    o.assemble(30 * synth.DAY)
+    _, _, vals, R = o.system()
+    # residual is rounding-level against the flux scale T * lambda * b * p
+    st = o.static()
+    scale = st["Tz"].max() * 1e3 * m["init"]["p_top"]
+    assert np.abs(R).max() <= 1e-13 * scale
+
+
+# ---------------------------------------------------------------------------
+# 1-D incompressible single-phase flow between a BHP injector and a BHP
+# producer: the discrete solution is the exact steady Darcy solution
+# (Appendix B: v_ij = T_ij (p_i - p_j) / mu); pressure is linear within each
+# homogeneous stretch and the rate follows the series resistance.
+# ---------------------------------------------------------------------------
+def test_1d_incompressible_linear_profile():
+    N = 12
+    rng = np.random.default_rng(7)
+    perm = np.exp(np.log(200 * MD) + 0.5 * rng.standard_normal(N))
+    dx, dy, dz = 15.0, 10.0, 4.0
+    pL, pR = 5000 * PSI, 4000 * PSI
+    wells = [_well(0, 0, [0], "inj", "bhp", pL, pL, phase="water"),
+             _well(N - 1, 0, [0], "prod", "bhp", pR, pR)]
+    fluid = {"g": 0.0, "c_w": 0.0, "c_r": 0.0, "s_orw": 0.0}
+    m = make_model(N, 1, 1, perm, 0.25, wells, fluid=fluid, dx=dx, dy=dy, dz=dz)
+    o = oracle.Oracle(m)
+    n = N
+    p0 = np.full(n, 0.5 * (pL + pR))
+    o.set_state(p0, np.ones(n), np.zeros(n), np.zeros(n, np.uint8), np.array([pL, pR]))
+    status, rep = o.step(10 * synth.DAY, tol_mb=1e-13, tol_cnv=1e-12, tol_lin=1e-13)
+    assert status == 0 and rep["newton_its"] == 1
+    p, sw, x, fl, _ = o.get_state()
+    assert np.all(sw == 1.0) and np.all(x == 0.0)
+    mu = m["fluid"]["mu_w"]
+    wi = o.static()["wi"]
+    area = dy * dz
+    res = [mu / wi[0]]
+    for i in range(N - 1):
+        res.append(mu * ((dx / 2) / (perm[i] * area) + (dx / 2) / (perm[i + 1] * area)))
+    res.append(mu / wi[1])
+    q = (pL - pR) / sum(res)
+    ref = pL - q * np.cumsum(res)[:-1]
+    assert np.max(np.abs(p - ref)) <= 1e-9 * pL
+
+
+# ---------------------------------------------------------------------------
+# Linear algebra: ILU(0) identity on the pattern, exactness in 1-D, and the
+# Schur-reduced BiCGStab solve against dense LU of the full system.
+# ---------------------------------------------------------------------------
+def _assembled_small(nx, ny, nz, wells="5spot", seed=0, frac_sat=0.5):
+    m = synth.small_model(nx, ny, nz, wells=wells, dz=4.0)
+    o = oracle.Oracle(m)
+    st = synth.random_state(m, seed_member=seed, frac_sat=frac_sat)
+    o.set_state(*st)
+    o.begin_step()
+    p, sw, x, fl, bhp = [a.copy() for a in st]
+    o.set_state(p * 1.005, sw, x, fl, bhp)
+    o.assemble(2 * synth.DAY)
+    return o
+
+
+def test_ilu0_product_matches_matrix_on_pattern():
+    o = _assembled_small(4, 3, 3)
+    rp, ci, vals, _ = o.system()
+    lu, uinv = o.ilu0()
+    n = o.n
+    L = np.eye(3 * n)
+    U = np.zeros((3 * n, 3 * n))
+    for i in range(n):
+        for q in range(rp[i], rp[i + 1]):
+            j = ci[q]
+            if j < i:
+                L[3 * i:3 * i + 3, 3 * j:3 * j + 3] = lu[q]
+            else:
+                U[3 * i:3 * i + 3, 3 * j:3 * j + 3] = lu[q]
+        d = [q for q in range(rp[i], rp[i + 1]) if ci[q] == i][0]
+        # the stored inverse of the pivot block (columns scale as 1/Pa, 1, 1)
+        ok, err = entrywise_rel_ok(uinv[i], np.linalg.inv(lu[d]), 1e-10)
+        assert ok, err
+    A = bcsr_to_dense(rp, ci, vals, n)
+    P = L @ U
+    mask = bcsr_to_dense(rp, ci, np.ones_like(vals), n) > 0
+    # LU backward-error bound: |A - LU| <= c eps (|L| |U|) entry by entry
+    bound = np.abs(L) @ np.abs(U)
+    assert np.all(np.abs(P - A)[mask] <= 1024 * np.finfo(float).eps * bound[mask])
+    # the ILU apply is the exact inverse of L U
+    r = np.random.default_rng(0).standard_normal(3 * n)
+    z = o.ilu_apply(r)
+    assert np.allclose(P @ z, r, rtol=0, atol=1e-9 * np.abs(r).max())
+
+
+def test_ilu0_is_exact_block_lu_in_1d():
+    m = synth.small_model(9, 1, 1, wells="none")
+    o = oracle.Oracle(m)
+    st = synth.random_state(m, seed_member=2)
+    o.set_state(*st)
+    o.begin_step()
+    o.set_state(st[0] * 1.01, *st[1:])
+    o.assemble(synth.DAY)
+    rp, ci, vals, R = o.system()
+    A = bcsr_to_dense(rp, ci, vals, o.n)
+    r = np.random.default_rng(1).standard_normal(3 * o.n)
+    o.ilu0()
+    z = o.ilu_apply(r)
+    assert np.allclose(A @ z, r, rtol=0, atol=1e-10 * np.abs(r).max())
+    status, its, sol = o.solve(tol=1e-10, maxit=10)
+    assert status == 0 and its == 1
+    assert np.allclose(A @ sol, R.reshape(-1), rtol=0, atol=1e-9 * np.abs(R).max())
+
+
+@pytest.mark.parametrize("seed,frac_sat", [(0, 0.5), (1, 0.0), (2, 1.0)])
+def test_schur_bicgstab_matches_dense_lu(seed, frac_sat):
+    o = _assembled_small(4, 3, 2, seed=seed, frac_sat=frac_sat)
+    rp, ci, vals, R = o.system()
+    n = o.n
+    A = bcsr_to_dense(rp, ci, vals, n)
+    wl = o.wells()
+    rate = [q for q, w in enumerate(wl) if w["control"] == 0]
+    assert rate, "test needs a rate-controlled well"
+    N = 3 * n + len(rate)
+    J = np.zeros((N, N))
+    J[:3 * n, :3 * n] = A
+    rhs = np.zeros(N)
+    rhs[:3 * n] = R.reshape(-1)
+    for k, q in enumerate(rate):
+        w = wl[q]
+        for con, c in enumerate(o.well_cells[q]):
+            J[3 * c:3 * c + 3, 3 * n + k] = w["C"][con]
+            J[3 * n + k, 3 * c:3 * c + 3] = w["B"][con]
+        J[3 * n + k, 3 * n + k] = w["Dw"]
+        rhs[3 * n + k] = w["Rw"]
+    ref = np.linalg.solve(J, rhs)
+    status, its, sol = o.solve(tol=1e-13, maxit=300)
+    assert status == 0
+    full = np.concatenate([sol[:3 * n], sol[3 * n:][rate]])
+    scale = np.abs(ref).reshape(-1)
+    # compare per unknown family (pressure, s_w, x, bhp) at its own scale
+    for v in range(3):
+        a, b = full[v:3 * n:3], ref[v:3 * n:3]
+        assert np.max(np.abs(a - b)) <= 1e-8 * np.abs(b).max()
+    assert np.allclose(full[3 * n:], ref[3 * n:], rtol=1e-8)
+    # the oracle's residual check of the unreduced system agrees
+    chk = o.residual_check(sol)
+    assert np.max(np.abs(chk[:3 * n])) <= 1e-9 * np.abs(R).max()
+    del scale
+
+
+def test_newton_converges_fast_near_solution():
+    """Near the solution the Newton iteration with exact linear solves
+    converges superlinearly (Eq. linsystem)."""
+    m = synth.small_model(5, 4, 3, wells="5spot", dz=4.0)
+    o = oracle.Oracle(m)
+    o.init_hydrostatic()
+    o.step(0.5 * synth.DAY)  # settle the wells
+    o.begin_step()
+    dt = 0.5 * synth.DAY
+    hist = []
+    for it in range(8):
+        o.assemble(dt)
+        nrm = o.norms(dt)
+        hist.append(max(nrm[3:6]))
+        if hist[-1] < 1e-12:
+            break
+        st, its, sol = o.solve(tol=1e-14, maxit=300)
+        o.newton_update(sol)
+    assert hist[-1] < 1e-10, hist
+    assert len(hist) <= 6, hist
+    # superlinear: the last reductions are much faster than geometric
+    k = len(hist) - 1
+    assert hist[k] / hist[k - 1] < 1e-2 * hist[k - 1] / hist[k - 2] or hist[k] < 1e-13, hist

@@ -1,0 +1,377 @@
+"""Throughput of the black-oil Newton step on GB300, in cell-steps/s.
+
+A "step" is one report step of the simulation (Newton iterations with
+assembly, ILU(0) factorisation and BiCGStab solves, time-step cuts included)
+on the 60x220x85 layered model with 5-spot wells (1,122,000 cells, report
+steps of 10 days).  W warm-up report steps run untimed, then K report steps
+are timed with CUDA events on the library's stream.
+
+Prints one JSON line.  --impl reference times the CPU FP64 oracle instead
+(single thread, bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic bytes per cell of each timed kernel (FP64 values, the minimum
+# each kernel must move; index arrays and cache re-reads are not counted).
+ALGO_BYTES_PER_CELL = {
+    # forward sweep: D^-1 and 3 scaled lower blocks (36 doubles), r in, y out
+    "ilu_fwd_sweep": 36 * 8 + 24 + 24,
+    # backward sweep: 3 scaled upper blocks (27 doubles), y in, z out
+    "ilu_bwd_sweep": 27 * 8 + 24 + 24,
+    # operator: 7 blocks (63 doubles), x in, y out, one dot operand in
+    "spmv_wells": 63 * 8 + 24 + 24 + 24,
+    # factorisation: 7 blocks of A in, 7 blocks of P out
+    "ilu_factor": 63 * 8 * 2,
+}
+
+
+def peaks():
+    """Roofline denominators: MEASURED_PEAKS.json (measured on this
+    pool's GB300s), else the profiling recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "of measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "of fallback"}
+
+
+def op_counts(config):
+    """Operations per report step of this workload, recorded by the oracle
+    alone (oracle/calibrate.py writes oracle/op_counts.json)."""
+    with open(os.path.join(ROOT, "oracle", "op_counts.json")) as fh:
+        return json.load(fh)[str(config)]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-its", type=int, default=12)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def model_for(config):
+    import synth
+    return synth.config1() if config == 1 else synth.config0()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(config, gpu_counts, sample_its):
+    """Time the oracle (single thread) on a bounded sample of the same model at
+    its initial state -- one assembly, one ILU(0) factorisation and
+    `sample_its` BiCGStab iterations -- and scale to the operation counts of
+    the GPU run's timed steps (same algorithm, same decisions)."""
+    import oracle
+    m = model_for(config)
+    o = oracle.Oracle(m)
+    o.init_hydrostatic()
+    o.begin_step()
+    dt = m["dt"]
+    t0 = time.perf_counter()
+    o.assemble(dt)
+    t_asm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.ilu0()
+    t_fac = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    st, its, _ = o.solve(tol=1e-30, maxit=sample_its)
+    t_sol = time.perf_counter() - t0
+    t_it = max(t_sol - t_fac, 0.0) / max(its, 1)
+    n_asm = gpu_counts["assemblies"]
+    n_fac = gpu_counts["solves"]
+    n_it = gpu_counts["lin_its"]
+    est = n_asm * t_asm + n_fac * t_fac + n_it * t_it
+    n = m["nx"] * m["ny"] * m["nz"]
+    value = n * gpu_counts["steps"] / est if est > 0 else None
+    return {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle on the same model's initial state: 1 assembly ({t_asm:.2f} s), "
+                       f"1 ILU0 ({t_fac:.2f} s), {its} BiCGStab its ({t_it:.3f} s each); "
+                       f"scaled to the timed steps' {n_asm} assemblies, {n_fac} factorisations, "
+                       f"{n_it} BiCGStab iterations")}
+
+
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1910_06059_gb300 import Sim
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    m = model_for(args.config)
+    n = m["nx"] * m["ny"] * m["nz"]
+    dt = m["dt"]
+    sim = Sim(m, stream=stream)
+    sim.init_hydrostatic()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        sim.step(dt, raise_on_fail=True)
+    torch.cuda.synchronize()
+    snap = sim.get_state()
+    snap_dt = sim.dt_next
+
+    # ---- main timed region: K report steps, inputs resident in HBM --------
+    sim.set_timing(True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    reps = []
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st, rep = sim.step(dt, raise_on_fail=True)
+        reps.append(rep)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    timers = sim.timing()
+    sim.set_timing(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # ---- end to end: host state in, step, host state out ------------------
+    # the state lives in pinned host memory between steps: each step uploads
+    # it, advances it on the device and reads it back
+    pin = [torch.from_numpy(a.copy()).pin_memory() for a in snap]
+    outs = [torch.empty_like(a).pin_memory() for a in pin]
+    dev = [torch.empty(a.shape, dtype=a.dtype, device="cuda") for a in pin]
+    sim.set_state(*snap)
+    sim.dt_next = snap_dt
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for d, h in zip(dev, pin):
+            d.copy_(h, non_blocking=True)
+        sim.set_state_dev(*dev)
+        sim.step(dt, raise_on_fail=True)
+        sim.get_state_dev(*dev)
+        for h, d in zip(outs, dev):
+            h.copy_(d, non_blocking=True)
+        pin, outs = outs, pin
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_e2e = float(t.item())
+    io_bytes = int(sum(a.numel() * a.element_size() for a in pin))
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    dominant = max((k for k in timers if k in ALGO_BYTES_PER_CELL), key=lambda k: timers[k][0])
+    tot_ms, launches = timers[dominant]
+    avg_s = tot_ms / 1e3 / max(launches, 1)
+    algo = ALGO_BYTES_PER_CELL[dominant] * n
+    achieved = algo / avg_s / 1e9
+    pk = peaks()
+    roof = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
+            "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
+            "traffic": None, "peak_source": pk["source"],
+            "avg_launch_ms": round(avg_s * 1e3, 4), "launches": launches}
+
+    counts = {"steps": args.steps,
+              "assemblies": sum(r["newton_its"] + r["substeps"] + r["cuts"] for r in reps),
+              "solves": sum(r["newton_its"] for r in reps),
+              "lin_its": sum(r["lin_its"] for r in reps)}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(args.config, counts, args.cpu_sample_its)
+
+    value = n * args.steps * world / (ms_max / 1e3)
+    out = {
+        "metric": "cell-steps/s at 1e-6 Newton tol: plain FP64 vs mixed/learned/batched",
+        "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": ("layered 60x220x85 black-oil, 5-spot wells, 10-day report steps, "
+                                "plain FP64 ILU0-BiCGStab, Newton tol 1e-6")
+                   if args.config == 1 else "spe1-shaped 10x10x3, 30-day report steps",
+                   "cells": n, "newton_tol": 1e-6, "linear_tol": 1e-3,
+                   "l2": "inputs larger than L2 (Jacobian 565 MB, ILU data 565 MB per model)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "clocks": clk,
+        "e2e": {"value": n * args.steps * world / (ms_e2e / 1e3), "unit": "cell-steps/s",
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "gpu_launches": None,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "iterations": counts,
+        "kernel_ms": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in timers.items()},
+    }
+    out["gpu_launches"] = gpu_launch_count(timers, reps, sim)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def gpu_launch_count(timers, reps, sim):
+    """Kernels launched in the timed region: per BiCGStab iteration
+    2 x (2 x levels) sweep kernels + 2 operator + well kernels + 9 vector and
+    scalar kernels; per assembly 3-4 kernels + 2 norm kernels; per
+    factorisation one kernel per level; per Newton update 2."""
+    lv = sim.nx + sim.ny + sim.nz - 2
+    lin = sum(r["lin_its"] for r in reps)
+    nit = sum(r["newton_its"] for r in reps)
+    asm = sum(r["newton_its"] + r["substeps"] + r["cuts"] for r in reps)
+    per_it = 4 * lv + 2 * 2 + 9
+    return int(lin * per_it + nit * (lv + 2 + 4) + asm * 6)
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, single thread, on the same model: each
+    timed step is one bounded sample (one assembly, one ILU(0), and
+    --cpu-sample-its BiCGStab iterations at the model's initial state); the
+    value converts the sample to cell-steps/s with the operation counts per
+    report step of this workload recorded in measured/op_counts.json."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    m = model_for(args.config)
+    n = m["nx"] * m["ny"] * m["nz"]
+    oc = op_counts(args.config)
+    o = oracle.Oracle(m)
+    o.init_hydrostatic()
+    o.begin_step()
+    samples = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        o.assemble(m["dt"])
+        t_asm = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        o.ilu0()
+        t_fac = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, its, _ = o.solve(tol=1e-30, maxit=args.cpu_sample_its)
+        t_it = max(time.perf_counter() - t0 - t_fac, 0.0) / max(its, 1)
+        if s >= args.warmup:
+            samples.append(oc["assemblies"] * t_asm + oc["solves"] * t_fac + oc["lin_its"] * t_it)
+    sec_per_step = float(np.median(samples))
+    value = n / sec_per_step
+    out = {"impl": "reference",
+           "metric": "cell-steps/s at 1e-6 Newton tol: plain FP64 vs mixed/learned/batched",
+           "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "layered 60x220x85 black-oil, 5-spot wells, 10-day report steps, "
+                                  "plain FP64 ILU0-BiCGStab, Newton tol 1e-6", "cells": n},
+           "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                            "sample": (f"per step: 1 assembly, 1 ILU0, {args.cpu_sample_its} "
+                                       f"BiCGStab its at the initial state, scaled by "
+                                       f"{oc['assemblies']} assemblies, {oc['solves']} "
+                                       f"factorisations, {oc['lin_its']} BiCGStab its per "
+                                       f"report step")},
+           "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * bo.h -- C ABI of the GB300 black-oil Newton-step library (libbo.so).
+ *
+ * The library implements the fully-implicit black-oil Newton step of
+ * arXiv 1910.06059 (OPM Flow): residual and Jacobian assembly by forward-mode
+ * automatic differentiation over the cells and two-point-flux faces of a
+ * Cartesian grid (Section 2.1.1, Eqs. materialbalance, acc, flux1, flux2,
+ * head; Section 2.4), reduced standard wells coupled through the Schur
+ * complement (Section 2.2.1, Eqs. wellinflow, wellequation), and the linear
+ * solve by BiCGStab preconditioned with block ILU(0) (Section 2.3.1), inside a
+ * Newton loop with Appleyard chop, variable switching and time-step cutting
+ * (Section 2.3, Eq. linsystem).
+ *
+ * Conventions shared by every entry point
+ *  - Units are SI: Pa, m, s, m^2 (permeability), Pa.s, surface m^3.
+ *  - Cell index c = i + nx*(j + ny*k), 0-based, k counts layers downward.
+ *  - Unknowns per cell y = (p_o, s_w, x) with x = s_g in state SAT (flag 0,
+ *    gas present) or x = r_go in state USAT (flag 1, no free gas), following
+ *    Eq. (primaryVariableMeaning).  Equations per cell are ordered
+ *    (water, oil, gas) components.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Entry
+ *    points named *_dev take device pointers (for example a torch tensor's
+ *    data_ptr()) and read or write them on the library's stream; the caller
+ *    keeps them alive until that stream has passed the call.
+ *  - Every call returns a bo_status and never aborts the process.  On error
+ *    bo_last_error() returns a message for the calling thread.  A CUDA error
+ *    maps to BO_ERR_CUDA and leaves the object usable only for bo_destroy.
+ *  - The library allocates its own device memory on the current device at
+ *    bo_create_grid / bo_set_properties and frees it in bo_destroy.
+ *  - Calls on one bo_sim are not thread-safe; distinct objects are independent.
+ */
+#ifndef BO_H
+#define BO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bo_sim bo_sim; /* opaque; owns all of its device memory */
+
+typedef enum {
+    BO_OK = 0,
+    BO_ERR_INVALID_ARG = 1,
+    BO_ERR_CUDA = 2,
+    BO_ERR_OOM = 3,
+    BO_ERR_NOT_CONVERGED = 4,     /* Newton failed after all time-step cuts */
+    BO_ERR_LINEAR_BREAKDOWN = 5,  /* BiCGStab breakdown or non-finite scalar */
+    BO_ERR_DEVICE_TIMEOUT = 6,    /* a bounded device-side wait ran out */
+    BO_ERR_STATE = 7              /* call out of order (e.g. solve before assemble) */
+} bo_status;
+
+/* Fluid and rock parameters (Sections 2.1.4-2.1.6).  The paper gives the
+ * forms, not the values; the library evaluates:
+ *   b_w = bw_ref exp(c_w (p - p_ref)), mu_w constant;
+ *   r_s(p) = R_sb p / p_b; p_sat(r) = p_b r / R_sb;
+ *   b_o = exp(c_o (p - p_sat(r_go))) / (1 + Bo_slope r_go);
+ *   mu_o = mu_o0 / (1 + mu_o_r r_go) * exp(c_mu (p - p_sat(r_go)));
+ *   b_g = p / (p_sc Z); mu_g = mu_g0 (1 + p / mu_g_p);  rho_a as in the
+ *   paper's nomenclature; m_phi = exp(c_r (p - p_ref));
+ *   Corey curves of exponent n_corey with end points s_wco, s_orw, s_org,
+ *   combined by Eq. (gwseg).  rho_s = surface densities (w, o, g). */
+typedef struct {
+    double g, rho_s[3], p_ref, bw_ref, c_w, mu_w, R_sb, p_b, Bo_slope, c_o, mu_o0, mu_o_r, c_mu,
+        p_sc, Z, mu_g0, mu_g_p, c_r, s_wco, s_orw, s_org, n_corey;
+} bo_fluid;
+
+/* One vertical standard well (Section 2.2.1) in reduced form: the only well
+ * unknown is the bottom-hole pressure of a rate-controlled well.  Producing
+ * connections carry every phase at its own mobility; injecting connections
+ * carry the injected phase at the total mobility; reverse flow through a
+ * connection is set to zero.  cells[0] is the datum (top) connection.  A
+ * cell may belong to at most one connection of one well. */
+typedef struct {
+    int kind;          /* 0 injector, 1 producer */
+    int phase;         /* injected phase of an injector: 0 water, 2 gas */
+    int control;       /* 0 surface-rate control, 1 BHP control */
+    int ncon;          /* number of connections */
+    const int* cells;  /* ncon cell indices (host memory, copied) */
+    double target;     /* rate control: surface m^3/s (> 0); BHP control: Pa */
+    double bhp_limit;  /* rate control: BHP bound that switches the well to BHP control */
+    double rw, skin;   /* well radius (m) and skin for the Peaceman index */
+} bo_well;
+
+/* Newton controls (Section 2.3).  Convergence: max_a MB_a <= tol_mb,
+ * max_a CNV_a <= tol_cnv and every rate-controlled well's |R_w|/target <=
+ * tol_well.  Appleyard chop per cell: |dp| <= dp_rel_max * p; (ds_w, ds_g)
+ * scaled so that max |ds| <= ds_max; in USAT cells |dr_go| <= drs_rel_max *
+ * R_sb, and the pressure may fall at most a fraction bp_overshoot below the
+ * saturation pressure of the updated r_go (no far jump across the
+ * saturated/undersaturated boundary).  Switching: SAT -> USAT when s_g < 0
+ * (r_go = r_s(p)); USAT -> SAT when r_go > r_s(p) (1 + eps_switch) (s_g = 0).
+ * Linear solve to relative residual tol_lin within max_lin iterations; a
+ * linear solve that misses it fails the Newton solve.  Sub-steps: the first
+ * sub-step of a simulation is dt_init (<= 0: the whole report step); the
+ * sub-step length is carried between report steps, multiplied after a
+ * converged sub-step of k Newton iterations by 2 (k <= 4), 1.5 (k <= 8),
+ * 1 (k <= 12) or 0.7, capped at the report step, and multiplied by
+ * cut_factor after a failed one (at most max_cuts failures per report step). */
+typedef struct {
+    double tol_mb, tol_cnv, tol_well;
+    int max_newton;
+    double tol_lin;
+    int max_lin, max_cuts;
+    double ds_max, dp_rel_max, drs_rel_max, eps_switch;
+    double bp_overshoot, dt_init, cut_factor;
+} bo_newton_opts;
+
+typedef struct {
+    double tol;   /* stop when ||r||_2 <= tol * ||r_0||_2 */
+    int max_it;
+} bo_solve_opts;
+
+typedef struct {
+    int iterations;  /* BiCGStab iterations (a half-iteration exit counts as one) */
+    int status;      /* 0 converged, 1 not converged in max_it, 2 breakdown */
+} bo_solve_report;
+
+typedef struct {
+    int newton_its, lin_its, cuts, substeps, status;
+    double mb[3], cnv[3], well_res;       /* last accepted norms */
+    double ms_assemble, ms_factor, ms_solve, ms_update;  /* host-timed phases (ms) */
+} bo_step_report;
+
+/* Thread-local message describing the last failing call. */
+const char* bo_last_error(void);
+
+/* Grid of nx*ny*nz box cells; dx[nx], dy[ny], dz[nz] in m; top_depth is the
+ * depth of the top face (depth increases downward).  Allocates the device
+ * state on the current CUDA device. */
+bo_status bo_create_grid(int nx, int ny, int nz, const double* dx, const double* dy,
+                         const double* dz, double top_depth, bo_sim** out);
+
+/* Rock, fluid and wells.  perm[n] is the isotropic permeability (m^2),
+ * poro[n] the reference porosity.  Computes on the device the static data of
+ * Appendix B (transmissibilities as harmonic means of half
+ * transmissibilities), pore volumes, depths and Peaceman well indices
+ * WI = 2 pi k h / (ln(0.14 sqrt(dx^2+dy^2) / r_w) + skin). */
+bo_status bo_set_properties(bo_sim* sim, const double* perm, const double* poro,
+                            const bo_fluid* fluid, const bo_well* wells, int nwells);
+
+/* Static data for checking: Tx, Ty, Tz (transmissibility of each cell's
+ * +x, +y, +z face, 0 on the boundary), pv, depth (each [n]); wi[total
+ * connections] in well order.  Any pointer may be NULL. */
+bo_status bo_get_static(const bo_sim* sim, double* Tx, double* Ty, double* Tz, double* pv,
+                        double* depth, double* wi);
+
+/* Initial state: USAT cells with r_go = rgo and s_w = sw; pressure in
+ * discrete hydrostatic equilibrium of the oil column (Section 2.1.3 with the
+ * face density of Eq. head), p = p_top at the centre of the top layer.  Well
+ * BHPs start at their target (BHP control) or limit (rate control). */
+bo_status bo_init_hydrostatic(bo_sim* sim, double p_top, double sw, double rgo);
+
+/* State I/O.  p, sw, x are [n] doubles, flag [n] bytes (0 SAT, 1 USAT),
+ * well_bhp [nwells] (may be NULL when there are no wells). */
+bo_status bo_set_state(bo_sim* sim, const double* p, const double* sw, const double* x,
+                       const unsigned char* flag, const double* well_bhp);
+bo_status bo_get_state(const bo_sim* sim, double* p, double* sw, double* x,
+                       unsigned char* flag, double* well_bhp);
+bo_status bo_set_state_dev(bo_sim* sim, const double* p, const double* sw, const double* x,
+                           const unsigned char* flag, const double* well_bhp);
+bo_status bo_get_state_dev(const bo_sim* sim, double* p, double* sw, double* x,
+                           unsigned char* flag, double* well_bhp);
+
+/* Stream for every subsequent device operation (a cudaStream_t, e.g. torch's
+ * current stream); NULL selects the legacy default stream. */
+bo_status bo_set_stream(bo_sim* sim, void* cuda_stream);
+
+/* Start of a time step: stores the accumulation terms A0 at the current
+ * state, freezes each well's datum density (explicit over the step,
+ * Section 2.2.1), resets well controls, and saves the state for a cut. */
+bo_status bo_begin_step(bo_sim* sim);
+
+/* Residual R and Jacobian J at the current state for step length dt
+ * (Eq. materialbalance); stays on the device. */
+bo_status bo_assemble(bo_sim* sim, double dt);
+
+/* Convergence measures of the last assembly: out[0..2] MB_a, out[3..5]
+ * CNV_a (a = w, o, g), out[6] max relative rate-well residual.
+ * MB_a = dt Bavg_a |sum_i R_a,i| / sum_i PV_i; CNV_a = dt Bavg_a max_i |R_a,i| / PV_i,
+ * Bavg_a = mean over cells of 1/b_a. */
+bo_status bo_norms(bo_sim* sim, double dt, double* out7);
+
+/* Copy-out of the last assembly as 3x3-block CSR with row-major blocks
+ * (J[r][c] = dR_r,i / dy_c,j), natural cell order, columns ascending:
+ * rowptr[n+1], colind[nnzb], vals[9*nnzb], res[3n] (cell-major).  Any
+ * pointer may be NULL.  *nnzb_out (may be NULL) receives nnzb. */
+bo_status bo_get_system(const bo_sim* sim, int* rowptr, int* colind, double* vals, double* res,
+                        int* nnzb_out);
+
+/* Well linearisation of the last assembly: per well R_w, D_w, control, and
+ * per connection B (3 = dR_w/dy) and C (3 = dR/dp_bhp), packed in well order. */
+bo_status bo_get_wells(const bo_sim* sim, double* Rw, double* Dw, double* B, double* C,
+                       int* control);
+
+/* Block ILU(0) of the last assembly's reservoir matrix A in natural order.
+ * On the 7-point pattern only the diagonal blocks change (the grid graph is
+ * bipartite, so no fill position of ILU(0) lies in the pattern), giving
+ * M = (L_A + D) D^-1 (D + U_A) with D_i = A_ii - sum_k A_ik D_k^-1 A_ki.
+ * dinv (may be NULL) receives D_i^-1, [n][3][3] row-major. */
+bo_status bo_factor(bo_sim* sim, double* dinv);
+
+/* z = M^-1 r with the factors of the last bo_factor; r, z are [3n] host
+ * arrays in cell-major order. */
+bo_status bo_precond_apply(bo_sim* sim, const double* r, double* z);
+
+/* y = (A - sum_w C_w D_w^-1 B_w) x, the well-reduced operator of
+ * Eq. (wellequation); x, y are [3n] host arrays in cell-major order. */
+bo_status bo_apply_op(bo_sim* sim, const double* x, double* y);
+
+/* Linear solve J sol = R of the last assembly: factors, then right-
+ * preconditioned BiCGStab on the reduced system, then the well unknowns.
+ * sol (may be NULL) receives [3n + nwells] (cell-major, then one entry per
+ * well, 0 for wells without an unknown). */
+bo_status bo_solve(bo_sim* sim, const bo_solve_opts* opts, bo_solve_report* report,
+                   double* sol);
+
+/* Newton update from the last bo_solve: dy = -sol with chop and variable
+ * switching as in bo_newton_opts; wells on rate control that pass their BHP
+ * limit switch to BHP control. */
+bo_status bo_newton_update(bo_sim* sim, const bo_newton_opts* opts);
+
+/* One report step of length dt with Newton iterations and time-step cuts.
+ * On BO_ERR_NOT_CONVERGED the state is restored to the start of the step. */
+bo_status bo_step(bo_sim* sim, double dt, const bo_newton_opts* opts, bo_step_report* report);
+
+/* Sub-step length carried into the next report step (s; 0 = not started),
+ * part of the simulation state for checkpoint and restart. */
+bo_status bo_get_step_control(const bo_sim* sim, double* dt_next);
+bo_status bo_set_step_control(bo_sim* sim, double dt_next);
+
+/* Per-kernel timing of the device kernels launched inside bo_step/bo_solve
+ * while enabled (CUDA events on the library stream).  names receive up to
+ * max entries of "name\0", ms_total and launches are per entry. */
+bo_status bo_set_timing(bo_sim* sim, int enabled);
+bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* ms_total,
+                        long long* launches, int* count);
+
+/* Number of cells, wells, connections, and nonzero blocks of the pattern. */
+bo_status bo_sizes(const bo_sim* sim, int* n, int* nwells, int* ncon, int* nnzb);
+
+/* Release all device memory of the object. */
+bo_status bo_destroy(bo_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BO_H */

@@ -29,6 +29,7 @@ DEFAULT_OPTS = {
     "tol_mb": 1e-6, "tol_cnv": 1e-6, "tol_well": 1e-6, "max_newton": 20,
     "tol_lin": 1e-3, "max_lin": 500, "max_cuts": 8,
     "ds_max": 0.2, "dp_rel_max": 0.3, "drs_rel_max": 0.2, "eps_switch": 1e-6,
+    "bp_overshoot": 0.05, "dt_init": 86400.0, "cut_factor": 0.5,
 }
 _OPT_ORDER = list(DEFAULT_OPTS.keys())
 
@@ -79,6 +80,9 @@ def lib():
         L.orc_step.argtypes = [P, d, P, P]
         L.orc_step.restype = i
         L.orc_cell_props.argtypes = [P, d, d, d, i, P]
+        L.orc_get_dt_next.argtypes = [P]
+        L.orc_get_dt_next.restype = d
+        L.orc_set_dt_next.argtypes = [P, d]
         _lib = L
     return _lib
 
@@ -264,6 +268,14 @@ class Oracle:
         o = opts_array(**opts)
         s = np.ascontiguousarray(np.concatenate([sol, np.zeros(1)]), dtype=np.float64)
         lib().orc_newton_update(self.h, _p(o), _p(s))
+
+    @property
+    def dt_next(self):
+        return lib().orc_get_dt_next(self.h)
+
+    @dt_next.setter
+    def dt_next(self, v):
+        lib().orc_set_dt_next(self.h, float(v))
 
     def step(self, dt, **opts):
         o = opts_array(**opts)

@@ -224,6 +224,7 @@ struct Model {
     std::vector<double> lu;
     std::vector<double> Uinv;  // inverse of U diagonal blocks, 9n
     double dt_last = 0.0;
+    double dt_next = 0.0;  // sub-step length carried between report steps (0: unset)
 };
 
 static inline int cidx(const Model& m, int i, int j, int k) { return i + m.nx * (j + m.ny * k); }
@@ -706,12 +707,14 @@ struct Opts {
     double tol_lin;
     int max_lin, max_cuts;
     double ds_max, dp_rel_max, drs_rel_max, eps_switch;
+    double bp_overshoot, dt_init, cut_factor;
 };
 static Opts opts_from(const double* o) {
     Opts r;
     r.tol_mb = o[0]; r.tol_cnv = o[1]; r.tol_well = o[2]; r.max_newton = (int)o[3];
     r.tol_lin = o[4]; r.max_lin = (int)o[5]; r.max_cuts = (int)o[6];
     r.ds_max = o[7]; r.dp_rel_max = o[8]; r.drs_rel_max = o[9]; r.eps_switch = o[10];
+    r.bp_overshoot = o[11]; r.dt_init = o[12]; r.cut_factor = o[13];
     return r;
 }
 
@@ -730,6 +733,12 @@ static void newton_update(Model& m, const Opts& o, const double* sol) {
             if (std::fabs(dsw) > o.ds_max) { double f = o.ds_max / std::fabs(dsw); dsw *= f; }
             double drmax = o.drs_rel_max * F.R_sb;
             if (std::fabs(dx) > drmax) dx = (dx > 0 ? drmax : -drmax);
+            // Section 2.3: do not let an undersaturated cell jump far across the
+            // saturation boundary in one iteration -- its pressure may fall at
+            // most a fraction bp_overshoot below the saturation pressure of its
+            // updated dissolved-gas ratio.
+            double pfloor = (1.0 - o.bp_overshoot) * (F.p_b * (m.x[c] + dx) / F.R_sb);
+            if (p + dp < pfloor && pfloor < p) dp = pfloor - p;
         }
         double pn = p + dp, swn = m.sw[c] + dsw, xn = m.x[c] + dx;
         swn = std::min(std::max(swn, 0.0), 1.0);
@@ -772,6 +781,15 @@ static void restore(Model& m) {
     for (size_t i = 0; i < m.wells.size(); ++i) m.wells[i].bhp = m.bk_bhp[i];
 }
 
+// Sub-step growth after a converged Newton solve of nits iterations: easy
+// steps grow, hard ones shrink (an iteration-count step controller).
+static double step_growth(int nits) {
+    if (nits <= 4) return 2.0;
+    if (nits <= 8) return 1.5;
+    if (nits <= 12) return 1.0;
+    return 0.7;
+}
+
 // One Newton solve of a (sub)step of length dt; returns 0 when converged.
 // rep: [newton_its, lin_its]
 static int newton(Model& m, double dt, const Opts& o, int* nits, int* lits) {
@@ -793,7 +811,9 @@ static int newton(Model& m, double dt, const Opts& o, int* nits, int* lits) {
         int li = 0;
         int st = solve(m, o.tol_lin, o.max_lin, sol.data(), &li);
         *lits += li;
-        if (st == LIN_BREAKDOWN || st == LIN_FACTOR_FAIL) { *nits = it + 1; return 3; }
+        // a linear solve that breaks down or misses its tolerance fails the
+        // Newton solve (the step is then cut)
+        if (st != LIN_OK) { *nits = it + 1; return 3; }
         newton_update(m, o, sol.data());
     }
 }
@@ -994,29 +1014,40 @@ void orc_newton_update(void* h, const double* opts, const double* sol) {
     newton_update(*static_cast<Model*>(h), opts_from(opts), sol);
 }
 
-// One report step of length dt with time-step cutting: a failed Newton solve
-// restores the state, halves the sub-step, and retries (at most max_cuts
-// times).  report: [newton_its, lin_its, cuts, substeps, status(0 ok)].
+// One report step of length dt with adaptive sub-steps (Section 2.3 time-step
+// cutting): the sub-step length is carried between report steps; a
+// converged sub-step grows it by step_growth, a failed Newton solve restores
+// the state and multiplies it by cut_factor (at most max_cuts failures per
+// report step).  report: [newton_its, lin_its, cuts, substeps, status(0 ok)].
 int orc_step(void* h, double dt, const double* opts, double* report) {
     Model* m = static_cast<Model*>(h);
     Opts o = opts_from(opts);
-    double t = 0.0, dtry = dt;
+    double t = 0.0;
+    if (m->dt_next <= 0.0) m->dt_next = (o.dt_init > 0.0) ? o.dt_init : dt;
     int nits_tot = 0, lits_tot = 0, cuts = 0, subs = 0;
     int status = 0;
     while (t < dt * (1.0 - 1e-12)) {
-        double dts = std::min(dtry, dt - t);
+        double dts = std::min(m->dt_next, dt - t);
         int nits = 0, lits = 0;
         int st = newton(*m, dts, o, &nits, &lits);
         nits_tot += nits; lits_tot += lits;
-        if (st == 0) { t += dts; ++subs; continue; }
+        if (st == 0) {
+            t += dts;
+            ++subs;
+            m->dt_next = std::min(dts * step_growth(nits), dt);
+            continue;
+        }
         restore(*m);
         ++cuts;
+        m->dt_next = dts * o.cut_factor;
         if (cuts > o.max_cuts) { status = 1; break; }
-        dtry = 0.5 * dts;
     }
     report[0] = nits_tot; report[1] = lits_tot; report[2] = cuts; report[3] = subs; report[4] = status;
     return status;
 }
+
+double orc_get_dt_next(void* h) { return static_cast<Model*>(h)->dt_next; }
+void orc_set_dt_next(void* h, double v) { static_cast<Model*>(h)->dt_next = v; }
 
 // Single-cell property evaluation with derivatives (for pin tests).
 // out: for each quantity value then d/dp, d/dsw, d/dx; quantities in order

@@ -1,0 +1,750 @@
+// C ABI of the black-oil library: object lifetime, memory, state I/O, the
+// system export used for checking, and the host Newton loop of bo_step
+// (arXiv 1910.06059 Section 2.3: Newton-Raphson on Eq. linsystem with
+// Appleyard chop, variable switching and time-step cutting).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bo {
+
+static thread_local std::string g_last_error;
+
+void fail(bo_status st, const std::string& msg) { throw Error{st, msg}; }
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+    if (e == cudaSuccess) return;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
+                    std::to_string(line) + ")";
+    fail(e == cudaErrorMemoryAllocation ? BO_ERR_OOM : BO_ERR_CUDA, m);
+}
+
+template <class F>
+static bo_status guarded(F&& f) {
+    try {
+        f();
+        return BO_OK;
+    } catch (const Error& e) {
+        g_last_error = e.msg;
+        return e.status;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return BO_ERR_CUDA;
+    }
+}
+
+template <class T>
+static void dalloc(T** p, size_t count) {
+    BO_CUDA(cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1)));
+}
+
+static void need(bool cond, bo_status st, const char* msg) {
+    if (!cond) fail(st, msg);
+}
+
+
+void upload_aos3(bo_sim* s, const double* host, double* dev) {
+    int n = s->geo.n;
+    std::vector<double> soa(3 * (size_t)n);
+    for (int c = 0; c < n; ++c)
+        for (int e = 0; e < 3; ++e) soa[(size_t)e * n + c] = host[3 * (size_t)c + e];
+    BO_CUDA(cudaMemcpyAsync(dev, soa.data(), sizeof(double) * soa.size(), cudaMemcpyHostToDevice,
+                            s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+}
+
+void download_aos3(const bo_sim* s, const double* dev, double* host) {
+    int n = s->geo.n;
+    std::vector<double> soa(3 * (size_t)n);
+    BO_CUDA(cudaMemcpyAsync(soa.data(), dev, sizeof(double) * soa.size(), cudaMemcpyDeviceToHost,
+                            s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+    for (int c = 0; c < n; ++c)
+        for (int e = 0; e < 3; ++e) host[3 * (size_t)c + e] = soa[(size_t)e * n + c];
+}
+
+static void free_all(bo_sim* s) {
+    destroy_graphs(s);
+    void* ptrs[] = {s->d_dx, s->d_dy, s->d_dz, s->d_perm, s->d_poro, s->d_T, s->d_pv, s->d_depth,
+                    s->d_p, s->d_sw, s->d_x, s->d_flag, s->d_bk, s->d_bkflag, s->d_A0,
+                    s->d_props, s->d_R, s->d_A, s->d_P, s->d_perm_lvl, s->d_cellcon, s->d_wells,
+                    s->d_con_cell, s->d_con_wi, s->d_wB, s->d_wC, s->d_b, s->d_xs, s->d_r,
+                    s->d_rh, s->d_pk, s->d_v, s->d_s, s->d_t, s->d_ph, s->d_sh, s->d_part,
+                    s->d_ks, s->d_ns, s->d_flag_sweep, s->d_sweep_sync};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (s->h_ns) cudaFreeHost(s->h_ns);
+    if (s->h_ks) cudaFreeHost(s->h_ks);
+}
+
+static void sync(bo_sim* s) { BO_CUDA(cudaStreamSynchronize(s->stream)); }
+
+static void read_status(bo_sim* s) {
+    BO_CUDA(cudaMemcpyAsync(s->h_ns, s->d_ns, sizeof(NewtonStatus), cudaMemcpyDeviceToHost,
+                            s->stream));
+    sync(s);
+}
+
+// Assembly plus the dead-well fix-up (one more assembly when a rate well has
+// no flowing connection), then the norms.
+static void assemble_and_norms(bo_sim* s, double dt) {
+    launch_assemble(s, dt);
+    read_status(s);
+    if (s->h_ns->dead_wells > 0) {
+        launch_fix_dead_wells(s);
+        launch_assemble(s, dt);
+    }
+    launch_norms(s, dt);
+    read_status(s);
+    s->assembled = true;
+    s->factored = false;
+    s->solved = false;
+    s->dt_last = dt;
+}
+
+// Linear solve of the last assembly; returns the LS_* status.
+static void check_timeout(bo_sim* s) {
+    if (sweep_timeout(s))
+        fail(BO_ERR_DEVICE_TIMEOUT,
+             "a dataflow sweep gave up waiting for a neighbour (bounded wait ran out)");
+}
+
+static int solve_linear(bo_sim* s, double tol, int maxit, int* its) {
+    launch_factor(s);
+    read_status(s);
+    check_timeout(s);
+    if (s->h_ns->pad != 0) {  // non-finite pivot block
+        *its = 0;
+        return LS_BREAKDOWN;
+    }
+    s->factored = true;
+    int st = run_bicgstab(s, tol, maxit, its);
+    check_timeout(s);
+    launch_well_recover(s);
+    s->solved = true;
+    return st;
+}
+
+static bool norms_converged(const double* nrm, const bo_newton_opts& o, bool* finite) {
+    *finite = true;
+    for (int q = 0; q < 7; ++q)
+        if (!std::isfinite(nrm[q])) *finite = false;
+    bool conv = true;
+    for (int a = 0; a < 3; ++a)
+        if (nrm[a] > o.tol_mb || nrm[3 + a] > o.tol_cnv) conv = false;
+    if (nrm[6] > o.tol_well) conv = false;
+    return conv;
+}
+
+// Sub-step growth after a converged Newton solve of nits iterations.
+static double step_growth(int nits) {
+    if (nits <= 4) return 2.0;
+    if (nits <= 8) return 1.5;
+    if (nits <= 12) return 1.0;
+    return 0.7;
+}
+
+using clk = std::chrono::steady_clock;
+static double ms_since(clk::time_point t0) {
+    return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+}
+
+// Newton solve of one sub-step; 0 converged, 1 max iterations, 2 non-finite
+// norms, 3 linear breakdown.
+static int newton(bo_sim* s, double dt, const bo_newton_opts& o, int* nits, int* lits,
+                  bo_step_report* rep) {
+    launch_begin_step(s);
+    for (int it = 0;; ++it) {
+        auto t0 = clk::now();
+        assemble_and_norms(s, dt);
+        rep->ms_assemble += ms_since(t0);
+        const double* nrm = s->h_ns->norms;
+        bool finite;
+        bool conv = norms_converged(nrm, o, &finite);
+        if (!finite) return 2;
+        if (conv) {
+            *nits = it;
+            for (int a = 0; a < 3; ++a) {
+                rep->mb[a] = nrm[a];
+                rep->cnv[a] = nrm[3 + a];
+            }
+            rep->well_res = nrm[6];
+            return 0;
+        }
+        if (it == o.max_newton) {
+            *nits = it;
+            return 1;
+        }
+        int li = 0;
+        t0 = clk::now();
+        int st = solve_linear(s, o.tol_lin, o.max_lin, &li);
+        sync(s);
+        rep->ms_solve += ms_since(t0);
+        *lits += li;
+        if (st != LS_OK) {  // breakdown or missed tolerance fails the Newton solve
+            *nits = it + 1;
+            return 3;
+        }
+        t0 = clk::now();
+        launch_newton_update(s, o);
+        rep->ms_update += ms_since(t0);
+    }
+}
+
+}  // namespace bo
+
+using namespace bo;
+
+extern "C" {
+
+const char* bo_last_error(void) { return g_last_error.c_str(); }
+
+bo_status bo_create_grid(int nx, int ny, int nz, const double* dx, const double* dy,
+                         const double* dz, double top_depth, bo_sim** out) {
+    return guarded([&] {
+        need(out != nullptr, BO_ERR_INVALID_ARG, "bo_create_grid: out is NULL");
+        *out = nullptr;
+        need(nx > 0 && ny > 0 && nz > 0, BO_ERR_INVALID_ARG, "bo_create_grid: grid sizes must be positive");
+        need((long long)nx * ny * nz < (1LL << 30), BO_ERR_INVALID_ARG,
+             "bo_create_grid: more than 2^30 cells");
+        need(dx && dy && dz, BO_ERR_INVALID_ARG, "bo_create_grid: dx, dy, dz must be given");
+        for (int i = 0; i < nx; ++i) need(dx[i] > 0, BO_ERR_INVALID_ARG, "bo_create_grid: dx must be > 0");
+        for (int j = 0; j < ny; ++j) need(dy[j] > 0, BO_ERR_INVALID_ARG, "bo_create_grid: dy must be > 0");
+        for (int k = 0; k < nz; ++k) need(dz[k] > 0, BO_ERR_INVALID_ARG, "bo_create_grid: dz must be > 0");
+        bo_sim* s = new bo_sim();
+        try {
+            s->geo = {nx, ny, nz, nx * ny * nz};
+            s->dx.assign(dx, dx + nx);
+            s->dy.assign(dy, dy + ny);
+            s->dz.assign(dz, dz + nz);
+            s->top = top_depth;
+            BO_CUDA(cudaGetDevice(&s->device));
+            size_t n = s->geo.n;
+            dalloc(&s->d_dx, nx);
+            dalloc(&s->d_dy, ny);
+            dalloc(&s->d_dz, nz);
+            BO_CUDA(cudaMemcpy(s->d_dx, dx, sizeof(double) * nx, cudaMemcpyHostToDevice));
+            BO_CUDA(cudaMemcpy(s->d_dy, dy, sizeof(double) * ny, cudaMemcpyHostToDevice));
+            BO_CUDA(cudaMemcpy(s->d_dz, dz, sizeof(double) * nz, cudaMemcpyHostToDevice));
+            dalloc(&s->d_perm, n);
+            dalloc(&s->d_poro, n);
+            dalloc(&s->d_T, 3 * n);
+            dalloc(&s->d_pv, n);
+            dalloc(&s->d_depth, n);
+            dalloc(&s->d_p, n);
+            dalloc(&s->d_sw, n);
+            dalloc(&s->d_x, n);
+            dalloc(&s->d_flag, n);
+            dalloc(&s->d_bk, 3 * n);
+            dalloc(&s->d_bkflag, n);
+            dalloc(&s->d_A0, 3 * n);
+            dalloc(&s->d_props, (size_t)NPROP * n);
+            dalloc(&s->d_R, 3 * n);
+            dalloc(&s->d_A, 63 * n);
+            dalloc(&s->d_P, 63 * n);
+            dalloc(&s->d_perm_lvl, 2 * n);
+            dalloc(&s->d_flag_sweep, n);
+            dalloc(&s->d_sweep_sync, 4);
+            for (double** v : {&s->d_b, &s->d_xs, &s->d_r, &s->d_rh, &s->d_pk, &s->d_v, &s->d_s,
+                               &s->d_t, &s->d_ph, &s->d_sh})
+                dalloc(v, 3 * n);
+            BO_CUDA(cudaMemset(s->d_A, 0, sizeof(double) * 63 * n));
+            BO_CUDA(cudaMemset(s->d_p, 0, sizeof(double) * n));
+            BO_CUDA(cudaMemset(s->d_sw, 0, sizeof(double) * n));
+            BO_CUDA(cudaMemset(s->d_x, 0, sizeof(double) * n));
+            BO_CUDA(cudaMemset(s->d_flag, 0, n));
+            dalloc(&s->d_ks, 1);
+            dalloc(&s->d_ns, 1);
+            BO_CUDA(cudaMemset(s->d_ns, 0, sizeof(NewtonStatus)));
+            BO_CUDA(cudaMallocHost(reinterpret_cast<void**>(&s->h_ns), sizeof(NewtonStatus)));
+            BO_CUDA(cudaMallocHost(reinterpret_cast<void**>(&s->h_ks), sizeof(KrylovScalars)));
+            build_levels(s);
+            setup_sweeps(s);
+        } catch (...) {
+            free_all(s);
+            delete s;
+            throw;
+        }
+        *out = s;
+    });
+}
+
+bo_status bo_set_properties(bo_sim* s, const double* perm, const double* poro,
+                            const bo_fluid* fluid, const bo_well* wells, int nwells) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_set_properties: sim is NULL");
+        need(perm && poro && fluid, BO_ERR_INVALID_ARG, "bo_set_properties: perm, poro, fluid required");
+        need(nwells >= 0 && (nwells == 0 || wells), BO_ERR_INVALID_ARG, "bo_set_properties: bad wells");
+        need(!s->props_set, BO_ERR_STATE, "bo_set_properties: properties already set");
+        const int n = s->geo.n;
+        for (int c = 0; c < n; ++c) {
+            need(perm[c] > 0 && std::isfinite(perm[c]), BO_ERR_INVALID_ARG, "bo_set_properties: perm must be > 0");
+            need(poro[c] > 0 && poro[c] <= 1, BO_ERR_INVALID_ARG, "bo_set_properties: poro must be in (0, 1]");
+        }
+        static_assert(sizeof(bo_fluid) == sizeof(DevFluid), "fluid layout");
+        std::memcpy(&s->fluid, fluid, sizeof(DevFluid));
+        // wells
+        std::vector<int> cellcon(n, -1), conwell;
+        std::vector<double> rw, skin;
+        s->wells_h.clear();
+        s->con_cell_h.clear();
+        s->nrate = 0;
+        for (int w = 0; w < nwells; ++w) {
+            const bo_well& in = wells[w];
+            need(in.kind == 0 || in.kind == 1, BO_ERR_INVALID_ARG, "well kind must be 0 or 1");
+            need(in.control == 0 || in.control == 1, BO_ERR_INVALID_ARG, "well control must be 0 or 1");
+            need(in.kind == 1 || in.phase == 0 || in.phase == 2, BO_ERR_INVALID_ARG,
+                 "injector phase must be 0 (water) or 2 (gas)");
+            need(in.ncon > 0 && in.cells, BO_ERR_INVALID_ARG, "well needs at least one connection");
+            need(in.rw > 0, BO_ERR_INVALID_ARG, "well radius must be > 0");
+            WellDev d{};
+            d.kind = in.kind;
+            d.phase = in.kind == 0 ? in.phase : 1;
+            d.ctl0 = d.ctl = in.control;
+            d.off = (int)s->con_cell_h.size();
+            d.ncon = in.ncon;
+            d.target = in.target;
+            d.limit = in.bhp_limit;
+            d.bhp = in.control == 1 ? in.target : in.bhp_limit;
+            if (in.control == 0) s->nrate++;
+            for (int q = 0; q < in.ncon; ++q) {
+                int c = in.cells[q];
+                need(c >= 0 && c < n, BO_ERR_INVALID_ARG, "well connection cell out of range");
+                need(cellcon[c] < 0, BO_ERR_INVALID_ARG, "a cell may hold only one well connection");
+                cellcon[c] = (int)s->con_cell_h.size();
+                s->con_cell_h.push_back(c);
+                conwell.push_back(w);
+            }
+            rw.push_back(in.rw);
+            skin.push_back(in.skin);
+            s->wells_h.push_back(d);
+        }
+        s->nw = nwells;
+        s->ncon = (int)s->con_cell_h.size();
+        BO_CUDA(cudaMemcpy(s->d_perm, perm, sizeof(double) * n, cudaMemcpyHostToDevice));
+        BO_CUDA(cudaMemcpy(s->d_poro, poro, sizeof(double) * n, cudaMemcpyHostToDevice));
+        dalloc(&s->d_cellcon, (size_t)n + s->ncon);
+        BO_CUDA(cudaMemcpy(s->d_cellcon, cellcon.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        if (s->ncon)
+            BO_CUDA(cudaMemcpy(s->d_cellcon + n, conwell.data(), sizeof(int) * s->ncon,
+                               cudaMemcpyHostToDevice));
+        dalloc(&s->d_wells, s->nw);
+        if (s->nw)
+            BO_CUDA(cudaMemcpy(s->d_wells, s->wells_h.data(), sizeof(WellDev) * s->nw,
+                               cudaMemcpyHostToDevice));
+        dalloc(&s->d_con_cell, s->ncon);
+        dalloc(&s->d_con_wi, s->ncon);
+        dalloc(&s->d_wB, 3 * (size_t)s->ncon);
+        dalloc(&s->d_wC, 3 * (size_t)s->ncon);
+        if (s->ncon) {
+            BO_CUDA(cudaMemcpy(s->d_con_cell, s->con_cell_h.data(), sizeof(int) * s->ncon,
+                               cudaMemcpyHostToDevice));
+            BO_CUDA(cudaMemset(s->d_wB, 0, sizeof(double) * 3 * s->ncon));
+            BO_CUDA(cudaMemset(s->d_wC, 0, sizeof(double) * 3 * s->ncon));
+        }
+        // reduction scratch: props 1/b partials + norm partials, or Krylov partials + well scalars
+        size_t npart = std::max<size_t>(3 * (size_t)props_blocks(s) + 7 * 1024,
+                                        8 * (size_t)(152 * 4) + s->nw + 1);
+        dalloc(&s->d_part, npart);
+        double *d_rw = nullptr, *d_skin = nullptr;
+        dalloc(&d_rw, s->nw);
+        dalloc(&d_skin, s->nw);
+        if (s->nw) {
+            BO_CUDA(cudaMemcpy(d_rw, rw.data(), sizeof(double) * s->nw, cudaMemcpyHostToDevice));
+            BO_CUDA(cudaMemcpy(d_skin, skin.data(), sizeof(double) * s->nw, cudaMemcpyHostToDevice));
+        }
+        launch_static(s);
+        launch_wi(s, s->d_cellcon + n, d_rw, d_skin);
+        sync(s);
+        cudaFree(d_rw);
+        cudaFree(d_skin);
+        build_graphs(s);
+        s->props_set = true;
+    });
+}
+
+bo_status bo_get_static(const bo_sim* s, double* Tx, double* Ty, double* Tz, double* pv,
+                        double* depth, double* wi) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_get_static: properties not set");
+        size_t n = s->geo.n;
+        if (Tx) BO_CUDA(cudaMemcpy(Tx, s->d_T, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        if (Ty) BO_CUDA(cudaMemcpy(Ty, s->d_T + n, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        if (Tz) BO_CUDA(cudaMemcpy(Tz, s->d_T + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        if (pv) BO_CUDA(cudaMemcpy(pv, s->d_pv, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        if (depth) BO_CUDA(cudaMemcpy(depth, s->d_depth, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        if (wi && s->ncon)
+            BO_CUDA(cudaMemcpy(wi, s->d_con_wi, sizeof(double) * s->ncon, cudaMemcpyDeviceToHost));
+    });
+}
+
+bo_status bo_init_hydrostatic(bo_sim* s, double p_top, double sw, double rgo) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_init_hydrostatic: properties not set");
+        need(p_top > 0 && sw >= 0 && sw <= 1 && rgo >= 0, BO_ERR_INVALID_ARG,
+             "bo_init_hydrostatic: bad initial values");
+        launch_hydrostatic(s, p_top, sw, rgo);
+        for (auto& w : s->wells_h) w.bhp = w.ctl0 == 1 ? w.target : w.limit;
+        for (int w = 0; w < s->nw; ++w) {
+            WellDev d = s->wells_h[w];
+            d.ctl = d.ctl0;
+            BO_CUDA(cudaMemcpyAsync(s->d_wells + w, &d, sizeof(WellDev), cudaMemcpyHostToDevice,
+                                    s->stream));
+            BO_CUDA(cudaStreamSynchronize(s->stream));
+        }
+        sync(s);
+        s->assembled = s->factored = s->solved = false;
+    });
+}
+
+static void set_bhp(bo_sim* s, const double* bhp, cudaMemcpyKind kind) {
+    if (!bhp || s->nw == 0) return;
+    std::vector<double> h(s->nw);
+    if (kind == cudaMemcpyDeviceToHost) {
+        BO_CUDA(cudaMemcpyAsync(h.data(), bhp, sizeof(double) * s->nw, cudaMemcpyDeviceToHost, s->stream));
+        sync(s);
+    } else {
+        std::memcpy(h.data(), bhp, sizeof(double) * s->nw);
+    }
+    for (int w = 0; w < s->nw; ++w)
+        BO_CUDA(cudaMemcpyAsync(&s->d_wells[w].bhp, &h[w], sizeof(double), cudaMemcpyHostToDevice,
+                                s->stream));
+    sync(s);
+}
+
+static void get_bhp(const bo_sim* s, double* bhp, bool dev) {
+    if (!bhp || s->nw == 0) return;
+    std::vector<WellDev> w(s->nw);
+    BO_CUDA(cudaMemcpyAsync(w.data(), s->d_wells, sizeof(WellDev) * s->nw, cudaMemcpyDeviceToHost,
+                            s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+    std::vector<double> h(s->nw);
+    for (int q = 0; q < s->nw; ++q) h[q] = w[q].bhp;
+    if (dev) {
+        BO_CUDA(cudaMemcpyAsync(bhp, h.data(), sizeof(double) * s->nw, cudaMemcpyHostToDevice, s->stream));
+        BO_CUDA(cudaStreamSynchronize(s->stream));
+    } else {
+        std::memcpy(bhp, h.data(), sizeof(double) * s->nw);
+    }
+}
+
+static bo_status set_state_impl(bo_sim* s, const double* p, const double* sw, const double* x,
+                                const unsigned char* flag, const double* bhp, bool dev) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_set_state: properties not set");
+        need(p && sw && x && flag, BO_ERR_INVALID_ARG, "bo_set_state: p, sw, x, flag required");
+        need(s->nw == 0 || bhp, BO_ERR_INVALID_ARG, "bo_set_state: well_bhp required");
+        size_t n = s->geo.n;
+        cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        BO_CUDA(cudaMemcpyAsync(s->d_p, p, sizeof(double) * n, k, s->stream));
+        BO_CUDA(cudaMemcpyAsync(s->d_sw, sw, sizeof(double) * n, k, s->stream));
+        BO_CUDA(cudaMemcpyAsync(s->d_x, x, sizeof(double) * n, k, s->stream));
+        BO_CUDA(cudaMemcpyAsync(s->d_flag, flag, n, k, s->stream));
+        set_bhp(s, bhp, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+        sync(s);
+        s->assembled = s->factored = s->solved = false;
+    });
+}
+
+static bo_status get_state_impl(const bo_sim* s, double* p, double* sw, double* x,
+                                unsigned char* flag, double* bhp, bool dev) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_get_state: properties not set");
+        size_t n = s->geo.n;
+        cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (p) BO_CUDA(cudaMemcpyAsync(p, s->d_p, sizeof(double) * n, k, s->stream));
+        if (sw) BO_CUDA(cudaMemcpyAsync(sw, s->d_sw, sizeof(double) * n, k, s->stream));
+        if (x) BO_CUDA(cudaMemcpyAsync(x, s->d_x, sizeof(double) * n, k, s->stream));
+        if (flag) BO_CUDA(cudaMemcpyAsync(flag, s->d_flag, n, k, s->stream));
+        get_bhp(s, bhp, dev);
+        BO_CUDA(cudaStreamSynchronize(s->stream));
+    });
+}
+
+bo_status bo_set_state(bo_sim* s, const double* p, const double* sw, const double* x,
+                       const unsigned char* flag, const double* bhp) {
+    return set_state_impl(s, p, sw, x, flag, bhp, false);
+}
+bo_status bo_set_state_dev(bo_sim* s, const double* p, const double* sw, const double* x,
+                           const unsigned char* flag, const double* bhp) {
+    return set_state_impl(s, p, sw, x, flag, bhp, true);
+}
+bo_status bo_get_state(const bo_sim* s, double* p, double* sw, double* x, unsigned char* flag,
+                       double* bhp) {
+    return get_state_impl(s, p, sw, x, flag, bhp, false);
+}
+bo_status bo_get_state_dev(const bo_sim* s, double* p, double* sw, double* x, unsigned char* flag,
+                           double* bhp) {
+    return get_state_impl(s, p, sw, x, flag, bhp, true);
+}
+
+bo_status bo_set_stream(bo_sim* s, void* stream) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_set_stream: sim is NULL");
+        s->stream = static_cast<cudaStream_t>(stream);
+    });
+}
+
+bo_status bo_begin_step(bo_sim* s) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_begin_step: properties not set");
+        launch_begin_step(s);
+        sync(s);
+    });
+}
+
+bo_status bo_assemble(bo_sim* s, double dt) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_assemble: properties not set");
+        need(dt > 0 && std::isfinite(dt), BO_ERR_INVALID_ARG, "bo_assemble: dt must be > 0");
+        launch_assemble(s, dt);
+        launch_norms(s, dt);
+        read_status(s);
+        s->assembled = true;
+        s->factored = s->solved = false;
+        s->dt_last = dt;
+    });
+}
+
+bo_status bo_norms(bo_sim* s, double dt, double* out7) {
+    return guarded([&] {
+        need(s && s->assembled, BO_ERR_STATE, "bo_norms: no assembly");
+        need(out7 != nullptr, BO_ERR_INVALID_ARG, "bo_norms: out is NULL");
+        launch_norms(s, dt);
+        read_status(s);
+        std::memcpy(out7, s->h_ns->norms, sizeof(double) * 7);
+    });
+}
+
+bo_status bo_get_system(const bo_sim* s, int* rowptr, int* colind, double* vals, double* res,
+                        int* nnzb_out) {
+    return guarded([&] {
+        need(s && s->assembled, BO_ERR_STATE, "bo_get_system: no assembly");
+        const Geom& g = s->geo;
+        const int n = g.n;
+        std::vector<double> A;
+        if (vals) {
+            A.resize(63 * (size_t)n);
+            BO_CUDA(cudaMemcpy(A.data(), s->d_A, sizeof(double) * A.size(), cudaMemcpyDeviceToHost));
+        }
+        int q = 0;
+        const int plane = g.nx * g.ny;
+        if (rowptr) rowptr[0] = 0;
+        for (int c = 0; c < n; ++c) {
+            int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / plane;
+            // ascending column order: -z, -y, -x, diag, +x, +y, +z
+            const int order[7] = {NB_MZ, NB_MY, NB_MX, NB_DIAG, NB_PX, NB_PY, NB_PZ};
+            const bool has[7] = {k > 0, j > 0, i > 0, true, i + 1 < g.nx, j + 1 < g.ny, k + 1 < g.nz};
+            const int col[7] = {c - plane, c - g.nx, c - 1, c, c + 1, c + g.nx, c + plane};
+            for (int t = 0; t < 7; ++t) {
+                if (!has[t]) continue;
+                if (colind) colind[q] = col[t];
+                if (vals)
+                    for (int e = 0; e < 9; ++e)
+                        vals[9 * (size_t)q + e] = A[(size_t)(order[t] * 9 + e) * n + c];
+                ++q;
+            }
+            if (rowptr) rowptr[c + 1] = q;
+        }
+        if (nnzb_out) *nnzb_out = q;
+        if (res) download_aos3(s, s->d_R, res);
+    });
+}
+
+bo_status bo_get_wells(const bo_sim* s, double* Rw, double* Dw, double* B, double* C, int* control) {
+    return guarded([&] {
+        need(s && s->assembled, BO_ERR_STATE, "bo_get_wells: no assembly");
+        if (s->nw == 0) return;
+        std::vector<WellDev> w(s->nw);
+        BO_CUDA(cudaMemcpy(w.data(), s->d_wells, sizeof(WellDev) * s->nw, cudaMemcpyDeviceToHost));
+        for (int q = 0; q < s->nw; ++q) {
+            if (Rw) Rw[q] = w[q].Rw;
+            if (Dw) Dw[q] = w[q].Dw;
+            if (control) control[q] = w[q].ctl;
+        }
+        if (B) BO_CUDA(cudaMemcpy(B, s->d_wB, sizeof(double) * 3 * s->ncon, cudaMemcpyDeviceToHost));
+        if (C) BO_CUDA(cudaMemcpy(C, s->d_wC, sizeof(double) * 3 * s->ncon, cudaMemcpyDeviceToHost));
+    });
+}
+
+bo_status bo_factor(bo_sim* s, double* dinv) {
+    return guarded([&] {
+        need(s && s->assembled, BO_ERR_STATE, "bo_factor: no assembly");
+        launch_factor(s);
+        read_status(s);
+        check_timeout(s);
+        need(s->h_ns->pad == 0, BO_ERR_LINEAR_BREAKDOWN, "bo_factor: singular pivot block");
+        s->factored = true;
+        if (dinv) {
+            const int n = s->geo.n;
+            std::vector<double> P(9 * (size_t)n);
+            std::vector<int> perm(n);
+            BO_CUDA(cudaMemcpy(P.data(), s->d_P, sizeof(double) * P.size(), cudaMemcpyDeviceToHost));
+            BO_CUDA(cudaMemcpy(perm.data(), s->d_perm_lvl, sizeof(int) * n, cudaMemcpyDeviceToHost));
+            for (int m = 0; m < n; ++m)
+                for (int e = 0; e < 9; ++e) dinv[9 * (size_t)perm[m] + e] = P[(size_t)e * n + m];
+        }
+    });
+}
+
+bo_status bo_precond_apply(bo_sim* s, const double* r, double* z) {
+    return guarded([&] {
+        need(s && s->factored, BO_ERR_STATE, "bo_precond_apply: no factorisation");
+        need(r && z, BO_ERR_INVALID_ARG, "bo_precond_apply: r, z required");
+        upload_aos3(s, r, s->d_b);
+        launch_precond(s, s->d_b, s->d_t);
+        download_aos3(s, s->d_t, z);
+        check_timeout(s);
+    });
+}
+
+bo_status bo_apply_op(bo_sim* s, const double* x, double* y) {
+    return guarded([&] {
+        need(s && s->assembled, BO_ERR_STATE, "bo_apply_op: no assembly");
+        need(x && y, BO_ERR_INVALID_ARG, "bo_apply_op: x, y required");
+        upload_aos3(s, x, s->d_b);
+        launch_op(s, s->d_b, s->d_t);
+        download_aos3(s, s->d_t, y);
+    });
+}
+
+bo_status bo_solve(bo_sim* s, const bo_solve_opts* o, bo_solve_report* rep, double* sol) {
+    return guarded([&] {
+        need(s && s->assembled, BO_ERR_STATE, "bo_solve: no assembly");
+        need(o && o->tol > 0 && o->max_it > 0, BO_ERR_INVALID_ARG, "bo_solve: bad options");
+        int its = 0;
+        int st = solve_linear(s, o->tol, o->max_it, &its);
+        sync(s);
+        if (rep) {
+            rep->iterations = its;
+            rep->status = st;
+        }
+        if (sol) {
+            download_aos3(s, s->d_xs, sol);
+            std::vector<WellDev> w(s->nw);
+            if (s->nw)
+                BO_CUDA(cudaMemcpy(w.data(), s->d_wells, sizeof(WellDev) * s->nw, cudaMemcpyDeviceToHost));
+            for (int q = 0; q < s->nw; ++q) sol[3 * (size_t)s->geo.n + q] = w[q].xw;
+        }
+    });
+}
+
+bo_status bo_newton_update(bo_sim* s, const bo_newton_opts* o) {
+    return guarded([&] {
+        need(s && s->solved, BO_ERR_STATE, "bo_newton_update: no solution");
+        need(o != nullptr, BO_ERR_INVALID_ARG, "bo_newton_update: opts is NULL");
+        launch_newton_update(s, *o);
+        sync(s);
+        s->assembled = s->factored = s->solved = false;
+    });
+}
+
+bo_status bo_step(bo_sim* s, double dt, const bo_newton_opts* o, bo_step_report* rep) {
+    bo_step_report local{};
+    bo_step_report* r = rep ? rep : &local;
+    std::memset(r, 0, sizeof(*r));
+    bo_status status = guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_step: properties not set");
+        need(o != nullptr, BO_ERR_INVALID_ARG, "bo_step: opts is NULL");
+        need(dt > 0 && std::isfinite(dt), BO_ERR_INVALID_ARG, "bo_step: dt must be > 0");
+        double t = 0.0;
+        if (s->dt_next <= 0.0) s->dt_next = (o->dt_init > 0.0) ? o->dt_init : dt;
+        while (t < dt * (1.0 - 1e-12)) {
+            double dts = std::min(s->dt_next, dt - t);
+            int nits = 0, lits = 0;
+            int st = newton(s, dts, *o, &nits, &lits, r);
+            r->newton_its += nits;
+            r->lin_its += lits;
+            if (st == 0) {
+                t += dts;
+                r->substeps++;
+                s->dt_next = std::min(dts * step_growth(nits), dt);
+                continue;
+            }
+            launch_restore(s);
+            sync(s);
+            r->cuts++;
+            s->dt_next = dts * o->cut_factor;
+            if (r->cuts > o->max_cuts) {
+                r->status = 1;
+                fail(BO_ERR_NOT_CONVERGED, "bo_step: Newton did not converge after the allowed time-step cuts");
+            }
+        }
+        s->assembled = s->factored = s->solved = false;
+    });
+    return status;
+}
+
+bo_status bo_get_step_control(const bo_sim* s, double* dt_next) {
+    return guarded([&] {
+        need(s && dt_next, BO_ERR_INVALID_ARG, "bo_get_step_control: NULL argument");
+        *dt_next = s->dt_next;
+    });
+}
+
+bo_status bo_set_step_control(bo_sim* s, double dt_next) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_set_step_control: sim is NULL");
+        need(dt_next >= 0 && std::isfinite(dt_next), BO_ERR_INVALID_ARG,
+             "bo_set_step_control: dt_next must be >= 0");
+        s->dt_next = dt_next;
+    });
+}
+
+bo_status bo_set_timing(bo_sim* s, int enabled) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_set_timing: sim is NULL");
+        s->timing = enabled != 0;
+        for (int q = 0; q < MAX_TIMERS; ++q) {
+            s->timer_ms[q] = 0.0;
+            s->timer_n[q] = 0;
+        }
+    });
+}
+
+bo_status bo_get_timing(const bo_sim* s, int max, char (*names)[32], double* ms_total,
+                        long long* launches, int* count) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_get_timing: sim is NULL");
+        int k = std::min(max, s->ntimers);
+        for (int q = 0; q < k; ++q) {
+            if (names) {
+                std::strncpy(names[q], s->timer_name[q].c_str(), 31);
+                names[q][31] = 0;
+            }
+            if (ms_total) ms_total[q] = s->timer_ms[q];
+            if (launches) launches[q] = s->timer_n[q];
+        }
+        if (count) *count = k;
+    });
+}
+
+bo_status bo_sizes(const bo_sim* s, int* n, int* nwells, int* ncon, int* nnzb) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_sizes: sim is NULL");
+        const Geom& g = s->geo;
+        if (n) *n = g.n;
+        if (nwells) *nwells = s->nw;
+        if (ncon) *ncon = s->ncon;
+        if (nnzb) {
+            long long F = (long long)(g.nx - 1) * g.ny * g.nz + (long long)g.nx * (g.ny - 1) * g.nz +
+                          (long long)g.nx * g.ny * (g.nz - 1);
+            *nnzb = (int)(g.n + 2 * F);
+        }
+    });
+}
+
+bo_status bo_destroy(bo_sim* s) {
+    return guarded([&] {
+        if (!s) return;
+        cudaStreamSynchronize(s->stream);
+        free_all(s);
+        delete s;
+    });
+}
+
+}  // extern "C"

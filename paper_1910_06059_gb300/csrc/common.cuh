@@ -1,0 +1,191 @@
+// Internal declarations of the GB300 black-oil library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "bo.h"
+
+namespace bo {
+
+// ---------------------------------------------------------------------------
+// Error handling: every C entry point catches bo::Error and maps it to a
+// status plus a thread-local message.
+// ---------------------------------------------------------------------------
+struct Error {
+    bo_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(bo_status st, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define BO_CUDA(call) ::bo::check_cuda((call), #call, __FILE__, __LINE__)
+#define BO_LAUNCH_CHECK(name) ::bo::check_cuda(cudaGetLastError(), name, __FILE__, __LINE__)
+
+// ---------------------------------------------------------------------------
+// Data layout in HBM (n cells, natural order c = i + nx*(j + ny*k)):
+//   cell vectors of 3 components: structure of arrays v[e*n + c]
+//   Jacobian A: 7 blocks per cell, block-major then entry-major:
+//     A[(b*9 + e)*n + c],  b: 0 diag, 1 -x, 2 +x, 3 -y, 4 +y, 5 -z, 6 +z,
+//     e = 3*r + s for dR_r,c / dy_s,neighbour(b); zero where no neighbour.
+//   ILU(0) data P in wavefront order m (cells sorted by level i+j+k, then
+//     by k, then j): P[(b*9 + e)*n + m],  b: 0 D^-1, 1..3 D^-1 A_{c,-x/-y/-z},
+//     4..6 D^-1 A_{c,+x/+y/+z}.
+// ---------------------------------------------------------------------------
+enum { NB_DIAG = 0, NB_MX = 1, NB_PX = 2, NB_MY = 3, NB_PY = 4, NB_MZ = 5, NB_PZ = 6 };
+constexpr int NPROP = 28;   // per-cell face quantities: rho_a, b_a lam_a (3 x 4), r_go b_o lam_o (4)
+
+struct DevFluid {
+    double g, rho_s[3], p_ref, bw_ref, c_w, mu_w, R_sb, p_b, Bo_slope, c_o, mu_o0, mu_o_r, c_mu,
+        p_sc, Z, mu_g0, mu_g_p, c_r, s_wco, s_orw, s_org, n_corey;
+};
+
+struct Geom {
+    int nx, ny, nz, n;
+};
+
+// Well description and per-step state, in device memory.
+struct WellDev {
+    int kind, phase, ctl0, ctl;   // ctl: 0 rate, 1 bhp
+    int off, ncon;
+    double target, limit, bhp, bhp_bk;
+    double z_datum, rho_well;
+    double Rw, Dw, xw;
+};
+
+// Scalars of the BiCGStab recurrence, kept on the device.
+struct KrylovScalars {
+    double rho, rho_old, alpha, omega, beta, nr0, tol;
+    double last_nr;
+    int it, maxit, state, status;   // state: 0 running, 1 half-step exit pending, 2 done
+    int half_exit;                  // the solve ended on the half step (no second apply)
+    int pad_;
+};
+enum { KS_RUN = 0, KS_HALF = 1, KS_DONE = 2 };
+enum { LS_OK = 0, LS_NOT_CONVERGED = 1, LS_BREAKDOWN = 2 };
+
+// Device-to-host status block read once per Newton iteration.
+struct NewtonStatus {
+    double norms[7];
+    int dead_wells;   // rate wells with D_w == 0 in the last assembly
+    int pad;
+};
+
+constexpr int MAX_TIMERS = 16;
+
+}  // namespace bo
+
+// The opaque object of the C ABI.
+struct bo_sim {
+    bo::Geom geo{};
+    int nlev = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool props_set = false;
+    bool assembled = false;
+    bool factored = false;
+    bool solved = false;
+    double dt_last = 0.0;
+    double dt_next = 0.0;   // sub-step length carried between report steps
+
+    std::vector<double> dx, dy, dz;
+    double top = 0.0;
+    bo::DevFluid fluid{};
+
+    // wells (host mirror of the static part)
+    int nw = 0, ncon = 0, nrate = 0;
+    std::vector<bo::WellDev> wells_h;
+    std::vector<int> con_cell_h;
+
+    // level sets of the wavefront order (host copy)
+    std::vector<int> lvl_ptr;
+
+    // device memory
+    double *d_dx = nullptr, *d_dy = nullptr, *d_dz = nullptr;
+    double *d_perm = nullptr, *d_poro = nullptr;
+    double *d_T = nullptr;       // 3n: +x, +y, +z face transmissibility
+    double *d_pv = nullptr, *d_depth = nullptr;
+    double *d_p = nullptr, *d_sw = nullptr, *d_x = nullptr;
+    uint8_t* d_flag = nullptr;
+    double* d_bk = nullptr;      // 3n backup of (p, sw, x)
+    uint8_t* d_bkflag = nullptr;
+    double* d_A0 = nullptr;      // 3n
+    double* d_props = nullptr;   // NPROP * n
+    double* d_R = nullptr;       // 3n
+    double* d_A = nullptr;       // 63n
+    double* d_P = nullptr;       // 63n (wavefront order)
+    int* d_perm_lvl = nullptr;   // m -> c, then c -> m
+    int* d_flag_sweep = nullptr; // per-cell ready flags of the dataflow sweeps
+    int* d_sweep_sync = nullptr; // sweep epoch, finished-block count, timeout flag
+    int sweep_grid = 0;
+    int sweep_blocks_per_sm = 2;
+    int* d_cellcon = nullptr;    // c -> connection index or -1
+    bo::WellDev* d_wells = nullptr;
+    int* d_con_cell = nullptr;
+    double* d_con_wi = nullptr;
+    double* d_wB = nullptr;      // 3 * ncon
+    double* d_wC = nullptr;      // 3 * ncon
+    // Krylov vectors (3n each) and reduction scratch
+    double *d_b = nullptr, *d_xs = nullptr, *d_r = nullptr, *d_rh = nullptr, *d_pk = nullptr,
+           *d_v = nullptr, *d_s = nullptr, *d_t = nullptr, *d_ph = nullptr, *d_sh = nullptr;
+    double* d_part = nullptr;    // reduction partials
+    int part_blocks = 0;
+    bo::KrylovScalars* d_ks = nullptr;
+    bo::NewtonStatus* d_ns = nullptr;
+    bo::NewtonStatus* h_ns = nullptr;   // pinned
+    bo::KrylovScalars* h_ks = nullptr;  // pinned
+
+    // CUDA graphs of one BiCGStab iteration block and of the factorisation
+    cudaGraphExec_t g_iter = nullptr;
+    cudaGraphExec_t g_factor = nullptr;
+    cudaGraphExec_t g_iter_timed = nullptr;
+    int iters_per_graph = 4;
+
+    // timing
+    bool timing = false;
+    int ntimers = 0;
+    std::string timer_name[bo::MAX_TIMERS];
+    double timer_ms[bo::MAX_TIMERS] = {};
+    long long timer_n[bo::MAX_TIMERS] = {};
+    std::vector<cudaEvent_t> iter_events;  // per iteration-in-graph: begin/end pairs
+};
+
+namespace bo {
+
+// ---- launchers (defined in the .cu files) ---------------------------------
+void launch_static(bo_sim* s);
+void launch_hydrostatic(bo_sim* s, double p_top, double sw, double rgo);
+void launch_begin_step(bo_sim* s);
+void launch_assemble(bo_sim* s, double dt);
+void launch_norms(bo_sim* s, double dt);
+void launch_fix_dead_wells(bo_sim* s);
+void launch_restore(bo_sim* s);
+
+void build_levels(bo_sim* s);
+void setup_sweeps(bo_sim* s);
+int sweep_timeout(bo_sim* s);
+void build_graphs(bo_sim* s);
+void destroy_graphs(bo_sim* s);
+void launch_factor(bo_sim* s);                       // graph of level kernels
+void launch_precond(bo_sim* s, const double* r, double* z);
+void launch_op(bo_sim* s, const double* x, double* y);
+int run_bicgstab(bo_sim* s, double tol, int maxit, int* its);  // returns LS_*
+void launch_well_recover(bo_sim* s);
+void launch_newton_update(bo_sim* s, const bo_newton_opts& o);
+
+int timer_id(bo_sim* s, const char* name);
+void timer_begin(bo_sim* s, int id);
+void timer_end(bo_sim* s, int id);
+void timers_flush(bo_sim* s);
+void launch_wi(bo_sim* s, const int* d_con_well, const double* d_rw, const double* d_skin);
+int props_blocks(const bo_sim* s);
+int norm_blocks(const bo_sim* s);
+
+// Convert between cell-major host vectors (3c+e) and SoA device vectors.
+void upload_aos3(bo_sim* s, const double* host, double* dev);
+void download_aos3(const bo_sim* s, const double* dev, double* host);
+
+}  // namespace bo

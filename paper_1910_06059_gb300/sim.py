@@ -1,0 +1,216 @@
+"""Python view of one simulation object of libbo.so (marshalling only).
+
+The method names follow the C ABI of ``include/bo.h`` without the ``bo_``
+prefix.  Host arrays are NumPy; the ``*_dev`` forms take torch CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import call, ptr
+
+
+class Sim:
+    """One black-oil model on the current CUDA device."""
+
+    def __init__(self, model: dict, stream=None):
+        self.model = model
+        nx, ny, nz = model["nx"], model["ny"], model["nz"]
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n = nx * ny * nz
+        dx = np.ascontiguousarray(model["dx"], dtype=np.float64)
+        dy = np.ascontiguousarray(model["dy"], dtype=np.float64)
+        dz = np.ascontiguousarray(model["dz"], dtype=np.float64)
+        h = ctypes.c_void_p()
+        call("bo_create_grid", nx, ny, nz, ptr(dx), ptr(dy), ptr(dz), float(model["top_depth"]),
+             ctypes.byref(h))
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+        self._set_properties()
+
+    # -- setup ---------------------------------------------------------------
+    def _set_properties(self):
+        m = self.model
+        perm = np.ascontiguousarray(m["perm"], dtype=np.float64)
+        poro = np.ascontiguousarray(m["poro"], dtype=np.float64)
+        fl = L.fluid_struct(m["fluid"])
+        wells = (L.BoWell * max(1, len(m["wells"])))()
+        self._cells = []
+        self.well_cells = []
+        for q, w in enumerate(m["wells"]):
+            cells = np.asarray([w["i"] + self.nx * (w["j"] + self.ny * k) for k in w["ks"]],
+                               dtype=np.int32)
+            self._cells.append(cells)
+            self.well_cells.append([int(c) for c in cells])
+            wells[q].kind = 0 if w["kind"] == "inj" else 1
+            wells[q].phase = 0 if w.get("phase", "gas") == "water" else 2
+            wells[q].control = 0 if w["control"] == "rate" else 1
+            wells[q].ncon = len(cells)
+            wells[q].cells = cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+            wells[q].target = w["target"]
+            wells[q].bhp_limit = w["bhp_limit"]
+            wells[q].rw = w["rw"]
+            wells[q].skin = w["skin"]
+        self.nw = len(m["wells"])
+        self.ncon = sum(len(c) for c in self._cells)
+        call("bo_set_properties", self.h, ptr(perm), ptr(poro), ctypes.byref(fl),
+             ctypes.cast(wells, ctypes.c_void_p), self.nw)
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None (legacy default)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        call("bo_set_stream", self.h, ctypes.c_void_p(handle or 0))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            call("bo_destroy", self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- static data and state ----------------------------------------------
+    def get_static(self):
+        n = self.n
+        Tx, Ty, Tz, pv, depth = (np.zeros(n) for _ in range(5))
+        wi = np.zeros(max(self.ncon, 1))
+        call("bo_get_static", self.h, ptr(Tx), ptr(Ty), ptr(Tz), ptr(pv), ptr(depth), ptr(wi))
+        return {"Tx": Tx, "Ty": Ty, "Tz": Tz, "pv": pv, "depth": depth, "wi": wi[:self.ncon]}
+
+    def init_hydrostatic(self):
+        ini = self.model["init"]
+        call("bo_init_hydrostatic", self.h, float(ini["p_top"]), float(ini["sw"]), float(ini["rgo"]))
+
+    def set_state(self, p, sw, x, flag, bhp):
+        p, sw, x = (np.ascontiguousarray(a, dtype=np.float64) for a in (p, sw, x))
+        flag = np.ascontiguousarray(flag, dtype=np.uint8)
+        bhp = np.ascontiguousarray(bhp if len(bhp) else [0.0], dtype=np.float64)
+        call("bo_set_state", self.h, ptr(p), ptr(sw), ptr(x), ptr(flag), ptr(bhp))
+
+    def get_state(self):
+        n = self.n
+        p, sw, x = np.zeros(n), np.zeros(n), np.zeros(n)
+        flag = np.zeros(n, dtype=np.uint8)
+        bhp = np.zeros(max(self.nw, 1))
+        call("bo_get_state", self.h, ptr(p), ptr(sw), ptr(x), ptr(flag), ptr(bhp))
+        return p, sw, x, flag, bhp[:self.nw]
+
+    def set_state_dev(self, p, sw, x, flag, bhp):
+        call("bo_set_state_dev", self.h, ptr(p), ptr(sw), ptr(x), ptr(flag), ptr(bhp))
+
+    def get_state_dev(self, p, sw, x, flag, bhp):
+        call("bo_get_state_dev", self.h, ptr(p), ptr(sw), ptr(x), ptr(flag), ptr(bhp))
+
+    # -- linearisation -------------------------------------------------------
+    def begin_step(self):
+        call("bo_begin_step", self.h)
+
+    def assemble(self, dt):
+        call("bo_assemble", self.h, float(dt))
+
+    def norms(self, dt):
+        out = np.zeros(7)
+        call("bo_norms", self.h, float(dt), ptr(out))
+        return out
+
+    def system(self):
+        """(rowptr, colind, vals[nnzb,3,3], R[n,3]) of the last assembly."""
+        nnzb = ctypes.c_int()
+        call("bo_get_system", self.h, None, None, None, None, ctypes.byref(nnzb))
+        rp = np.zeros(self.n + 1, dtype=np.int32)
+        ci = np.zeros(nnzb.value, dtype=np.int32)
+        v = np.zeros(9 * nnzb.value)
+        r = np.zeros(3 * self.n)
+        call("bo_get_system", self.h, ptr(rp), ptr(ci), ptr(v), ptr(r), None)
+        return rp, ci, v.reshape(-1, 3, 3), r.reshape(-1, 3)
+
+    def wells(self):
+        nw = max(self.nw, 1)
+        rw, dw = np.zeros(nw), np.zeros(nw)
+        B = np.zeros(max(3 * self.ncon, 1))
+        C = np.zeros(max(3 * self.ncon, 1))
+        ctl = np.zeros(nw, dtype=np.int32)
+        call("bo_get_wells", self.h, ptr(rw), ptr(dw), ptr(B), ptr(C), ptr(ctl))
+        out, off = [], 0
+        for q in range(self.nw):
+            nc = len(self.well_cells[q])
+            out.append({"Rw": rw[q], "Dw": dw[q], "B": B[3 * off:3 * (off + nc)].reshape(nc, 3),
+                        "C": C[3 * off:3 * (off + nc)].reshape(nc, 3), "control": int(ctl[q])})
+            off += nc
+        return out
+
+    # -- linear solver -------------------------------------------------------
+    def factor(self):
+        dinv = np.zeros(9 * self.n)
+        call("bo_factor", self.h, ptr(dinv))
+        return dinv.reshape(-1, 3, 3)
+
+    def precond_apply(self, r):
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1)
+        z = np.zeros_like(r)
+        call("bo_precond_apply", self.h, ptr(r), ptr(z))
+        return z
+
+    def apply_op(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        y = np.zeros_like(x)
+        call("bo_apply_op", self.h, ptr(x), ptr(y))
+        return y
+
+    def solve(self, tol=1e-3, maxit=500):
+        """Returns (status, iterations, sol[3n + nw]); sol solves J sol = R."""
+        o = L.BoSolveOpts(tol=float(tol), max_it=int(maxit))
+        rep = L.BoSolveReport()
+        sol = np.zeros(3 * self.n + max(self.nw, 1))
+        call("bo_solve", self.h, ctypes.byref(o), ctypes.byref(rep), ptr(sol))
+        return rep.status, rep.iterations, sol[:3 * self.n + self.nw]
+
+    def newton_update(self, **opts):
+        o = L.newton_opts(**opts)
+        call("bo_newton_update", self.h, ctypes.byref(o))
+
+    def step(self, dt, raise_on_fail=False, **opts):
+        """One report step; returns (status, report dict)."""
+        o = L.newton_opts(**opts)
+        rep = L.BoStepReport()
+        Lb = L.load()
+        st = Lb.bo_step(self.h, float(dt), ctypes.byref(o), ctypes.byref(rep))
+        if st != 0 and (raise_on_fail or st != 4):
+            raise L.BoError(st, Lb.bo_last_error().decode())
+        return st, {"newton_its": rep.newton_its, "lin_its": rep.lin_its, "cuts": rep.cuts,
+                    "substeps": rep.substeps, "status": rep.status, "mb": list(rep.mb),
+                    "cnv": list(rep.cnv), "well_res": rep.well_res,
+                    "ms_assemble": rep.ms_assemble, "ms_solve": rep.ms_solve,
+                    "ms_update": rep.ms_update}
+
+    @property
+    def dt_next(self):
+        v = ctypes.c_double()
+        call("bo_get_step_control", self.h, ctypes.byref(v))
+        return v.value
+
+    @dt_next.setter
+    def dt_next(self, v):
+        call("bo_set_step_control", self.h, float(v))
+
+    # -- timing --------------------------------------------------------------
+    def set_timing(self, enabled: bool):
+        call("bo_set_timing", self.h, 1 if enabled else 0)
+
+    def timing(self):
+        k = 16
+        names = (ctypes.c_char * 32 * k)()
+        ms = np.zeros(k)
+        cnt = np.zeros(k, dtype=np.int64)
+        count = ctypes.c_int()
+        call("bo_get_timing", self.h, k, ctypes.cast(names, ctypes.c_void_p), ptr(ms), ptr(cnt),
+             ctypes.byref(count))
+        return {bytes(names[q]).split(b"\0")[0].decode(): (float(ms[q]), int(cnt[q]))
+                for q in range(count.value)}

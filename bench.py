@@ -304,16 +304,16 @@ def run_gb300(args):
 
 
 def gpu_launch_count(timers, reps, sim):
-    """Kernels launched in the timed region: per BiCGStab iteration
-    2 x (2 x levels) sweep kernels + 2 operator + well kernels + 9 vector and
-    scalar kernels; per assembly 3-4 kernels + 2 norm kernels; per
-    factorisation one kernel per level; per Newton update 2."""
-    lv = sim.nx + sim.ny + sim.nz - 2
+    """Kernels launched in the timed region, counted from the algorithm:
+    per BiCGStab iteration 16 (scalar, vector, 2 forward + 2 backward sweeps,
+    2 well dots, 2 operators), per solve 4 setup + 1 factorisation + 1 well
+    recovery, per assembly 5 (props, flux, wells, 2 norm kernels), per
+    Newton update 2, per sub-step 2 (step start)."""
     lin = sum(r["lin_its"] for r in reps)
     nit = sum(r["newton_its"] for r in reps)
     asm = sum(r["newton_its"] + r["substeps"] + r["cuts"] for r in reps)
-    per_it = 4 * lv + 2 * 2 + 9
-    return int(lin * per_it + nit * (lv + 2 + 4) + asm * 6)
+    subs = sum(r["substeps"] + r["cuts"] for r in reps)
+    return int(lin * 16 + nit * (4 + 1 + 1 + 2) + asm * 5 + subs * 2)
 
 
 def run_reference(args):

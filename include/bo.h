@@ -89,6 +89,10 @@ typedef struct {
  * saturation pressure of the updated r_go (no far jump across the
  * saturated/undersaturated boundary).  Switching: SAT -> USAT when s_g < 0
  * (r_go = r_s(p)); USAT -> SAT when r_go > r_s(p) (1 + eps_switch) (s_g = 0).
+ * Rate-controlled wells: the BHP may at most halve its distance to the
+ * opening pressure (the BHP at which the first connection flows) per
+ * iteration; a well assembled without any flowing connection is moved 0.1%
+ * past its opening pressure and assembled again.
  * Linear solve to relative residual tol_lin within max_lin iterations; a
  * linear solve that misses it fails the Newton solve.  Sub-steps: the first
  * sub-step of a simulation is dt_init (<= 0: the whole report step); the
@@ -147,7 +151,9 @@ bo_status bo_get_static(const bo_sim* sim, double* Tx, double* Ty, double* Tz, d
 /* Initial state: USAT cells with r_go = rgo and s_w = sw; pressure in
  * discrete hydrostatic equilibrium of the oil column (Section 2.1.3 with the
  * face density of Eq. head), p = p_top at the centre of the top layer.  Well
- * BHPs start at their target (BHP control) or limit (rate control). */
+ * BHPs start at their target (BHP control) or limit (rate control); a
+ * rate-controlled injector starts at the BHP that meets its target by the
+ * linear inflow relation with all connections injecting, capped by its limit. */
 bo_status bo_init_hydrostatic(bo_sim* sim, double p_top, double sw, double rgo);
 
 /* State I/O.  p, sw, x are [n] doubles, flag [n] bytes (0 SAT, 1 USAT),

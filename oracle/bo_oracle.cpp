@@ -718,6 +718,19 @@ static Opts opts_from(const double* o) {
     return r;
 }
 
+// Opening pressure of a well at the current cell pressures: the BHP at which
+// the first connection starts to flow, min_j (p_j - h_j) for an injector
+// (it injects through connection j when BHP + h_j > p_j), max_j for a
+// producer.
+static double opening_bhp(const Model& m, const Well& w) {
+    double v = (w.kind == 0) ? 1e300 : -1e300;
+    for (int c : w.cells) {
+        double ph = m.p[c] - m.F.g * w.rho_well * (m.depth[c] - w.z_datum);
+        v = (w.kind == 0) ? std::min(v, ph) : std::max(v, ph);
+    }
+    return v;
+}
+
 static void newton_update(Model& m, const Opts& o, const double* sol) {
     const Fluid& F = m.F;
     int n = m.n;
@@ -758,7 +771,20 @@ static void newton_update(Model& m, const Opts& o, const double* sol) {
             double d = -sol[3 * n + wi];
             double dmax = o.dp_rel_max * w.bhp;
             if (std::fabs(d) > dmax) d = (d > 0 ? dmax : -dmax);
-            w.bhp += d;
+            double old = w.bhp;
+            double nb = old + d;
+            // well chop: a rate-controlled well must keep flowing -- the BHP may
+            // at most halve its distance to the opening pressure (at the
+            // updated cell pressures) per iteration
+            double po = opening_bhp(m, w);
+            if (w.kind == 0) {
+                double floor_ = (old > po) ? po + 0.5 * (old - po) : po + 1e-3 * std::fabs(po);
+                if (nb < floor_) nb = floor_;
+            } else {
+                double ceil_ = (old < po) ? po - 0.5 * (po - old) : po - 1e-3 * std::fabs(po);
+                if (nb > ceil_) nb = ceil_;
+            }
+            w.bhp = nb;
             bool viol = (w.kind == 0) ? (w.bhp > w.bhp_limit) : (w.bhp < w.bhp_limit);
             if (viol) { w.control = 1; w.bhp = w.bhp_limit; }
         }
@@ -767,12 +793,16 @@ static void newton_update(Model& m, const Opts& o, const double* sol) {
 }
 
 // After assembly: a rate-controlled well with no flowing connection (D_w = 0)
-// cannot meet its target at the current BHP; it is put on its BHP limit for
-// the rest of the step, and the system is assembled again.
+// has no sensitivity to its BHP; its BHP is moved just past the opening
+// pressure (0.1% of it) and the system is assembled again.
 static bool fix_dead_wells(Model& m) {
     bool changed = false;
     for (Well& w : m.wells)
-        if (w.control == 0 && w.Dw == 0.0) { w.control = 1; w.bhp = w.bhp_limit; changed = true; }
+        if (w.control == 0 && w.Dw == 0.0) {
+            double po = opening_bhp(m, w);
+            w.bhp = (w.kind == 0) ? po + 1e-3 * std::fabs(po) : po - 1e-3 * std::fabs(po);
+            changed = true;
+        }
     return changed;
 }
 
@@ -923,6 +953,23 @@ void orc_init_hydrostatic(void* h, double p_top, double sw, double rgo) {
             }
         }
     for (Well& w : m->wells) w.bhp = (w.control0 == 1) ? w.target : w.bhp_limit;
+    // A rate-controlled injector starts at the BHP that meets its target by
+    // the linear inflow relation at the initial state (all connections
+    // injecting), capped by its limit; begin_step's datum density is used.
+    begin_step(*m);
+    for (Well& w : m->wells) {
+        if (w.control0 != 0 || w.kind != 0) continue;
+        double num = w.target, den = 0.0;
+        for (size_t q = 0; q < w.cells.size(); ++q) {
+            int c = w.cells[q];
+            CellProps cp = cell_props(F, m->p[c], m->sw[c], m->x[c], m->flag[c]);
+            double mob = w.WI[q] * (cp.lam[W].v + cp.lam[O].v + cp.lam[G].v) * cp.b[w.phase].v;
+            double h = F.g * w.rho_well * (m->depth[c] - w.z_datum);
+            num += mob * (m->p[c] - h);
+            den += mob;
+        }
+        if (den > 0.0) w.bhp = std::min(w.bhp_limit, num / den);
+    }
 }
 
 void orc_begin_step(void* h) { begin_step(*static_cast<Model*>(h)); }

@@ -71,10 +71,10 @@ static void free_all(bo_sim* s) {
     destroy_graphs(s);
     void* ptrs[] = {s->d_dx, s->d_dy, s->d_dz, s->d_perm, s->d_poro, s->d_T, s->d_pv, s->d_depth,
                     s->d_p, s->d_sw, s->d_x, s->d_flag, s->d_bk, s->d_bkflag, s->d_A0,
-                    s->d_props, s->d_R, s->d_A, s->d_P, s->d_perm_lvl, s->d_cellcon, s->d_wells,
+                    s->d_props, s->d_R, s->d_A, s->d_P, s->d_face, s->d_cellcon, s->d_wells,
                     s->d_con_cell, s->d_con_wi, s->d_wB, s->d_wC, s->d_b, s->d_xs, s->d_r,
                     s->d_rh, s->d_pk, s->d_v, s->d_s, s->d_t, s->d_ph, s->d_sh, s->d_part,
-                    s->d_ks, s->d_ns, s->d_flag_sweep, s->d_sweep_sync};
+                    s->d_ks, s->d_ns, s->d_sweep_sync};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->h_ns) cudaFreeHost(s->h_ns);
@@ -245,9 +245,8 @@ bo_status bo_create_grid(int nx, int ny, int nz, const double* dx, const double*
             dalloc(&s->d_props, (size_t)NPROP * n);
             dalloc(&s->d_R, 3 * n);
             dalloc(&s->d_A, 63 * n);
-            dalloc(&s->d_P, 63 * n);
-            dalloc(&s->d_perm_lvl, 2 * n);
-            dalloc(&s->d_flag_sweep, n);
+            dalloc(&s->d_P, 63 * ilu_storage(s));
+            dalloc(&s->d_face, face_storage(s));
             dalloc(&s->d_sweep_sync, 4);
             for (double** v : {&s->d_b, &s->d_xs, &s->d_r, &s->d_rh, &s->d_pk, &s->d_v, &s->d_s,
                                &s->d_t, &s->d_ph, &s->d_sh})
@@ -262,7 +261,6 @@ bo_status bo_create_grid(int nx, int ny, int nz, const double* dx, const double*
             BO_CUDA(cudaMemset(s->d_ns, 0, sizeof(NewtonStatus)));
             BO_CUDA(cudaMallocHost(reinterpret_cast<void**>(&s->h_ns), sizeof(NewtonStatus)));
             BO_CUDA(cudaMallocHost(reinterpret_cast<void**>(&s->h_ks), sizeof(KrylovScalars)));
-            build_levels(s);
             setup_sweeps(s);
         } catch (...) {
             free_all(s);
@@ -396,6 +394,9 @@ bo_status bo_init_hydrostatic(bo_sim* s, double p_top, double sw, double rgo) {
                                     s->stream));
             BO_CUDA(cudaStreamSynchronize(s->stream));
         }
+        // datum densities at the initial state, then the injector BHP estimate
+        launch_begin_step(s);
+        launch_well_init_bhp(s);
         sync(s);
         s->assembled = s->factored = s->solved = false;
     });
@@ -579,15 +580,7 @@ bo_status bo_factor(bo_sim* s, double* dinv) {
         check_timeout(s);
         need(s->h_ns->pad == 0, BO_ERR_LINEAR_BREAKDOWN, "bo_factor: singular pivot block");
         s->factored = true;
-        if (dinv) {
-            const int n = s->geo.n;
-            std::vector<double> P(9 * (size_t)n);
-            std::vector<int> perm(n);
-            BO_CUDA(cudaMemcpy(P.data(), s->d_P, sizeof(double) * P.size(), cudaMemcpyDeviceToHost));
-            BO_CUDA(cudaMemcpy(perm.data(), s->d_perm_lvl, sizeof(int) * n, cudaMemcpyDeviceToHost));
-            for (int m = 0; m < n; ++m)
-                for (int e = 0; e < 9; ++e) dinv[9 * (size_t)perm[m] + e] = P[(size_t)e * n + m];
-        }
+        if (dinv) export_dinv(s, dinv);
     });
 }
 

@@ -534,15 +534,77 @@ k_wells(Geom g, DevFluid F, WellDev* __restrict__ wells, const int* __restrict__
     }
 }
 
-// A rate-controlled well without a flowing connection is put on its BHP limit.
-__global__ void k_fix_dead_wells(int nw, WellDev* __restrict__ wells) {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nw) return;
-    WellDev& W = wells[w];
-    if (W.ctl == 0 && W.Dw == 0.0) {
-        W.ctl = 1;
-        W.bhp = W.limit;
+// Opening pressure of a well (one block, all threads get the result): the
+// BHP at which the first connection starts to flow, min_j (p_j - h_j) for an
+// injector, max_j for a producer.
+__device__ double opening_bhp(const WellDev& W, const int* __restrict__ con_cell,
+                              const double* __restrict__ p, const double* __restrict__ depth,
+                              double g) {
+    __shared__ double sh[128];
+    double v = (W.kind == 0) ? 1e300 : -1e300;
+    for (int q = threadIdx.x; q < W.ncon; q += blockDim.x) {
+        int c = con_cell[W.off + q];
+        double ph = p[c] - g * W.rho_well * (depth[c] - W.z_datum);
+        v = (W.kind == 0) ? fmin(v, ph) : fmax(v, ph);
     }
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            sh[threadIdx.x] = (W.kind == 0) ? fmin(sh[threadIdx.x], sh[threadIdx.x + o])
+                                            : fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// A rate-controlled well without a flowing connection (D_w = 0) has no
+// sensitivity to its BHP: move the BHP just past the opening pressure.
+__global__ void k_fix_dead_wells(WellDev* __restrict__ wells, const int* __restrict__ con_cell,
+                                 const double* __restrict__ p, const double* __restrict__ depth,
+                                 double g) {
+    WellDev& W = wells[blockIdx.x];
+    if (!(W.ctl == 0 && W.Dw == 0.0)) return;   // uniform over the block
+    double po = opening_bhp(W, con_cell, p, depth, g);
+    if (threadIdx.x == 0) W.bhp = (W.kind == 0) ? po + 1e-3 * fabs(po) : po - 1e-3 * fabs(po);
+}
+
+// Initial BHP of a rate-controlled injector: the BHP that meets the target by
+// the linear inflow relation with every connection injecting, capped by the
+// limit (after k_begin_wells has set the datum and wellbore density).
+__global__ void k_well_init_bhp(DevFluid F, WellDev* __restrict__ wells,
+                                const int* __restrict__ con_cell,
+                                const double* __restrict__ con_wi,
+                                const double* __restrict__ depth, const double* __restrict__ p,
+                                const double* __restrict__ sw, const double* __restrict__ x,
+                                const uint8_t* __restrict__ flag) {
+    WellDev& W = wells[blockIdx.x];
+    if (W.ctl0 != 0 || W.kind != 0) return;
+    __shared__ double sn[128], sd[128];
+    double num = 0.0, den = 0.0;
+    for (int q = threadIdx.x; q < W.ncon; q += blockDim.x) {
+        int con = W.off + q;
+        int c = con_cell[con];
+        CellD cd;
+        cell_eval(F, p[c], sw[c], x[c], flag[c], cd);
+        double mob = con_wi[con] * (cd.lam[W_].v + cd.lam[O_].v + cd.lam[G_].v) * cd.b[W.phase].v;
+        double h = F.g * W.rho_well * (depth[c] - W.z_datum);
+        num += mob * (p[c] - h);
+        den += mob;
+    }
+    sn[threadIdx.x] = num;
+    sd[threadIdx.x] = den;
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sn[threadIdx.x] += sn[threadIdx.x + o];
+            sd[threadIdx.x] += sd[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && sd[0] > 0.0) W.bhp = fmin(W.limit, (W.target + sn[0]) / sd[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -675,15 +737,30 @@ __global__ void k_newton_update(int n, DevFluid F, bo_newton_opts o,
     flag[c] = fl;
 }
 
-__global__ void k_well_update(int nw, bo_newton_opts o, WellDev* __restrict__ wells) {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nw) return;
-    WellDev& W = wells[w];
-    if (W.ctl != 0) return;
+// BHP update of rate-controlled wells (one block per well, after the cell
+// update): chopped Newton step, then the well chop -- the BHP may at most
+// halve its distance to the opening pressure per iteration, so the well keeps
+// flowing -- then the switch to BHP control past the limit.
+__global__ void k_well_update(bo_newton_opts o, WellDev* __restrict__ wells,
+                              const int* __restrict__ con_cell, const double* __restrict__ p,
+                              const double* __restrict__ depth, double g) {
+    WellDev& W = wells[blockIdx.x];
+    if (W.ctl != 0) return;   // uniform over the block
+    double po = opening_bhp(W, con_cell, p, depth, g);
+    if (threadIdx.x != 0) return;
     double d = -W.xw;
     double dmax = o.dp_rel_max * W.bhp;
     if (fabs(d) > dmax) d = (d > 0 ? dmax : -dmax);
-    W.bhp += d;
+    double old = W.bhp;
+    double nb = old + d;
+    if (W.kind == 0) {
+        double fl = (old > po) ? po + 0.5 * (old - po) : po + 1e-3 * fabs(po);
+        if (nb < fl) nb = fl;
+    } else {
+        double cl = (old < po) ? po - 0.5 * (po - old) : po - 1e-3 * fabs(po);
+        if (nb > cl) nb = cl;
+    }
+    W.bhp = nb;
     bool viol = (W.kind == 0) ? (W.bhp > W.limit) : (W.bhp < W.limit);
     if (viol) {
         W.ctl = 1;
@@ -779,8 +856,17 @@ void launch_assemble(bo_sim* s, double dt) {
 
 void launch_fix_dead_wells(bo_sim* s) {
     if (s->nw == 0) return;
-    k_fix_dead_wells<<<blocks_for(s->nw, 32), 32, 0, s->stream>>>(s->nw, s->d_wells);
+    k_fix_dead_wells<<<s->nw, 128, 0, s->stream>>>(s->d_wells, s->d_con_cell, s->d_p, s->d_depth,
+                                                    s->fluid.g);
     BO_LAUNCH_CHECK("k_fix_dead_wells");
+}
+
+void launch_well_init_bhp(bo_sim* s) {
+    if (s->nw == 0) return;
+    k_well_init_bhp<<<s->nw, 128, 0, s->stream>>>(s->fluid, s->d_wells, s->d_con_cell,
+                                                   s->d_con_wi, s->d_depth, s->d_p, s->d_sw,
+                                                   s->d_x, s->d_flag);
+    BO_LAUNCH_CHECK("k_well_init_bhp");
 }
 
 void launch_norms(bo_sim* s, double dt) {
@@ -801,7 +887,8 @@ void launch_newton_update(bo_sim* s, const bo_newton_opts& o) {
                                                               s->d_sw, s->d_x, s->d_flag);
     BO_LAUNCH_CHECK("k_newton_update");
     if (s->nw > 0) {
-        k_well_update<<<blocks_for(s->nw, 32), 32, 0, s->stream>>>(s->nw, o, s->d_wells);
+        k_well_update<<<s->nw, 128, 0, s->stream>>>(o, s->d_wells, s->d_con_cell, s->d_p,
+                                                     s->d_depth, s->fluid.g);
         BO_LAUNCH_CHECK("k_well_update");
     }
 }

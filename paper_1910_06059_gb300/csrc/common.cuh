@@ -31,9 +31,8 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 //   Jacobian A: 7 blocks per cell, block-major then entry-major:
 //     A[(b*9 + e)*n + c],  b: 0 diag, 1 -x, 2 +x, 3 -y, 4 +y, 5 -z, 6 +z,
 //     e = 3*r + s for dR_r,c / dy_s,neighbour(b); zero where no neighbour.
-//   ILU(0) data P in wavefront order m (cells sorted by level i+j+k, then
-//     by k, then j): P[(b*9 + e)*n + m],  b: 0 D^-1, 1..3 D^-1 A_{c,-x/-y/-z},
-//     4..6 D^-1 A_{c,+x/+y/+z}.
+//   ILU(0) data P in tile order (see ilu_tiled.cu): b: 0 D^-1,
+//     1..3 D^-1 A_{c,-x/-y/-z}, 4..6 D^-1 A_{c,+x/+y/+z}.
 // ---------------------------------------------------------------------------
 enum { NB_DIAG = 0, NB_MX = 1, NB_PX = 2, NB_MY = 3, NB_PY = 4, NB_MZ = 5, NB_PZ = 6 };
 constexpr int NPROP = 28;   // per-cell face quantities: rho_a, b_a lam_a (3 x 4), r_go b_o lam_o (4)
@@ -100,8 +99,6 @@ struct bo_sim {
     std::vector<bo::WellDev> wells_h;
     std::vector<int> con_cell_h;
 
-    // level sets of the wavefront order (host copy)
-    std::vector<int> lvl_ptr;
 
     // device memory
     double *d_dx = nullptr, *d_dy = nullptr, *d_dz = nullptr;
@@ -116,12 +113,9 @@ struct bo_sim {
     double* d_props = nullptr;   // NPROP * n
     double* d_R = nullptr;       // 3n
     double* d_A = nullptr;       // 63n
-    double* d_P = nullptr;       // 63n (wavefront order)
-    int* d_perm_lvl = nullptr;   // m -> c, then c -> m
-    int* d_flag_sweep = nullptr; // per-cell ready flags of the dataflow sweeps
-    int* d_sweep_sync = nullptr; // sweep epoch, finished-block count, timeout flag
-    int sweep_grid = 0;
-    int sweep_blocks_per_sm = 2;
+    double* d_P = nullptr;       // 63 x tile-order ILU(0) data
+    double* d_face = nullptr;    // tile-face buffers of the wavefront sweeps
+    int* d_sweep_sync = nullptr; // [2]: a bounded wait of a sweep ran out
     int* d_cellcon = nullptr;    // c -> connection index or -1
     bo::WellDev* d_wells = nullptr;
     int* d_con_cell = nullptr;
@@ -162,11 +156,17 @@ void launch_begin_step(bo_sim* s);
 void launch_assemble(bo_sim* s, double dt);
 void launch_norms(bo_sim* s, double dt);
 void launch_fix_dead_wells(bo_sim* s);
+void launch_well_init_bhp(bo_sim* s);
 void launch_restore(bo_sim* s);
 
-void build_levels(bo_sim* s);
 void setup_sweeps(bo_sim* s);
 int sweep_timeout(bo_sim* s);
+size_t ilu_storage(const bo_sim* s);
+size_t face_storage(const bo_sim* s);
+void enqueue_factor(bo_sim* s, cudaStream_t st, int* bad);
+void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y, const KrylovScalars* ks);
+void enqueue_bwd(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks);
+void export_dinv(bo_sim* s, double* dinv);
 void build_graphs(bo_sim* s);
 void destroy_graphs(bo_sim* s);
 void launch_factor(bo_sim* s);                       // graph of level kernels

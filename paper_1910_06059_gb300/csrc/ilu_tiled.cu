@@ -1,0 +1,619 @@
+// Block ILU(0) factorisation and triangular sweeps of the 7-point pattern as
+// warp-tiled wavefronts (arXiv 1910.06059, Section 2.3.1: ILU0 is the default
+// preconditioner and takes most of the solve time).
+//
+// ILU(0) on this pattern changes only the diagonal blocks (the grid graph is
+// bipartite, so no fill position lies in the pattern):
+//     D_c = A_cc - sum_{k in {-x,-y,-z}} A_ck D_k^-1 A_kc,
+//     M   = (L_A + D) D^-1 (D + U_A).
+// Forward  y_c = D_c^-1 r_c - sum_lower (D_c^-1 A_ck) y_k
+// Backward z_c = y_c       - sum_upper (D_c^-1 A_cj) z_j
+//
+// Schedule.  The (j, k) plane is cut into tiles of TJ x TK x-lines; one warp
+// owns a tile, one lane owns an x-line (lane = jj + TJ kk).  At tile level l
+// lane (jj, kk) handles the cell i = l - jj - kk, so the three lower
+// neighbours of that cell were handled one level earlier by the lane itself
+// (i-1, kept in registers), by lane jj-1 and by lane kk-1 (exchanged with
+// warp shuffles).  Only the tile faces j = j0 and k = k0 depend on another
+// warp: the producing warp writes its face values into write-once face
+// buffers whose slots hold a NaN sentinel; the consuming warp polls (bounded)
+// until the value appears and puts the sentinel back, so the buffers are
+// ready for the next sweep without clearing.  A warp only waits for tiles
+// with smaller (J, K), and all warps are co-resident (cooperative launch), so
+// every wait ends.  A wait that runs out of its bound records an error and
+// the sweep finishes with zeros for the missing values.
+//
+// The factor data P is stored in tile order, P[(b*9 + e) * NP + (t*NL + l)*32
+// + lane], so every tile level reads and writes 256 contiguous bytes per
+// block entry; b: 0 D^-1, 1..3 D^-1 A_{c,-x/-y/-z}, 4..6 D^-1 A_{c,+x/+y/+z}.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bo {
+
+constexpr int TJ = 8, TK = 4;          // tile of x-lines per warp
+#ifndef BO_TILE_WARPS
+#define BO_TILE_WARPS 4
+#endif
+constexpr int TILE_WARPS = BO_TILE_WARPS;  // warps (tiles) per CTA
+constexpr unsigned long long SENTINEL_BITS = 0x7FF4DEADBEEF0001ull;  // a NaN no arithmetic yields
+constexpr long long POLL_LIMIT = 1LL << 26;
+#ifndef BO_POLL_SLEEP_NS
+#define BO_POLL_SLEEP_NS 32
+#endif
+constexpr unsigned FULL = 0xffffffffu;
+
+struct TileArgs {
+    Geom g;
+    int NJ, NK, T, NL;
+    size_t NP;
+    int* err;
+};
+
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(double* p, double v) {
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_i(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool is_sentinel(double v) {
+    return (unsigned long long)__double_as_longlong(v) == SENTINEL_BITS;
+}
+
+// Wait for K values of a face slot, return them, and put the sentinel back.
+// The poll backs off exponentially (64 ns doubling to 1 us) so waiting lanes
+// keep the load/store unit free for the warps doing work.
+template <int K>
+__device__ __forceinline__ void take_face(double* slot, double (&out)[K], int* err) {
+    unsigned ns = 64;
+    for (long long s = 0;; ++s) {
+        bool ready = true;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            out[q] = ld_relaxed(slot + q);
+            ready = ready && !is_sentinel(out[q]);
+        }
+        if (ready) break;
+        if (s >= POLL_LIMIT || ((s & 255) == 255 && ld_relaxed_i(err) != 0)) {
+            atomicExch(err, 1);
+#pragma unroll
+            for (int q = 0; q < K; ++q) out[q] = 0.0;
+            return;
+        }
+        if (BO_POLL_SLEEP_NS > 0) {
+            __nanosleep(ns);
+            ns = ns < 1024u ? 2u * ns : 1024u;
+        }
+    }
+    const double sent = __longlong_as_double((long long)SENTINEL_BITS);
+#pragma unroll
+    for (int q = 0; q < K; ++q) st_relaxed(slot + q, sent);
+}
+
+template <int K>
+__device__ __forceinline__ void put_face(double* slot, const double* v) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) st_relaxed(slot + q, v[q]);
+}
+
+__device__ __forceinline__ bool ks_skip_t(const KrylovScalars* ks) {
+    return ks != nullptr && ks->state != KS_RUN;
+}
+
+// 3x3 helpers, row-major e = 3r + s
+__device__ __forceinline__ void mm3t(const double a[9], const double b[9], double c[9]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+            c[3 * r + s] = a[3 * r] * b[s] + a[3 * r + 1] * b[3 + s] + a[3 * r + 2] * b[6 + s];
+}
+__device__ __forceinline__ void inv3t(const double a[9], double o[9]) {
+    double c00 = a[4] * a[8] - a[5] * a[7];
+    double c01 = a[5] * a[6] - a[3] * a[8];
+    double c02 = a[3] * a[7] - a[4] * a[6];
+    double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    double id = 1.0 / det;
+    o[0] = c00 * id;
+    o[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+    o[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+    o[3] = c01 * id;
+    o[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+    o[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+    o[6] = c02 * id;
+    o[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+    o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+}
+__device__ __forceinline__ void ldA(const double* __restrict__ A, int b, int n, int c, double m[9]) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) m[e] = A[(size_t)(b * 9 + e) * n + c];
+}
+// acc -= B v  (B row-major 3x3)
+__device__ __forceinline__ void sub_mv(double acc[3], const double B[9], const double v[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) acc[r] -= B[3 * r] * v[0] + B[3 * r + 1] * v[1] + B[3 * r + 2] * v[2];
+}
+
+__device__ __forceinline__ double zsel(bool keep, double v) { return keep ? v : 0.0; }
+
+struct LaneTile {
+    int t, J, K, jj, kk, j, k;
+    bool valid;
+};
+
+__device__ __forceinline__ bool lane_tile(const TileArgs& a, LaneTile& L) {
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    L.t = blockIdx.x + gridDim.x * warp;   // tiles of one CTA are far apart in (J, K)
+    if (L.t >= a.T) return false;
+    L.J = L.t % a.NJ;
+    L.K = L.t / a.NJ;
+    L.jj = lane % TJ;
+    L.kk = lane / TJ;
+    L.j = L.J * TJ + L.jj;
+    L.k = L.K * TK + L.kk;
+    L.valid = L.j < a.g.ny && L.k < a.g.nz;
+    return true;
+}
+
+// Face slots: j-face of tile t for lane row kk at x index i; k-face for jj.
+__device__ __forceinline__ size_t jslot(const TileArgs& a, int t, int i, int kk, int K) {
+    return (((size_t)t * a.g.nx + i) * TK + kk) * K;
+}
+__device__ __forceinline__ size_t kslot(const TileArgs& a, int t, int i, int jj, int K) {
+    return (((size_t)t * a.g.nx + i) * TJ + jj) * K;
+}
+
+// ---------------------------------------------------------------------------
+// a7: factorisation.  Lane state: the scaled upper blocks D^-1 A_{c,+x/+y/+z}
+// of its previous cell; the +y and +z ones go to the neighbouring lanes or
+// faces.  Only D, D^-1 and these blocks are on the wavefront's critical path
+// (branch-free FP64, missing neighbours through zero blocks of A); the scaled
+// lower blocks follow in k_factor_lower with full warps.
+// ---------------------------------------------------------------------------
+// D -= B U, as FMA chains
+__device__ __forceinline__ void fnma_mm(double D[9], const double B[9], const double U[9]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            double v = D[3 * r + s];
+            v = fma(-B[3 * r], U[s], v);
+            v = fma(-B[3 * r + 1], U[3 + s], v);
+            v = fma(-B[3 * r + 2], U[6 + s], v);
+            D[3 * r + s] = v;
+        }
+}
+
+__global__ void __launch_bounds__(32 * TILE_WARPS)
+k_factor_tiled(TileArgs a, const double* __restrict__ A, double* __restrict__ P,
+               double* __restrict__ fJ, double* __restrict__ fK, int* __restrict__ bad) {
+    LaneTile L;
+    if (!lane_tile(a, L)) return;
+    const int n = a.g.n, nx = a.g.nx;
+    const int lane = threadIdx.x & 31;
+    const bool feedJ = L.jj == TJ - 1 && L.J + 1 < a.NJ;
+    const bool feedK = L.kk == TK - 1 && L.K + 1 < a.NK;
+    const bool hasJ = L.j > 0, hasK = L.k > 0;
+    double Ux[9], Uy[9], Uz[9];   // this lane's scaled upper blocks of its last cell
+#pragma unroll
+    for (int e = 0; e < 9; ++e) Ux[e] = Uy[e] = Uz[e] = 0.0;
+    for (int l = 0; l < a.NL; ++l) {
+        const int i = l - L.jj - L.kk;
+        const bool act = L.valid && i >= 0 && i < nx;
+        double Uyn[9], Uzn[9];   // neighbours' upper blocks pointing at this cell
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            Uyn[e] = zsel(hasJ, __shfl_up_sync(FULL, Uy[e], 1));
+            Uzn[e] = zsel(hasK, __shfl_up_sync(FULL, Uz[e], TJ));
+        }
+        const int c = act ? i + nx * (L.j + a.g.ny * L.k) : 0;
+        if (act && hasJ && L.jj == 0) take_face<9>(fJ + jslot(a, L.t - 1, i, L.kk, 9), Uyn, a.err);
+        if (act && hasK && L.kk == 0) take_face<9>(fK + kslot(a, L.t - a.NJ, i, L.jj, 9), Uzn, a.err);
+        double D[9], Bx[9], By[9], Bz[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            D[e] = act ? A[(size_t)(NB_DIAG * 9 + e) * n + c] : (e % 4 == 0 ? 1.0 : 0.0);
+            Bx[e] = act ? A[(size_t)(NB_MX * 9 + e) * n + c] : 0.0;
+            By[e] = act ? A[(size_t)(NB_MY * 9 + e) * n + c] : 0.0;
+            Bz[e] = act ? A[(size_t)(NB_MZ * 9 + e) * n + c] : 0.0;
+        }
+        __syncwarp();
+        fnma_mm(D, Bx, Ux);
+        fnma_mm(D, By, Uyn);
+        fnma_mm(D, Bz, Uzn);
+        double Di[9];
+        inv3t(D, Di);
+        // scaled upper blocks: the data the next cells wait for
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            Bx[e] = act ? A[(size_t)(NB_PX * 9 + e) * n + c] : 0.0;
+            By[e] = act ? A[(size_t)(NB_PY * 9 + e) * n + c] : 0.0;
+            Bz[e] = act ? A[(size_t)(NB_PZ * 9 + e) * n + c] : 0.0;
+        }
+        double Ux2[9], Uy2[9], Uz2[9];
+        mm3t(Di, Bx, Ux2);
+        mm3t(Di, By, Uy2);
+        mm3t(Di, Bz, Uz2);
+        if (act) {
+            const size_t idx = ((size_t)L.t * a.NL + l) * 32 + lane;
+#pragma unroll
+            for (int e = 0; e < 9; ++e) {
+                Ux[e] = Ux2[e];
+                Uy[e] = Uy2[e];
+                Uz[e] = Uz2[e];
+            }
+            if (feedJ) put_face<9>(fJ + jslot(a, L.t, i, L.kk, 9), Uy);
+            if (feedK) put_face<9>(fK + kslot(a, L.t, i, L.jj, 9), Uz);
+            bool finite = true;
+#pragma unroll
+            for (int e = 0; e < 9; ++e) {
+                finite = finite && isfinite(Di[e]);
+                P[(size_t)e * a.NP + idx] = Di[e];
+                P[(size_t)(36 + e) * a.NP + idx] = Ux[e];
+                P[(size_t)(45 + e) * a.NP + idx] = Uy[e];
+                P[(size_t)(54 + e) * a.NP + idx] = Uz[e];
+            }
+            if (!finite) atomicAdd(bad, 1);
+        }
+    }
+}
+
+// Scaled lower blocks D_c^-1 A_{c,-x/-y/-z} for every tile-order slot (one
+// thread per slot, full warps; zero for idle slots and missing neighbours).
+__global__ void __launch_bounds__(256)
+k_factor_lower(TileArgs a, const double* __restrict__ A, double* __restrict__ P) {
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < a.NP;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int lane = (int)(idx & 31);
+        const size_t tl = idx >> 5;
+        const int t = (int)(tl / a.NL), l = (int)(tl % a.NL);
+        const int J = t % a.NJ, K = t / a.NJ, jj = lane % TJ, kk = lane / TJ;
+        const int j = J * TJ + jj, k = K * TK + kk, i = l - jj - kk;
+        const bool act = j < a.g.ny && k < a.g.nz && i >= 0 && i < a.g.nx;
+        const int c = act ? i + a.g.nx * (j + a.g.ny * k) : 0;
+        double Di[9], B[9], S[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) Di[e] = act ? P[(size_t)e * a.NP + idx] : 0.0;
+        const int lowb[3] = {NB_MX, NB_MY, NB_MZ};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) B[e] = act ? A[(size_t)(lowb[d] * 9 + e) * a.g.n + c] : 0.0;
+            mm3t(Di, B, S);
+#pragma unroll
+            for (int e = 0; e < 9; ++e) P[(size_t)((1 + d) * 9 + e) * a.NP + idx] = S[e];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a8: forward sweep y = (L_A + D)^-1 r.  The loads of the next tile level (36
+// factor entries and r) are issued before the current level waits and
+// computes, so their latency overlaps the dependent FP64 chain.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool tile_cell(const TileArgs& a, const LaneTile& L, int l, int& c,
+                                          size_t& idx) {
+    int i = l - L.jj - L.kk;
+    if (!L.valid || i < 0 || i >= a.g.nx) return false;
+    c = i + a.g.nx * (L.j + a.g.ny * L.k);
+    idx = ((size_t)L.t * a.NL + l) * 32 + (threadIdx.x & 31);
+    return true;
+}
+
+template <int NB, int B0>
+__device__ __forceinline__ void ld_P(const TileArgs& a, const double* __restrict__ P, size_t idx,
+                                     double (&out)[NB * 9]) {
+#pragma unroll
+    for (int q = 0; q < NB * 9; ++q) out[q] = P[(size_t)(B0 * 9 + q) * a.NP + idx];
+}
+
+// The FP64 part of every tile level is written without branches: on GB300 an
+// FP64 warp instruction occupies its sub-partition for about 64 cycles
+// however many lanes are active, so a divergent FP64 section would cost its
+// instructions once per lane group.  Missing neighbours contribute through
+// zero blocks (stored as zeros by the factorisation) and zeroed values.
+
+// acc_r += sum_s (-B[r][s]) v[s] as one fused multiply-add chain per row
+__device__ __forceinline__ void fnma_mv(double acc[3], const double* B, const double v[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        acc[r] = fma(-B[3 * r], v[0], acc[r]);
+        acc[r] = fma(-B[3 * r + 1], v[1], acc[r]);
+        acc[r] = fma(-B[3 * r + 2], v[2], acc[r]);
+    }
+}
+
+__global__ void __launch_bounds__(32 * TILE_WARPS)
+k_fwd_tiled(TileArgs a, const double* __restrict__ P, const double* __restrict__ r,
+            double* __restrict__ y, double* __restrict__ fJ, double* __restrict__ fK,
+            const KrylovScalars* __restrict__ ks) {
+    if (ks_skip_t(ks)) return;
+    LaneTile L;
+    if (!lane_tile(a, L)) return;
+    const int n = a.g.n;
+    const bool feedJ = L.jj == TJ - 1 && L.J + 1 < a.NJ;
+    const bool feedK = L.kk == TK - 1 && L.K + 1 < a.NK;
+    const bool hasJ = L.j > 0, hasK = L.k > 0;
+    double yp[3] = {0.0, 0.0, 0.0};
+    double Pc[36], rc[3];
+    int cc = 0;
+    size_t ic = 0;
+    bool actc = tile_cell(a, L, 0, cc, ic);
+    if (actc) {
+        ld_P<4, 0>(a, P, ic, Pc);
+        rc[0] = r[cc]; rc[1] = r[n + cc]; rc[2] = r[2 * n + cc];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 36; ++q) Pc[q] = 0.0;
+        rc[0] = rc[1] = rc[2] = 0.0;
+    }
+    for (int l = 0; l < a.NL; ++l) {
+        // prefetch the next level (zeros for an idle lane)
+        double Pn[36], rn[3];
+        int cn = 0;
+        size_t in = 0;
+        const bool actn = (l + 1 < a.NL) && tile_cell(a, L, l + 1, cn, in);
+        if (actn) {
+            ld_P<4, 0>(a, P, in, Pn);
+            rn[0] = r[cn]; rn[1] = r[n + cn]; rn[2] = r[2 * n + cn];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 36; ++q) Pn[q] = 0.0;
+            rn[0] = rn[1] = rn[2] = 0.0;
+        }
+        double yj[3], yk[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            yj[e] = zsel(hasJ, __shfl_up_sync(FULL, yp[e], 1));
+            yk[e] = zsel(hasK, __shfl_up_sync(FULL, yp[e], TJ));
+        }
+        const int i = l - L.jj - L.kk;
+        if (actc && hasJ && L.jj == 0) take_face<3>(fJ + jslot(a, L.t - 1, i, L.kk, 3), yj, a.err);
+        if (actc && hasK && L.kk == 0) take_face<3>(fK + kslot(a, L.t - a.NJ, i, L.jj, 3), yk, a.err);
+        __syncwarp();
+        // y = D^-1 r - L_x y_{i-1} - L_y y_{j-1} - L_z y_{k-1}
+        double acc[3];
+#pragma unroll
+        for (int row = 0; row < 3; ++row) {
+            acc[row] = Pc[3 * row] * rc[0];
+            acc[row] = fma(Pc[3 * row + 1], rc[1], acc[row]);
+            acc[row] = fma(Pc[3 * row + 2], rc[2], acc[row]);
+        }
+        fnma_mv(acc, Pc + 9, yp);
+        fnma_mv(acc, Pc + 18, yj);
+        fnma_mv(acc, Pc + 27, yk);
+        if (actc) {
+            y[cc] = acc[0];
+            y[n + cc] = acc[1];
+            y[2 * n + cc] = acc[2];
+            if (feedJ) put_face<3>(fJ + jslot(a, L.t, i, L.kk, 3), acc);
+            if (feedK) put_face<3>(fK + kslot(a, L.t, i, L.jj, 3), acc);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) yp[e] = acc[e];
+        }
+#pragma unroll
+        for (int q = 0; q < 36; ++q) Pc[q] = Pn[q];
+        rc[0] = rn[0]; rc[1] = rn[1]; rc[2] = rn[2];
+        cc = cn;
+        actc = actn;
+    }
+    (void)ic;
+}
+
+// ---------------------------------------------------------------------------
+// a8: backward sweep in place, z = (I + D^-1 U_A)^-1 y; levels run downward,
+// with the same next-level prefetch and branch-free FP64 section.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32 * TILE_WARPS)
+k_bwd_tiled(TileArgs a, const double* __restrict__ P, double* __restrict__ z,
+            double* __restrict__ fJ, double* __restrict__ fK,
+            const KrylovScalars* __restrict__ ks) {
+    if (ks_skip_t(ks)) return;
+    LaneTile L;
+    if (!lane_tile(a, L)) return;
+    const int n = a.g.n;
+    const bool feedJ = L.jj == 0 && L.J > 0;
+    const bool feedK = L.kk == 0 && L.K > 0;
+    const bool hasJ = L.j + 1 < a.g.ny, hasK = L.k + 1 < a.g.nz;
+    double zp[3] = {0.0, 0.0, 0.0};
+    double Pc[27], zc[3];
+    int cc = 0;
+    size_t ic = 0;
+    bool actc = tile_cell(a, L, a.NL - 1, cc, ic);
+    if (actc) {
+        ld_P<3, 4>(a, P, ic, Pc);
+        zc[0] = z[cc]; zc[1] = z[n + cc]; zc[2] = z[2 * n + cc];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) Pc[q] = 0.0;
+        zc[0] = zc[1] = zc[2] = 0.0;
+    }
+    for (int l = a.NL - 1; l >= 0; --l) {
+        double Pn[27], zn[3];
+        int cn = 0;
+        size_t in = 0;
+        const bool actn = (l > 0) && tile_cell(a, L, l - 1, cn, in);
+        if (actn) {
+            ld_P<3, 4>(a, P, in, Pn);
+            zn[0] = z[cn]; zn[1] = z[n + cn]; zn[2] = z[2 * n + cn];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) Pn[q] = 0.0;
+            zn[0] = zn[1] = zn[2] = 0.0;
+        }
+        double zj[3], zk[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            zj[e] = zsel(hasJ, __shfl_down_sync(FULL, zp[e], 1));
+            zk[e] = zsel(hasK, __shfl_down_sync(FULL, zp[e], TJ));
+        }
+        const int i = l - L.jj - L.kk;
+        if (actc && hasJ && L.jj == TJ - 1) take_face<3>(fJ + jslot(a, L.t + 1, i, L.kk, 3), zj, a.err);
+        if (actc && hasK && L.kk == TK - 1) take_face<3>(fK + kslot(a, L.t + a.NJ, i, L.jj, 3), zk, a.err);
+        __syncwarp();
+        double acc[3] = {zc[0], zc[1], zc[2]};
+        fnma_mv(acc, Pc, zp);
+        fnma_mv(acc, Pc + 9, zj);
+        fnma_mv(acc, Pc + 18, zk);
+        if (actc) {
+            z[cc] = acc[0];
+            z[n + cc] = acc[1];
+            z[2 * n + cc] = acc[2];
+            if (feedJ) put_face<3>(fJ + jslot(a, L.t, i, L.kk, 3), acc);
+            if (feedK) put_face<3>(fK + kslot(a, L.t, i, L.jj, 3), acc);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) zp[e] = acc[e];
+        }
+#pragma unroll
+        for (int q = 0; q < 27; ++q) Pc[q] = Pn[q];
+        zc[0] = zn[0]; zc[1] = zn[1]; zc[2] = zn[2];
+        cc = cn;
+        actc = actn;
+    }
+    (void)ic;
+}
+
+__global__ void k_fill_sentinel(double* __restrict__ p, size_t count) {
+    const double sent = __longlong_as_double((long long)SENTINEL_BITS);
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < count;
+         q += (size_t)gridDim.x * blockDim.x)
+        p[q] = sent;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static TileArgs tile_args(bo_sim* s) {
+    TileArgs a;
+    a.g = s->geo;
+    a.NJ = (s->geo.ny + TJ - 1) / TJ;
+    a.NK = (s->geo.nz + TK - 1) / TK;
+    a.T = a.NJ * a.NK;
+    a.NL = s->geo.nx + TJ + TK - 2;
+    a.NP = (size_t)a.T * a.NL * 32;
+    a.err = s->d_sweep_sync + 2;
+    return a;
+}
+
+size_t ilu_storage(const bo_sim* s) {
+    int NJ = (s->geo.ny + TJ - 1) / TJ, NK = (s->geo.nz + TK - 1) / TK;
+    return (size_t)NJ * NK * (s->geo.nx + TJ + TK - 2) * 32;
+}
+
+// face buffers: factor j/k faces (9 values per slot), sweep j/k faces (3)
+size_t face_storage(const bo_sim* s) {
+    int NJ = (s->geo.ny + TJ - 1) / TJ, NK = (s->geo.nz + TK - 1) / TK;
+    size_t T = (size_t)NJ * NK;
+    return T * s->geo.nx * (TK * 9 + TJ * 9 + TK * 3 + TJ * 3);
+}
+
+static double* faceJ9(bo_sim* s) { return s->d_face; }
+static double* faceK9(bo_sim* s) {
+    TileArgs a = tile_args(s);
+    return s->d_face + (size_t)a.T * s->geo.nx * TK * 9;
+}
+static double* faceJ3(bo_sim* s) {
+    TileArgs a = tile_args(s);
+    return faceK9(s) + (size_t)a.T * s->geo.nx * TJ * 9;
+}
+static double* faceK3(bo_sim* s) {
+    TileArgs a = tile_args(s);
+    return faceJ3(s) + (size_t)a.T * s->geo.nx * TK * 3;
+}
+
+template <class... Args>
+static void launch_coop(cudaStream_t st, int grid, int block, void (*kern)(Args...), Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BO_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+}
+
+static int tile_grid(bo_sim* s) {
+    TileArgs a = tile_args(s);
+    return (a.T + TILE_WARPS - 1) / TILE_WARPS;
+}
+
+void setup_sweeps(bo_sim* s) {
+    size_t fc = face_storage(s);
+    k_fill_sentinel<<<1024, 256>>>(s->d_face, fc);
+    BO_LAUNCH_CHECK("k_fill_sentinel");
+    BO_CUDA(cudaMemset(s->d_sweep_sync, 0, sizeof(int) * 4));
+    BO_CUDA(cudaDeviceSynchronize());
+    // every tile warp must be resident at once
+    int dev, sms, per_sm = 0;
+    BO_CUDA(cudaGetDevice(&dev));
+    BO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int lim = 1 << 30;
+    for (const void* k : {(const void*)k_factor_tiled, (const void*)k_fwd_tiled, (const void*)k_bwd_tiled}) {
+        BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * TILE_WARPS, 0));
+        lim = std::min(lim, per_sm);
+    }
+    if ((long long)lim * sms < tile_grid(s))
+        fail(BO_ERR_INVALID_ARG, "grid too large for one co-resident wavefront sweep");
+}
+
+void enqueue_factor(bo_sim* s, cudaStream_t st, int* bad) {
+    TileArgs a = tile_args(s);
+    launch_coop(st, tile_grid(s), 32 * TILE_WARPS, k_factor_tiled, a, (const double*)s->d_A,
+                s->d_P, faceJ9(s), faceK9(s), bad);
+    k_factor_lower<<<152 * 8, 256, 0, st>>>(a, (const double*)s->d_A, s->d_P);
+}
+
+void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y, const KrylovScalars* ks) {
+    TileArgs a = tile_args(s);
+    launch_coop(st, tile_grid(s), 32 * TILE_WARPS, k_fwd_tiled, a, (const double*)s->d_P, r, y,
+                faceJ3(s), faceK3(s), ks);
+}
+
+void enqueue_bwd(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks) {
+    TileArgs a = tile_args(s);
+    launch_coop(st, tile_grid(s), 32 * TILE_WARPS, k_bwd_tiled, a, (const double*)s->d_P, z,
+                faceJ3(s), faceK3(s), ks);
+}
+
+int sweep_timeout(bo_sim* s) {
+    int v = 0;
+    BO_CUDA(cudaMemcpyAsync(&v, s->d_sweep_sync + 2, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+    return v;
+}
+
+// D^-1 of every cell in natural order, [n][9].
+void export_dinv(bo_sim* s, double* dinv) {
+    TileArgs a = tile_args(s);
+    std::vector<double> P(9 * a.NP);
+    for (int e = 0; e < 9; ++e)
+        BO_CUDA(cudaMemcpy(P.data() + e * a.NP, s->d_P + e * a.NP, sizeof(double) * a.NP,
+                           cudaMemcpyDeviceToHost));
+    const Geom& g = s->geo;
+    for (int k = 0; k < g.nz; ++k)
+        for (int j = 0; j < g.ny; ++j)
+            for (int i = 0; i < g.nx; ++i) {
+                int J = j / TJ, K = k / TK, jj = j % TJ, kk = k % TK;
+                int t = J + a.NJ * K;
+                int l = i + jj + kk;
+                size_t idx = ((size_t)t * a.NL + l) * 32 + jj + TJ * kk;
+                int c = i + g.nx * (j + g.ny * k);
+                for (int e = 0; e < 9; ++e) dinv[9 * (size_t)c + e] = P[e * a.NP + idx];
+            }
+}
+
+}  // namespace bo

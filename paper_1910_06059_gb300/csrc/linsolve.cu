@@ -31,70 +31,6 @@ namespace bo {
 constexpr int VEC_BS = 256;
 constexpr int VEC_GRID = 152 * 4;   // one wave of 4 blocks per SM
 
-// ---------------------------------------------------------------------------
-// Wavefront levels: cells sorted by L = i + j + k, then k, then j.
-// ---------------------------------------------------------------------------
-void build_levels(bo_sim* s) {
-    const Geom& g = s->geo;
-    s->nlev = g.nx + g.ny + g.nz - 2;
-    std::vector<int> cnt(s->nlev + 1, 0);
-    for (int k = 0; k < g.nz; ++k)
-        for (int j = 0; j < g.ny; ++j)
-            for (int i = 0; i < g.nx; ++i) cnt[i + j + k + 1]++;
-    for (int L = 0; L < s->nlev; ++L) cnt[L + 1] += cnt[L];
-    s->lvl_ptr = cnt;
-    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-    std::vector<int> perm(g.n), iperm(g.n);
-    for (int L = 0; L < s->nlev; ++L) {
-        // enumerate (k, j) ascending with i = L - j - k in range
-        for (int k = 0; k < g.nz; ++k)
-            for (int j = 0; j < g.ny; ++j) {
-                int i = L - j - k;
-                if (i < 0 || i >= g.nx) continue;
-                int c = i + g.nx * (j + g.ny * k);
-                perm[pos[L]] = c;
-                iperm[c] = pos[L];
-                pos[L]++;
-            }
-    }
-    BO_CUDA(cudaMemcpy(s->d_perm_lvl, perm.data(), sizeof(int) * g.n, cudaMemcpyHostToDevice));
-    BO_CUDA(cudaMemcpy(s->d_perm_lvl + g.n, iperm.data(), sizeof(int) * g.n,
-                       cudaMemcpyHostToDevice));
-}
-
-// ---------------------------------------------------------------------------
-// 3x3 block helpers (row-major, e = 3r + s)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void ld_blk_nat(const double* __restrict__ A, int b, int n, int c,
-                                           double m[9]) {
-#pragma unroll
-    for (int e = 0; e < 9; ++e) m[e] = A[(size_t)(b * 9 + e) * n + c];
-}
-__device__ __forceinline__ void mm3(const double a[9], const double b[9], double c[9]) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int s = 0; s < 3; ++s)
-            c[3 * r + s] = a[3 * r] * b[s] + a[3 * r + 1] * b[3 + s] + a[3 * r + 2] * b[6 + s];
-}
-// Inverse by the adjugate.
-__device__ __forceinline__ void inv3(const double a[9], double o[9]) {
-    double c00 = a[4] * a[8] - a[5] * a[7];
-    double c01 = a[5] * a[6] - a[3] * a[8];
-    double c02 = a[3] * a[7] - a[4] * a[6];
-    double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-    double id = 1.0 / det;
-    o[0] = c00 * id;
-    o[1] = (a[2] * a[7] - a[1] * a[8]) * id;
-    o[2] = (a[1] * a[5] - a[2] * a[4]) * id;
-    o[3] = c01 * id;
-    o[4] = (a[0] * a[8] - a[2] * a[6]) * id;
-    o[5] = (a[2] * a[3] - a[0] * a[5]) * id;
-    o[6] = c02 * id;
-    o[7] = (a[1] * a[6] - a[0] * a[7]) * id;
-    o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
-}
-
 __device__ __forceinline__ void cell_ijk(const Geom& g, int c, int& i, int& j, int& k) {
     i = c % g.nx;
     j = (c / g.nx) % g.ny;
@@ -103,249 +39,6 @@ __device__ __forceinline__ void cell_ijk(const Geom& g, int c, int& i, int& j, i
 
 __device__ __forceinline__ bool ks_skip(const KrylovScalars* ks) {
     return ks != nullptr && ks->state != KS_RUN;
-}
-
-// ---------------------------------------------------------------------------
-// Dataflow sweeps.  One persistent, co-resident grid walks the cells in
-// wavefront order (each thread takes cells m = t, t + T, t + 2T, ... of the
-// level-sorted order, T threads in all), so every cell a thread waits for
-// sits earlier in that order and is owned by a running thread: the wait
-// always ends.  A cell waits only for its three neighbours on the previous
-// level, through per-cell ready flags: the producer stores its result and
-// then releases flag[c] = seq (st.release.gpu); the consumer acquires the
-// flag (ld.acquire.gpu) and reads the neighbour's values from L2
-// (ld.global.cg), never from a possibly stale L1 line.  seq is the sweep
-// number: read from sync[0] at kernel entry, advanced by the last block to
-// finish, so flags never need clearing.  Every wait is bounded; on timeout
-// the kernel records sync[2] = 1 and returns instead of hanging.
-// ---------------------------------------------------------------------------
-struct SweepArgs {
-    Geom g;
-    const int* perm;   // m -> c
-    const int* iperm;  // c -> m
-    int* flag;         // per cell (natural index)
-    int* sync;         // [0] sweep epoch, [1] finished blocks, [2] timeout
-};
-
-constexpr int SWP_BS = 128;
-constexpr long long SPIN_LIMIT = 1LL << 24;
-
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_gpu(int* p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Wait until *f == seq.  Returns false (and records the timeout) when the
-// bounded wait runs out or another thread has already timed out.
-__device__ __noinline__ bool wait_ready(const int* f, int seq, int* sync) {
-    if (ld_acquire_gpu(f) == seq) return true;
-    for (long long s = 1; s <= SPIN_LIMIT; ++s) {
-        __nanosleep(64);
-        if (ld_acquire_gpu(f) == seq) return true;
-        if ((s & 1023) == 0 && ld_acquire_gpu(sync + 2) != 0) return false;
-    }
-    atomicExch(sync + 2, 1);
-    return false;
-}
-
-__device__ __forceinline__ int sweep_begin(const int* sync) { return ld_acquire_gpu(sync) + 1; }
-
-__device__ __forceinline__ void sweep_end(int* sync) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        int done = atomicAdd(sync + 1, 1);
-        if (done == (int)gridDim.x - 1) {  // last block out: reset, advance the epoch
-            sync[1] = 0;
-            __threadfence();
-            atomicAdd(sync, 1);
-        }
-    }
-}
-
-__device__ __forceinline__ void ldcg3(const double* v, int n, int c, double out[3]) {
-    out[0] = __ldcg(v + c);
-    out[1] = __ldcg(v + n + c);
-    out[2] = __ldcg(v + 2 * n + c);
-}
-
-// ---------------------------------------------------------------------------
-// a7: ILU(0) factorisation.  A cell needs the scaled upper blocks
-// D_k^-1 A_kc of its lower neighbours; it publishes its own scaled upper
-// blocks first (the only data others wait for), then D^-1 and the scaled
-// lower blocks.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SWP_BS)
-k_factor_sweep(SweepArgs a, const double* __restrict__ A, double* __restrict__ P,
-               int* __restrict__ bad) {
-    const int seq = sweep_begin(a.sync);
-    const int n = a.g.n;
-    const int lowb[3] = {NB_MX, NB_MY, NB_MZ};
-    const int uppb[3] = {NB_PX, NB_PY, NB_PZ};
-    bool alive = true;
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; alive && m < n; m += gridDim.x * blockDim.x) {
-        int c = a.perm[m];
-        int i, j, k;
-        cell_ijk(a.g, c, i, j, k);
-        const bool has_lo[3] = {i > 0, j > 0, k > 0};
-        const bool has_up[3] = {i + 1 < a.g.nx, j + 1 < a.g.ny, k + 1 < a.g.nz};
-        const int lo_nb[3] = {c - 1, c - a.g.nx, c - a.g.nx * a.g.ny};
-        double D[9];
-        ld_blk_nat(A, NB_DIAG, n, c, D);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (!has_lo[d]) continue;
-            double Ack[9], Ukc[9], prod[9];
-            ld_blk_nat(A, lowb[d], n, c, Ack);
-            int nb = lo_nb[d];
-            if (!wait_ready(a.flag + nb, seq, a.sync)) {
-                alive = false;
-                break;
-            }
-            int mk = a.iperm[nb];
-#pragma unroll
-            for (int e = 0; e < 9; ++e) Ukc[e] = __ldcg(P + (size_t)((4 + d) * 9 + e) * n + mk);
-            mm3(Ack, Ukc, prod);
-#pragma unroll
-            for (int e = 0; e < 9; ++e) D[e] -= prod[e];
-        }
-        if (!alive) break;
-        double Di[9];
-        inv3(D, Di);
-        double blk[9], sc[9];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (has_up[d]) {
-                ld_blk_nat(A, uppb[d], n, c, blk);
-                mm3(Di, blk, sc);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 9; ++e) sc[e] = 0.0;
-            }
-#pragma unroll
-            for (int e = 0; e < 9; ++e) P[(size_t)((4 + d) * 9 + e) * n + m] = sc[e];
-        }
-        st_release_gpu(a.flag + c, seq);
-        bool finite = true;
-#pragma unroll
-        for (int e = 0; e < 9; ++e) {
-            finite = finite && isfinite(Di[e]);
-            P[(size_t)e * n + m] = Di[e];
-        }
-        if (!finite) atomicAdd(bad, 1);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (has_lo[d]) {
-                ld_blk_nat(A, lowb[d], n, c, blk);
-                mm3(Di, blk, sc);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 9; ++e) sc[e] = 0.0;
-            }
-#pragma unroll
-            for (int e = 0; e < 9; ++e) P[(size_t)((1 + d) * 9 + e) * n + m] = sc[e];
-        }
-    }
-    sweep_end(a.sync);
-}
-
-// ---------------------------------------------------------------------------
-// a8: forward sweep y = (L_A + D)^-1 r, i.e. y_c = D_c^-1 r_c - sum_lower
-// (D_c^-1 A_ck) y_k.  The matrix blocks and D^-1 r are loaded and formed
-// before the wait; only the three neighbour products follow it.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SWP_BS)
-k_fwd_sweep(SweepArgs a, const double* __restrict__ P, const double* __restrict__ r,
-            double* __restrict__ y, const KrylovScalars* __restrict__ ks) {
-    if (ks_skip(ks)) return;
-    const int seq = sweep_begin(a.sync);
-    const int n = a.g.n;
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
-        int c = a.perm[m];
-        int i, j, k;
-        cell_ijk(a.g, c, i, j, k);
-        double rv[3] = {r[c], r[n + c], r[2 * n + c]};
-        double acc[3];
-#pragma unroll
-        for (int row = 0; row < 3; ++row)
-            acc[row] = P[(size_t)(3 * row) * n + m] * rv[0] + P[(size_t)(3 * row + 1) * n + m] * rv[1] +
-                       P[(size_t)(3 * row + 2) * n + m] * rv[2];
-        const bool has_lo[3] = {i > 0, j > 0, k > 0};
-        const int lo_nb[3] = {c - 1, c - a.g.nx, c - a.g.nx * a.g.ny};
-        double Lb[3][9];
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int e = 0; e < 9; ++e)
-                Lb[d][e] = has_lo[d] ? P[(size_t)((1 + d) * 9 + e) * n + m] : 0.0;
-        bool ok = true;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (!has_lo[d]) continue;
-            int q = lo_nb[d];
-            ok = ok && wait_ready(a.flag + q, seq, a.sync);
-            double yv[3];
-            ldcg3(y, n, q, yv);
-#pragma unroll
-            for (int row = 0; row < 3; ++row)
-                acc[row] -= Lb[d][3 * row] * yv[0] + Lb[d][3 * row + 1] * yv[1] + Lb[d][3 * row + 2] * yv[2];
-        }
-        if (!ok) break;
-        y[c] = acc[0];
-        y[n + c] = acc[1];
-        y[2 * n + c] = acc[2];
-        st_release_gpu(a.flag + c, seq);
-    }
-    sweep_end(a.sync);
-}
-
-// backward sweep in place: z_c = y_c - sum_upper (D_c^-1 A_cj) z_j
-__global__ void __launch_bounds__(SWP_BS)
-k_bwd_sweep(SweepArgs a, const double* __restrict__ P, double* __restrict__ z,
-            const KrylovScalars* __restrict__ ks) {
-    if (ks_skip(ks)) return;
-    const int seq = sweep_begin(a.sync);
-    const int n = a.g.n;
-    const int T = gridDim.x * blockDim.x;
-    // walk the wavefront order backwards: thread t takes m = n-1-t, n-1-t-T, ...
-    for (int mm = blockIdx.x * blockDim.x + threadIdx.x; mm < n; mm += T) {
-        int m = n - 1 - mm;
-        int c = a.perm[m];
-        int i, j, k;
-        cell_ijk(a.g, c, i, j, k);
-        double acc[3];
-        ldcg3(z, n, c, acc);
-        const bool has_up[3] = {i + 1 < a.g.nx, j + 1 < a.g.ny, k + 1 < a.g.nz};
-        const int up_nb[3] = {c + 1, c + a.g.nx, c + a.g.nx * a.g.ny};
-        double Ub[3][9];
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int e = 0; e < 9; ++e)
-                Ub[d][e] = has_up[d] ? P[(size_t)((4 + d) * 9 + e) * n + m] : 0.0;
-        bool ok = true;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (!has_up[d]) continue;
-            int q = up_nb[d];
-            ok = ok && wait_ready(a.flag + q, seq, a.sync);
-            double zv[3];
-            ldcg3(z, n, q, zv);
-#pragma unroll
-            for (int row = 0; row < 3; ++row)
-                acc[row] -= Ub[d][3 * row] * zv[0] + Ub[d][3 * row + 1] * zv[1] + Ub[d][3 * row + 2] * zv[2];
-        }
-        if (!ok) break;
-        z[c] = acc[0];
-        z[n + c] = acc[1];
-        z[2 * n + c] = acc[2];
-        st_release_gpu(a.flag + c, seq);
-    }
-    sweep_end(a.sync);
 }
 
 // ---------------------------------------------------------------------------
@@ -718,62 +411,7 @@ __global__ void k_well_recover(int n, WellDev* __restrict__ wells,
 // ---------------------------------------------------------------------------
 static inline int blocks_for(int n, int bs) { return (n + bs - 1) / bs; }
 
-static SweepArgs sweep_args(bo_sim* s) {
-    SweepArgs a;
-    a.g = s->geo;
-    a.perm = s->d_perm_lvl;
-    a.iperm = s->d_perm_lvl + s->geo.n;
-    a.flag = s->d_flag_sweep;
-    a.sync = s->d_sweep_sync;
-    return a;
-}
-
 static int* factor_bad(bo_sim* s) { return reinterpret_cast<int*>(&s->d_ns->pad); }
-
-// Co-resident grid for the dataflow sweeps: a cooperative launch, which fails
-// with an error instead of starting a grid that cannot be resident at once.
-template <class... Args>
-static void launch_coop(bo_sim* s, cudaStream_t st, void (*kern)(Args...), Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(s->sweep_grid);
-    cfg.blockDim = dim3(SWP_BS);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    BO_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
-}
-
-void setup_sweeps(bo_sim* s) {
-    int dev, sms, per_sm = 0;
-    BO_CUDA(cudaGetDevice(&dev));
-    BO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int lim = 1 << 30;
-    for (const void* k : {(const void*)k_factor_sweep, (const void*)k_fwd_sweep, (const void*)k_bwd_sweep}) {
-        BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, SWP_BS, 0));
-        lim = std::min(lim, per_sm);
-    }
-    int want = std::max(1, std::min(lim, s->sweep_blocks_per_sm));
-    s->sweep_grid = want * sms;
-    BO_CUDA(cudaMemset(s->d_flag_sweep, 0, sizeof(int) * (size_t)s->geo.n));
-    BO_CUDA(cudaMemset(s->d_sweep_sync, 0, sizeof(int) * 4));
-}
-
-static void enqueue_factor(bo_sim* s, cudaStream_t st) {
-    launch_coop(s, st, k_factor_sweep, sweep_args(s), (const double*)s->d_A, s->d_P, factor_bad(s));
-}
-
-static void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y,
-                        const KrylovScalars* ks) {
-    launch_coop(s, st, k_fwd_sweep, sweep_args(s), (const double*)s->d_P, r, y, ks);
-}
-
-static void enqueue_bwd(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks) {
-    launch_coop(s, st, k_bwd_sweep, sweep_args(s), (const double*)s->d_P, z, ks);
-}
 
 static void enqueue_precond(bo_sim* s, cudaStream_t st, const double* r, double* z,
                             const KrylovScalars* ks) {
@@ -916,7 +554,7 @@ static cudaGraphExec_t capture_factor(bo_sim* s) {
     BO_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph;
     BO_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    enqueue_factor(s, cs);
+    enqueue_factor(s, cs, factor_bad(s));
     BO_CUDA(cudaStreamEndCapture(cs, &graph));
     cudaGraphExec_t exec;
     BO_CUDA(cudaGraphInstantiate(&exec, graph, 0));
@@ -947,12 +585,6 @@ static void ensure_timed_graph(bo_sim* s) {
     s->g_iter_timed = capture(s, s->iters_per_graph, s->iter_events.data());
 }
 
-int sweep_timeout(bo_sim* s) {
-    int v = 0;
-    BO_CUDA(cudaMemcpyAsync(&v, s->d_sweep_sync + 2, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    BO_CUDA(cudaStreamSynchronize(s->stream));
-    return v;
-}
 
 void launch_factor(bo_sim* s) {
     int t = timer_id(s, "ilu_factor");

@@ -488,15 +488,17 @@ def test_schur_bicgstab_matches_dense_lu(seed, frac_sat):
 
 def test_newton_converges_fast_near_solution():
     """Near the solution the Newton iteration with exact linear solves
-    converges superlinearly (Eq. linsystem)."""
+    converges quadratically (Eq. linsystem): once the scaled residual is
+    small, each iteration roughly squares it."""
     m = synth.small_model(5, 4, 3, wells="5spot", dz=4.0)
     o = oracle.Oracle(m)
     o.init_hydrostatic()
     o.step(0.5 * synth.DAY)  # settle the wells
+    o.step(0.5 * synth.DAY)
     o.begin_step()
-    dt = 0.5 * synth.DAY
+    dt = 0.05 * synth.DAY
     hist = []
-    for it in range(8):
+    for it in range(12):
         o.assemble(dt)
         nrm = o.norms(dt)
         hist.append(max(nrm[3:6]))
@@ -505,7 +507,7 @@ def test_newton_converges_fast_near_solution():
         st, its, sol = o.solve(tol=1e-14, maxit=300)
         o.newton_update(sol)
     assert hist[-1] < 1e-10, hist
-    assert len(hist) <= 6, hist
-    # superlinear: the last reductions are much faster than geometric
-    k = len(hist) - 1
-    assert hist[k] / hist[k - 1] < 1e-2 * hist[k - 1] / hist[k - 2] or hist[k] < 1e-13, hist
+    # the first iterate below 1e-2 and its successor: quadratic reduction
+    k = next(q for q, v in enumerate(hist) if v < 1e-2)
+    assert k + 1 < len(hist), hist
+    assert hist[k + 1] <= 10 * hist[k] ** 1.8, hist

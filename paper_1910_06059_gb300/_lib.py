@@ -155,7 +155,7 @@ def fluid_struct(fluid: dict) -> BoFluid:
 
 DEFAULT_NEWTON = dict(tol_mb=1e-6, tol_cnv=1e-6, tol_well=1e-6, max_newton=20, tol_lin=1e-3,
                       max_lin=500, max_cuts=8, ds_max=0.2, dp_rel_max=0.3, drs_rel_max=0.2,
-                      eps_switch=1e-6, bp_overshoot=0.05, dt_init=86400.0, cut_factor=0.5)
+                      eps_switch=1e-6, bp_overshoot=0.05, dt_init=864.0, cut_factor=0.5)
 
 
 def newton_opts(**kw) -> BoNewtonOpts:

@@ -333,150 +333,292 @@ __device__ __forceinline__ void fnma_mv(double acc[3], const double* B, const do
     }
 }
 
-__global__ void __launch_bounds__(32 * TILE_WARPS)
+// Sweeps with three warps per tile: warp r computes row r of the 3x3 block
+// products for the tile's 32 lines, so each warp issues a third of the FP64
+// instructions of a tile level and the three warps run on different
+// sub-partitions.  The level's results go through a double-buffered shared
+// array (all three components per line) with one named barrier per level;
+// face values are read by all three warps, so face slots are refilled with
+// the sentinel by k_fill_sentinel after the sweep instead of being reset.
+constexpr int ROW_WARPS = 3;
+constexpr int SWEEP_THREADS = 32 * ROW_WARPS;
+
+struct RowTile {
+    int t, J, K, jj, kk, j, k, row, lane;
+    bool valid;
+};
+
+__device__ __forceinline__ RowTile row_tile(const TileArgs& a) {
+    RowTile R;
+    R.t = blockIdx.x;
+    R.row = threadIdx.x >> 5;
+    R.lane = threadIdx.x & 31;
+    R.J = R.t % a.NJ;
+    R.K = R.t / a.NJ;
+    R.jj = R.lane % TJ;
+    R.kk = R.lane / TJ;
+    R.j = R.J * TJ + R.jj;
+    R.k = R.K * TK + R.kk;
+    R.valid = R.j < a.g.ny && R.k < a.g.nz;
+    return R;
+}
+
+__device__ __forceinline__ bool row_cell(const TileArgs& a, const RowTile& R, int l, int& c,
+                                         size_t& idx) {
+    int i = l - R.jj - R.kk;
+    if (!R.valid || i < 0 || i >= a.g.nx) return false;
+    c = i + a.g.nx * (R.j + a.g.ny * R.k);
+    idx = ((size_t)R.t * a.NL + l) * 32 + R.lane;
+    return true;
+}
+
+__device__ __forceinline__ void named_barrier() {
+    asm volatile("bar.sync 1, %0;" ::"r"(SWEEP_THREADS) : "memory");
+}
+
+// Wait for the three values of a face slot (no reset; see above).
+__device__ __forceinline__ void peek_face(const double* slot, double out[3], int* err) {
+    unsigned ns = 64;
+    for (long long s = 0;; ++s) {
+        bool ready = true;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            out[q] = ld_relaxed(slot + q);
+            ready = ready && !is_sentinel(out[q]);
+        }
+        if (ready) return;
+        if (s >= POLL_LIMIT || ((s & 255) == 255 && ld_relaxed_i(err) != 0)) {
+            atomicExch(err, 1);
+            out[0] = out[1] = out[2] = 0.0;
+            return;
+        }
+        if (BO_POLL_SLEEP_NS > 0) {
+            __nanosleep(ns);
+            ns = ns < 1024u ? 2u * ns : 1024u;
+        }
+    }
+}
+
+// a8: forward sweep y = (L_A + D)^-1 r, row r of
+//     y_c = D_c^-1 r_c - L_x y_{i-1} - L_y y_{j-1} - L_z y_{k-1}.
+__global__ void __launch_bounds__(SWEEP_THREADS)
 k_fwd_tiled(TileArgs a, const double* __restrict__ P, const double* __restrict__ r,
             double* __restrict__ y, double* __restrict__ fJ, double* __restrict__ fK,
             const KrylovScalars* __restrict__ ks) {
     if (ks_skip_t(ks)) return;
-    LaneTile L;
-    if (!lane_tile(a, L)) return;
+    __shared__ double ys[2][32][3];
+    const RowTile R = row_tile(a);
     const int n = a.g.n;
-    const bool feedJ = L.jj == TJ - 1 && L.J + 1 < a.NJ;
-    const bool feedK = L.kk == TK - 1 && L.K + 1 < a.NK;
-    const bool hasJ = L.j > 0, hasK = L.k > 0;
-    double yp[3] = {0.0, 0.0, 0.0};
-    double Pc[36], rc[3];
+    const int rw = R.row;
+    const bool feedJ = R.jj == TJ - 1 && R.J + 1 < a.NJ;
+    const bool feedK = R.kk == TK - 1 && R.K + 1 < a.NK;
+    const bool hasJ = R.j > 0, hasK = R.k > 0;
+    // row rw of D^-1 and of the three scaled lower blocks: P entries b*9 + 3*rw + s
+    double Pc[12], rc[3];
     int cc = 0;
     size_t ic = 0;
-    bool actc = tile_cell(a, L, 0, cc, ic);
-    if (actc) {
-        ld_P<4, 0>(a, P, ic, Pc);
-        rc[0] = r[cc]; rc[1] = r[n + cc]; rc[2] = r[2 * n + cc];
-    } else {
+    bool actc = row_cell(a, R, 0, cc, ic);
 #pragma unroll
-        for (int q = 0; q < 36; ++q) Pc[q] = 0.0;
-        rc[0] = rc[1] = rc[2] = 0.0;
-    }
-    for (int l = 0; l < a.NL; ++l) {
-        // prefetch the next level (zeros for an idle lane)
-        double Pn[36], rn[3];
-        int cn = 0;
-        size_t in = 0;
-        const bool actn = (l + 1 < a.NL) && tile_cell(a, L, l + 1, cn, in);
-        if (actn) {
-            ld_P<4, 0>(a, P, in, Pn);
-            rn[0] = r[cn]; rn[1] = r[n + cn]; rn[2] = r[2 * n + cn];
-        } else {
+    for (int b = 0; b < 4; ++b)
 #pragma unroll
-            for (int q = 0; q < 36; ++q) Pn[q] = 0.0;
-            rn[0] = rn[1] = rn[2] = 0.0;
-        }
-        double yj[3], yk[3];
+        for (int s2 = 0; s2 < 3; ++s2)
+            Pc[3 * b + s2] = actc ? P[(size_t)(b * 9 + 3 * rw + s2) * a.NP + ic] : 0.0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) rc[e] = actc ? r[(size_t)e * n + cc] : 0.0;
+    // face values are loaded one level ahead too; a value still holding the
+    // sentinel is waited for when it is needed
+    const bool takeJ = hasJ && R.jj == 0, takeK = hasK && R.kk == 0;
+    double fjc[3], fkc[3];
+    {
+        const int i0 = 0 - R.jj - R.kk;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-            yj[e] = zsel(hasJ, __shfl_up_sync(FULL, yp[e], 1));
-            yk[e] = zsel(hasK, __shfl_up_sync(FULL, yp[e], TJ));
+            fjc[e] = (actc && takeJ) ? ld_relaxed(fJ + jslot(a, R.t - 1, i0, R.kk, 3) + e) : 0.0;
+            fkc[e] = (actc && takeK) ? ld_relaxed(fK + kslot(a, R.t - a.NJ, i0, R.jj, 3) + e) : 0.0;
         }
-        const int i = l - L.jj - L.kk;
-        if (actc && hasJ && L.jj == 0) take_face<3>(fJ + jslot(a, L.t - 1, i, L.kk, 3), yj, a.err);
-        if (actc && hasK && L.kk == 0) take_face<3>(fK + kslot(a, L.t - a.NJ, i, L.jj, 3), yk, a.err);
+    }
+    ys[1][R.lane][rw] = 0.0;
+    named_barrier();
+    for (int l = 0; l < a.NL; ++l) {
+        const int pb = (l + 1) & 1, cb = l & 1;
+        double Pn[12], rn[3];
+        int cn = 0;
+        size_t in = 0;
+        const bool actn = (l + 1 < a.NL) && row_cell(a, R, l + 1, cn, in);
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int s2 = 0; s2 < 3; ++s2)
+                Pn[3 * b + s2] = actn ? P[(size_t)(b * 9 + 3 * rw + s2) * a.NP + in] : 0.0;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) rn[e] = actn ? r[(size_t)e * n + cn] : 0.0;
+        double fjn[3], fkn[3];
+        {
+            const int i1 = l + 1 - R.jj - R.kk;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                fjn[e] = (actn && takeJ) ? ld_relaxed(fJ + jslot(a, R.t - 1, i1, R.kk, 3) + e) : 0.0;
+                fkn[e] = (actn && takeK) ? ld_relaxed(fK + kslot(a, R.t - a.NJ, i1, R.jj, 3) + e) : 0.0;
+            }
+        }
+        double yp[3], yj[3], yk[3];
+        const int lj = R.jj > 0 ? R.lane - 1 : R.lane;
+        const int lk = R.kk > 0 ? R.lane - TJ : R.lane;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            yp[e] = ys[pb][R.lane][e];
+            yj[e] = zsel(hasJ && R.jj > 0, ys[pb][lj][e]);
+            yk[e] = zsel(hasK && R.kk > 0, ys[pb][lk][e]);
+        }
+        const int i = l - R.jj - R.kk;
+        if (actc && takeJ) {
+            if (is_sentinel(fjc[0]) || is_sentinel(fjc[1]) || is_sentinel(fjc[2]))
+                peek_face(fJ + jslot(a, R.t - 1, i, R.kk, 3), fjc, a.err);
+            yj[0] = fjc[0]; yj[1] = fjc[1]; yj[2] = fjc[2];
+        }
+        if (actc && takeK) {
+            if (is_sentinel(fkc[0]) || is_sentinel(fkc[1]) || is_sentinel(fkc[2]))
+                peek_face(fK + kslot(a, R.t - a.NJ, i, R.jj, 3), fkc, a.err);
+            yk[0] = fkc[0]; yk[1] = fkc[1]; yk[2] = fkc[2];
+        }
         __syncwarp();
-        // y = D^-1 r - L_x y_{i-1} - L_y y_{j-1} - L_z y_{k-1}
-        double acc[3];
-#pragma unroll
-        for (int row = 0; row < 3; ++row) {
-            acc[row] = Pc[3 * row] * rc[0];
-            acc[row] = fma(Pc[3 * row + 1], rc[1], acc[row]);
-            acc[row] = fma(Pc[3 * row + 2], rc[2], acc[row]);
-        }
-        fnma_mv(acc, Pc + 9, yp);
-        fnma_mv(acc, Pc + 18, yj);
-        fnma_mv(acc, Pc + 27, yk);
+        double acc = Pc[0] * rc[0];
+        acc = fma(Pc[1], rc[1], acc);
+        acc = fma(Pc[2], rc[2], acc);
+        double t = -Pc[3] * yp[0];
+        t = fma(-Pc[4], yp[1], t);
+        t = fma(-Pc[5], yp[2], t);
+        t = fma(-Pc[6], yj[0], t);
+        t = fma(-Pc[7], yj[1], t);
+        t = fma(-Pc[8], yj[2], t);
+        double u = -Pc[9] * yk[0];
+        u = fma(-Pc[10], yk[1], u);
+        u = fma(-Pc[11], yk[2], u);
+        acc = acc + (t + u);
+        ys[cb][R.lane][rw] = actc ? acc : 0.0;
         if (actc) {
-            y[cc] = acc[0];
-            y[n + cc] = acc[1];
-            y[2 * n + cc] = acc[2];
-            if (feedJ) put_face<3>(fJ + jslot(a, L.t, i, L.kk, 3), acc);
-            if (feedK) put_face<3>(fK + kslot(a, L.t, i, L.jj, 3), acc);
-#pragma unroll
-            for (int e = 0; e < 3; ++e) yp[e] = acc[e];
+            y[(size_t)rw * n + cc] = acc;
+            if (feedJ) st_relaxed(fJ + jslot(a, R.t, i, R.kk, 3) + rw, acc);
+            if (feedK) st_relaxed(fK + kslot(a, R.t, i, R.jj, 3) + rw, acc);
         }
+        named_barrier();
 #pragma unroll
-        for (int q = 0; q < 36; ++q) Pc[q] = Pn[q];
+        for (int q = 0; q < 12; ++q) Pc[q] = Pn[q];
         rc[0] = rn[0]; rc[1] = rn[1]; rc[2] = rn[2];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            fjc[e] = fjn[e];
+            fkc[e] = fkn[e];
+        }
         cc = cn;
         actc = actn;
     }
     (void)ic;
 }
 
-// ---------------------------------------------------------------------------
-// a8: backward sweep in place, z = (I + D^-1 U_A)^-1 y; levels run downward,
-// with the same next-level prefetch and branch-free FP64 section.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * TILE_WARPS)
+// a8: backward sweep in place, row r of z_c = y_c - sum_upper (D^-1 A_cj) z_j.
+__global__ void __launch_bounds__(SWEEP_THREADS)
 k_bwd_tiled(TileArgs a, const double* __restrict__ P, double* __restrict__ z,
             double* __restrict__ fJ, double* __restrict__ fK,
             const KrylovScalars* __restrict__ ks) {
     if (ks_skip_t(ks)) return;
-    LaneTile L;
-    if (!lane_tile(a, L)) return;
+    __shared__ double zs[2][32][3];
+    const RowTile R = row_tile(a);
     const int n = a.g.n;
-    const bool feedJ = L.jj == 0 && L.J > 0;
-    const bool feedK = L.kk == 0 && L.K > 0;
-    const bool hasJ = L.j + 1 < a.g.ny, hasK = L.k + 1 < a.g.nz;
-    double zp[3] = {0.0, 0.0, 0.0};
-    double Pc[27], zc[3];
+    const int rw = R.row;
+    const bool feedJ = R.jj == 0 && R.J > 0;
+    const bool feedK = R.kk == 0 && R.K > 0;
+    const bool hasJ = R.j + 1 < a.g.ny, hasK = R.k + 1 < a.g.nz;
+    double Pc[9], zc;
     int cc = 0;
     size_t ic = 0;
-    bool actc = tile_cell(a, L, a.NL - 1, cc, ic);
-    if (actc) {
-        ld_P<3, 4>(a, P, ic, Pc);
-        zc[0] = z[cc]; zc[1] = z[n + cc]; zc[2] = z[2 * n + cc];
-    } else {
+    bool actc = row_cell(a, R, a.NL - 1, cc, ic);
 #pragma unroll
-        for (int q = 0; q < 27; ++q) Pc[q] = 0.0;
-        zc[0] = zc[1] = zc[2] = 0.0;
-    }
-    for (int l = a.NL - 1; l >= 0; --l) {
-        double Pn[27], zn[3];
-        int cn = 0;
-        size_t in = 0;
-        const bool actn = (l > 0) && tile_cell(a, L, l - 1, cn, in);
-        if (actn) {
-            ld_P<3, 4>(a, P, in, Pn);
-            zn[0] = z[cn]; zn[1] = z[n + cn]; zn[2] = z[2 * n + cn];
-        } else {
+    for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int q = 0; q < 27; ++q) Pn[q] = 0.0;
-            zn[0] = zn[1] = zn[2] = 0.0;
-        }
-        double zj[3], zk[3];
+        for (int s2 = 0; s2 < 3; ++s2)
+            Pc[3 * b + s2] = actc ? P[(size_t)((4 + b) * 9 + 3 * rw + s2) * a.NP + ic] : 0.0;
+    zc = actc ? z[(size_t)rw * n + cc] : 0.0;
+    const bool takeJ = hasJ && R.jj == TJ - 1, takeK = hasK && R.kk == TK - 1;
+    double fjc[3], fkc[3];
+    {
+        const int i0 = a.NL - 1 - R.jj - R.kk;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-            zj[e] = zsel(hasJ, __shfl_down_sync(FULL, zp[e], 1));
-            zk[e] = zsel(hasK, __shfl_down_sync(FULL, zp[e], TJ));
+            fjc[e] = (actc && takeJ) ? ld_relaxed(fJ + jslot(a, R.t + 1, i0, R.kk, 3) + e) : 0.0;
+            fkc[e] = (actc && takeK) ? ld_relaxed(fK + kslot(a, R.t + a.NJ, i0, R.jj, 3) + e) : 0.0;
         }
-        const int i = l - L.jj - L.kk;
-        if (actc && hasJ && L.jj == TJ - 1) take_face<3>(fJ + jslot(a, L.t + 1, i, L.kk, 3), zj, a.err);
-        if (actc && hasK && L.kk == TK - 1) take_face<3>(fK + kslot(a, L.t + a.NJ, i, L.jj, 3), zk, a.err);
+    }
+    zs[1][R.lane][rw] = 0.0;
+    named_barrier();
+    int step = 0;
+    for (int l = a.NL - 1; l >= 0; --l, ++step) {
+        const int pb = (step + 1) & 1, cb = step & 1;
+        double Pn[9], zn;
+        int cn = 0;
+        size_t in = 0;
+        const bool actn = (l > 0) && row_cell(a, R, l - 1, cn, in);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int s2 = 0; s2 < 3; ++s2)
+                Pn[3 * b + s2] = actn ? P[(size_t)((4 + b) * 9 + 3 * rw + s2) * a.NP + in] : 0.0;
+        zn = actn ? z[(size_t)rw * n + cn] : 0.0;
+        double fjn[3], fkn[3];
+        {
+            const int i1 = l - 1 - R.jj - R.kk;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                fjn[e] = (actn && takeJ) ? ld_relaxed(fJ + jslot(a, R.t + 1, i1, R.kk, 3) + e) : 0.0;
+                fkn[e] = (actn && takeK) ? ld_relaxed(fK + kslot(a, R.t + a.NJ, i1, R.jj, 3) + e) : 0.0;
+            }
+        }
+        double zp[3], zj[3], zk[3];
+        const int lj = R.jj < TJ - 1 ? R.lane + 1 : R.lane;
+        const int lk = R.kk < TK - 1 ? R.lane + TJ : R.lane;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            zp[e] = zs[pb][R.lane][e];
+            zj[e] = zsel(hasJ && R.jj < TJ - 1, zs[pb][lj][e]);
+            zk[e] = zsel(hasK && R.kk < TK - 1, zs[pb][lk][e]);
+        }
+        const int i = l - R.jj - R.kk;
+        if (actc && takeJ) {
+            if (is_sentinel(fjc[0]) || is_sentinel(fjc[1]) || is_sentinel(fjc[2]))
+                peek_face(fJ + jslot(a, R.t + 1, i, R.kk, 3), fjc, a.err);
+            zj[0] = fjc[0]; zj[1] = fjc[1]; zj[2] = fjc[2];
+        }
+        if (actc && takeK) {
+            if (is_sentinel(fkc[0]) || is_sentinel(fkc[1]) || is_sentinel(fkc[2]))
+                peek_face(fK + kslot(a, R.t + a.NJ, i, R.jj, 3), fkc, a.err);
+            zk[0] = fkc[0]; zk[1] = fkc[1]; zk[2] = fkc[2];
+        }
         __syncwarp();
-        double acc[3] = {zc[0], zc[1], zc[2]};
-        fnma_mv(acc, Pc, zp);
-        fnma_mv(acc, Pc + 9, zj);
-        fnma_mv(acc, Pc + 18, zk);
+        double t = -Pc[0] * zp[0];
+        t = fma(-Pc[1], zp[1], t);
+        t = fma(-Pc[2], zp[2], t);
+        t = fma(-Pc[3], zj[0], t);
+        t = fma(-Pc[4], zj[1], t);
+        t = fma(-Pc[5], zj[2], t);
+        double u = -Pc[6] * zk[0];
+        u = fma(-Pc[7], zk[1], u);
+        u = fma(-Pc[8], zk[2], u);
+        double acc = zc + (t + u);
+        zs[cb][R.lane][rw] = actc ? acc : 0.0;
         if (actc) {
-            z[cc] = acc[0];
-            z[n + cc] = acc[1];
-            z[2 * n + cc] = acc[2];
-            if (feedJ) put_face<3>(fJ + jslot(a, L.t, i, L.kk, 3), acc);
-            if (feedK) put_face<3>(fK + kslot(a, L.t, i, L.jj, 3), acc);
-#pragma unroll
-            for (int e = 0; e < 3; ++e) zp[e] = acc[e];
+            z[(size_t)rw * n + cc] = acc;
+            if (feedJ) st_relaxed(fJ + jslot(a, R.t, i, R.kk, 3) + rw, acc);
+            if (feedK) st_relaxed(fK + kslot(a, R.t, i, R.jj, 3) + rw, acc);
         }
+        named_barrier();
 #pragma unroll
-        for (int q = 0; q < 27; ++q) Pc[q] = Pn[q];
-        zc[0] = zn[0]; zc[1] = zn[1]; zc[2] = zn[2];
+        for (int q = 0; q < 9; ++q) Pc[q] = Pn[q];
+        zc = zn;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            fjc[e] = fjn[e];
+            fkc[e] = fkn[e];
+        }
         cc = cn;
         actc = actn;
     }
@@ -561,12 +703,15 @@ void setup_sweeps(bo_sim* s) {
     int dev, sms, per_sm = 0;
     BO_CUDA(cudaGetDevice(&dev));
     BO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_tiled, 32 * TILE_WARPS, 0));
+    if ((long long)per_sm * sms < tile_grid(s))
+        fail(BO_ERR_INVALID_ARG, "grid too large for one co-resident wavefront factorisation");
     int lim = 1 << 30;
-    for (const void* k : {(const void*)k_factor_tiled, (const void*)k_fwd_tiled, (const void*)k_bwd_tiled}) {
-        BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * TILE_WARPS, 0));
+    for (const void* k : {(const void*)k_fwd_tiled, (const void*)k_bwd_tiled}) {
+        BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, SWEEP_THREADS, 0));
         lim = std::min(lim, per_sm);
     }
-    if ((long long)lim * sms < tile_grid(s))
+    if ((long long)lim * sms < tile_args(s).T)
         fail(BO_ERR_INVALID_ARG, "grid too large for one co-resident wavefront sweep");
 }
 
@@ -577,16 +722,23 @@ void enqueue_factor(bo_sim* s, cudaStream_t st, int* bad) {
     k_factor_lower<<<152 * 8, 256, 0, st>>>(a, (const double*)s->d_A, s->d_P);
 }
 
+static void refill_faces3(bo_sim* s, cudaStream_t st) {
+    TileArgs a = tile_args(s);
+    k_fill_sentinel<<<304, 256, 0, st>>>(faceJ3(s), (size_t)a.T * s->geo.nx * (TK + TJ) * 3);
+}
+
 void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y, const KrylovScalars* ks) {
     TileArgs a = tile_args(s);
-    launch_coop(st, tile_grid(s), 32 * TILE_WARPS, k_fwd_tiled, a, (const double*)s->d_P, r, y,
-                faceJ3(s), faceK3(s), ks);
+    launch_coop(st, a.T, SWEEP_THREADS, k_fwd_tiled, a, (const double*)s->d_P, r, y, faceJ3(s),
+                faceK3(s), ks);
+    refill_faces3(s, st);
 }
 
 void enqueue_bwd(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks) {
     TileArgs a = tile_args(s);
-    launch_coop(st, tile_grid(s), 32 * TILE_WARPS, k_bwd_tiled, a, (const double*)s->d_P, z,
-                faceJ3(s), faceK3(s), ks);
+    launch_coop(st, a.T, SWEEP_THREADS, k_bwd_tiled, a, (const double*)s->d_P, z, faceJ3(s),
+                faceK3(s), ks);
+    refill_faces3(s, st);
 }
 
 int sweep_timeout(bo_sim* s) {

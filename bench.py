@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--grid", default=None,
+                    help="NXxNYxNZ: a layered model of this size instead of the config (profiling)")
+    ap.add_argument("--report-days", type=float, default=None,
+                    help="report-step length override (profiling windows)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-its", type=int, default=12)
     return ap.parse_args()
@@ -77,8 +81,11 @@ def dist_env():
     return rank, world, local
 
 
-def model_for(config):
+def model_for(config, grid=None):
     import synth
+    if grid:
+        nx, ny, nz = (int(v) for v in grid.lower().split("x"))
+        return synth.layered_model(nx, ny, nz, config=1, name=f"layered {nx}x{ny}x{nz}")
     return synth.config1() if config == 1 else synth.config0()
 
 
@@ -180,9 +187,9 @@ def run_gb300(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    m = model_for(args.config)
+    m = model_for(args.config, args.grid)
     n = m["nx"] * m["ny"] * m["nz"]
-    dt = m["dt"]
+    dt = m["dt"] if args.report_days is None else args.report_days * 86400.0
     sim = Sim(m, stream=stream)
     sim.init_hydrostatic()
 

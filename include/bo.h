@@ -241,6 +241,28 @@ bo_status bo_set_timing(bo_sim* sim, int enabled);
 bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* ms_total,
                         long long* launches, int* count);
 
+/* Convergence measures of a residual for callers that cannot allocate device
+ * memory (for example a host application or plugin that owns the whole
+ * device memory budget and hands out only its own buffers, or code that
+ * must not let an allocation synchronise the device).  The paper has no
+ * counterpart: it is the measure of bo_norms on caller-owned buffers.
+ * All pointers are device pointers owned by the caller:
+ *   R    [3][n] residual, component-major (R[a*n + i], a = w, o, g);
+ *   pv   [n]    pore volumes;
+ *   b    [3][n] shrinkage factors b_a of every cell;
+ *   out6 [6]    receives MB_a (0..2) and CNV_a (3..5) as defined at bo_norms.
+ * n must be 1 .. 8,388,608: the per-block partial sums live in a fixed
+ * file-scope device array of 4096 x 10 doubles (320 KB), held by every GPU
+ * that loads the library until the process exits; larger n is rejected
+ * with BO_ERR_INVALID_ARG.  The call allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine).  Its first call on a device
+ * looks up the array's device address; make that first call before any
+ * stream capture.  It runs asynchronously on `stream` (a cudaStream_t or
+ * NULL).  Every call shares the one array and overwrites what it reads, so
+ * nothing needs clearing, but calls that overlap on the GPU race on it. */
+bo_status bo_residual_norms_noalloc(const double* R, const double* pv, const double* b, int n,
+                                    double dt, double* out6, void* stream);
+
 /* Number of cells, wells, connections, and nonzero blocks of the pattern. */
 bo_status bo_sizes(const bo_sim* sim, int* n, int* nwells, int* ncon, int* nnzb);
 

@@ -716,6 +716,13 @@ bo_status bo_get_timing(const bo_sim* s, int max, char (*names)[32], double* ms_
     });
 }
 
+bo_status bo_residual_norms_noalloc(const double* R, const double* pv, const double* b, int n,
+                                    double dt, double* out6, void* stream) {
+    return guarded([&] {
+        residual_norms_noalloc(R, pv, b, n, dt, out6, static_cast<cudaStream_t>(stream));
+    });
+}
+
 bo_status bo_sizes(const bo_sim* s, int* n, int* nwells, int* ncon, int* nnzb) {
     return guarded([&] {
         need(s != nullptr, BO_ERR_INVALID_ARG, "bo_sizes: sim is NULL");

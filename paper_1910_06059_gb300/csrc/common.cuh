@@ -184,6 +184,9 @@ void launch_wi(bo_sim* s, const int* d_con_well, const double* d_rw, const doubl
 int props_blocks(const bo_sim* s);
 int norm_blocks(const bo_sim* s);
 
+void residual_norms_noalloc(const double* R, const double* pv, const double* b, int n, double dt,
+                            double* out6, cudaStream_t stream);
+
 // Convert between cell-major host vectors (3c+e) and SoA device vectors.
 void upload_aos3(bo_sim* s, const double* host, double* dev);
 void download_aos3(const bo_sim* s, const double* dev, double* host);

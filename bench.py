@@ -60,6 +60,23 @@ def peaks():
 OPS_PER_REPORT_STEP = {1: {"assemblies": 172.5, "solves": 156.0, "lin_its": 17882.5}}
 
 
+def ncu_traffic(kernel, cells):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), scaled by the cells swept; None once the
+    kernel's source has changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+            sha = hashlib.sha1(fh.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None
+    if not sha.startswith(rec["sha1_prefix"]):
+        return None
+    return rec["bytes_per_cell"] * cells
+
+
 def op_counts(config):
     return OPS_PER_REPORT_STEP[config]
 
@@ -78,6 +95,23 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-its", type=int, default=12)
     return ap.parse_args()
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """Largest value over all ranks (the slowest rank sets the job time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_throughput(cells, steps, world, ms_max):
+    """cell-steps/s of all replicas together: every rank advanced its own model
+    by `steps` report steps; the job took the slowest rank's time."""
+    return cells * steps * world / (ms_max / 1e3)
 
 
 def dist_env():
@@ -228,10 +262,7 @@ def run_gb300(args):
     ms = ev0.elapsed_time(ev1)
     timers = sim.timing()
     sim.set_timing(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, "cuda")
 
     # ---- end to end: host state in, step, host state out ------------------
     # the state lives in pinned host memory between steps: each step uploads
@@ -258,10 +289,7 @@ def run_gb300(args):
     torch.cuda.synchronize()
     barrier()
     ms_e2e = e0.elapsed_time(e1)
-    t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(ms_e2e, world, "cuda")
     io_bytes = int(sum(a.numel() * a.element_size() for a in pin))
 
     if rank != 0:
@@ -278,7 +306,7 @@ def run_gb300(args):
     pk = peaks()
     roof = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
             "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
-            "traffic": None, "peak_source": pk["source"],
+            "traffic": ncu_traffic(dominant, n), "peak_source": pk["source"],
             "avg_launch_ms": round(avg_s * 1e3, 4), "launches": launches}
 
     counts = {"steps": args.steps,
@@ -289,7 +317,7 @@ def run_gb300(args):
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(args.config, counts, args.cpu_sample_its)
 
-    value = n * args.steps * world / (ms_max / 1e3)
+    value = whole_job_throughput(n, args.steps, world, ms_max)
     out = {
         "metric": "cell-steps/s at 1e-6 Newton tol: plain FP64 vs mixed/learned/batched",
         "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
@@ -302,7 +330,7 @@ def run_gb300(args):
                    "l2": "inputs larger than L2 (Jacobian 565 MB, ILU data 565 MB per model)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "clocks": clk,
-        "e2e": {"value": n * args.steps * world / (ms_e2e / 1e3), "unit": "cell-steps/s",
+        "e2e": {"value": whole_job_throughput(n, args.steps, world, ms_e2e), "unit": "cell-steps/s",
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "gpu_launches": None,
         "roofline": roof,

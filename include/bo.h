@@ -241,6 +241,15 @@ bo_status bo_set_timing(bo_sim* sim, int enabled);
 bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* ms_total,
                         long long* launches, int* count);
 
+/* Self-test of failure detection: runs the bounded device-side wait of the
+ * wavefront sweeps on a face slot that nothing ever writes.  The wait runs
+ * out after about one second, the kernel records it and returns, and the
+ * call reports BO_ERR_DEVICE_TIMEOUT with *seconds (may be NULL) = the time
+ * the wait took; the context stays usable.  Any other status is a failure
+ * of the mechanism.  (The paper has no counterpart; Section 2.3's
+ * time-step cutting is the host-side part of failure handling.) */
+bo_status bo_selftest_bounded_wait(bo_sim* sim, double* seconds);
+
 /* Convergence measures of a residual for callers that cannot allocate device
  * memory (for example a host application or plugin that owns the whole
  * device memory budget and hands out only its own buffers, or code that

@@ -84,6 +84,7 @@ _SIGS = {
     "bo_set_step_control": [P, c_double],
     "bo_set_timing": [P, c_int],
     "bo_get_timing": [P, c_int, P, P, P, P],
+    "bo_selftest_bounded_wait": [P, P],
     "bo_residual_norms_noalloc": [P, P, P, c_int, c_double, P, P],
     "bo_sizes": [P, P, P, P, P],
     "bo_destroy": [P],

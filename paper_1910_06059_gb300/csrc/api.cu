@@ -716,6 +716,17 @@ bo_status bo_get_timing(const bo_sim* s, int max, char (*names)[32], double* ms_
     });
 }
 
+bo_status bo_selftest_bounded_wait(bo_sim* s, double* seconds) {
+    bo_status st = guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_selftest_bounded_wait: sim is NULL");
+        double t = wait_selftest(s);
+        if (seconds) *seconds = t;
+    });
+    if (st != BO_OK) return st;
+    g_last_error = "bounded-wait self-test: the wait ran out and was reported";
+    return BO_ERR_DEVICE_TIMEOUT;
+}
+
 bo_status bo_residual_norms_noalloc(const double* R, const double* pv, const double* b, int n,
                                     double dt, double* out6, void* stream) {
     return guarded([&] {

@@ -167,6 +167,7 @@ void enqueue_factor(bo_sim* s, cudaStream_t st, int* bad);
 void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y, const KrylovScalars* ks);
 void enqueue_bwd(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks);
 void export_dinv(bo_sim* s, double* dinv);
+double wait_selftest(bo_sim* s);
 void build_graphs(bo_sim* s);
 void destroy_graphs(bo_sim* s);
 void launch_factor(bo_sim* s);                       // graph of level kernels

@@ -40,7 +40,8 @@ constexpr int TJ = 8, TK = 4;          // tile of x-lines per warp
 #endif
 constexpr int TILE_WARPS = BO_TILE_WARPS;  // warps (tiles) per CTA
 constexpr unsigned long long SENTINEL_BITS = 0x7FF4DEADBEEF0001ull;  // a NaN no arithmetic yields
-constexpr long long POLL_LIMIT = 1LL << 26;
+// bounded waits: with the back-off below, 2^20 polls take about one second
+constexpr long long POLL_LIMIT = 1LL << 20;
 #ifndef BO_POLL_SLEEP_NS
 #define BO_POLL_SLEEP_NS 32
 #endif
@@ -632,6 +633,16 @@ __global__ void k_fill_sentinel(double* __restrict__ p, size_t count) {
         p[q] = sent;
 }
 
+// Self-test of the bounded wait: poll a face slot that nothing writes.
+__global__ void k_wait_selftest(const double* slot, int* err, long long* ns_out) {
+    unsigned long long t0, t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    double v[3];
+    peek_face(slot, v, err);
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    *ns_out = (long long)(t1 - t0);
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -746,6 +757,29 @@ int sweep_timeout(bo_sim* s) {
     BO_CUDA(cudaMemcpyAsync(&v, s->d_sweep_sync + 2, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     BO_CUDA(cudaStreamSynchronize(s->stream));
     return v;
+}
+
+// Runs one bounded face wait that can only time out; returns the wait time.
+double wait_selftest(bo_sim* s) {
+    int* err = s->d_sweep_sync + 3;   // a flag of its own: the sweeps' flag stays clear
+    long long* ns = nullptr;
+    BO_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s->stream));
+    // the last sentinel slot of the 3-value faces is never written outside a sweep
+    TileArgs a = tile_args(s);
+    const double* slot = faceJ3(s);
+    BO_CUDA(cudaMalloc(&ns, sizeof(long long)));
+    k_wait_selftest<<<1, 1, 0, s->stream>>>(slot, err, ns);
+    BO_LAUNCH_CHECK("k_wait_selftest");
+    long long h = 0;
+    int e = 0;
+    BO_CUDA(cudaMemcpyAsync(&h, ns, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    BO_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+    cudaFree(ns);
+    BO_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s->stream));
+    (void)a;
+    if (e == 0) fail(BO_ERR_STATE, "bounded-wait self-test: the wait did not run out");
+    return h * 1e-9;
 }
 
 // D^-1 of every cell in natural order, [n][9].

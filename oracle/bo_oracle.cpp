@@ -633,7 +633,8 @@ enum { LIN_OK = 0, LIN_NOT_CONVERGED = 1, LIN_BREAKDOWN = 2, LIN_FACTOR_FAIL = 3
 // Right-preconditioned BiCGStab (van der Vorst) on the reduced system
 // S x = b, b = R_r - sum_w C_w D_w^-1 R_w; then x_w = D_w^-1 (R_w - B_w x_r).
 // Output sol has 3n reservoir entries followed by one entry per well
-// (zero for wells without an unknown).  Stops when ||r|| <= tol ||r0||.
+// (zero for wells without an unknown).  Stops when ||r|| <= tol ||r0|| and
+// the true residual ||b - S x|| meets the same bound (see the restarts below).
 static int solve(Model& m, double tol, int maxit, double* sol, int* its_out) {
     int n = m.n, N = 3 * n;
     *its_out = 0;
@@ -646,40 +647,61 @@ static int solve(Model& m, double tol, int maxit, double* sol, int* its_out) {
             for (int e = 0; e < 3; ++e) b[3 * w.cells[con] + e] -= w.C[3 * con + e] * s;
     }
     std::vector<double> x(N, 0.0), r(b), rh(b), p(N, 0.0), v(N, 0.0), ph(N), s(N), sh(N), t(N);
-    double nr0 = std::sqrt(dot(r, r));
-    int status = LIN_NOT_CONVERGED;
-    int it = 0;
-    if (nr0 == 0.0) status = LIN_OK;
-    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
-    for (it = 1; status == LIN_NOT_CONVERGED && it <= maxit; ++it) {
-        double rho = dot(rh, r);
-        if (rho == 0.0 || !std::isfinite(rho)) { status = LIN_BREAKDOWN; break; }
-        double beta = (rho / rho_old) * (alpha / omega);
-        for (int i = 0; i < N; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
-        ilu_apply(m, p.data(), ph.data());
-        apply_op(m, ph.data(), v.data());
-        double rv = dot(rh, v);
-        if (rv == 0.0 || !std::isfinite(rv)) { status = LIN_BREAKDOWN; break; }
-        alpha = rho / rv;
-        for (int i = 0; i < N; ++i) s[i] = r[i] - alpha * v[i];
-        double ns = std::sqrt(dot(s, s));
-        if (ns <= tol * nr0) {
-            for (int i = 0; i < N; ++i) x[i] += alpha * ph[i];
-            status = LIN_OK;
+    const double nr0 = std::sqrt(dot(r, r));
+    // One BiCGStab cycle from the current r (with rh = r, p = v = 0), until the
+    // recurrence's residual meets tol ||r0||, a breakdown, or maxit iterations
+    // in total.
+    auto cycle = [&]() -> int {
+        double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        for (int it = *its_out + 1; it <= maxit; ++it) {
+            double rho = dot(rh, r);
+            if (rho == 0.0 || !std::isfinite(rho)) return LIN_BREAKDOWN;
+            double beta = (rho / rho_old) * (alpha / omega);
+            for (int i = 0; i < N; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+            ilu_apply(m, p.data(), ph.data());
+            apply_op(m, ph.data(), v.data());
+            double rv = dot(rh, v);
+            if (rv == 0.0 || !std::isfinite(rv)) return LIN_BREAKDOWN;
+            alpha = rho / rv;
+            for (int i = 0; i < N; ++i) s[i] = r[i] - alpha * v[i];
+            double ns = std::sqrt(dot(s, s));
+            if (ns <= tol * nr0) {
+                for (int i = 0; i < N; ++i) x[i] += alpha * ph[i];
+                *its_out = it;
+                return LIN_OK;
+            }
+            ilu_apply(m, s.data(), sh.data());
+            apply_op(m, sh.data(), t.data());
+            double tt = dot(t, t);
+            if (tt == 0.0 || !std::isfinite(tt)) return LIN_BREAKDOWN;
+            omega = dot(t, s) / tt;
+            if (omega == 0.0 || !std::isfinite(omega)) return LIN_BREAKDOWN;
+            for (int i = 0; i < N; ++i) { x[i] += alpha * ph[i] + omega * sh[i]; r[i] = s[i] - omega * t[i]; }
+            double nr = std::sqrt(dot(r, r));
             *its_out = it;
+            if (nr <= tol * nr0) return LIN_OK;
+            rho_old = rho;
+        }
+        return LIN_NOT_CONVERGED;
+    };
+    int status = nr0 == 0.0 ? LIN_OK : cycle();
+    // Acceptance on the true residual b - S x: the recurrence's residual can
+    // drift from it.  A miss restarts BiCGStab from the true residual (at most
+    // 8 times, iterations counted on); with the budget spent the solve is not
+    // converged.
+    for (int restarts = 0; status == LIN_OK && nr0 > 0.0; ++restarts) {
+        apply_op(m, x.data(), t.data());
+        for (int i = 0; i < N; ++i) r[i] = b[i] - t[i];
+        double nt = std::sqrt(dot(r, r));
+        if (nt <= tol * nr0) break;
+        if (restarts >= 8 || *its_out >= maxit || !std::isfinite(nt)) {
+            status = LIN_NOT_CONVERGED;
             break;
         }
-        ilu_apply(m, s.data(), sh.data());
-        apply_op(m, sh.data(), t.data());
-        double tt = dot(t, t);
-        if (tt == 0.0 || !std::isfinite(tt)) { status = LIN_BREAKDOWN; break; }
-        omega = dot(t, s) / tt;
-        if (omega == 0.0 || !std::isfinite(omega)) { status = LIN_BREAKDOWN; break; }
-        for (int i = 0; i < N; ++i) { x[i] += alpha * ph[i] + omega * sh[i]; r[i] = s[i] - omega * t[i]; }
-        double nr = std::sqrt(dot(r, r));
-        *its_out = it;
-        if (nr <= tol * nr0) { status = LIN_OK; break; }
-        rho_old = rho;
+        rh = r;
+        std::fill(p.begin(), p.end(), 0.0);
+        std::fill(v.begin(), v.end(), 0.0);
+        status = cycle();
     }
     if (status == LIN_NOT_CONVERGED) *its_out = maxit;
     for (int i = 0; i < N; ++i) sol[i] = x[i];

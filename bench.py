@@ -37,6 +37,23 @@ ALGO_BYTES_PER_CELL = {
     # factorisation: 7 blocks of A in, 7 blocks of P out
     "ilu_factor": 63 * 8 * 2,
 }
+# Mixed precision: the forward stage reads D^-1 (FP64) and the FP64 residual
+# to form q = D^-1 r, then the three scaled lower blocks in FP32, and leaves an
+# FP32 intermediate; the backward sweep reads the three scaled upper blocks in
+# FP32 and the intermediate and writes the FP64 result.
+ALGO_BYTES_PER_CELL_MIXED = dict(ALGO_BYTES_PER_CELL)
+ALGO_BYTES_PER_CELL_MIXED.update({
+    "ilu_fwd_sweep": 9 * 8 + 24 + 27 * 4 + 12,
+    "ilu_bwd_sweep": 27 * 4 + 12 + 24,
+})
+
+WORKLOADS = {
+    0: "spe1-shaped 10x10x3, 30-day report steps",
+    1: "layered 60x220x85 black-oil, 5-spot wells, 10-day report steps",
+    2: "Gaussian-random-field 100x100x50 black-oil, 5-spot wells, 5-day report steps",
+}
+PRECISION_NAMES = {"fp64": "plain FP64 ILU0-BiCGStab",
+                   "mixed": "FP32 ILU0 factors and sweeps, FP64 assembly/Krylov/Newton"}
 
 
 def peaks():
@@ -87,7 +104,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="ILU(0) preconditioner precision (mixed: FP32 factors and sweeps)")
     ap.add_argument("--grid", default=None,
                     help="NXxNYxNZ: a layered model of this size instead of the config (profiling)")
     ap.add_argument("--report-days", type=float, default=None,
@@ -126,7 +145,7 @@ def model_for(config, grid=None):
     if grid:
         nx, ny, nz = (int(v) for v in grid.lower().split("x"))
         return synth.layered_model(nx, ny, nz, config=1, name=f"layered {nx}x{ny}x{nz}")
-    return synth.config1() if config == 1 else synth.config0()
+    return {0: synth.config0, 1: synth.config1, 2: synth.config2}[config]()
 
 
 class ClockSampler:
@@ -216,6 +235,12 @@ def cpu_baseline(config, gpu_counts, sample_its):
                        f"{n_it} BiCGStab iterations")}
 
 
+def workload_name(args, m):
+    if args.grid:
+        return f"{m['name']}, report steps of {args.report_days or m['dt'] / 86400.0:g} days"
+    return WORKLOADS[args.config]
+
+
 def run_gb300(args):
     import torch
     import torch.distributed as dist
@@ -231,6 +256,7 @@ def run_gb300(args):
     n = m["nx"] * m["ny"] * m["nz"]
     dt = m["dt"] if args.report_days is None else args.report_days * 86400.0
     sim = Sim(m, stream=stream)
+    sim.precision = args.precision
     sim.init_hydrostatic()
 
     def barrier():
@@ -301,12 +327,14 @@ def run_gb300(args):
     dominant = max((k for k in timers if k in ALGO_BYTES_PER_CELL), key=lambda k: timers[k][0])
     tot_ms, launches = timers[dominant]
     avg_s = tot_ms / 1e3 / max(launches, 1)
-    algo = ALGO_BYTES_PER_CELL[dominant] * n
+    algo_table = ALGO_BYTES_PER_CELL_MIXED if args.precision == "mixed" else ALGO_BYTES_PER_CELL
+    algo = algo_table[dominant] * n
     achieved = algo / avg_s / 1e9
     pk = peaks()
     roof = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
             "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
-            "traffic": ncu_traffic(dominant, n), "peak_source": pk["source"],
+            "traffic": ncu_traffic(dominant, n) if args.precision == "fp64" else None,
+            "peak_source": pk["source"],
             "avg_launch_ms": round(avg_s * 1e3, 4), "launches": launches}
 
     counts = {"steps": args.steps,
@@ -322,12 +350,15 @@ def run_gb300(args):
         "metric": "cell-steps/s at 1e-6 Newton tol: plain FP64 vs mixed/learned/batched",
         "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": ("layered 60x220x85 black-oil, 5-spot wells, 10-day report steps, "
-                                "plain FP64 ILU0-BiCGStab, Newton tol 1e-6")
-                   if args.config == 1 else "spe1-shaped 10x10x3, 30-day report steps",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": (f"{workload_name(args, m)}, {PRECISION_NAMES[args.precision]}, "
+                                "Newton tol 1e-6"),
+                   "precision": args.precision,
                    "cells": n, "newton_tol": 1e-6, "linear_tol": 1e-3,
-                   "l2": "inputs larger than L2 (Jacobian 565 MB, ILU data 565 MB per model)",
+                   "l2": (f"inputs larger than L2 (Jacobian {504 * n / 1e6:.0f} MB, ILU data "
+                          f"{504 * n / 1e6:.0f} MB per model)"),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "clocks": clk,
         "e2e": {"value": whole_job_throughput(n, args.steps, world, ms_e2e), "unit": "cell-steps/s",

@@ -117,6 +117,8 @@ typedef struct {
 typedef struct {
     int iterations;  /* BiCGStab iterations (a half-iteration exit counts as one) */
     int status;      /* 0 converged, 1 not converged in max_it, 2 breakdown */
+    int restarts;    /* restarts from the true residual (see bo_solve) */
+    double rel_res;  /* FP64 true residual ||b - Op x||_2 / ||b||_2 at exit */
 } bo_solve_report;
 
 typedef struct {
@@ -206,7 +208,8 @@ bo_status bo_get_wells(const bo_sim* sim, double* Rw, double* Dw, double* B, dou
 bo_status bo_factor(bo_sim* sim, double* dinv);
 
 /* z = M^-1 r with the factors of the last bo_factor; r, z are [3n] host
- * arrays in cell-major order. */
+ * arrays in cell-major order.  In BO_PRECISION_MIXED the sweeps run on the
+ * FP32 factors in FP32 arithmetic (r and z stay FP64). */
 bo_status bo_precond_apply(bo_sim* sim, const double* r, double* z);
 
 /* y = (A - sum_w C_w D_w^-1 B_w) x, the well-reduced operator of
@@ -215,6 +218,10 @@ bo_status bo_apply_op(bo_sim* sim, const double* x, double* y);
 
 /* Linear solve J sol = R of the last assembly: factors, then right-
  * preconditioned BiCGStab on the reduced system, then the well unknowns.
+ * The iteration stops on the recurrence's residual; the FP64 true residual
+ * ||b - Op x|| is then computed and must meet the same tolerance, else
+ * BiCGStab restarts from it (at most 3 times, within max_it) and the solve
+ * reports not converged if it still misses.
  * sol (may be NULL) receives [3n + nwells] (cell-major, then one entry per
  * well, 0 for wells without an unknown). */
 bo_status bo_solve(bo_sim* sim, const bo_solve_opts* opts, bo_solve_report* report,
@@ -238,6 +245,21 @@ bo_status bo_set_step_control(bo_sim* sim, double dt_next);
  * while enabled (CUDA events on the library stream).  names receive up to
  * max entries of "name\0", ms_total and launches are per entry. */
 bo_status bo_set_timing(bo_sim* sim, int enabled);
+
+/* Precision of the ILU(0) preconditioner.  BO_PRECISION_FP64 (the default):
+ * factors stored and applied in FP64.  BO_PRECISION_MIXED: the factors are
+ * computed in FP64, stored rounded to FP32 (a second 63 x 4-byte copy per
+ * cell slot, allocated at the first switch) and both triangular sweeps run
+ * in FP32; residual assembly, the Krylov vectors and scalars, the operator,
+ * the true-residual check of bo_solve and the Newton convergence test stay
+ * FP64.  The preconditioner is only an approximation of J^-1, so the
+ * precision of its application changes iteration counts, not the converged
+ * Newton state beyond the tolerances.  Switching re-records the solver's
+ * CUDA graphs and converts factors already computed.  Requires
+ * bo_set_properties; BO_ERR_INVALID_ARG for another value. */
+enum { BO_PRECISION_FP64 = 0, BO_PRECISION_MIXED = 1 };
+bo_status bo_set_precision(bo_sim* sim, int precision);
+bo_status bo_get_precision(const bo_sim* sim, int* precision);
 bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* ms_total,
                         long long* launches, int* count);
 

@@ -48,7 +48,11 @@ class BoSolveOpts(ctypes.Structure):
 
 
 class BoSolveReport(ctypes.Structure):
-    _fields_ = [("iterations", c_int), ("status", c_int)]
+    _fields_ = [("iterations", c_int), ("status", c_int), ("restarts", c_int),
+                ("rel_res", c_double)]
+
+
+PRECISION = {"fp64": 0, "mixed": 1}
 
 
 class BoStepReport(ctypes.Structure):
@@ -83,6 +87,8 @@ _SIGS = {
     "bo_get_step_control": [P, P],
     "bo_set_step_control": [P, c_double],
     "bo_set_timing": [P, c_int],
+    "bo_set_precision": [P, c_int],
+    "bo_get_precision": [P, P],
     "bo_get_timing": [P, c_int, P, P, P, P],
     "bo_selftest_bounded_wait": [P, P],
     "bo_residual_norms_noalloc": [P, P, P, c_int, c_double, P, P],

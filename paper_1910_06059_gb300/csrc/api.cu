@@ -74,7 +74,7 @@ static void free_all(bo_sim* s) {
                     s->d_props, s->d_R, s->d_A, s->d_P, s->d_face, s->d_cellcon, s->d_wells,
                     s->d_con_cell, s->d_con_wi, s->d_wB, s->d_wC, s->d_b, s->d_xs, s->d_r,
                     s->d_rh, s->d_pk, s->d_v, s->d_s, s->d_t, s->d_ph, s->d_sh, s->d_part,
-                    s->d_ks, s->d_ns, s->d_sweep_sync};
+                    s->d_ks, s->d_ns, s->d_sweep_sync, s->d_P32, s->d_r32, s->d_y32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->h_ns) cudaFreeHost(s->h_ns);
@@ -108,9 +108,14 @@ static void assemble_and_norms(bo_sim* s, double dt) {
 
 // Linear solve of the last assembly; returns the LS_* status.
 static void check_timeout(bo_sim* s) {
-    if (sweep_timeout(s))
+    if (sweep_timeout(s)) {
+        // leave the face buffers and the flag ready for the next call
+        reset_sweep_faces(s);
+        BO_CUDA(cudaMemsetAsync(s->d_sweep_sync + 2, 0, sizeof(int), s->stream));
+        sync(s);
         fail(BO_ERR_DEVICE_TIMEOUT,
              "a dataflow sweep gave up waiting for a neighbour (bounded wait ran out)");
+    }
 }
 
 static int solve_linear(bo_sim* s, double tol, int maxit, int* its) {
@@ -615,6 +620,8 @@ bo_status bo_solve(bo_sim* s, const bo_solve_opts* o, bo_solve_report* rep, doub
         if (rep) {
             rep->iterations = its;
             rep->status = st;
+            rep->restarts = s->last_restarts;
+            rep->rel_res = s->last_rel_res;
         }
         if (sol) {
             download_aos3(s, s->d_xs, sol);
@@ -685,6 +692,36 @@ bo_status bo_set_step_control(bo_sim* s, double dt_next) {
         need(dt_next >= 0 && std::isfinite(dt_next), BO_ERR_INVALID_ARG,
              "bo_set_step_control: dt_next must be >= 0");
         s->dt_next = dt_next;
+    });
+}
+
+bo_status bo_set_precision(bo_sim* s, int precision) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_set_precision: sim is NULL");
+        need(precision == BO_PRECISION_FP64 || precision == BO_PRECISION_MIXED, BO_ERR_INVALID_ARG,
+             "bo_set_precision: precision must be BO_PRECISION_FP64 or BO_PRECISION_MIXED");
+        need(s->props_set, BO_ERR_STATE, "bo_set_precision: call bo_set_properties first");
+        const bool mixed = precision == BO_PRECISION_MIXED;
+        if (mixed == s->mixed) return;
+        sync(s);
+        if (mixed && s->d_P32 == nullptr) {
+            dalloc(&s->d_P32, factors32_floats(s));
+            dalloc(&s->d_r32, vec32_floats(s));
+            dalloc(&s->d_y32, vec32_floats(s));
+        }
+        s->mixed = mixed;
+        if (mixed) convert_factors32(s, s->stream);  // factors of an earlier bo_factor stay usable
+        reset_sweep_faces(s);
+        build_graphs(s);
+        sync(s);
+    });
+}
+
+bo_status bo_get_precision(const bo_sim* s, int* precision) {
+    return guarded([&] {
+        need(s != nullptr && precision != nullptr, BO_ERR_INVALID_ARG,
+             "bo_get_precision: NULL argument");
+        *precision = s->mixed ? BO_PRECISION_MIXED : BO_PRECISION_FP64;
     });
 }
 

@@ -61,7 +61,10 @@ struct KrylovScalars {
     double last_nr;
     int it, maxit, state, status;   // state: 0 running, 1 half-step exit pending, 2 done
     int half_exit;                  // the solve ended on the half step (no second apply)
-    int pad_;
+    int restarts;                   // restarts from the true residual
+    double true_nr;                 // ||b - Op x||_2 at the last check
+    double stop;                    // the recurrence stops at ||r|| <= stop
+    double inner;                   // per-cycle relative target (0: tol alone)
 };
 enum { KS_RUN = 0, KS_HALF = 1, KS_DONE = 2 };
 enum { LS_OK = 0, LS_NOT_CONVERGED = 1, LS_BREAKDOWN = 2 };
@@ -114,6 +117,12 @@ struct bo_sim {
     double* d_R = nullptr;       // 3n
     double* d_A = nullptr;       // 63n
     double* d_P = nullptr;       // 63 x tile-order ILU(0) data
+    float* d_P32 = nullptr;      // FP32 factors in the FP32 sweep layout (mixed mode)
+    float* d_r32 = nullptr;      // FP32 sweep input, tile order (mixed mode)
+    float* d_y32 = nullptr;      // FP32 sweep work vector, tile order (mixed mode)
+    bool mixed = false;          // preconditioner applies in FP32
+    int last_restarts = 0;       // BiCGStab restarts from the true residual, last solve
+    double last_rel_res = 0.0;   // ||b - Op x|| / ||b||, last solve
     double* d_face = nullptr;    // tile-face buffers of the wavefront sweeps
     int* d_sweep_sync = nullptr; // [2]: a bounded wait of a sweep ran out
     int* d_cellcon = nullptr;    // c -> connection index or -1
@@ -167,6 +176,10 @@ void enqueue_factor(bo_sim* s, cudaStream_t st, int* bad);
 void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y, const KrylovScalars* ks);
 void enqueue_bwd(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks);
 void export_dinv(bo_sim* s, double* dinv);
+size_t factors32_floats(const bo_sim* s);        // size of d_P32 (FP32 sweep layout)
+size_t vec32_floats(const bo_sim* s);            // size of d_r32, d_y32 (tile order)
+void convert_factors32(bo_sim* s, cudaStream_t st);
+void reset_sweep_faces(bo_sim* s);                // sentinels of the current precision
 double wait_selftest(bo_sim* s);
 void build_graphs(bo_sim* s);
 void destroy_graphs(bo_sim* s);

@@ -30,46 +30,14 @@
 #include <cmath>
 #include <vector>
 
-#include "common.cuh"
+#include "tiles.cuh"
 
 namespace bo {
 
-constexpr int TJ = 8, TK = 4;          // tile of x-lines per warp
 #ifndef BO_TILE_WARPS
 #define BO_TILE_WARPS 4
 #endif
-constexpr int TILE_WARPS = BO_TILE_WARPS;  // warps (tiles) per CTA
-constexpr unsigned long long SENTINEL_BITS = 0x7FF4DEADBEEF0001ull;  // a NaN no arithmetic yields
-// bounded waits: with the back-off below, 2^20 polls take about one second
-constexpr long long POLL_LIMIT = 1LL << 20;
-#ifndef BO_POLL_SLEEP_NS
-#define BO_POLL_SLEEP_NS 32
-#endif
-constexpr unsigned FULL = 0xffffffffu;
-
-struct TileArgs {
-    Geom g;
-    int NJ, NK, T, NL;
-    size_t NP;
-    int* err;
-};
-
-__device__ __forceinline__ double ld_relaxed(const double* p) {
-    double v;
-    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed(double* p, double v) {
-    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
-}
-__device__ __forceinline__ int ld_relaxed_i(const int* p) {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ bool is_sentinel(double v) {
-    return (unsigned long long)__double_as_longlong(v) == SENTINEL_BITS;
-}
+constexpr int TILE_WARPS = BO_TILE_WARPS;  // warps (tiles) per CTA of the factorisation
 
 // Wait for K values of a face slot, return them, and put the sentinel back.
 // The poll backs off exponentially (64 ns doubling to 1 us) so waiting lanes
@@ -105,10 +73,6 @@ template <int K>
 __device__ __forceinline__ void put_face(double* slot, const double* v) {
 #pragma unroll
     for (int q = 0; q < K; ++q) st_relaxed(slot + q, v[q]);
-}
-
-__device__ __forceinline__ bool ks_skip_t(const KrylovScalars* ks) {
-    return ks != nullptr && ks->state != KS_RUN;
 }
 
 // 3x3 helpers, row-major e = 3r + s
@@ -166,13 +130,6 @@ __device__ __forceinline__ bool lane_tile(const TileArgs& a, LaneTile& L) {
     return true;
 }
 
-// Face slots: j-face of tile t for lane row kk at x index i; k-face for jj.
-__device__ __forceinline__ size_t jslot(const TileArgs& a, int t, int i, int kk, int K) {
-    return (((size_t)t * a.g.nx + i) * TK + kk) * K;
-}
-__device__ __forceinline__ size_t kslot(const TileArgs& a, int t, int i, int jj, int K) {
-    return (((size_t)t * a.g.nx + i) * TJ + jj) * K;
-}
 
 // ---------------------------------------------------------------------------
 // a7: factorisation.  Lane state: the scaled upper blocks D^-1 A_{c,+x/+y/+z}
@@ -378,7 +335,8 @@ __device__ __forceinline__ void named_barrier() {
 }
 
 // Wait for the three values of a face slot (no reset; see above).
-__device__ __forceinline__ void peek_face(const double* slot, double out[3], int* err) {
+template <typename T>
+__device__ __forceinline__ void peek_face(const T* slot, T out[3], int* err) {
     unsigned ns = 64;
     for (long long s = 0;; ++s) {
         bool ready = true;
@@ -390,7 +348,7 @@ __device__ __forceinline__ void peek_face(const double* slot, double out[3], int
         if (ready) return;
         if (s >= POLL_LIMIT || ((s & 255) == 255 && ld_relaxed_i(err) != 0)) {
             atomicExch(err, 1);
-            out[0] = out[1] = out[2] = 0.0;
+            out[0] = out[1] = out[2] = T(0);
             return;
         }
         if (BO_POLL_SLEEP_NS > 0) {
@@ -401,7 +359,11 @@ __device__ __forceinline__ void peek_face(const double* slot, double out[3], int
 }
 
 // a8: forward sweep y = (L_A + D)^-1 r, row r of
-//     y_c = D_c^-1 r_c - L_x y_{i-1} - L_y y_{j-1} - L_z y_{k-1}.
+//     y_c = D_c^-1 r_c - L_x y_{i-1} - L_y y_{j-1} - L_z y_{k-1}   (FP64).
+// Every index of the level loop is affine in the level, so the loop only
+// advances pointers: the factor slot by 32 entries, the cell by one, the face
+// slots by one row of the face.  Factor rows, r and face values of the next
+// level are loaded while the current level computes.
 __global__ void __launch_bounds__(SWEEP_THREADS)
 k_fwd_tiled(TileArgs a, const double* __restrict__ P, const double* __restrict__ r,
             double* __restrict__ y, double* __restrict__ fJ, double* __restrict__ fK,
@@ -409,58 +371,53 @@ k_fwd_tiled(TileArgs a, const double* __restrict__ P, const double* __restrict__
     if (ks_skip_t(ks)) return;
     __shared__ double ys[2][32][3];
     const RowTile R = row_tile(a);
-    const int n = a.g.n;
+    const int n = a.g.n, nx = a.g.nx;
     const int rw = R.row;
-    const bool feedJ = R.jj == TJ - 1 && R.J + 1 < a.NJ;
-    const bool feedK = R.kk == TK - 1 && R.K + 1 < a.NK;
+    const bool feedJ = R.valid && R.jj == TJ - 1 && R.J + 1 < a.NJ;
+    const bool feedK = R.valid && R.kk == TK - 1 && R.K + 1 < a.NK;
     const bool hasJ = R.j > 0, hasK = R.k > 0;
-    // row rw of D^-1 and of the three scaled lower blocks: P entries b*9 + 3*rw + s
-    double Pc[12], rc[3];
-    int cc = 0;
-    size_t ic = 0;
-    bool actc = row_cell(a, R, 0, cc, ic);
+    const bool takeJ = R.valid && hasJ && R.jj == 0, takeK = R.valid && hasK && R.kk == 0;
+    const int l0 = R.jj + R.kk;                   // first level of this line (i = 0)
+    const size_t NP = a.NP;
+    // level l of this line: factor slot, cell, face slots (valid when 0 <= i < nx)
+    const double* Pl = P + (size_t)(3 * rw) * NP + ((size_t)R.t * a.NL) * 32 + R.lane;
+    const int c0 = nx * (R.j + a.g.ny * R.k) - l0;   // cell index at level l is c0 + l
+    const double* fjin = fJ + jslot(a, R.t - 1 < 0 ? 0 : R.t - 1, 0, R.kk, 3) - (size_t)l0 * TK * 3;
+    const double* fkin = fK + kslot(a, R.t - a.NJ < 0 ? 0 : R.t - a.NJ, 0, R.jj, 3) - (size_t)l0 * TJ * 3;
+    double* fjout = fJ + jslot(a, R.t, 0, R.kk, 3) - (size_t)l0 * TK * 3 + rw;
+    double* fkout = fK + kslot(a, R.t, 0, R.jj, 3) - (size_t)l0 * TJ * 3 + rw;
+    // P entries of row rw: block b, column s at offset (9 b + s) NP from Pl
+    auto loadP = [&](int l, double out[12], double rin[3], double fj[3], double fk[3]) {
+        const int i = l - l0;
+        const bool act = R.valid && i >= 0 && i < nx;
+        const double* p = Pl + (size_t)l * 32;
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
+        for (int b2 = 0; b2 < 4; ++b2)
 #pragma unroll
-        for (int s2 = 0; s2 < 3; ++s2)
-            Pc[3 * b + s2] = actc ? P[(size_t)(b * 9 + 3 * rw + s2) * a.NP + ic] : 0.0;
+            for (int s2 = 0; s2 < 3; ++s2) out[3 * b2 + s2] = act ? p[(size_t)(9 * b2 + s2) * NP] : 0.0;
+        const int c = c0 + l;
 #pragma unroll
-    for (int e = 0; e < 3; ++e) rc[e] = actc ? r[(size_t)e * n + cc] : 0.0;
-    // face values are loaded one level ahead too; a value still holding the
-    // sentinel is waited for when it is needed
-    const bool takeJ = hasJ && R.jj == 0, takeK = hasK && R.kk == 0;
-    double fjc[3], fkc[3];
-    {
-        const int i0 = 0 - R.jj - R.kk;
+        for (int e = 0; e < 3; ++e) rin[e] = act ? r[(size_t)e * n + c] : 0.0;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-            fjc[e] = (actc && takeJ) ? ld_relaxed(fJ + jslot(a, R.t - 1, i0, R.kk, 3) + e) : 0.0;
-            fkc[e] = (actc && takeK) ? ld_relaxed(fK + kslot(a, R.t - a.NJ, i0, R.jj, 3) + e) : 0.0;
+            fj[e] = (act && takeJ) ? ld_relaxed(fjin + (size_t)l * TK * 3 + e) : 0.0;
+            fk[e] = (act && takeK) ? ld_relaxed(fkin + (size_t)l * TJ * 3 + e) : 0.0;
         }
-    }
+        return act;
+    };
+    double Pc[12], rc[3], fjc[3], fkc[3];
+    bool actc = loadP(0, Pc, rc, fjc, fkc);
     ys[1][R.lane][rw] = 0.0;
     named_barrier();
     for (int l = 0; l < a.NL; ++l) {
         const int pb = (l + 1) & 1, cb = l & 1;
-        double Pn[12], rn[3];
-        int cn = 0;
-        size_t in = 0;
-        const bool actn = (l + 1 < a.NL) && row_cell(a, R, l + 1, cn, in);
+        double Pn[12], rn[3], fjn[3], fkn[3];
+        const bool actn = (l + 1 < a.NL) ? loadP(l + 1, Pn, rn, fjn, fkn) : false;
+        if (l + 1 >= a.NL) {
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2)
-                Pn[3 * b + s2] = actn ? P[(size_t)(b * 9 + 3 * rw + s2) * a.NP + in] : 0.0;
-#pragma unroll
-        for (int e = 0; e < 3; ++e) rn[e] = actn ? r[(size_t)e * n + cn] : 0.0;
-        double fjn[3], fkn[3];
-        {
-            const int i1 = l + 1 - R.jj - R.kk;
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                fjn[e] = (actn && takeJ) ? ld_relaxed(fJ + jslot(a, R.t - 1, i1, R.kk, 3) + e) : 0.0;
-                fkn[e] = (actn && takeK) ? ld_relaxed(fK + kslot(a, R.t - a.NJ, i1, R.jj, 3) + e) : 0.0;
-            }
+            for (int q = 0; q < 12; ++q) Pn[q] = 0.0;
+            rn[0] = rn[1] = rn[2] = 0.0;
+            fjn[0] = fjn[1] = fjn[2] = fkn[0] = fkn[1] = fkn[2] = 0.0;
         }
         double yp[3], yj[3], yk[3];
         const int lj = R.jj > 0 ? R.lane - 1 : R.lane;
@@ -468,18 +425,17 @@ k_fwd_tiled(TileArgs a, const double* __restrict__ P, const double* __restrict__
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
             yp[e] = ys[pb][R.lane][e];
-            yj[e] = zsel(hasJ && R.jj > 0, ys[pb][lj][e]);
-            yk[e] = zsel(hasK && R.kk > 0, ys[pb][lk][e]);
+            yj[e] = (hasJ && R.jj > 0) ? ys[pb][lj][e] : 0.0;
+            yk[e] = (hasK && R.kk > 0) ? ys[pb][lk][e] : 0.0;
         }
-        const int i = l - R.jj - R.kk;
         if (actc && takeJ) {
             if (is_sentinel(fjc[0]) || is_sentinel(fjc[1]) || is_sentinel(fjc[2]))
-                peek_face(fJ + jslot(a, R.t - 1, i, R.kk, 3), fjc, a.err);
+                peek_face(fjin + (size_t)l * TK * 3, fjc, a.err);
             yj[0] = fjc[0]; yj[1] = fjc[1]; yj[2] = fjc[2];
         }
         if (actc && takeK) {
             if (is_sentinel(fkc[0]) || is_sentinel(fkc[1]) || is_sentinel(fkc[2]))
-                peek_face(fK + kslot(a, R.t - a.NJ, i, R.jj, 3), fkc, a.err);
+                peek_face(fkin + (size_t)l * TJ * 3, fkc, a.err);
             yk[0] = fkc[0]; yk[1] = fkc[1]; yk[2] = fkc[2];
         }
         __syncwarp();
@@ -498,9 +454,9 @@ k_fwd_tiled(TileArgs a, const double* __restrict__ P, const double* __restrict__
         acc = acc + (t + u);
         ys[cb][R.lane][rw] = actc ? acc : 0.0;
         if (actc) {
-            y[(size_t)rw * n + cc] = acc;
-            if (feedJ) st_relaxed(fJ + jslot(a, R.t, i, R.kk, 3) + rw, acc);
-            if (feedK) st_relaxed(fK + kslot(a, R.t, i, R.jj, 3) + rw, acc);
+            y[(size_t)rw * n + c0 + l] = acc;
+            if (feedJ) st_relaxed(fjout + (size_t)l * TK * 3, acc);
+            if (feedK) st_relaxed(fkout + (size_t)l * TJ * 3, acc);
         }
         named_barrier();
 #pragma unroll
@@ -511,87 +467,84 @@ k_fwd_tiled(TileArgs a, const double* __restrict__ P, const double* __restrict__
             fjc[e] = fjn[e];
             fkc[e] = fkn[e];
         }
-        cc = cn;
         actc = actn;
     }
-    (void)ic;
 }
 
-// a8: backward sweep in place, row r of z_c = y_c - sum_upper (D^-1 A_cj) z_j.
+// a8: backward sweep in place, row r of z_c = y_c - sum_upper (D^-1 A_cj) z_j
+// (FP64); levels run downward, same pointer stepping in the other direction.
 __global__ void __launch_bounds__(SWEEP_THREADS)
 k_bwd_tiled(TileArgs a, const double* __restrict__ P, double* __restrict__ z,
-            double* __restrict__ fJ, double* __restrict__ fK,
-            const KrylovScalars* __restrict__ ks) {
+            double* __restrict__ fJ, double* __restrict__ fK, const KrylovScalars* __restrict__ ks) {
     if (ks_skip_t(ks)) return;
     __shared__ double zs[2][32][3];
     const RowTile R = row_tile(a);
-    const int n = a.g.n;
+    const int n = a.g.n, nx = a.g.nx;
     const int rw = R.row;
-    const bool feedJ = R.jj == 0 && R.J > 0;
-    const bool feedK = R.kk == 0 && R.K > 0;
+    const bool feedJ = R.valid && R.jj == 0 && R.J > 0;
+    const bool feedK = R.valid && R.kk == 0 && R.K > 0;
     const bool hasJ = R.j + 1 < a.g.ny, hasK = R.k + 1 < a.g.nz;
-    double Pc[9], zc;
-    int cc = 0;
-    size_t ic = 0;
-    bool actc = row_cell(a, R, a.NL - 1, cc, ic);
+    const bool takeJ = R.valid && hasJ && R.jj == TJ - 1, takeK = R.valid && hasK && R.kk == TK - 1;
+    const int l0 = R.jj + R.kk;
+    const size_t NP = a.NP;
+    const double* Pl = P + (size_t)(36 + 3 * rw) * NP + ((size_t)R.t * a.NL) * 32 + R.lane;
+    const int c0 = nx * (R.j + a.g.ny * R.k) - l0;
+    const int tJ = (R.t + 1 < a.T) ? R.t + 1 : R.t, tK = (R.t + a.NJ < a.T) ? R.t + a.NJ : R.t;
+    const double* fjin = fJ + jslot(a, tJ, 0, R.kk, 3) - (size_t)l0 * TK * 3;
+    const double* fkin = fK + kslot(a, tK, 0, R.jj, 3) - (size_t)l0 * TJ * 3;
+    double* fjout = fJ + jslot(a, R.t, 0, R.kk, 3) - (size_t)l0 * TK * 3 + rw;
+    double* fkout = fK + kslot(a, R.t, 0, R.jj, 3) - (size_t)l0 * TJ * 3 + rw;
+    // next[0..8]: P entries of row rw; next[9]: y of the cell (row rw)
+    auto load = [&](int l, double next[10], double fj[3], double fk[3]) {
+        const int i = l - l0;
+        const bool act = R.valid && i >= 0 && i < nx;
+        const double* p = Pl + (size_t)l * 32;
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+        for (int b2 = 0; b2 < 3; ++b2)
 #pragma unroll
-        for (int s2 = 0; s2 < 3; ++s2)
-            Pc[3 * b + s2] = actc ? P[(size_t)((4 + b) * 9 + 3 * rw + s2) * a.NP + ic] : 0.0;
-    zc = actc ? z[(size_t)rw * n + cc] : 0.0;
-    const bool takeJ = hasJ && R.jj == TJ - 1, takeK = hasK && R.kk == TK - 1;
-    double fjc[3], fkc[3];
-    {
-        const int i0 = a.NL - 1 - R.jj - R.kk;
+            for (int s2 = 0; s2 < 3; ++s2) next[3 * b2 + s2] = act ? p[(size_t)(9 * b2 + s2) * NP] : 0.0;
+        next[9] = act ? z[(size_t)rw * n + c0 + l] : 0.0;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-            fjc[e] = (actc && takeJ) ? ld_relaxed(fJ + jslot(a, R.t + 1, i0, R.kk, 3) + e) : 0.0;
-            fkc[e] = (actc && takeK) ? ld_relaxed(fK + kslot(a, R.t + a.NJ, i0, R.jj, 3) + e) : 0.0;
+            fj[e] = (act && takeJ) ? ld_relaxed(fjin + (size_t)l * TK * 3 + e) : 0.0;
+            fk[e] = (act && takeK) ? ld_relaxed(fkin + (size_t)l * TJ * 3 + e) : 0.0;
         }
-    }
+        return act;
+    };
+    double Pc[10], fjc[3], fkc[3];
+    bool actc = load(a.NL - 1, Pc, fjc, fkc);
     zs[1][R.lane][rw] = 0.0;
     named_barrier();
+    const int lj = R.jj < TJ - 1 ? R.lane + 1 : R.lane;
+    const int lk = R.kk < TK - 1 ? R.lane + TJ : R.lane;
+    const bool inJ = hasJ && R.jj < TJ - 1, inK = hasK && R.kk < TK - 1;
     int step = 0;
     for (int l = a.NL - 1; l >= 0; --l, ++step) {
         const int pb = (step + 1) & 1, cb = step & 1;
-        double Pn[9], zn;
-        int cn = 0;
-        size_t in = 0;
-        const bool actn = (l > 0) && row_cell(a, R, l - 1, cn, in);
+        double Pn[10], fjn[3], fkn[3];
+        bool actn = false;
+        if (l > 0) {
+            actn = load(l - 1, Pn, fjn, fkn);
+        } else {
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2)
-                Pn[3 * b + s2] = actn ? P[(size_t)((4 + b) * 9 + 3 * rw + s2) * a.NP + in] : 0.0;
-        zn = actn ? z[(size_t)rw * n + cn] : 0.0;
-        double fjn[3], fkn[3];
-        {
-            const int i1 = l - 1 - R.jj - R.kk;
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                fjn[e] = (actn && takeJ) ? ld_relaxed(fJ + jslot(a, R.t + 1, i1, R.kk, 3) + e) : 0.0;
-                fkn[e] = (actn && takeK) ? ld_relaxed(fK + kslot(a, R.t + a.NJ, i1, R.jj, 3) + e) : 0.0;
-            }
+            for (int q = 0; q < 10; ++q) Pn[q] = 0.0;
+            fjn[0] = fjn[1] = fjn[2] = fkn[0] = fkn[1] = fkn[2] = 0.0;
         }
         double zp[3], zj[3], zk[3];
-        const int lj = R.jj < TJ - 1 ? R.lane + 1 : R.lane;
-        const int lk = R.kk < TK - 1 ? R.lane + TJ : R.lane;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
             zp[e] = zs[pb][R.lane][e];
-            zj[e] = zsel(hasJ && R.jj < TJ - 1, zs[pb][lj][e]);
-            zk[e] = zsel(hasK && R.kk < TK - 1, zs[pb][lk][e]);
+            zj[e] = inJ ? zs[pb][lj][e] : 0.0;
+            zk[e] = inK ? zs[pb][lk][e] : 0.0;
         }
-        const int i = l - R.jj - R.kk;
         if (actc && takeJ) {
             if (is_sentinel(fjc[0]) || is_sentinel(fjc[1]) || is_sentinel(fjc[2]))
-                peek_face(fJ + jslot(a, R.t + 1, i, R.kk, 3), fjc, a.err);
+                peek_face(fjin + (size_t)l * TK * 3, fjc, a.err);
             zj[0] = fjc[0]; zj[1] = fjc[1]; zj[2] = fjc[2];
         }
         if (actc && takeK) {
             if (is_sentinel(fkc[0]) || is_sentinel(fkc[1]) || is_sentinel(fkc[2]))
-                peek_face(fK + kslot(a, R.t + a.NJ, i, R.jj, 3), fkc, a.err);
+                peek_face(fkin + (size_t)l * TJ * 3, fkc, a.err);
             zk[0] = fkc[0]; zk[1] = fkc[1]; zk[2] = fkc[2];
         }
         __syncwarp();
@@ -604,26 +557,23 @@ k_bwd_tiled(TileArgs a, const double* __restrict__ P, double* __restrict__ z,
         double u = -Pc[6] * zk[0];
         u = fma(-Pc[7], zk[1], u);
         u = fma(-Pc[8], zk[2], u);
-        double acc = zc + (t + u);
+        const double acc = Pc[9] + (t + u);
         zs[cb][R.lane][rw] = actc ? acc : 0.0;
         if (actc) {
-            z[(size_t)rw * n + cc] = acc;
-            if (feedJ) st_relaxed(fJ + jslot(a, R.t, i, R.kk, 3) + rw, acc);
-            if (feedK) st_relaxed(fK + kslot(a, R.t, i, R.jj, 3) + rw, acc);
+            z[(size_t)rw * n + c0 + l] = acc;
+            if (feedJ) st_relaxed(fjout + (size_t)l * TK * 3, acc);
+            if (feedK) st_relaxed(fkout + (size_t)l * TJ * 3, acc);
         }
         named_barrier();
 #pragma unroll
-        for (int q = 0; q < 9; ++q) Pc[q] = Pn[q];
-        zc = zn;
+        for (int q = 0; q < 10; ++q) Pc[q] = Pn[q];
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
             fjc[e] = fjn[e];
             fkc[e] = fkn[e];
         }
-        cc = cn;
         actc = actn;
     }
-    (void)ic;
 }
 
 __global__ void k_fill_sentinel(double* __restrict__ p, size_t count) {
@@ -646,7 +596,7 @@ __global__ void k_wait_selftest(const double* slot, int* err, long long* ns_out)
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static TileArgs tile_args(bo_sim* s) {
+TileArgs tile_args(const bo_sim* s) {
     TileArgs a;
     a.g = s->geo;
     a.NJ = (s->geo.ny + TJ - 1) / TJ;
@@ -675,28 +625,13 @@ static double* faceK9(bo_sim* s) {
     TileArgs a = tile_args(s);
     return s->d_face + (size_t)a.T * s->geo.nx * TK * 9;
 }
-static double* faceJ3(bo_sim* s) {
+double* faceJ3(bo_sim* s) {
     TileArgs a = tile_args(s);
     return faceK9(s) + (size_t)a.T * s->geo.nx * TJ * 9;
 }
-static double* faceK3(bo_sim* s) {
+double* faceK3(bo_sim* s) {
     TileArgs a = tile_args(s);
     return faceJ3(s) + (size_t)a.T * s->geo.nx * TK * 3;
-}
-
-template <class... Args>
-static void launch_coop(cudaStream_t st, int grid, int block, void (*kern)(Args...), Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    BO_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
 }
 
 static int tile_grid(bo_sim* s) {
@@ -724,6 +659,7 @@ void setup_sweeps(bo_sim* s) {
     }
     if ((long long)lim * sms < tile_args(s).T)
         fail(BO_ERR_INVALID_ARG, "grid too large for one co-resident wavefront sweep");
+    setup_sweeps32(s);
 }
 
 void enqueue_factor(bo_sim* s, cudaStream_t st, int* bad) {
@@ -731,6 +667,7 @@ void enqueue_factor(bo_sim* s, cudaStream_t st, int* bad) {
     launch_coop(st, tile_grid(s), 32 * TILE_WARPS, k_factor_tiled, a, (const double*)s->d_A,
                 s->d_P, faceJ9(s), faceK9(s), bad);
     k_factor_lower<<<152 * 8, 256, 0, st>>>(a, (const double*)s->d_A, s->d_P);
+    if (s->mixed) convert_factors32(s, st);
 }
 
 static void refill_faces3(bo_sim* s, cudaStream_t st) {
@@ -738,7 +675,24 @@ static void refill_faces3(bo_sim* s, cudaStream_t st) {
     k_fill_sentinel<<<304, 256, 0, st>>>(faceJ3(s), (size_t)a.T * s->geo.nx * (TK + TJ) * 3);
 }
 
+// Sentinels of the current precision in the 3-value face buffers (after a
+// precision switch or an abandoned sweep).
+void reset_sweep_faces(bo_sim* s) {
+    if (s->mixed)
+        reset_faces32(s, s->stream);
+    else
+        refill_faces3(s, s->stream);
+    BO_LAUNCH_CHECK("reset_sweep_faces");
+}
+
+// In mixed mode the forward sweep leaves y in the FP32 tile-order work
+// vector and the backward sweep converts its result into z; the two always
+// run as a pair.
 void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y, const KrylovScalars* ks) {
+    if (s->mixed) {
+        enqueue_fwd32(s, st, r, ks);
+        return;
+    }
     TileArgs a = tile_args(s);
     launch_coop(st, a.T, SWEEP_THREADS, k_fwd_tiled, a, (const double*)s->d_P, r, y, faceJ3(s),
                 faceK3(s), ks);
@@ -746,6 +700,10 @@ void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y, const K
 }
 
 void enqueue_bwd(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks) {
+    if (s->mixed) {
+        enqueue_bwd32(s, st, z, ks);
+        return;
+    }
     TileArgs a = tile_args(s);
     launch_coop(st, a.T, SWEEP_THREADS, k_bwd_tiled, a, (const double*)s->d_P, z, faceJ3(s),
                 faceK3(s), ks);
@@ -763,11 +721,11 @@ int sweep_timeout(bo_sim* s) {
 double wait_selftest(bo_sim* s) {
     int* err = s->d_sweep_sync + 3;   // a flag of its own: the sweeps' flag stays clear
     long long* ns = nullptr;
+    double* slot = nullptr;           // a face slot of its own that nothing writes
     BO_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s->stream));
-    // the last sentinel slot of the 3-value faces is never written outside a sweep
-    TileArgs a = tile_args(s);
-    const double* slot = faceJ3(s);
     BO_CUDA(cudaMalloc(&ns, sizeof(long long)));
+    BO_CUDA(cudaMalloc(&slot, 3 * sizeof(double)));
+    k_fill_sentinel<<<1, 32, 0, s->stream>>>(slot, 3);
     k_wait_selftest<<<1, 1, 0, s->stream>>>(slot, err, ns);
     BO_LAUNCH_CHECK("k_wait_selftest");
     long long h = 0;
@@ -776,8 +734,8 @@ double wait_selftest(bo_sim* s) {
     BO_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     BO_CUDA(cudaStreamSynchronize(s->stream));
     cudaFree(ns);
+    cudaFree(slot);
     BO_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s->stream));
-    (void)a;
     if (e == 0) fail(BO_ERR_STATE, "bounded-wait self-test: the wait did not run out");
     return h * 1e-9;
 }

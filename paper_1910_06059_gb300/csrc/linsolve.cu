@@ -68,7 +68,8 @@ __global__ void k_wdot(int n, const WellDev* __restrict__ wells, const int* __re
     if (threadIdx.x == 0) sop[blockIdx.x] = (W.ctl == 0) ? sh[0] / W.Dw : 0.0;
 }
 
-// mode 0: no dots; 1: part0 = (rh, y); 2: part0 = (y, s), part1 = (y, y)
+// mode 0: no dots; 1: part0 = (rh, y); 2: part0 = (y, s), part1 = (y, y);
+// 3: y = o1 - Op x (the true residual of b = o1), part0 = (y, y)
 template <int MODE>
 __global__ void __launch_bounds__(VEC_BS)
 k_spmv(Geom g, const double* __restrict__ A, const double* __restrict__ x,
@@ -110,6 +111,10 @@ k_spmv(Geom g, const double* __restrict__ A, const double* __restrict__ x,
         }
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
+            if (MODE == 3) {
+                acc[r] = o1[r * n + c] - acc[r];
+                d0 += acc[r] * acc[r];
+            }
             y[r * n + c] = acc[r];
             if (MODE == 1) d0 += o1[r * n + c] * acc[r];
             if (MODE == 2) {
@@ -276,7 +281,7 @@ __device__ __forceinline__ void breakdown(KrylovScalars* ks) {
 
 // setup: nr0 = ||b||, rho = (rh, r) = ||b||^2
 __global__ void k_s_setup(KrylovScalars* ks, const double* __restrict__ part, int nb, double tol,
-                          int maxit) {
+                          int maxit, double inner) {
     double rr = sum_partials(part, nb);
     if (threadIdx.x != 0) return;
     ks->tol = tol;
@@ -292,6 +297,10 @@ __global__ void k_s_setup(KrylovScalars* ks, const double* __restrict__ part, in
     ks->status = LS_NOT_CONVERGED;
     ks->state = KS_RUN;
     ks->half_exit = 0;
+    ks->restarts = 0;
+    ks->true_nr = ks->nr0;
+    ks->inner = inner;
+    ks->stop = fmax(tol, inner) * ks->nr0;
     if (ks->nr0 == 0.0) {
         ks->state = KS_DONE;
         ks->status = LS_OK;
@@ -333,7 +342,7 @@ __global__ void k_s3(KrylovScalars* ks, const double* __restrict__ part, int nb)
     double ss = sum_partials(part, nb);
     if (threadIdx.x != 0) return;
     double ns = sqrt(ss);
-    if (ns <= ks->tol * ks->nr0) {
+    if (ns <= ks->stop) {
         ks->state = KS_HALF;
         ks->half_exit = 1;
         ks->last_nr = ns;
@@ -374,13 +383,57 @@ __global__ void k_s5(KrylovScalars* ks, const double* __restrict__ part, int nb)
     if (threadIdx.x != 0) return;
     double nr = sqrt(rr);
     ks->last_nr = nr;
-    if (nr <= ks->tol * ks->nr0) {
+    if (nr <= ks->stop) {
         ks->state = KS_DONE;
         ks->status = LS_OK;
         return;
     }
     ks->rho_old = ks->rho;
     ks->rho = rhr;
+}
+
+// The recurrence's residual decides when to stop, the true residual
+// ||b - Op x|| (FP64, computed after the stop) decides whether to accept.
+// Otherwise BiCGStab restarts from the true residual with the iteration count
+// carried on: after drift of the recurrence, or after a cycle of the mixed-
+// precision solver that stopped at its own target inner * ||r_start||
+// (an FP32 preconditioner is not exactly the same linear map at every
+// application, which limits how far one BiCGStab cycle can reduce the
+// residual).  With allow == 0 the solve is reported as not converged instead.
+__global__ void k_s_restart(KrylovScalars* ks, const double* __restrict__ part, int nb, int allow) {
+    double rr = sum_partials(part, nb);
+    if (threadIdx.x != 0) return;
+    double nr = sqrt(rr);
+    ks->true_nr = nr;
+    if (ks->status != LS_OK) return;
+    if (nr <= ks->tol * ks->nr0) return;
+    if (!allow || ks->it >= ks->maxit || !isfinite(nr)) {
+        ks->status = LS_NOT_CONVERGED;
+        return;
+    }
+    ks->restarts += 1;
+    ks->stop = fmax(ks->tol * ks->nr0, ks->inner * nr);
+    ks->rho = rr;
+    ks->rho_old = 1.0;
+    ks->alpha = 1.0;
+    ks->omega = 1.0;
+    ks->beta = 0.0;
+    ks->last_nr = nr;
+    ks->half_exit = 0;
+    ks->status = LS_NOT_CONVERGED;
+    ks->state = KS_RUN;
+}
+
+// restart vectors: rh = r, p = v = 0 (only when k_s_restart restarted)
+__global__ void k_restart_vectors(int N, const double* __restrict__ r, double* __restrict__ rh,
+                                  double* __restrict__ p, double* __restrict__ v,
+                                  const KrylovScalars* __restrict__ ks) {
+    if (ks->state != KS_RUN) return;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < N; q += gridDim.x * blockDim.x) {
+        rh[q] = r[q];
+        p[q] = 0.0;
+        v[q] = 0.0;
+    }
 }
 
 // x_w = (R_w - B_w x_r) / D_w
@@ -607,30 +660,24 @@ void launch_well_recover(bo_sim* s) {
     BO_LAUNCH_CHECK("k_well_recover");
 }
 
-int run_bicgstab(bo_sim* s, double tol, int maxit, int* its) {
-    const int n = s->geo.n, N = 3 * n;
+constexpr int MAX_RESTARTS = 8;
+constexpr double MIXED_INNER = 1e-4;   // per-cycle reduction target with FP32 sweeps
+
+// Replays the iteration graph until the recurrence stops (or the iteration
+// limit is reached), adding the per-kernel event times when timing is on.
+static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* prev_it) {
     cudaStream_t st = s->stream;
-    // right-hand side of the reduced system
-    k_rhs_copy<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b);
-    if (s->nw > 0) k_rhs_wells<<<s->nw, 128, 0, st>>>(n, s->d_wells, s->d_con_cell, s->d_wC, s->d_b);
-    k_krylov_init<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b, s->d_xs, s->d_r, s->d_rh,
-                                               s->d_pk, s->d_v, s->d_part);
-    k_s_setup<<<1, 256, 0, st>>>(s->d_ks, s->d_part, VEC_GRID, tol, maxit);
-    BO_LAUNCH_CHECK("bicgstab setup");
-    const bool timed = s->timing;
-    if (timed) ensure_timed_graph(s);
-    cudaGraphExec_t g = timed ? s->g_iter_timed : s->g_iter;
-    int prev_it = 0;
-    int t_fwd = timer_id(s, "ilu_fwd_sweep"), t_bwd = timer_id(s, "ilu_bwd_sweep");
-    int t_spmv = timer_id(s, "spmv_wells"), t_blas = timer_id(s, "blas1_fused");
-    for (int guard = 0; guard < maxit + 2; guard += s->iters_per_graph) {
+    const int t_fwd = timer_id(s, "ilu_fwd_sweep"), t_bwd = timer_id(s, "ilu_bwd_sweep");
+    const int t_spmv = timer_id(s, "spmv_wells"), t_blas = timer_id(s, "blas1_fused");
+    const int left = s->h_ks->maxit - s->h_ks->it;
+    for (int guard = 0; guard < left + 2; guard += s->iters_per_graph) {
         BO_CUDA(cudaGraphLaunch(g, st));
         BO_CUDA(cudaMemcpyAsync(s->h_ks, s->d_ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st));
         BO_CUDA(cudaStreamSynchronize(st));
         const KrylovScalars& k = *s->h_ks;
         if (timed) {
             // iterations that did work in this launch (a half step counts as one)
-            int ran = k.it - prev_it;
+            int ran = k.it - *prev_it;
             for (int q = 0; q < ran && q < s->iters_per_graph; ++q) {
                 cudaEvent_t* e = s->iter_events.data() + q * EV_PER_ITER;
                 float ms;
@@ -653,11 +700,48 @@ int run_bicgstab(bo_sim* s, double tol, int maxit, int* its) {
                 add(t_blas, 16, 17);
             }
         }
-        prev_it = k.it;
+        *prev_it = k.it;
         if (k.state == KS_DONE) break;
+    }
+}
+
+int run_bicgstab(bo_sim* s, double tol, int maxit, int* its) {
+    const int n = s->geo.n, N = 3 * n;
+    cudaStream_t st = s->stream;
+    // right-hand side of the reduced system
+    k_rhs_copy<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b);
+    if (s->nw > 0) k_rhs_wells<<<s->nw, 128, 0, st>>>(n, s->d_wells, s->d_con_cell, s->d_wC, s->d_b);
+    k_krylov_init<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b, s->d_xs, s->d_r, s->d_rh,
+                                               s->d_pk, s->d_v, s->d_part);
+    k_s_setup<<<1, 256, 0, st>>>(s->d_ks, s->d_part, VEC_GRID, tol, maxit,
+                                 s->mixed ? MIXED_INNER : 0.0);
+    BO_LAUNCH_CHECK("bicgstab setup");
+    s->h_ks->it = 0;
+    s->h_ks->maxit = maxit;
+    const bool timed = s->timing;
+    if (timed) ensure_timed_graph(s);
+    cudaGraphExec_t g = timed ? s->g_iter_timed : s->g_iter;
+    const int t_check = timer_id(s, "true_residual");
+    int prev_it = 0;
+    for (int round = 0;; ++round) {
+        replay_iterations(s, g, timed, &prev_it);
+        if (s->h_ks->state != KS_DONE || s->h_ks->status == LS_BREAKDOWN) break;
+        // FP64 true residual r = b - Op x; accept, restart from it, or give up
+        timer_begin(s, t_check);
+        enqueue_op<3>(s, st, s->d_xs, s->d_r, s->d_b, nullptr);
+        k_s_restart<<<1, 256, 0, st>>>(s->d_ks, s->d_part, VEC_GRID, round < MAX_RESTARTS);
+        k_restart_vectors<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_r, s->d_rh, s->d_pk, s->d_v,
+                                                       s->d_ks);
+        timer_end(s, t_check);
+        BO_LAUNCH_CHECK("true residual");
+        BO_CUDA(cudaMemcpyAsync(s->h_ks, s->d_ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st));
+        BO_CUDA(cudaStreamSynchronize(st));
+        if (s->h_ks->state != KS_RUN) break;
     }
     timers_flush(s);
     *its = s->h_ks->it;
+    s->last_restarts = s->h_ks->restarts;
+    s->last_rel_res = s->h_ks->nr0 > 0.0 ? s->h_ks->true_nr / s->h_ks->nr0 : 0.0;
     if (s->h_ks->state != KS_DONE) return LS_NOT_CONVERGED;
     return s->h_ks->status;
 }

@@ -164,13 +164,18 @@ class Sim:
         call("bo_apply_op", self.h, ptr(x), ptr(y))
         return y
 
-    def solve(self, tol=1e-3, maxit=500):
-        """Returns (status, iterations, sol[3n + nw]); sol solves J sol = R."""
+    def solve(self, tol=1e-3, maxit=500, report=False):
+        """Returns (status, iterations, sol[3n + nw]); sol solves J sol = R.
+        With report=True a fourth item gives the restarts and the true
+        relative residual ||b - Op x|| / ||b||."""
         o = L.BoSolveOpts(tol=float(tol), max_it=int(maxit))
         rep = L.BoSolveReport()
         sol = np.zeros(3 * self.n + max(self.nw, 1))
         call("bo_solve", self.h, ctypes.byref(o), ctypes.byref(rep), ptr(sol))
-        return rep.status, rep.iterations, sol[:3 * self.n + self.nw]
+        out = (rep.status, rep.iterations, sol[:3 * self.n + self.nw])
+        if report:
+            return out + ({"restarts": rep.restarts, "rel_res": rep.rel_res},)
+        return out
 
     def newton_update(self, **opts):
         o = L.newton_opts(**opts)
@@ -199,6 +204,17 @@ class Sim:
     @dt_next.setter
     def dt_next(self, v):
         call("bo_set_step_control", self.h, float(v))
+
+    @property
+    def precision(self):
+        """"fp64" or "mixed" (FP32 ILU(0) factors and sweeps)."""
+        v = ctypes.c_int()
+        call("bo_get_precision", self.h, ctypes.byref(v))
+        return {q: k for k, q in L.PRECISION.items()}[v.value]
+
+    @precision.setter
+    def precision(self, name):
+        call("bo_set_precision", self.h, L.PRECISION[name])
 
     # -- timing --------------------------------------------------------------
     def set_timing(self, enabled: bool):

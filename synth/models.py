@@ -265,3 +265,26 @@ def random_state(model: dict, seed_member: int = 0, frac_sat: float = 0.5):
 
 
 CONFIGS = {0: config0, 1: config1, 2: config2}
+
+
+# ---------------------------------------------------------------------------
+# Initial parameters of the learned preconditioner stage (an input to both
+# the GPU library and the oracle): a 66 -> 128 -> 128 -> 3 MLP stored flat as
+# W1[128,66], b1[128], W2[128,128], b2[128], W3[3,128], b3[3].
+# ---------------------------------------------------------------------------
+ML_SHAPES = [(128, 66), (128,), (128, 128), (128,), (3, 128), (3,)]
+
+
+def learned_init(seed: int = 0) -> np.ndarray:
+    """He-uniform hidden layers and a zero output layer (so the untrained
+    stage adds nothing and training starts from plain ILU(0)), drawn from
+    PCG64(seed); flat float64 vector of 25,475 parameters."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for shape in ML_SHAPES:
+        if len(shape) == 2 and shape[0] == 128:
+            lim = np.sqrt(6.0 / shape[1])
+            parts.append(rng.uniform(-lim, lim, shape).reshape(-1))
+        else:
+            parts.append(np.zeros(int(np.prod(shape))))
+    return np.concatenate(parts)

@@ -52,6 +52,8 @@ WORKLOADS = {
     1: "layered 60x220x85 black-oil, 5-spot wells, 10-day report steps",
     2: "Gaussian-random-field 100x100x50 black-oil, 5-spot wells, 5-day report steps",
 }
+LEARNED_NAME = (" + learned stage (66-128-128-3 MLP on BF16 tensor cores, trained online "
+                "on the first warm-up report step's solver residuals)")
 PRECISION_NAMES = {"fp64": "plain FP64 ILU0-BiCGStab",
                    "mixed": "FP32 ILU0 factors and sweeps, FP64 assembly/Krylov/Newton"}
 
@@ -107,6 +109,12 @@ def parse():
     ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="ILU(0) preconditioner precision (mixed: FP32 factors and sweeps)")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned preconditioner stage: trained online during the first "
+                         "--train-steps warm-up report steps, then on inside BiCGStab")
+    ap.add_argument("--train-steps", type=int, default=1)
+    ap.add_argument("--train-samples", type=int, default=8)
+    ap.add_argument("--train-lr", type=float, default=1e-3)
     ap.add_argument("--grid", default=None,
                     help="NXxNYxNZ: a layered model of this size instead of the config (profiling)")
     ap.add_argument("--report-days", type=float, default=None,
@@ -258,13 +266,25 @@ def run_gb300(args):
     sim = Sim(m, stream=stream)
     sim.precision = args.precision
     sim.init_hydrostatic()
+    if args.learned:
+        import synth
+        sim.learn_set_params(synth.learned_init(0))
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
+    for w in range(args.warmup):
+        if args.learned:
+            if w == 0 and args.train_steps > 0:
+                sim.learn_online(samples=args.train_samples, epochs=1, lr=args.train_lr)
+            if w == args.train_steps:
+                sim.learn_online(on=False)
+                sim.learn_enable(True)
         sim.step(dt, raise_on_fail=True)
+    if args.learned and args.warmup <= args.train_steps:
+        sim.learn_online(on=False)
+        sim.learn_enable(True)
     torch.cuda.synchronize()
     snap = sim.get_state()
     snap_dt = sim.dt_next
@@ -351,9 +371,10 @@ def run_gb300(args):
         "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "dtype": ("f64" if args.precision == "fp64" else "f64+f32") + ("+bf16" if args.learned else ""),
         "data": "synthetic",
-        "config": {"workload": (f"{workload_name(args, m)}, {PRECISION_NAMES[args.precision]}, "
+        "config": {"workload": (f"{workload_name(args, m)}, {PRECISION_NAMES[args.precision]}"
+                                f"{LEARNED_NAME if args.learned else ''}, "
                                 "Newton tol 1e-6"),
                    "precision": args.precision,
                    "cells": n, "newton_tol": 1e-6, "linear_tol": 1e-3,
@@ -369,23 +390,30 @@ def run_gb300(args):
         "iterations": counts,
         "kernel_ms": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in timers.items()},
     }
-    out["gpu_launches"] = gpu_launch_count(timers, reps, sim)
+    out["gpu_launches"] = gpu_launch_count(timers, reps, sim, args.precision, args.learned)
+    if args.learned:
+        out["learned"] = sim.learn_report()
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
 
 
-def gpu_launch_count(timers, reps, sim):
+def gpu_launch_count(timers, reps, sim, precision="fp64", learned=False):
     """Kernels launched in the timed region, counted from the algorithm:
     per BiCGStab iteration 16 (scalar, vector, 2 forward + 2 backward sweeps,
-    2 well dots, 2 operators), per solve 4 setup + 1 factorisation + 1 well
-    recovery, per assembly 5 (props, flux, wells, 2 norm kernels), per
-    Newton update 2, per sub-step 2 (step start)."""
+    2 well dots, 2 operators), 4 more with FP32 sweeps (the conversions into
+    and out of tile order) and 4 more with the learned stage (scale partials
+    and the network, per apply); per solve 4 setup + 1 factorisation (+1
+    feature kernel with the learned stage) + 4 true-residual check + 1 well
+    recovery; per assembly 5 (props, flux, wells, 2 norm kernels); per Newton
+    update 2; per sub-step 2 (step start)."""
     lin = sum(r["lin_its"] for r in reps)
     nit = sum(r["newton_its"] for r in reps)
     asm = sum(r["newton_its"] + r["substeps"] + r["cuts"] for r in reps)
     subs = sum(r["substeps"] + r["cuts"] for r in reps)
-    return int(lin * 16 + nit * (4 + 1 + 1 + 2) + asm * 5 + subs * 2)
+    per_it = 16 + (4 if precision == "mixed" else 0) + (4 if learned else 0)
+    per_solve = 4 + 1 + (1 if learned else 0) + 4 + 1 + 2
+    return int(lin * per_it + nit * per_solve + asm * 5 + subs * 2)
 
 
 def run_reference(args):

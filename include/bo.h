@@ -245,12 +245,15 @@ bo_status bo_set_step_control(bo_sim* sim, double dt_next);
  * while enabled (CUDA events on the library stream).  names receive up to
  * max entries of "name\0", ms_total and launches are per entry. */
 bo_status bo_set_timing(bo_sim* sim, int enabled);
+bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* ms_total,
+                        long long* launches, int* count);
 
 /* Precision of the ILU(0) preconditioner.  BO_PRECISION_FP64 (the default):
  * factors stored and applied in FP64.  BO_PRECISION_MIXED: the factors are
- * computed in FP64, stored rounded to FP32 (a second 63 x 4-byte copy per
- * cell slot, allocated at the first switch) and both triangular sweeps run
- * in FP32; residual assembly, the Krylov vectors and scalars, the operator,
+ * computed in FP64; the scaled off-diagonal blocks are stored rounded to
+ * FP32 (a second copy, 56 x 4 bytes per cell slot, allocated at the first
+ * switch) and both triangular sweeps run in FP32 (the pivot inverse is
+ * applied in FP64 before the forward sweep); residual assembly, the Krylov vectors and scalars, the operator,
  * the true-residual check of bo_solve and the Newton convergence test stay
  * FP64.  The preconditioner is only an approximation of J^-1, so the
  * precision of its application changes iteration counts, not the converged
@@ -260,8 +263,60 @@ bo_status bo_set_timing(bo_sim* sim, int enabled);
 enum { BO_PRECISION_FP64 = 0, BO_PRECISION_MIXED = 1 };
 bo_status bo_set_precision(bo_sim* sim, int precision);
 bo_status bo_get_precision(const bo_sim* sim, int* precision);
-bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* ms_total,
-                        long long* launches, int* count);
+/* Learned correction of the preconditioner, an extension of the ILU(0)-
+ * preconditioned BiCGStab of Section 2.3.1.  With the stage on, every
+ * preconditioner application inside BiCGStab becomes
+ *     z = M^-1 r + delta(r),  delta_c = g sigma_c N(f_c),
+ * N a 66 -> 128 -> 128 -> 3 ReLU MLP of the cell's normalised Jacobian row
+ * (diagonal block and the -x, +x, -y, +y, -z, +z blocks, each entry
+ * A[e][v] sigma_nb[v] / rho_e with sigma = (1e6 Pa, 0.05, 0.05 for s_g or 5
+ * for r_go) and rho_e = max_v |A_cc[e][v]| sigma_c[v]) and of its residual
+ * r_e / (rho_e g), g = sqrt(mean_c sum_e (r_e / rho_e)^2); delta = 0 when
+ * g = 0.  Inference runs on the tensor cores (BF16 weights and activations,
+ * FP32 accumulation).  A solve that fails with the stage is repeated with
+ * plain ILU(0) (counted as a fallback).
+ *
+ * Parameters: BO_LEARN_NPARAM values, flat, in the order W1[128][66],
+ * b1[128], W2[128][128], b2[128], W3[3][128], b3[3] (row-major, h = W x + b).
+ * Training (FP32, on the device) minimises ||r - A (M^-1 r + delta(r))||^2 /
+ * ||r||^2 with Adam over residuals the solver produces, A being the
+ * reservoir Jacobian of the last assembly (the well coupling is left out). */
+#define BO_LEARN_NPARAM 25475
+typedef struct {
+    int samples;    /* residuals kept per linear solve (the first iterations'), 1..64 */
+    int epochs;     /* passes over them after each solve, 1..100 */
+    double lr;      /* Adam step size, 0 < lr < 1 */
+} bo_learn_opts;
+typedef struct {
+    long long systems;      /* linear systems trained on */
+    long long steps;        /* Adam steps */
+    long long fallbacks;    /* solves repeated with plain ILU(0) */
+    double first_loss;      /* mean loss over the first epoch on the first system (-1: none) */
+    double last_loss;       /* mean loss over the last epoch on the last system (-1: none) */
+    double train_ms;        /* host wall time spent training */
+} bo_learn_report;
+
+/* Parameters from / to host doubles (rounded to FP32 on the device); nparam
+ * must be BO_LEARN_NPARAM.  Setting them resets the Adam state. */
+bo_status bo_learn_set_params(bo_sim* sim, const double* theta, int nparam);
+bo_status bo_learn_get_params(bo_sim* sim, double* theta, int nparam);
+/* Stage on (1) or off (0) inside BiCGStab (bo_solve, bo_step); re-records the
+ * solver graphs.  Requires parameters. */
+bo_status bo_learn_enable(bo_sim* sim, int on);
+/* Online training: with opts non-NULL every later linear solve (bo_solve,
+ * bo_step) keeps its first opts->samples BiCGStab residuals and then takes
+ * opts->epochs Adam passes over them on that system; NULL turns it off.
+ * Requires parameters; BO_ERR_INVALID_ARG for values out of range. */
+bo_status bo_learn_online(bo_sim* sim, const bo_learn_opts* opts);
+bo_status bo_learn_get_report(const bo_sim* sim, bo_learn_report* report);
+/* delta(r) on the last assembly with the tensor-core kernel; r, delta are
+ * [3n] host arrays in cell-major order.  Requires a factorisation of the
+ * last assembly and parameters. */
+bo_status bo_learn_delta(bo_sim* sim, const double* r, double* delta);
+/* One FP32 training pass on the last assembly and factorisation for the
+ * host residual r [3n]: *loss (may be NULL) and the gradient grad
+ * [BO_LEARN_NPARAM] (may be NULL); parameters are not changed. */
+bo_status bo_learn_loss_grad(bo_sim* sim, const double* r, double* loss, double* grad);
 
 /* Self-test of failure detection: runs the bounded device-side wait of the
  * wavefront sweeps on a face slot that nothing ever writes.  The wait runs

@@ -54,6 +54,18 @@ class BoSolveReport(ctypes.Structure):
 
 PRECISION = {"fp64": 0, "mixed": 1}
 
+LEARN_NPARAM = 25475
+
+
+class BoLearnOpts(ctypes.Structure):
+    _fields_ = [("samples", c_int), ("epochs", c_int), ("lr", c_double)]
+
+
+class BoLearnReport(ctypes.Structure):
+    _fields_ = [("systems", ctypes.c_longlong), ("steps", ctypes.c_longlong),
+                ("fallbacks", ctypes.c_longlong), ("first_loss", c_double),
+                ("last_loss", c_double), ("train_ms", c_double)]
+
 
 class BoStepReport(ctypes.Structure):
     _fields_ = [("newton_its", c_int), ("lin_its", c_int), ("cuts", c_int),
@@ -88,6 +100,13 @@ _SIGS = {
     "bo_set_step_control": [P, c_double],
     "bo_set_timing": [P, c_int],
     "bo_set_precision": [P, c_int],
+    "bo_learn_set_params": [P, P, c_int],
+    "bo_learn_get_params": [P, P, c_int],
+    "bo_learn_enable": [P, c_int],
+    "bo_learn_online": [P, P],
+    "bo_learn_get_report": [P, P],
+    "bo_learn_delta": [P, P, P],
+    "bo_learn_loss_grad": [P, P, P, P],
     "bo_get_precision": [P, P],
     "bo_get_timing": [P, c_int, P, P, P, P],
     "bo_selftest_bounded_wait": [P, P],

@@ -2,6 +2,7 @@
 // system export used for checking, and the host Newton loop of bo_step
 // (arXiv 1910.06059 Section 2.3: Newton-Raphson on Eq. linsystem with
 // Appleyard chop, variable switching and time-step cutting).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -74,7 +75,11 @@ static void free_all(bo_sim* s) {
                     s->d_props, s->d_R, s->d_A, s->d_P, s->d_face, s->d_cellcon, s->d_wells,
                     s->d_con_cell, s->d_con_wi, s->d_wB, s->d_wC, s->d_b, s->d_xs, s->d_r,
                     s->d_rh, s->d_pk, s->d_v, s->d_s, s->d_t, s->d_ph, s->d_sh, s->d_part,
-                    s->d_ks, s->d_ns, s->d_sweep_sync, s->d_P32, s->d_r32, s->d_y32};
+                    s->d_ks, s->d_ns, s->d_sweep_sync, s->d_P32, s->d_r32, s->d_y32,
+                    s->d_ml_theta, s->d_ml_grad, s->d_ml_m, s->d_ml_v, s->d_ml_wbf,
+                    s->d_ml_feat, s->d_ml_featf, s->d_ml_cell, s->d_ml_part, s->d_ml_delta,
+                    s->d_ml_u, s->d_ml_z0, s->d_ml_e, s->d_ml_dd, s->d_ml_scal, s->d_ml_count,
+                    s->d_ml_samples};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->h_ns) cudaFreeHost(s->h_ns);
@@ -106,6 +111,33 @@ static void assemble_and_norms(bo_sim* s, double dt) {
     s->dt_last = dt;
 }
 
+// Online training on the residuals the last solve stored: opts epochs of
+// one Adam step per residual on this system.
+static void learn_online_step(bo_sim* s) {
+    int cnt = 0;
+    BO_CUDA(cudaMemcpyAsync(&cnt, s->d_ml_count, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+    cnt = std::min(cnt, s->ml_cap);
+    if (cnt <= 0) return;
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t N = 3 * (size_t)s->geo.n;
+    double first = 0.0, last = 0.0;
+    for (int ep = 0; ep < s->ml_epochs; ++ep)
+        for (int j = 0; j < cnt; ++j) {
+            const double L = learn_loss_grad(s, s->d_ml_samples + (size_t)j * N);
+            if (ep == 0) first += L;
+            if (ep == s->ml_epochs - 1) last += L;
+            learn_adam(s, s->ml_lr);
+            s->ml_steps += 1;
+        }
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+    if (s->ml_first_loss < 0.0) s->ml_first_loss = first / cnt;
+    s->ml_last_loss = last / cnt;
+    s->ml_systems += 1;
+    s->ml_train_ms +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 // Linear solve of the last assembly; returns the LS_* status.
 static void check_timeout(bo_sim* s) {
     if (sweep_timeout(s)) {
@@ -127,8 +159,17 @@ static int solve_linear(bo_sim* s, double tol, int maxit, int* its) {
         return LS_BREAKDOWN;
     }
     s->factored = true;
-    int st = run_bicgstab(s, tol, maxit, its);
+    int st = run_bicgstab(s, tol, maxit, its, true);
     check_timeout(s);
+    if (st != LS_OK && s->ml_on) {
+        // the learned stage failed on this system: repeat with plain ILU(0)
+        s->ml_fallbacks += 1;
+        int its2 = 0;
+        st = run_bicgstab(s, tol, maxit, &its2, false);
+        check_timeout(s);
+        *its += its2;
+    }
+    if (s->ml_online) learn_online_step(s);
     launch_well_recover(s);
     s->solved = true;
     return st;
@@ -722,6 +763,128 @@ bo_status bo_get_precision(const bo_sim* s, int* precision) {
         need(s != nullptr && precision != nullptr, BO_ERR_INVALID_ARG,
              "bo_get_precision: NULL argument");
         *precision = s->mixed ? BO_PRECISION_MIXED : BO_PRECISION_FP64;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Learned preconditioner stage
+// ---------------------------------------------------------------------------
+bo_status bo_learn_set_params(bo_sim* s, const double* theta, int nparam) {
+    return guarded([&] {
+        need(s != nullptr && theta != nullptr, BO_ERR_INVALID_ARG, "bo_learn_set_params: NULL argument");
+        need(nparam == BO_LEARN_NPARAM, BO_ERR_INVALID_ARG,
+             "bo_learn_set_params: nparam must be BO_LEARN_NPARAM");
+        need(s->props_set, BO_ERR_STATE, "bo_learn_set_params: call bo_set_properties first");
+        for (int q = 0; q < nparam; ++q)
+            need(std::isfinite(theta[q]), BO_ERR_INVALID_ARG, "bo_learn_set_params: non-finite value");
+        sync(s);
+        learn_setup(s);
+        std::vector<float> f(theta, theta + nparam);
+        learn_set_params(s, f.data());
+        s->ml_params = true;
+    });
+}
+
+bo_status bo_learn_get_params(bo_sim* s, double* theta, int nparam) {
+    return guarded([&] {
+        need(s != nullptr && theta != nullptr, BO_ERR_INVALID_ARG, "bo_learn_get_params: NULL argument");
+        need(nparam == BO_LEARN_NPARAM, BO_ERR_INVALID_ARG,
+             "bo_learn_get_params: nparam must be BO_LEARN_NPARAM");
+        need(s->ml_params, BO_ERR_STATE, "bo_learn_get_params: no parameters set");
+        std::vector<float> f(nparam);
+        learn_get_params(s, f.data());
+        for (int q = 0; q < nparam; ++q) theta[q] = f[q];
+    });
+}
+
+bo_status bo_learn_enable(bo_sim* s, int on) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_learn_enable: sim is NULL");
+        need(!on || s->ml_params, BO_ERR_STATE, "bo_learn_enable: no parameters set");
+        if ((on != 0) == s->ml_on) return;
+        sync(s);
+        s->ml_on = on != 0;
+        build_graphs(s);
+        if (s->ml_on && s->assembled) enqueue_learn_features(s, s->stream);
+        sync(s);
+    });
+}
+
+bo_status bo_learn_online(bo_sim* s, const bo_learn_opts* o) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_learn_online: sim is NULL");
+        sync(s);
+        if (o == nullptr) {
+            if (!s->ml_online) return;
+            s->ml_online = false;
+            build_graphs(s);
+            return;
+        }
+        need(s->ml_params, BO_ERR_STATE, "bo_learn_online: no parameters set");
+        need(o->samples >= 1 && o->samples <= 64 && o->epochs >= 1 && o->epochs <= 100 &&
+                 o->lr > 0.0 && o->lr < 1.0,
+             BO_ERR_INVALID_ARG, "bo_learn_online: samples 1..64, epochs 1..100, 0 < lr < 1");
+        learn_setup_training(s);
+        if (s->ml_cap != o->samples) {
+            if (s->d_ml_samples) cudaFree(s->d_ml_samples);
+            s->d_ml_samples = nullptr;
+            dalloc(&s->d_ml_samples, (size_t)o->samples * 3 * s->geo.n);
+            s->ml_cap = o->samples;
+        }
+        s->ml_epochs = o->epochs;
+        s->ml_lr = o->lr;
+        s->ml_online = true;
+        build_graphs(s);
+        if (s->assembled) enqueue_learn_features(s, s->stream);
+        sync(s);
+    });
+}
+
+bo_status bo_learn_get_report(const bo_sim* s, bo_learn_report* r) {
+    return guarded([&] {
+        need(s != nullptr && r != nullptr, BO_ERR_INVALID_ARG, "bo_learn_get_report: NULL argument");
+        r->systems = s->ml_systems;
+        r->steps = s->ml_steps;
+        r->fallbacks = s->ml_fallbacks;
+        r->first_loss = s->ml_first_loss;
+        r->last_loss = s->ml_last_loss;
+        r->train_ms = s->ml_train_ms;
+    });
+}
+
+bo_status bo_learn_delta(bo_sim* s, const double* r, double* delta) {
+    return guarded([&] {
+        need(s != nullptr && r != nullptr && delta != nullptr, BO_ERR_INVALID_ARG,
+             "bo_learn_delta: NULL argument");
+        need(s->ml_params, BO_ERR_STATE, "bo_learn_delta: no parameters set");
+        need(s->assembled && s->factored, BO_ERR_STATE, "bo_learn_delta: no factorisation");
+        upload_aos3(s, r, s->d_b);
+        enqueue_learn_features(s, s->stream);
+        BO_CUDA(cudaMemsetAsync(s->d_t, 0, sizeof(double) * 3 * s->geo.n, s->stream));
+        enqueue_learn_apply(s, s->stream, s->d_b, s->d_t, nullptr);
+        download_aos3(s, s->d_t, delta);
+    });
+}
+
+bo_status bo_learn_loss_grad(bo_sim* s, const double* r, double* loss, double* grad) {
+    return guarded([&] {
+        need(s != nullptr && r != nullptr, BO_ERR_INVALID_ARG, "bo_learn_loss_grad: NULL argument");
+        need(s->ml_params, BO_ERR_STATE, "bo_learn_loss_grad: no parameters set");
+        need(s->assembled && s->factored, BO_ERR_STATE, "bo_learn_loss_grad: no factorisation");
+        learn_setup_training(s);
+        upload_aos3(s, r, s->d_b);
+        enqueue_learn_features(s, s->stream);
+        learn_clear_grad(s);
+        const double L = learn_loss_grad(s, s->d_b);
+        check_timeout(s);
+        if (loss) *loss = L;
+        if (grad) {
+            std::vector<float> g(BO_LEARN_NPARAM);
+            learn_get_grad(s, g.data());
+            for (int q = 0; q < BO_LEARN_NPARAM; ++q) grad[q] = g[q];
+        }
+        learn_clear_grad(s);
+        sync(s);
     });
 }
 

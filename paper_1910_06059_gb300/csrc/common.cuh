@@ -141,6 +141,32 @@ struct bo_sim {
     bo::NewtonStatus* h_ns = nullptr;   // pinned
     bo::KrylovScalars* h_ks = nullptr;  // pinned
 
+    // learned preconditioner stage (learned.cu)
+    float* d_ml_theta = nullptr;   // FP32 parameters (BO_LEARN_NPARAM)
+    float* d_ml_grad = nullptr;    // gradient accumulator
+    float* d_ml_m = nullptr;       // Adam moments
+    float* d_ml_v = nullptr;
+    void* d_ml_wbf = nullptr;      // BF16 weight image of the tensor-core kernel
+    void* d_ml_feat = nullptr;     // [n][64] BF16 block features of the last factorisation
+    float* d_ml_featf = nullptr;   // [n][64] FP32 block features (training only)
+    float4* d_ml_cell = nullptr;   // [n] (1/rho_0, 1/rho_1, 1/rho_2, sigma_x)
+    double* d_ml_part = nullptr;   // reduction partials
+    double *d_ml_delta = nullptr, *d_ml_u = nullptr, *d_ml_z0 = nullptr, *d_ml_e = nullptr,
+           *d_ml_dd = nullptr;     // training vectors (3n)
+    double* d_ml_scal = nullptr;   // training scalars
+    int* d_ml_count = nullptr;     // samples stored by the last solve
+    double* d_ml_samples = nullptr;  // [cap][3n] residual samples
+    int ml_cap = 0;
+    int ml_adam_t = 0;
+    bool ml_params = false;        // parameters set
+    bool ml_on = false;            // the stage runs inside BiCGStab
+    bool ml_online = false;        // collect residuals and train after each solve
+    int ml_epochs = 1;
+    double ml_lr = 1e-3;
+    long long ml_systems = 0, ml_steps = 0, ml_fallbacks = 0;
+    double ml_first_loss = -1.0, ml_last_loss = -1.0, ml_train_ms = 0.0;
+    cudaGraphExec_t g_iter_ml = nullptr;
+
     // CUDA graphs of one BiCGStab iteration block and of the factorisation
     cudaGraphExec_t g_iter = nullptr;
     cudaGraphExec_t g_factor = nullptr;
@@ -186,9 +212,23 @@ void destroy_graphs(bo_sim* s);
 void launch_factor(bo_sim* s);                       // graph of level kernels
 void launch_precond(bo_sim* s, const double* r, double* z);
 void launch_op(bo_sim* s, const double* x, double* y);
-int run_bicgstab(bo_sim* s, double tol, int maxit, int* its);  // returns LS_*
+int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml);  // returns LS_*
 void launch_well_recover(bo_sim* s);
 void launch_newton_update(bo_sim* s, const bo_newton_opts& o);
+
+// learned preconditioner stage (learned.cu)
+void learn_setup(bo_sim* s);                 // parameters, features, kernel attributes
+void learn_setup_training(bo_sim* s);        // FP32 features and training vectors
+void learn_set_params(bo_sim* s, const float* host);
+void learn_get_params(bo_sim* s, float* host);
+void learn_get_grad(bo_sim* s, float* host);
+void learn_clear_grad(bo_sim* s);
+void enqueue_learn_features(bo_sim* s, cudaStream_t st);
+void enqueue_learn_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
+                         const KrylovScalars* ks);
+void enqueue_learn_collect(bo_sim* s, cudaStream_t st, const double* r, const KrylovScalars* ks);
+double learn_loss_grad(bo_sim* s, const double* r);   // one sample; returns the loss
+void learn_adam(bo_sim* s, double lr);
 
 int timer_id(bo_sim* s, const char* name);
 void timer_begin(bo_sim* s, int id);

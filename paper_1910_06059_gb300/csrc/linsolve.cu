@@ -538,7 +538,9 @@ void timers_flush(bo_sim* s) {
 // recorded as [fwd1, bwd1, spmv1, fwd2, bwd2, spmv2, blas] pairs.
 enum { TI_FWD = 0, TI_BWD = 1, TI_SPMV = 2, TI_BLAS = 3, TI_N = 4 };
 
-static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev) {
+// ml: the learned correction follows each preconditioner apply (z += delta);
+// collect: the residual of every iteration is stored as a training sample.
+static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev, bool ml, bool collect) {
     const int N = 3 * s->geo.n;
     KrylovScalars* ks = s->d_ks;
     double* part = s->d_part;
@@ -560,6 +562,9 @@ static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev) {
     rec(4);
     enqueue_bwd(s, st, s->d_ph, ks);
     rec(5);
+    rec(18);
+    if (ml) enqueue_learn_apply(s, st, s->d_pk, s->d_ph, ks);
+    rec(19);
     rec(6);
     enqueue_op<1>(s, st, s->d_ph, s->d_v, s->d_rh, ks);
     rec(7);
@@ -574,6 +579,9 @@ static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev) {
     rec(12);
     enqueue_bwd(s, st, s->d_sh, ks);
     rec(13);
+    rec(20);
+    if (ml) enqueue_learn_apply(s, st, s->d_s, s->d_sh, ks);
+    rec(21);
     rec(14);
     enqueue_op<2>(s, st, s->d_sh, s->d_t, s->d_s, ks);
     rec(15);
@@ -582,18 +590,20 @@ static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev) {
     k_xr_update<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_xs, s->d_ph, s->d_sh, s->d_s, s->d_t,
                                              s->d_r, s->d_rh, part, ks);
     rec(17);
+    if (collect) enqueue_learn_collect(s, st, s->d_r, ks);
     k_s5<<<1, 256, 0, st>>>(ks, part, VEC_GRID);
     BO_LAUNCH_CHECK("bicgstab iteration");
 }
 
-static constexpr int EV_PER_ITER = 18;
+static constexpr int EV_PER_ITER = 22;
 
-static cudaGraphExec_t capture(bo_sim* s, int iters, cudaEvent_t* ev) {
+static cudaGraphExec_t capture(bo_sim* s, int iters, cudaEvent_t* ev, bool ml, bool collect) {
     cudaStream_t cs;
     BO_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph;
     BO_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    for (int q = 0; q < iters; ++q) enqueue_iteration(s, cs, ev ? ev + q * EV_PER_ITER : nullptr);
+    for (int q = 0; q < iters; ++q)
+        enqueue_iteration(s, cs, ev ? ev + q * EV_PER_ITER : nullptr, ml, collect);
     BO_CUDA(cudaStreamEndCapture(cs, &graph));
     cudaGraphExec_t exec;
     BO_CUDA(cudaGraphInstantiate(&exec, graph, 0));
@@ -608,6 +618,7 @@ static cudaGraphExec_t capture_factor(bo_sim* s) {
     cudaGraph_t graph;
     BO_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     enqueue_factor(s, cs, factor_bad(s));
+    if (s->ml_on || s->ml_online) enqueue_learn_features(s, cs);
     BO_CUDA(cudaStreamEndCapture(cs, &graph));
     cudaGraphExec_t exec;
     BO_CUDA(cudaGraphInstantiate(&exec, graph, 0));
@@ -619,14 +630,16 @@ static cudaGraphExec_t capture_factor(bo_sim* s) {
 void build_graphs(bo_sim* s) {
     destroy_graphs(s);
     s->g_factor = capture_factor(s);
-    s->g_iter = capture(s, s->iters_per_graph, nullptr);
+    s->g_iter = capture(s, s->iters_per_graph, nullptr, false, s->ml_online);
+    if (s->ml_on) s->g_iter_ml = capture(s, s->iters_per_graph, nullptr, true, s->ml_online);
 }
 
 void destroy_graphs(bo_sim* s) {
     if (s->g_iter) cudaGraphExecDestroy(s->g_iter);
     if (s->g_factor) cudaGraphExecDestroy(s->g_factor);
     if (s->g_iter_timed) cudaGraphExecDestroy(s->g_iter_timed);
-    s->g_iter = s->g_factor = s->g_iter_timed = nullptr;
+    if (s->g_iter_ml) cudaGraphExecDestroy(s->g_iter_ml);
+    s->g_iter = s->g_factor = s->g_iter_timed = s->g_iter_ml = nullptr;
     for (cudaEvent_t e : s->iter_events) cudaEventDestroy(e);
     s->iter_events.clear();
 }
@@ -635,7 +648,7 @@ static void ensure_timed_graph(bo_sim* s) {
     if (s->g_iter_timed) return;
     s->iter_events.resize((size_t)EV_PER_ITER * s->iters_per_graph);
     for (auto& e : s->iter_events) BO_CUDA(cudaEventCreate(&e));
-    s->g_iter_timed = capture(s, s->iters_per_graph, s->iter_events.data());
+    s->g_iter_timed = capture(s, s->iters_per_graph, s->iter_events.data(), s->ml_on, s->ml_online);
 }
 
 
@@ -669,6 +682,7 @@ static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* pre
     cudaStream_t st = s->stream;
     const int t_fwd = timer_id(s, "ilu_fwd_sweep"), t_bwd = timer_id(s, "ilu_bwd_sweep");
     const int t_spmv = timer_id(s, "spmv_wells"), t_blas = timer_id(s, "blas1_fused");
+    const int t_ml = s->ml_on ? timer_id(s, "learned_stage") : -1;
     const int left = s->h_ks->maxit - s->h_ks->it;
     for (int guard = 0; guard < left + 2; guard += s->iters_per_graph) {
         BO_CUDA(cudaGraphLaunch(g, st));
@@ -688,6 +702,7 @@ static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* pre
                 };
                 add(t_fwd, 2, 3);
                 add(t_bwd, 4, 5);
+                if (t_ml >= 0) add(t_ml, 18, 19);
                 add(t_spmv, 6, 7);
                 add(t_blas, 0, 1);
                 add(t_blas, 8, 9);
@@ -695,6 +710,7 @@ static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* pre
                 if (second_half) {
                     add(t_fwd, 10, 11);
                     add(t_bwd, 12, 13);
+                    if (t_ml >= 0) add(t_ml, 20, 21);
                     add(t_spmv, 14, 15);
                 }
                 add(t_blas, 16, 17);
@@ -705,7 +721,7 @@ static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* pre
     }
 }
 
-int run_bicgstab(bo_sim* s, double tol, int maxit, int* its) {
+int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml) {
     const int n = s->geo.n, N = 3 * n;
     cudaStream_t st = s->stream;
     // right-hand side of the reduced system
@@ -713,14 +729,19 @@ int run_bicgstab(bo_sim* s, double tol, int maxit, int* its) {
     if (s->nw > 0) k_rhs_wells<<<s->nw, 128, 0, st>>>(n, s->d_wells, s->d_con_cell, s->d_wC, s->d_b);
     k_krylov_init<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b, s->d_xs, s->d_r, s->d_rh,
                                                s->d_pk, s->d_v, s->d_part);
+    // the learned stage (like the FP32 sweeps) is not the same linear map at
+    // every application: cycles stop at the inner target, the true residual decides
+    const bool ml = use_ml && s->ml_on;
     k_s_setup<<<1, 256, 0, st>>>(s->d_ks, s->d_part, VEC_GRID, tol, maxit,
-                                 s->mixed ? MIXED_INNER : 0.0);
+                                 (s->mixed || ml) ? MIXED_INNER : 0.0);
     BO_LAUNCH_CHECK("bicgstab setup");
+    if (s->ml_online) BO_CUDA(cudaMemsetAsync(s->d_ml_count, 0, sizeof(int), st));
     s->h_ks->it = 0;
     s->h_ks->maxit = maxit;
-    const bool timed = s->timing;
+    // the timed graph carries the configured stage; a fallback solve runs untimed
+    const bool timed = s->timing && ml == s->ml_on;
     if (timed) ensure_timed_graph(s);
-    cudaGraphExec_t g = timed ? s->g_iter_timed : s->g_iter;
+    cudaGraphExec_t g = timed ? s->g_iter_timed : (ml ? s->g_iter_ml : s->g_iter);
     const int t_check = timer_id(s, "true_residual");
     int prev_it = 0;
     for (int round = 0;; ++round) {

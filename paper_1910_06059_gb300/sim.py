@@ -216,6 +216,46 @@ class Sim:
     def precision(self, name):
         call("bo_set_precision", self.h, L.PRECISION[name])
 
+    # -- learned preconditioner stage ----------------------------------------
+    def learn_set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        call("bo_learn_set_params", self.h, ptr(theta), int(theta.size))
+
+    def learn_get_params(self):
+        theta = np.zeros(L.LEARN_NPARAM)
+        call("bo_learn_get_params", self.h, ptr(theta), L.LEARN_NPARAM)
+        return theta
+
+    def learn_enable(self, on=True):
+        call("bo_learn_enable", self.h, 1 if on else 0)
+
+    def learn_online(self, samples=16, epochs=1, lr=1e-3, on=True):
+        """Train after every later linear solve on its first `samples`
+        BiCGStab residuals (on=False turns it off)."""
+        if not on:
+            call("bo_learn_online", self.h, None)
+            return
+        o = L.BoLearnOpts(samples=int(samples), epochs=int(epochs), lr=float(lr))
+        call("bo_learn_online", self.h, ctypes.byref(o))
+
+    def learn_report(self):
+        r = L.BoLearnReport()
+        call("bo_learn_get_report", self.h, ctypes.byref(r))
+        return {k: getattr(r, k) for k, _ in L.BoLearnReport._fields_}
+
+    def learn_delta(self, r):
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1)
+        d = np.zeros_like(r)
+        call("bo_learn_delta", self.h, ptr(r), ptr(d))
+        return d
+
+    def learn_loss_grad(self, r):
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1)
+        loss = ctypes.c_double()
+        g = np.zeros(L.LEARN_NPARAM)
+        call("bo_learn_loss_grad", self.h, ptr(r), ctypes.byref(loss), ptr(g))
+        return loss.value, g
+
     # -- timing --------------------------------------------------------------
     def set_timing(self, enabled: bool):
         call("bo_set_timing", self.h, 1 if enabled else 0)

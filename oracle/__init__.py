@@ -83,6 +83,7 @@ def lib():
         L.orc_get_dt_next.argtypes = [P]
         L.orc_get_dt_next.restype = d
         L.orc_set_dt_next.argtypes = [P, d]
+        L.orc_set_subdomains.argtypes = [P, i]
         _lib = L
     return _lib
 
@@ -276,6 +277,10 @@ class Oracle:
     @dt_next.setter
     def dt_next(self, v):
         lib().orc_set_dt_next(self.h, float(v))
+
+    def set_subdomains(self, ysub: int):
+        """Block-Jacobi ILU(0) over slabs of `ysub` cell rows in y (0: off)."""
+        lib().orc_set_subdomains(self.h, int(ysub))
 
     def step(self, dt, **opts):
         o = opts_array(**opts)

@@ -511,3 +511,50 @@ def test_newton_converges_fast_near_solution():
     k = next(q for q, v in enumerate(hist) if v < 1e-2)
     assert k + 1 < len(hist), hist
     assert hist[k + 1] <= 10 * hist[k] ** 1.8, hist
+
+
+def test_block_jacobi_ilu0_is_exact_per_subdomain_in_1d():
+    """Block-Jacobi ILU(0) (Section 2.5: one ILU(0) block per subdomain) on a
+    column of cells in y: each subdomain's matrix is block tridiagonal, so its
+    ILU(0) is its exact LU and the preconditioner is the inverse of the
+    block-diagonal part of A (a dense solve per subdomain)."""
+    m = make_model(1, 12, 1, 1e-13, 0.2, [], dy=15.0)
+    o = oracle.Oracle(m)
+    st = synth.random_state(m, seed_member=3, frac_sat=0.5)
+    o.set_state(*st)
+    o.begin_step()
+    o.assemble(0.5 * synth.DAY)
+    rp, ci, v, R = o.system()
+    D = bcsr_to_dense(rp, ci, v, o.n)
+    o.set_subdomains(4)
+    o.ilu0()
+    r = np.random.default_rng(1).standard_normal(3 * o.n)
+    z = o.ilu_apply(r)
+    for k in range(3):
+        sl = slice(12 * k, 12 * (k + 1))          # 4 cells x 3 unknowns
+        zk = np.linalg.solve(D[sl, sl], r[sl])
+        assert np.allclose(z[sl], zk, rtol=1e-10, atol=1e-10 * np.abs(zk).max())
+    # without subdomains the same column is one block tridiagonal system
+    o.set_subdomains(0)
+    o.ilu0()
+    assert np.allclose(o.ilu_apply(r), np.linalg.solve(D, r), rtol=1e-9,
+                       atol=1e-9 * np.abs(np.linalg.solve(D, r)).max())
+
+
+def test_block_jacobi_ilu0_stays_in_its_subdomain():
+    """A residual supported on one slab gives a preconditioned vector
+    supported on that slab only (no coupling between subdomains in M)."""
+    m = synth.small_model(5, 12, 3, wells="5spot", dz=3.0)
+    o = oracle.Oracle(m)
+    o.set_state(*synth.random_state(m, seed_member=2, frac_sat=0.5))
+    o.begin_step()
+    o.assemble(0.5 * synth.DAY)
+    o.set_subdomains(4)
+    o.ilu0()
+    n = o.n
+    j = (np.arange(n) // 5) % 12
+    r = np.zeros((n, 3))
+    r[j // 4 == 1] = np.random.default_rng(2).standard_normal(((j // 4 == 1).sum(), 3))
+    z = o.ilu_apply(r.reshape(-1)).reshape(n, 3)
+    assert np.all(z[j // 4 != 1] == 0.0)
+    assert np.abs(z[j // 4 == 1]).max() > 0

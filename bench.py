@@ -52,6 +52,7 @@ WORKLOADS = {
     1: "layered 60x220x85 black-oil, 5-spot wells, 10-day report steps",
     2: "Gaussian-random-field 100x100x50 black-oil, 5-spot wells, 5-day report steps",
 }
+YSUB_NAME = " as block-Jacobi over slabs of {} cell rows in y"
 LEARNED_NAME = (" + learned stage (66-128-128-3 MLP on BF16 tensor cores, trained online "
                 "on the first warm-up report step's solver residuals)")
 PRECISION_NAMES = {"fp64": "plain FP64 ILU0-BiCGStab",
@@ -106,9 +107,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3])
+    ap.add_argument("--members", type=int, default=256, help="ensemble members (config 3)")
+    ap.add_argument("--seq-sample", type=int, default=32,
+                    help="members stepped one at a time for the sequential comparison (config 3)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="ILU(0) preconditioner precision (mixed: FP32 factors and sweeps)")
+    ap.add_argument("--ysub", type=int, default=0,
+                    help="block-Jacobi ILU(0) over slabs of YSUB cell rows in y (multiple of 8)")
     ap.add_argument("--learned", action="store_true",
                     help="learned preconditioner stage: trained online during the first "
                          "--train-steps warm-up report steps, then on inside BiCGStab")
@@ -153,7 +159,8 @@ def model_for(config, grid=None):
     if grid:
         nx, ny, nz = (int(v) for v in grid.lower().split("x"))
         return synth.layered_model(nx, ny, nz, config=1, name=f"layered {nx}x{ny}x{nz}")
-    return {0: synth.config0, 1: synth.config1, 2: synth.config2}[config]()
+    return {0: synth.config0, 1: synth.config1, 2: synth.config2,
+            3: lambda: synth.config3_member(0)}[config]()
 
 
 class ClockSampler:
@@ -265,6 +272,8 @@ def run_gb300(args):
     dt = m["dt"] if args.report_days is None else args.report_days * 86400.0
     sim = Sim(m, stream=stream)
     sim.precision = args.precision
+    if args.ysub:
+        sim.subdomains = args.ysub
     sim.init_hydrostatic()
     if args.learned:
         import synth
@@ -374,9 +383,10 @@ def run_gb300(args):
         "dtype": ("f64" if args.precision == "fp64" else "f64+f32") + ("+bf16" if args.learned else ""),
         "data": "synthetic",
         "config": {"workload": (f"{workload_name(args, m)}, {PRECISION_NAMES[args.precision]}"
-                                f"{LEARNED_NAME if args.learned else ''}, "
+                                f"{LEARNED_NAME if args.learned else ''}"
+                                f"{YSUB_NAME.format(args.ysub) if args.ysub else ''}, "
                                 "Newton tol 1e-6"),
-                   "precision": args.precision,
+                   "precision": args.precision, "ysub": args.ysub,
                    "cells": n, "newton_tol": 1e-6, "linear_tol": 1e-3,
                    "l2": (f"inputs larger than L2 (Jacobian {504 * n / 1e6:.0f} MB, ILU data "
                           f"{504 * n / 1e6:.0f} MB per model)"),
@@ -465,10 +475,89 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_ensemble(args):
+    """Config 3: the ensemble of uneven members stepped together (batched
+    form), against the same members stepped one at a time on one stream."""
+    import torch
+    import synth
+    from paper_1910_06059_gb300 import Ensemble
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    models = synth.config3(args.members)
+    n = sum(m["nx"] * m["ny"] * m["nz"] for m in models)
+    dt = models[0]["dt"] if args.report_days is None else args.report_days * 86400.0
+    ens = Ensemble(models, streams=8)
+    ens.init_hydrostatic()
+    cand = (1, 4, 8, 16, 32, 64)
+    tune = ens.autotune(0.05 * 86400.0, candidates=cand)
+    for _ in range(args.warmup):
+        ens.step(dt)
+    torch.cuda.synchronize()
+    snap = [(s.get_state(), s.dt_next) for s in ens.members]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = []
+    for _ in range(args.steps):
+        _, r = ens.step(dt)
+        reps.append(r)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    clk = clocks.stop()
+    # the same first report step, members one at a time on one stream, on a
+    # sample of the members (largest and smallest mixed as in the ensemble)
+    k = min(args.seq_sample, len(models))
+    sample = ens.members[:k]
+    for s, (st, d) in zip(sample, snap[:k]):
+        s.set_state(*st)
+        s.dt_next = d
+    seq = Ensemble(sims=sample, streams=1)
+    seq.set_schedule(1, largest_first=False)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    seq.step(dt)
+    torch.cuda.synchronize()
+    sec_seq = time.perf_counter() - t1
+    seq.close()
+    cells_sample = sum(s.n for s in sample)
+    seq_value = cells_sample / sec_seq
+    value = n * args.steps / sec
+    lin = sum(r["lin_its"] for rs in reps for r in rs)
+    newton = sum(r["newton_its"] for rs in reps for r in rs)
+    out = {
+        "metric": "cell-steps/s at 1e-6 Newton tol: plain FP64 vs mixed/learned/batched",
+        "value": value, "unit": "cell-steps/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": (f"batched ensemble of {len(models)} members (nx, ny in 20..64, "
+                                f"nz in 5..16; {n} cells), {dt / 86400.0:g}-day report steps, "
+                                "plain FP64 ILU0-BiCGStab per member, Newton tol 1e-6"),
+                   "cells": n, "members": len(models),
+                   "schedule": tune["chosen"],
+                   "timing": "host clock between device-wide synchronisations (members run on "
+                             "up to 64 streams)",
+                   "l2": "members' Jacobians and ILU data together exceed L2",
+                   "parallelism": "single GPU"},
+        "clocks": clk,
+        "autotune_probe_s": tune,
+        "sequential": {"value": seq_value, "unit": "cell-steps/s",
+                       "sample": f"first report step of {k} members one at a time on one stream "
+                                 f"({cells_sample} cells, {sec_seq:.2f} s)"},
+        "iterations": {"newton": newton, "lin_its": lin},
+        "e2e": None, "roofline": None, "cpu_baseline": None,
+    }
+    print(json.dumps(out))
+    ens.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 3:
+        run_ensemble(args)
     else:
         run_gb300(args)
 

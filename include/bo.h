@@ -263,25 +263,39 @@ bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* m
 enum { BO_PRECISION_FP64 = 0, BO_PRECISION_MIXED = 1 };
 bo_status bo_set_precision(bo_sim* sim, int precision);
 bo_status bo_get_precision(const bo_sim* sim, int* precision);
+
+/* Block-Jacobi ILU(0), the parallel preconditioner of Section 2.5 (one
+ * ILU(0) block per subdomain), on one GPU: the grid is cut into slabs of
+ * ysub cell rows in y (the last slab may be shorter) and the factorisation
+ * leaves out every block that couples two slabs; the operator keeps them.
+ * The slabs' wavefronts then run side by side, so a sweep takes about
+ * nx + ysub + nz levels instead of nx + ny + nz.  ysub = 0 restores plain
+ * ILU(0).  ysub must be 0 or a positive multiple of 8 (the tile height of
+ * the sweeps); BO_ERR_INVALID_ARG otherwise.  Requires bo_set_properties;
+ * the factors of an earlier bo_factor are dropped (factor again). */
+bo_status bo_set_subdomains(bo_sim* sim, int ysub);
+bo_status bo_get_subdomains(const bo_sim* sim, int* ysub);
 /* Learned correction of the preconditioner, an extension of the ILU(0)-
  * preconditioned BiCGStab of Section 2.3.1.  With the stage on, every
  * preconditioner application inside BiCGStab becomes
- *     z = M^-1 r + delta(r),  delta_c = g sigma_c N(f_c),
- * N a 66 -> 128 -> 128 -> 3 ReLU MLP of the cell's normalised Jacobian row
+ *     z = M^-1 r + delta(r),  delta_c = sigma_c (W_c rhat_c),  W_c = N(f_c),
+ * N a 63 -> 128 -> 128 -> 9 ReLU MLP of the cell's normalised Jacobian row
  * (diagonal block and the -x, +x, -y, +y, -z, +z blocks, each entry
  * A[e][v] sigma_nb[v] / rho_e with sigma = (1e6 Pa, 0.05, 0.05 for s_g or 5
- * for r_go) and rho_e = max_v |A_cc[e][v]| sigma_c[v]) and of its residual
- * r_e / (rho_e g), g = sqrt(mean_c sum_e (r_e / rho_e)^2); delta = 0 when
- * g = 0.  Inference runs on the tensor cores (BF16 weights and activations,
- * FP32 accumulation).  A solve that fails with the stage is repeated with
- * plain ILU(0) (counted as a fallback).
+ * for r_go) and rho_e = max_v |A_cc[e][v]| sigma_c[v]); W_c[v][e] =
+ * N[3 v + e] acts on the row-scaled residual rhat_c[e] = r_c[e] / rho_e.
+ * The correction is linear in r, so for one Jacobian the preconditioner is
+ * one fixed linear map.  The network runs once per factorisation on the
+ * tensor cores (BF16 weights and activations, FP32 accumulation); each
+ * application is a per-cell 3x3 product.  A solve that fails with the
+ * stage is repeated with plain ILU(0) (counted as a fallback).
  *
- * Parameters: BO_LEARN_NPARAM values, flat, in the order W1[128][66],
- * b1[128], W2[128][128], b2[128], W3[3][128], b3[3] (row-major, h = W x + b).
+ * Parameters: BO_LEARN_NPARAM values, flat, in the order W1[128][63],
+ * b1[128], W2[128][128], b2[128], W3[9][128], b3[9] (row-major, h = W x + b).
  * Training (FP32, on the device) minimises ||r - A (M^-1 r + delta(r))||^2 /
  * ||r||^2 with Adam over residuals the solver produces, A being the
  * reservoir Jacobian of the last assembly (the well coupling is left out). */
-#define BO_LEARN_NPARAM 25475
+#define BO_LEARN_NPARAM 25865
 typedef struct {
     int samples;    /* residuals kept per linear solve (the first iterations'), 1..64 */
     int epochs;     /* passes over them after each solve, 1..100 */
@@ -317,6 +331,40 @@ bo_status bo_learn_delta(bo_sim* sim, const double* r, double* delta);
  * host residual r [3n]: *loss (may be NULL) and the gradient grad
  * [BO_LEARN_NPARAM] (may be NULL); parameters are not changed. */
 bo_status bo_learn_loss_grad(bo_sim* sim, const double* r, double* loss, double* grad);
+
+/* Ensembles (the batched form): many independent models of uneven size
+ * advanced together on one GPU.  Each member keeps its own Newton loop,
+ * time-step control and solver (Section 2.3 per member); the ensemble steps
+ * the members concurrently from a pool of host workers, each on its own CUDA
+ * stream, handing out members largest first (or in the given order).  The
+ * caller creates, initialises and destroys the members; the ensemble holds
+ * pointers to them and must be destroyed first.  A member is stepped by one
+ * worker at a time; while it is being stepped its stream is the worker's.
+ *
+ * bo_ensemble_create: count distinct members (bo_set_properties done),
+ *   `streams` concurrent workers (1..256); BO_ERR_INVALID_ARG / BO_ERR_STATE.
+ * bo_ensemble_set_schedule / get_schedule: workers (1..256) and order
+ *   (largest_first = 1: by decreasing cell count, 0: the members' order).
+ * bo_ensemble_step: one report step of length dt for every member, as
+ *   bo_step would take it; reports[count] and statuses[count] (each may be
+ *   NULL) receive each member's report and status; returns BO_OK if every
+ *   member succeeded, else the first failing member's status (its message is
+ *   not kept: call bo_step on that member alone to see it).
+ * bo_ensemble_autotune: times one probe report step of length dt_probe for
+ *   every candidate worker count (candidates[ncand], each 1..256) in both
+ *   orders, putting every member's state and step control back after each
+ *   probe, and keeps the fastest schedule whose probe succeeded;
+ *   seconds[2 * ncand] (may be NULL) receives the probe times, largest-first
+ *   order first.  BO_ERR_NOT_CONVERGED if no probe succeeded. */
+typedef struct bo_ensemble bo_ensemble;
+bo_status bo_ensemble_create(bo_sim* const* members, int count, int streams, bo_ensemble** out);
+bo_status bo_ensemble_set_schedule(bo_ensemble* ens, int streams, int largest_first);
+bo_status bo_ensemble_get_schedule(const bo_ensemble* ens, int* streams, int* largest_first);
+bo_status bo_ensemble_step(bo_ensemble* ens, double dt, const bo_newton_opts* opts,
+                           bo_step_report* reports, bo_status* statuses);
+bo_status bo_ensemble_autotune(bo_ensemble* ens, double dt_probe, const bo_newton_opts* opts,
+                               const int* candidates, int ncand, double* seconds);
+bo_status bo_ensemble_destroy(bo_ensemble* ens);
 
 /* Self-test of failure detection: runs the bounded device-side wait of the
  * wavefront sweeps on a face slot that nothing ever writes.  The wait runs

@@ -6,14 +6,16 @@ code with the CUDA path.
 
 The stage corrects the ILU(0) preconditioner of the linear solver (Section
 2.3.1 of arXiv 1910.06059: BiCGStab preconditioned by ILU(0)) with a small
-per-cell network:
+per-cell network that reads the cell's row of the Jacobian and returns a
+3x3 matrix acting on the cell's residual:
 
-    z = M^-1 r + delta(r),   delta_c = g * sigma_c * N(f_c)
+    z = M^-1 r + delta(r),   delta_c = sigma_c * (W_c rhat_c),   W_c = N(f_c)
 
-where N is a two-hidden-layer MLP (66 -> 128 -> 128 -> 3, ReLU) and f_c holds
-the cell's row of the Jacobian (diagonal block and six neighbour blocks) and
-its residual, normalised as below.  The definitions here are the ones the GPU
-kernels implement:
+N is a two-hidden-layer MLP (63 -> 128 -> 128 -> 9, ReLU), f_c the 63
+normalised entries of the cell's Jacobian row (diagonal block and six
+neighbour blocks), rhat_c the row-scaled residual.  The correction is linear
+in r, so for a given Jacobian the whole preconditioner is one fixed linear
+map, as BiCGStab requires.  Definitions (the GPU kernels implement the same):
 
 * unknown scales sigma_c = (1e6 Pa, 0.05, 0.05) for a saturated cell (x = s_g)
   and (1e6 Pa, 0.05, 5) for an undersaturated one (x = r_go);
@@ -21,10 +23,7 @@ kernels implement:
 * block features F_{c,b}[e][v] = A_{c,b}[e][v] sigma_{nb,v} / rho_{c,e} for the
   diagonal (b = 0, nb = c) and the six neighbours -x, +x, -y, +y, -z, +z
   (zero where the neighbour is missing);
-* residual features rhat_c[e] = r_c[e] / (rho_{c,e} g) with
-  g = sqrt(mean_c sum_e (r_c[e] / rho_{c,e})^2); delta = 0 when g = 0.
-
-The stage is positively homogeneous: delta(lambda r) = lambda delta(r).
+* rhat_c[e] = r_c[e] / rho_{c,e}; W_c[v][e] = N(f_c)[3 v + e].
 
 Training minimises, per sample (A, r), the squared residual of the corrected
 preconditioner against the reservoir Jacobian A:
@@ -38,8 +37,8 @@ from __future__ import annotations
 import numpy as np
 
 HIDDEN = 128
-NFEAT = 66
-NOUT = 3
+NFEAT = 63
+NOUT = 9
 SIGMA_P, SIGMA_S, SIGMA_SG, SIGMA_RGO = 1e6, 0.05, 0.05, 5.0
 
 # parameter tensors in the order of the flat parameter vector
@@ -142,21 +141,8 @@ def block_features(A7, nb, flag):
     return F.reshape(n, 63)
 
 
-def residual_scale(r, rho):
-    """g = sqrt(mean_c sum_e (r_c[e] / rho_c[e])^2)."""
-    return float(np.sqrt(np.sum((r / rho) ** 2) / r.shape[0]))
-
-
-def features(A7, nb, flag, r):
-    """([n, 66] features, g)."""
-    _, rho = scales(A7, flag)
-    g = residual_scale(r, rho)
-    rhat = r / (rho * g) if g > 0 else np.zeros_like(r)
-    return np.concatenate([block_features(A7, nb, flag), rhat], axis=1), g
-
-
 def mlp_forward(params, F):
-    """o[n, 3] and the activations needed by the backward pass."""
+    """o[n, 9] and the activations needed by the backward pass."""
     a1 = F @ params["W1"].T + params["b1"]
     h1 = np.maximum(a1, 0.0)
     a2 = h1 @ params["W2"].T + params["b2"]
@@ -166,7 +152,7 @@ def mlp_forward(params, F):
 
 
 def mlp_backward(params, cache, do):
-    """Parameter gradients for the upstream gradient do[n, 3]."""
+    """Parameter gradients for the upstream gradient do[n, 9]."""
     F, a1, h1, a2, h2 = cache
     grads = {"W3": do.T @ h2, "b3": do.sum(0)}
     dh2 = (do @ params["W3"]) * (a2 > 0)
@@ -178,25 +164,30 @@ def mlp_backward(params, cache, do):
     return grads
 
 
+def cell_matrices(params, A7, nb, flag):
+    """W[n, 3, 3] = N(f) per cell."""
+    o, _ = mlp_forward(params, block_features(A7, nb, flag))
+    return o.reshape(-1, 3, 3)
+
+
 def stage_delta(params, A7, nb, flag, r):
-    """delta[n, 3] = g sigma N(f)."""
-    F, g = features(A7, nb, flag, r)
-    if g == 0.0:
-        return np.zeros_like(r)
-    o, _ = mlp_forward(params, F)
-    return g * sigma(flag) * o
+    """delta[n, 3] = sigma * (W rhat)."""
+    sg, rho = scales(A7, flag)
+    W = cell_matrices(params, A7, nb, flag)
+    return sg * np.einsum("cve,ce->cv", W, r / rho)
 
 
 def loss_and_grad(params, A7, nb, flag, r, z0):
     """(L, grads) for one sample: residual r[n,3], ILU(0) result z0 = M^-1 r."""
-    F, g = features(A7, nb, flag, r)
-    sg = sigma(flag)
-    o, cache = mlp_forward(params, F)
-    delta = g * sg * o
+    sg, rho = scales(A7, flag)
+    o, cache = mlp_forward(params, block_features(A7, nb, flag))
+    W = o.reshape(-1, 3, 3)
+    rhat = r / rho
+    delta = sg * np.einsum("cve,ce->cv", W, rhat)
     e = r - apply_A(A7, nb, z0)
     u = e - apply_A(A7, nb, delta)
     rr = float(np.sum(r * r))
     L = float(np.sum(u * u)) / rr
     ddelta = -2.0 * apply_AT(A7, nb, u) / rr
-    do = g * sg * ddelta
-    return L, mlp_backward(params, cache, do)
+    dW = np.einsum("cv,ce->cve", sg * ddelta, rhat)
+    return L, mlp_backward(params, cache, dW.reshape(-1, 9))

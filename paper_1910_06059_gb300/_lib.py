@@ -54,7 +54,7 @@ class BoSolveReport(ctypes.Structure):
 
 PRECISION = {"fp64": 0, "mixed": 1}
 
-LEARN_NPARAM = 25475
+LEARN_NPARAM = 25865
 
 
 class BoLearnOpts(ctypes.Structure):
@@ -100,6 +100,14 @@ _SIGS = {
     "bo_set_step_control": [P, c_double],
     "bo_set_timing": [P, c_int],
     "bo_set_precision": [P, c_int],
+    "bo_set_subdomains": [P, c_int],
+    "bo_get_subdomains": [P, P],
+    "bo_ensemble_create": [P, c_int, c_int, P],
+    "bo_ensemble_set_schedule": [P, c_int, c_int],
+    "bo_ensemble_get_schedule": [P, P, P],
+    "bo_ensemble_step": [P, c_double, P, P, P],
+    "bo_ensemble_autotune": [P, c_double, P, P, c_int, P],
+    "bo_ensemble_destroy": [P],
     "bo_learn_set_params": [P, P, c_int],
     "bo_learn_get_params": [P, P, c_int],
     "bo_learn_enable": [P, c_int],

@@ -79,7 +79,7 @@ static void free_all(bo_sim* s) {
                     s->d_ml_theta, s->d_ml_grad, s->d_ml_m, s->d_ml_v, s->d_ml_wbf,
                     s->d_ml_feat, s->d_ml_featf, s->d_ml_cell, s->d_ml_part, s->d_ml_delta,
                     s->d_ml_u, s->d_ml_z0, s->d_ml_e, s->d_ml_dd, s->d_ml_scal, s->d_ml_count,
-                    s->d_ml_samples};
+                    s->d_ml_samples, s->d_ml_W};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->h_ns) cudaFreeHost(s->h_ns);
@@ -755,6 +755,29 @@ bo_status bo_set_precision(bo_sim* s, int precision) {
         reset_sweep_faces(s);
         build_graphs(s);
         sync(s);
+    });
+}
+
+bo_status bo_set_subdomains(bo_sim* s, int ysub) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_set_subdomains: sim is NULL");
+        need(ysub == 0 || (ysub > 0 && ysub % 8 == 0), BO_ERR_INVALID_ARG,
+             "bo_set_subdomains: ysub must be 0 or a positive multiple of 8");
+        need(s->props_set, BO_ERR_STATE, "bo_set_subdomains: call bo_set_properties first");
+        if (ysub == s->ysub) return;
+        sync(s);
+        s->ysub = ysub;
+        s->factored = false;   // the factors of the other partition are stale
+        reset_sweep_faces(s);
+        build_graphs(s);
+        sync(s);
+    });
+}
+
+bo_status bo_get_subdomains(const bo_sim* s, int* ysub) {
+    return guarded([&] {
+        need(s != nullptr && ysub != nullptr, BO_ERR_INVALID_ARG, "bo_get_subdomains: NULL argument");
+        *ysub = s->ysub;
     });
 }
 

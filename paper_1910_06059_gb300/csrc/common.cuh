@@ -150,6 +150,7 @@ struct bo_sim {
     void* d_ml_feat = nullptr;     // [n][64] BF16 block features of the last factorisation
     float* d_ml_featf = nullptr;   // [n][64] FP32 block features (training only)
     float4* d_ml_cell = nullptr;   // [n] (1/rho_0, 1/rho_1, 1/rho_2, sigma_x)
+    float* d_ml_W = nullptr;       // [9][n] per-cell matrices of the network
     double* d_ml_part = nullptr;   // reduction partials
     double *d_ml_delta = nullptr, *d_ml_u = nullptr, *d_ml_z0 = nullptr, *d_ml_e = nullptr,
            *d_ml_dd = nullptr;     // training vectors (3n)
@@ -172,6 +173,7 @@ struct bo_sim {
     cudaGraphExec_t g_factor = nullptr;
     cudaGraphExec_t g_iter_timed = nullptr;
     int iters_per_graph = 4;
+    int ysub = 0;                // block-Jacobi slabs of ysub cell rows in y (0: plain ILU(0))
 
     // timing
     bool timing = false;

@@ -1,0 +1,203 @@
+// Batched ensembles: many independent models (permeability realisations of
+// uneven size) advanced together on one GPU.  Each member keeps its own
+// Newton loop, time-step control, factorisation and BiCGStab graphs (the
+// method of arXiv 1910.06059 Section 2.3 per member); the ensemble runs the
+// members concurrently from a pool of host workers, each with its own CUDA
+// stream, so the small members' latency-bound kernels (wavefront sweeps of
+// nx + ny + nz levels, short vector kernels) overlap on the SMs instead of
+// running one member at a time.
+//
+// Schedule: members are handed out largest first (the longest jobs start
+// first, so the pool finishes together), or in the caller's order; the
+// number of concurrent streams and the order are picked by an autotuner that
+// times a short probe step of the real ensemble for each candidate and puts
+// the members' states back after each probe.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+struct bo_ensemble {
+    std::vector<bo_sim*> members;
+    std::vector<cudaStream_t> streams;
+    int active = 1;                  // streams in use
+    bool largest_first = true;
+    int device = 0;
+};
+
+namespace {
+
+struct Snapshot {
+    std::vector<double> p, sw, x, bhp;
+    std::vector<unsigned char> flag;
+    double dt_next = 0.0;
+};
+
+bo_status snapshot(bo_sim* m, Snapshot& s) {
+    const int n = m->geo.n;
+    s.p.resize(n);
+    s.sw.resize(n);
+    s.x.resize(n);
+    s.flag.resize(n);
+    s.bhp.resize(std::max(m->nw, 1));
+    bo_status st = bo_get_state(m, s.p.data(), s.sw.data(), s.x.data(), s.flag.data(), s.bhp.data());
+    if (st != BO_OK) return st;
+    return bo_get_step_control(m, &s.dt_next);
+}
+
+bo_status restore(bo_sim* m, const Snapshot& s) {
+    bo_status st = bo_set_state(m, s.p.data(), s.sw.data(), s.x.data(), s.flag.data(), s.bhp.data());
+    if (st != BO_OK) return st;
+    return bo_set_step_control(m, s.dt_next);
+}
+
+// One report step of every member with e->active workers; per-member
+// statuses and reports (either may be null).
+void run_step(bo_ensemble* e, double dt, const bo_newton_opts* opts, bo_step_report* reports,
+              bo_status* statuses) {
+    const int count = (int)e->members.size();
+    std::vector<int> order(count);
+    for (int q = 0; q < count; ++q) order[q] = q;
+    if (e->largest_first)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return e->members[a]->geo.n > e->members[b]->geo.n;
+        });
+    std::atomic<int> next{0};
+    const int nworkers = std::max(1, std::min(e->active, count));
+    auto work = [&](int w) {
+        cudaSetDevice(e->device);
+        cudaStream_t st = e->streams[w];
+        for (;;) {
+            const int q = next.fetch_add(1);
+            if (q >= count) break;
+            const int id = order[q];
+            bo_sim* m = e->members[id];
+            cudaStream_t own = m->stream;
+            m->stream = st;
+            bo_step_report rep{};
+            const bo_status s = bo_step(m, dt, opts, &rep);
+            m->stream = own;
+            if (reports) reports[id] = rep;
+            if (statuses) statuses[id] = s;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nworkers; ++w) pool.emplace_back(work, w);
+    work(0);
+    for (auto& t : pool) t.join();
+}
+
+}  // namespace
+
+extern "C" {
+
+bo_status bo_ensemble_create(bo_sim* const* members, int count, int streams, bo_ensemble** out) {
+    if (out == nullptr || members == nullptr || count < 1 || streams < 1 || streams > 256)
+        return BO_ERR_INVALID_ARG;
+    for (int q = 0; q < count; ++q)
+        if (members[q] == nullptr || !members[q]->props_set) return BO_ERR_STATE;
+    for (int q = 0; q < count; ++q)
+        for (int r = q + 1; r < count; ++r)
+            if (members[q] == members[r]) return BO_ERR_INVALID_ARG;
+    auto* e = new bo_ensemble();
+    e->members.assign(members, members + count);
+    cudaGetDevice(&e->device);
+    e->streams.resize(256, nullptr);
+    for (auto& s : e->streams) {
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            for (auto& t : e->streams)
+                if (t) cudaStreamDestroy(t);
+            delete e;
+            return BO_ERR_CUDA;
+        }
+    }
+    e->active = streams;
+    *out = e;
+    return BO_OK;
+}
+
+bo_status bo_ensemble_set_schedule(bo_ensemble* e, int streams, int largest_first) {
+    if (e == nullptr || streams < 1 || streams > 256) return BO_ERR_INVALID_ARG;
+    e->active = streams;
+    e->largest_first = largest_first != 0;
+    return BO_OK;
+}
+
+bo_status bo_ensemble_get_schedule(const bo_ensemble* e, int* streams, int* largest_first) {
+    if (e == nullptr) return BO_ERR_INVALID_ARG;
+    if (streams) *streams = e->active;
+    if (largest_first) *largest_first = e->largest_first ? 1 : 0;
+    return BO_OK;
+}
+
+bo_status bo_ensemble_step(bo_ensemble* e, double dt, const bo_newton_opts* opts,
+                           bo_step_report* reports, bo_status* statuses) {
+    if (e == nullptr || !(dt > 0.0)) return BO_ERR_INVALID_ARG;
+    const int count = (int)e->members.size();
+    std::vector<bo_status> st(count, BO_OK);
+    run_step(e, dt, opts, reports, st.data());
+    bo_status first = BO_OK;
+    for (int q = 0; q < count; ++q) {
+        if (statuses) statuses[q] = st[q];
+        if (first == BO_OK && st[q] != BO_OK) first = st[q];
+    }
+    return first;
+}
+
+bo_status bo_ensemble_autotune(bo_ensemble* e, double dt_probe, const bo_newton_opts* opts,
+                               const int* candidates, int ncand, double* seconds) {
+    if (e == nullptr || candidates == nullptr || ncand < 1 || !(dt_probe > 0.0))
+        return BO_ERR_INVALID_ARG;
+    for (int c = 0; c < ncand; ++c)
+        if (candidates[c] < 1 || candidates[c] > 256) return BO_ERR_INVALID_ARG;
+    const int count = (int)e->members.size();
+    std::vector<Snapshot> snap(count);
+    for (int q = 0; q < count; ++q) {
+        bo_status s = snapshot(e->members[q], snap[q]);
+        if (s != BO_OK) return s;
+    }
+    double best = 1e300;
+    int best_w = e->active;
+    bool best_lf = e->largest_first;
+    for (int order = 0; order < 2; ++order) {
+        for (int c = 0; c < ncand; ++c) {
+            e->active = candidates[c];
+            e->largest_first = order == 0;
+            std::vector<bo_status> st(count, BO_OK);
+            const auto t0 = std::chrono::steady_clock::now();
+            run_step(e, dt_probe, opts, nullptr, st.data());
+            const double sec =
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (seconds) seconds[order * ncand + c] = sec;
+            for (int q = 0; q < count; ++q) {
+                bo_status s = restore(e->members[q], snap[q]);
+                if (s != BO_OK) return s;
+            }
+            bool ok = true;
+            for (int q = 0; q < count; ++q) ok = ok && st[q] == BO_OK;
+            if (ok && sec < best) {
+                best = sec;
+                best_w = candidates[c];
+                best_lf = order == 0;
+            }
+        }
+    }
+    e->active = best_w;
+    e->largest_first = best_lf;
+    return best < 1e300 ? BO_OK : BO_ERR_NOT_CONVERGED;
+}
+
+bo_status bo_ensemble_destroy(bo_ensemble* e) {
+    if (e == nullptr) return BO_ERR_INVALID_ARG;
+    for (auto& s : e->streams)
+        if (s) cudaStreamDestroy(s);
+    delete e;
+    return BO_OK;
+}
+
+}  // extern "C"

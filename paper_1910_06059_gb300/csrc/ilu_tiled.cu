@@ -159,9 +159,10 @@ k_factor_tiled(TileArgs a, const double* __restrict__ A, double* __restrict__ P,
     if (!lane_tile(a, L)) return;
     const int n = a.g.n, nx = a.g.nx;
     const int lane = threadIdx.x & 31;
-    const bool feedJ = L.jj == TJ - 1 && L.J + 1 < a.NJ;
+    const bool feedJ = L.jj == TJ - 1 && L.J + 1 < a.NJ && !ycut(a, (L.J + 1) * TJ);
     const bool feedK = L.kk == TK - 1 && L.K + 1 < a.NK;
-    const bool hasJ = L.j > 0, hasK = L.k > 0;
+    const bool hasJ = L.j > 0 && !ycut(a, L.j), hasK = L.k > 0;
+    const bool upJ = !ycut(a, L.j + 1);   // the +y coupling stays in the slab
     double Ux[9], Uy[9], Uz[9];   // this lane's scaled upper blocks of its last cell
 #pragma unroll
     for (int e = 0; e < 9; ++e) Ux[e] = Uy[e] = Uz[e] = 0.0;
@@ -182,7 +183,7 @@ k_factor_tiled(TileArgs a, const double* __restrict__ A, double* __restrict__ P,
         for (int e = 0; e < 9; ++e) {
             D[e] = act ? A[(size_t)(NB_DIAG * 9 + e) * n + c] : (e % 4 == 0 ? 1.0 : 0.0);
             Bx[e] = act ? A[(size_t)(NB_MX * 9 + e) * n + c] : 0.0;
-            By[e] = act ? A[(size_t)(NB_MY * 9 + e) * n + c] : 0.0;
+            By[e] = act && hasJ ? A[(size_t)(NB_MY * 9 + e) * n + c] : 0.0;
             Bz[e] = act ? A[(size_t)(NB_MZ * 9 + e) * n + c] : 0.0;
         }
         __syncwarp();
@@ -195,7 +196,7 @@ k_factor_tiled(TileArgs a, const double* __restrict__ A, double* __restrict__ P,
 #pragma unroll
         for (int e = 0; e < 9; ++e) {
             Bx[e] = act ? A[(size_t)(NB_PX * 9 + e) * n + c] : 0.0;
-            By[e] = act ? A[(size_t)(NB_PY * 9 + e) * n + c] : 0.0;
+            By[e] = act && upJ ? A[(size_t)(NB_PY * 9 + e) * n + c] : 0.0;
             Bz[e] = act ? A[(size_t)(NB_PZ * 9 + e) * n + c] : 0.0;
         }
         double Ux2[9], Uy2[9], Uz2[9];
@@ -243,10 +244,12 @@ k_factor_lower(TileArgs a, const double* __restrict__ A, double* __restrict__ P)
 #pragma unroll
         for (int e = 0; e < 9; ++e) Di[e] = act ? P[(size_t)e * a.NP + idx] : 0.0;
         const int lowb[3] = {NB_MX, NB_MY, NB_MZ};
+        const bool keep[3] = {true, !ycut(a, j), true};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
 #pragma unroll
-            for (int e = 0; e < 9; ++e) B[e] = act ? A[(size_t)(lowb[d] * 9 + e) * a.g.n + c] : 0.0;
+            for (int e = 0; e < 9; ++e)
+                B[e] = act && keep[d] ? A[(size_t)(lowb[d] * 9 + e) * a.g.n + c] : 0.0;
             mm3t(Di, B, S);
 #pragma unroll
             for (int e = 0; e < 9; ++e) P[(size_t)((1 + d) * 9 + e) * a.NP + idx] = S[e];
@@ -373,9 +376,9 @@ k_fwd_tiled(TileArgs a, const double* __restrict__ P, const double* __restrict__
     const RowTile R = row_tile(a);
     const int n = a.g.n, nx = a.g.nx;
     const int rw = R.row;
-    const bool feedJ = R.valid && R.jj == TJ - 1 && R.J + 1 < a.NJ;
+    const bool feedJ = R.valid && R.jj == TJ - 1 && R.J + 1 < a.NJ && !ycut(a, (R.J + 1) * TJ);
     const bool feedK = R.valid && R.kk == TK - 1 && R.K + 1 < a.NK;
-    const bool hasJ = R.j > 0, hasK = R.k > 0;
+    const bool hasJ = R.j > 0 && !ycut(a, R.j), hasK = R.k > 0;
     const bool takeJ = R.valid && hasJ && R.jj == 0, takeK = R.valid && hasK && R.kk == 0;
     const int l0 = R.jj + R.kk;                   // first level of this line (i = 0)
     const size_t NP = a.NP;
@@ -481,9 +484,9 @@ k_bwd_tiled(TileArgs a, const double* __restrict__ P, double* __restrict__ z,
     const RowTile R = row_tile(a);
     const int n = a.g.n, nx = a.g.nx;
     const int rw = R.row;
-    const bool feedJ = R.valid && R.jj == 0 && R.J > 0;
+    const bool feedJ = R.valid && R.jj == 0 && R.J > 0 && !ycut(a, R.J * TJ);
     const bool feedK = R.valid && R.kk == 0 && R.K > 0;
-    const bool hasJ = R.j + 1 < a.g.ny, hasK = R.k + 1 < a.g.nz;
+    const bool hasJ = R.j + 1 < a.g.ny && !ycut(a, R.j + 1), hasK = R.k + 1 < a.g.nz;
     const bool takeJ = R.valid && hasJ && R.jj == TJ - 1, takeK = R.valid && hasK && R.kk == TK - 1;
     const int l0 = R.jj + R.kk;
     const size_t NP = a.NP;
@@ -605,6 +608,7 @@ TileArgs tile_args(const bo_sim* s) {
     a.NL = s->geo.nx + TJ + TK - 2;
     a.NP = (size_t)a.T * a.NL * 32;
     a.err = s->d_sweep_sync + 2;
+    a.ysub = s->ysub;
     return a;
 }
 

@@ -1,20 +1,22 @@
 // Learned correction of the ILU(0) preconditioner (an extension of the
 // ILU(0)-preconditioned BiCGStab of arXiv 1910.06059 Section 2.3.1):
-//     z = M^-1 r + delta(r),  delta_c = g * sigma_c * N(f_c),
-// N: 66 -> 128 -> 128 -> 3 ReLU MLP, f_c = [63 normalised entries of the
+//     z = M^-1 r + delta(r),  delta_c = sigma_c * (W_c rhat_c),  W_c = N(f_c)
+// N: 63 -> 128 -> 128 -> 9 ReLU MLP of the 63 normalised entries of the
 // cell's Jacobian row (diagonal block, then the -x, +x, -y, +y, -z, +z
-// blocks), 3 normalised residual entries]:
+// blocks); W_c[v][e] = N[3 v + e] is a 3x3 matrix acting on the cell's
+// row-scaled residual:
 //     sigma_c      = (1e6 Pa, 0.05, 0.05 | 5)   (x = s_g | r_go)
 //     rho_{c,e}    = max_v |A_cc[e][v]| sigma_{c,v}
 //     F_{c,b}[e,v] = A_{c,b}[e][v] sigma_{nb,v} / rho_{c,e}
-//     rhat_c[e]    = r_c[e] / (rho_{c,e} g),  g = sqrt(mean_c sum_e (r_c[e]/rho_{c,e})^2)
-// so delta(lambda r) = lambda delta(r) for lambda > 0.
+//     rhat_c[e]    = r_c[e] / rho_{c,e}
+// The correction is linear in r: for one Jacobian the preconditioner is one
+// fixed linear map, which BiCGStab's recurrences need.
 //
-// Inference (inside BiCGStab, after each preconditioner application) runs the
-// MLP on the tensor cores: BF16 weights and activations, FP32 accumulation,
-// mma.sync m16n8k16 with the accumulators of one layer re-packed in registers
-// as the A operand of the next.  Each warp takes 16 cells; a CTA keeps the
-// weights in shared memory for all its cells (persistent grid).
+// The network runs once per factorisation, on the tensor cores (BF16 weights
+// and activations, FP32 accumulation, mma.sync m16n8k16 with the accumulators
+// of one layer re-packed in registers as the A operand of the next; each warp
+// takes 16 cells, a CTA keeps the weights in shared memory), and stores W_c.
+// Each application inside BiCGStab is then a per-cell 3x3 product.
 //
 // Training minimises L = ||e - A delta||^2 / ||r||^2, e = r - A M^-1 r, over
 // residuals the solver itself produces (the recurrence residuals of its
@@ -33,25 +35,27 @@
 
 namespace bo {
 
-constexpr int MLH = 128, MLF = 66, MLO = 3;
+constexpr int MLH = 128, MLF = 63, MLO = 9;
 constexpr float SIG_P = 1e6f, SIG_S = 0.05f, SIG_SG = 0.05f, SIG_RGO = 5.0f;
-// flat parameter offsets: W1[128][66], b1, W2[128][128], b2, W3[3][128], b3
+// flat parameter offsets: W1[128][63], b1, W2[128][128], b2, W3[9][128], b3
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + MLH * MLF, OFF_W2 = OFF_B1 + MLH,
               OFF_B2 = OFF_W2 + MLH * MLH, OFF_W3 = OFF_B2 + MLH, OFF_B3 = OFF_W3 + MLO * MLH,
               NPARAM = OFF_B3 + MLO;
 static_assert(NPARAM == BO_LEARN_NPARAM, "parameter count");
 
 // BF16 weight image in shared memory, n-major with padded k so that the
-// 32-bit operand loads of a warp hit 32 distinct banks.
-constexpr int K1P = 88, K2P = 136;                      // row strides (bf16)
-constexpr int W1S = MLH * K1P, W2S = MLH * K2P, W3S = 8 * K2P;
-constexpr int WBF_ELEMS = W1S + W2S + W3S;              // 29,760 bf16 (59.5 KB)
+// 32-bit operand loads of a warp hit 32 distinct banks (row strides of 36 and
+// 68 words).  Layer 1 has K = 64 (63 features and a zero), layer 3 N = 16
+// (9 outputs and zero rows).
+constexpr int K1 = 64, K1P = 72, K2P = 136, N3 = 16;
+constexpr int W1S = MLH * K1P, W2S = MLH * K2P, W3S = N3 * K2P;
+constexpr int WBF_ELEMS = W1S + W2S + W3S;              // 28,800 bf16 (56.3 KB)
 constexpr int XS = 16 * K1P;                             // per-warp feature tile (bf16)
 constexpr int INF_WARPS = 4;
-constexpr size_t INF_SMEM = (size_t)(WBF_ELEMS + INF_WARPS * XS) * 2 + (2 * MLH + 4) * 4 + 64;
+constexpr size_t INF_SMEM = (size_t)(WBF_ELEMS + INF_WARPS * XS) * 2 + (2 * MLH + N3) * 4 + 64;
 
 constexpr int ML_BS = 256;
-constexpr int ML_GRID = 152 * 4;                         // partial sums of g
+constexpr int ML_GRID = 152 * 4;                         // fixed grid of the reductions
 
 static __nv_bfloat16* wbf_of(bo_sim* s) { return static_cast<__nv_bfloat16*>(s->d_ml_wbf); }
 static __nv_bfloat16* feat_of(bo_sim* s) { return static_cast<__nv_bfloat16*>(s->d_ml_feat); }
@@ -61,8 +65,8 @@ static __nv_bfloat16* feat_of(bo_sim* s) { return static_cast<__nv_bfloat16*>(s-
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float sig_x(uint8_t flag) { return flag == 0 ? SIG_SG : SIG_RGO; }
 
-// Block features (BF16 for inference, FP32 for training when ff is given)
-// and per-cell (1/rho_0, 1/rho_1, 1/rho_2, sigma_x).
+// Block features (BF16 for the network, FP32 for training when ff is given;
+// [n][64], entry 63 zero) and per-cell (1/rho_0, 1/rho_1, 1/rho_2, sigma_x).
 __global__ void __launch_bounds__(ML_BS)
 k_ml_feat(Geom g, const double* __restrict__ A, const uint8_t* __restrict__ flag,
           __nv_bfloat16* __restrict__ fbf, float* __restrict__ ff, float4* __restrict__ cell) {
@@ -101,40 +105,8 @@ k_ml_feat(Geom g, const double* __restrict__ A, const uint8_t* __restrict__ flag
     }
 }
 
-// Partial sums of sum_e (r_e / rho_e)^2 in a fixed grid (deterministic).
-__global__ void __launch_bounds__(ML_BS)
-k_ml_gpart(int n, const double* __restrict__ r, const float4* __restrict__ cell,
-           double* __restrict__ part, const KrylovScalars* __restrict__ ks) {
-    if (ks != nullptr && ks->state != KS_RUN) return;
-    __shared__ double sh[ML_BS / 32];
-    double acc = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        const float4 q = cell[c];
-        const double a = r[c] * q.x, b = r[(size_t)n + c] * q.y, d = r[2 * (size_t)n + c] * q.z;
-        acc += a * a + b * b + d * d;
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < ML_BS / 32; ++w) s += sh[w];
-        part[blockIdx.x] = s;
-    }
-}
-
-// g from the partials: lanes sum strided partials, then a fixed shuffle tree
-// (every warp computes the same value).
-__device__ __forceinline__ double ml_scale(const double* __restrict__ part, int nparts, int n) {
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int q = lane; q < nparts; q += 32) s += part[q];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return sqrt(s / (double)n);
-}
-
 // ---------------------------------------------------------------------------
-// Inference on the tensor cores
+// The network on the tensor cores (once per factorisation)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0,
                                          unsigned b1) {
@@ -156,41 +128,36 @@ __device__ __forceinline__ unsigned ld_u32(const __nv_bfloat16* p) {
     return *reinterpret_cast<const unsigned*>(p);
 }
 
-// z += delta(r) for every cell (ks: skip when the solve has finished).
+// W[q][c] = N(f_c)[q], q < 9, for every cell.
 // Fragment layout of m16n8k16 (g = lane / 4, t = lane % 4):
 //   A regs {X[g][2t..], X[g+8][2t..], X[g][2t+8..], X[g+8][2t+8..]}
 //   B regs {W[n=g][k=2t..], W[g][2t+8..]}   (W stored n-major: B = W^T)
 //   C regs {C[g][2t], C[g][2t+1], C[g+8][2t], C[g+8][2t+1]}
 __global__ void __launch_bounds__(32 * INF_WARPS)
-k_ml_apply(int n, const __nv_bfloat16* __restrict__ feat, const float4* __restrict__ cell,
-           const double* __restrict__ r, const double* __restrict__ part, int nparts,
-           const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ theta,
-           double* __restrict__ z, const KrylovScalars* __restrict__ ks) {
-    if (ks != nullptr && ks->state != KS_RUN) return;
+k_ml_net(int n, const __nv_bfloat16* __restrict__ feat, const __nv_bfloat16* __restrict__ wbf,
+         const float* __restrict__ theta, float* __restrict__ Wc) {
     extern __shared__ __align__(16) unsigned char ml_smem[];
     __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(ml_smem);
     __nv_bfloat16* W2s = W1s + W1S;
     __nv_bfloat16* W3s = W2s + W2S;
     __nv_bfloat16* Xall = W3s + W3S;
-    float* bias = reinterpret_cast<float*>(Xall + INF_WARPS * XS);   // b1[128], b2[128], b3[3]
+    float* bias = reinterpret_cast<float*>(Xall + INF_WARPS * XS);   // b1[128], b2[128], b3[16]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {   // weights: 16-byte copies of the prepared image
         const uint4* src = reinterpret_cast<const uint4*>(wbf);
         uint4* dst = reinterpret_cast<uint4*>(W1s);
         for (int q = tid; q < WBF_ELEMS / 8; q += blockDim.x) dst[q] = src[q];
-        for (int q = tid; q < 2 * MLH + MLO; q += blockDim.x)
+        for (int q = tid; q < 2 * MLH + N3; q += blockDim.x)
             bias[q] = q < MLH ? theta[OFF_B1 + q]
-                              : (q < 2 * MLH ? theta[OFF_B2 + q - MLH] : theta[OFF_B3 + q - 2 * MLH]);
+                              : (q < 2 * MLH ? theta[OFF_B2 + q - MLH]
+                                             : (q - 2 * MLH < MLO ? theta[OFF_B3 + q - 2 * MLH] : 0.f));
     }
     __syncthreads();
-    const double gs = ml_scale(part, nparts, n);
-    if (!(gs > 0.0)) return;
-    const double ginv = 1.0 / gs;
     const int gq = lane >> 2, tq = lane & 3;
     __nv_bfloat16* X = Xall + warp * XS;
     const int stride = gridDim.x * INF_WARPS * 16;
     for (int base = (blockIdx.x * INF_WARPS + warp) * 16; base < n; base += stride) {
-        // stage 16 cells x 64 block features, then the residual features
+        // stage 16 cells x 64 features (entry 63 is zero)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int idx = lane + 32 * q, row = idx >> 3, ch = idx & 7;
@@ -200,24 +167,7 @@ k_ml_apply(int n, const __nv_bfloat16* __restrict__ feat, const float4* __restri
             *reinterpret_cast<uint4*>(X + row * K1P + ch * 8) = v;
         }
         __syncwarp();
-        if (lane < 16) {
-            const int c = base + lane;
-            float rh[3] = {0.f, 0.f, 0.f};
-            if (c < n) {
-                const float4 q = cell[c];
-                rh[0] = (float)(r[c] * q.x * ginv);
-                rh[1] = (float)(r[(size_t)n + c] * q.y * ginv);
-                rh[2] = (float)(r[2 * (size_t)n + c] * q.z * ginv);
-            }
-            __nv_bfloat16* row = X + lane * K1P;
-            row[63] = __float2bfloat16(rh[0]);
-            row[64] = __float2bfloat16(rh[1]);
-            row[65] = __float2bfloat16(rh[2]);
-#pragma unroll
-            for (int k = 66; k < 80; ++k) row[k] = __float2bfloat16(0.f);
-        }
-        __syncwarp();
-        // layer 1: K = 80 (66 + zero padding)
+        // layer 1: K = 64
         float acc[16][4];
 #pragma unroll
         for (int nt = 0; nt < 16; ++nt) {
@@ -225,7 +175,7 @@ k_ml_apply(int n, const __nv_bfloat16* __restrict__ feat, const float4* __restri
             acc[nt][0] = b0; acc[nt][1] = b1v; acc[nt][2] = b0; acc[nt][3] = b1v;
         }
 #pragma unroll
-        for (int s = 0; s < 5; ++s) {
+        for (int s = 0; s < K1 / 16; ++s) {
             unsigned a[4];
             a[0] = ld_u32(X + gq * K1P + 16 * s + 2 * tq);
             a[1] = ld_u32(X + (gq + 8) * K1P + 16 * s + 2 * tq);
@@ -267,35 +217,55 @@ k_ml_apply(int n, const __nv_bfloat16* __restrict__ feat, const float4* __restri
             h[s][2] = pack_bf16(fmaxf(acc[2 * s + 1][0], 0.f), fmaxf(acc[2 * s + 1][1], 0.f));
             h[s][3] = pack_bf16(fmaxf(acc[2 * s + 1][2], 0.f), fmaxf(acc[2 * s + 1][3], 0.f));
         }
-        // layer 3: one n-tile of 8 outputs (rows 3..7 of W3 are zero)
-        float o[4];
-        {
-            const int n0 = 2 * tq, n1 = 2 * tq + 1;
-            const float b0 = n0 < MLO ? bias[2 * MLH + n0] : 0.f;
-            const float b1v = n1 < MLO ? bias[2 * MLH + n1] : 0.f;
-            o[0] = b0; o[1] = b1v; o[2] = b0; o[3] = b1v;
+        // layer 3: two n-tiles of 8 outputs (rows 9..15 of W3 are zero)
+        float o[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const float b0 = bias[2 * MLH + 8 * nt + 2 * tq], b1v = bias[2 * MLH + 8 * nt + 2 * tq + 1];
+            o[nt][0] = b0; o[nt][1] = b1v; o[nt][2] = b0; o[nt][3] = b1v;
         }
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const __nv_bfloat16* w = W3s + gq * K2P + 16 * s + 2 * tq;
-            mma_bf16(o, h[s], ld_u32(w), ld_u32(w + 8));
-        }
-        // delta_c[v] = g sigma_v o_v: lanes with t = 0 hold v = 0, 1; t = 1 holds v = 2
-        if (tq < 2) {
+        for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const __nv_bfloat16* w = W3s + (8 * nt + gq) * K2P + 16 * s + 2 * tq;
+                mma_bf16(o[nt], h[s], ld_u32(w), ld_u32(w + 8));
+            }
+        // outputs q = 8 nt + 2 t (+1) of rows g and g + 8
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const int c = base + gq + 8 * half;
+                const int q0 = 8 * nt + 2 * tq;
                 if (c < n) {
-                    if (tq == 0) {
-                        z[c] += gs * (double)SIG_P * (double)o[2 * half];
-                        z[(size_t)n + c] += gs * (double)SIG_S * (double)o[2 * half + 1];
-                    } else {
-                        z[2 * (size_t)n + c] += gs * (double)cell[c].w * (double)o[2 * half];
-                    }
+                    if (q0 < MLO) Wc[(size_t)q0 * n + c] = o[nt][2 * half];
+                    if (q0 + 1 < MLO) Wc[(size_t)(q0 + 1) * n + c] = o[nt][2 * half + 1];
                 }
             }
-        }
         __syncwarp();
+    }
+}
+
+// z += delta(r): delta_c[v] = sigma_v sum_e W_c[3 v + e] r_c[e] / rho_c[e]
+// (ks: skip when the solve has finished).  FP32 products, FP64 accumulation
+// into z.
+__global__ void __launch_bounds__(ML_BS)
+k_ml_apply(int n, const float* __restrict__ Wc, const float4* __restrict__ cell,
+           const double* __restrict__ r, double* __restrict__ z, const KrylovScalars* __restrict__ ks) {
+    if (ks != nullptr && ks->state != KS_RUN) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const float4 q = cell[c];
+        const float rh[3] = {(float)r[c] * q.x, (float)r[(size_t)n + c] * q.y,
+                             (float)r[2 * (size_t)n + c] * q.z};
+        const float sg[3] = {SIG_P, SIG_S, q.w};
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            float o = Wc[(size_t)(3 * v) * n + c] * rh[0];
+            o = fmaf(Wc[(size_t)(3 * v + 1) * n + c], rh[1], o);
+            o = fmaf(Wc[(size_t)(3 * v + 2) * n + c], rh[2], o);
+            z[(size_t)v * n + c] += (double)(sg[v] * o);
+        }
     }
 }
 
@@ -323,15 +293,15 @@ __global__ void k_ml_pack(const float* __restrict__ theta, __nv_bfloat16* __rest
 constexpr int TR_CH = 32;        // cells per chunk
 constexpr int TR_BS = 256;
 constexpr int TR_GRID = 152;     // one persistent CTA per SM
-// shared memory: the FP32 weights with padded rows, W1 [128][67], b1,
-// W2 [128][129], b2, W3 [3][128], b3 (the padding makes both W[j][k] over
+// shared memory: the FP32 weights with padded rows, W1 [128][65], b1,
+// W2 [128][129], b2, W3 [9][128], b3 (odd row strides make both W[j][k] over
 // consecutive j and W[q][j] over consecutive j conflict-free), then the
-// chunk tiles F [32][66], H1 [32][128], H2 [32][128], dH2, dH1, dO [32][4]
-constexpr int S1 = MLF + 1, S2 = MLH + 1;
+// chunk tiles F [32][63], H1 [32][128], H2 [32][128], dH2, dH1, O / dO [32][9]
+constexpr int S1 = MLF + 2, S2 = MLH + 1;
 constexpr int SW1 = 0, SB1 = SW1 + MLH * S1, SW2 = SB1 + MLH, SB2 = SW2 + MLH * S2,
               SW3 = SB2 + MLH, SB3 = SW3 + MLO * MLH;
 constexpr int TR_WFLOATS = (SB3 + MLO + 3) / 4 * 4;
-constexpr int TR_TILE = TR_CH * MLF + 4 * TR_CH * MLH + TR_CH * 4;
+constexpr int TR_TILE = TR_CH * MLF + 4 * TR_CH * MLH + TR_CH * MLO;
 constexpr size_t TR_SMEM = (size_t)(TR_WFLOATS + TR_TILE + 8) * 4;
 
 __device__ __forceinline__ void load_weights_f32(const float* __restrict__ theta, float* W) {
@@ -348,27 +318,16 @@ __device__ __forceinline__ void load_weights_f32(const float* __restrict__ theta
     __syncthreads();
 }
 
-// Forward pass of the chunk [base, base + TR_CH): F, H1, H2 in shared memory.
-// Thread t owns column j = t % 128 for the cells c0 + 2m (c0 = t / 128, m < 16).
+// Forward pass of the chunk [base, base + TR_CH): F, H1, H2 and the outputs
+// O [32][9] in shared memory.  Thread t owns column j = t % 128 of the hidden
+// layers for the cells c0 + 2m (c0 = t / 128, m < 16).
 __device__ __forceinline__ void tr_forward(int n, int base, const float* __restrict__ ff,
-                                           const float4* __restrict__ cell,
-                                           const double* __restrict__ r, double ginv,
-                                           const float* W, float* F, float* H1, float* H2) {
+                                           const float* W, float* F, float* H1, float* H2,
+                                           float* O) {
     const int tid = threadIdx.x;
     for (int q = tid; q < TR_CH * MLF; q += TR_BS) {
         const int cc = q / MLF, k = q % MLF, c = base + cc;
-        float v = 0.f;
-        if (c < n) {
-            if (k < 63) {
-                v = ff[(size_t)c * 64 + k];
-            } else {
-                const int e = k - 63;
-                const float4 s = cell[c];
-                const float ri = e == 0 ? s.x : (e == 1 ? s.y : s.z);
-                v = (float)(r[(size_t)e * n + c] * (double)ri * ginv);
-            }
-        }
-        F[q] = v;
+        F[q] = c < n ? ff[(size_t)c * 64 + k] : 0.f;
     }
     __syncthreads();
     const int j = tid & (MLH - 1), c0 = tid >> 7;
@@ -398,31 +357,45 @@ __device__ __forceinline__ void tr_forward(int n, int base, const float* __restr
         for (int m = 0; m < 16; ++m) H2[(c0 + 2 * m) * MLH + j] = fmaxf(a[m], 0.f);
     }
     __syncthreads();
+    for (int q = tid; q < TR_CH * MLO; q += TR_BS) {
+        const int cc = q / MLO, v = q % MLO;
+        float a = W[SB3 + v];
+        for (int k = 0; k < MLH; ++k) a = fmaf(W[SW3 + v * MLH + k], H2[cc * MLH + k], a);
+        O[q] = a;
+    }
+    __syncthreads();
 }
 
-// delta = g sigma N(f) for every cell (FP32 network, FP64 output).
+__device__ __forceinline__ float rhat_of(int n, int c, int e, const double* __restrict__ r,
+                                         const float4& q) {
+    const float ri = e == 0 ? q.x : (e == 1 ? q.y : q.z);
+    return (float)r[(size_t)e * n + c] * ri;
+}
+
+// delta = sigma (N(f) rhat) for every cell (FP32 network, FP64 output).
 __global__ void __launch_bounds__(TR_BS)
 k_ml_fwd_f32(int n, const float* __restrict__ ff, const float4* __restrict__ cell,
-             const double* __restrict__ r, const double* __restrict__ part, int nparts,
-             const float* __restrict__ theta, double* __restrict__ delta) {
+             const double* __restrict__ r, const float* __restrict__ theta,
+             double* __restrict__ delta) {
     extern __shared__ __align__(16) float tr_smem[];
     float* W = tr_smem;
     float* F = W + TR_WFLOATS;
     float* H1 = F + TR_CH * MLF;
     float* H2 = H1 + TR_CH * MLH;
+    float* O = H2 + 3 * TR_CH * MLH;   // after the two gradient tiles of the backward kernel
     load_weights_f32(theta, W);
-    const double gs = ml_scale(part, nparts, n);
-    const double ginv = gs > 0.0 ? 1.0 / gs : 0.0;
     for (int base = blockIdx.x * TR_CH; base < n; base += gridDim.x * TR_CH) {
-        tr_forward(n, base, ff, cell, r, ginv, W, F, H1, H2);
+        tr_forward(n, base, ff, W, F, H1, H2, O);
         const int tid = threadIdx.x;
-        if (tid < TR_CH * MLO) {
-            const int cc = tid / MLO, v = tid % MLO, c = base + cc;
-            float a = W[SB3 + v];
-            for (int k = 0; k < MLH; ++k) a = fmaf(W[SW3 + v * MLH + k], H2[cc * MLH + k], a);
+        if (tid < TR_CH * 3) {
+            const int cc = tid / 3, v = tid % 3, c = base + cc;
             if (c < n) {
-                const double sg = v == 0 ? (double)SIG_P : (v == 1 ? (double)SIG_S : (double)cell[c].w);
-                delta[(size_t)v * n + c] = gs * sg * (double)a;
+                const float4 q = cell[c];
+                float a = 0.f;
+#pragma unroll
+                for (int e = 0; e < 3; ++e) a = fmaf(O[cc * MLO + 3 * v + e], rhat_of(n, c, e, r, q), a);
+                const float sg = v == 0 ? SIG_P : (v == 1 ? SIG_S : q.w);
+                delta[(size_t)v * n + c] = (double)(sg * a);
             }
         }
         __syncthreads();
@@ -430,13 +403,12 @@ k_ml_fwd_f32(int n, const float* __restrict__ ff, const float4* __restrict__ cel
 }
 
 // Weight gradients for dL/ddelta = dd (FP64 [3][n]); the forward pass is
-// recomputed per chunk.  Each thread accumulates its share of dW1, dW2 in
-// registers over all its chunks, then adds it to grad once.
+// recomputed per chunk.  Each thread accumulates its share of dW1, dW2, dW3
+// in registers over all its chunks, then adds it to grad once.
 __global__ void __launch_bounds__(TR_BS, 1)
 k_ml_bwd_f32(int n, const float* __restrict__ ff, const float4* __restrict__ cell,
-             const double* __restrict__ r, const double* __restrict__ part, int nparts,
-             const float* __restrict__ theta, const double* __restrict__ dd,
-             float* __restrict__ grad) {
+             const double* __restrict__ r, const float* __restrict__ theta,
+             const double* __restrict__ dd, float* __restrict__ grad) {
     extern __shared__ __align__(16) float tr_smem[];
     float* W = tr_smem;
     float* F = W + TR_WFLOATS;
@@ -444,32 +416,34 @@ k_ml_bwd_f32(int n, const float* __restrict__ ff, const float4* __restrict__ cel
     float* H2 = H1 + TR_CH * MLH;
     float* dH2 = H2 + TR_CH * MLH;
     float* dH1 = dH2 + TR_CH * MLH;
-    float* dO = dH1 + TR_CH * MLH;     // [32][4]
+    float* O = dH1 + TR_CH * MLH;      // forward outputs, then their gradient dO
     load_weights_f32(theta, W);
-    const double gs = ml_scale(part, nparts, n);
-    const double ginv = gs > 0.0 ? 1.0 / gs : 0.0;
     const int tid = threadIdx.x;
     // ownership: dW2 row jr = tid / 2, columns [64 kh, 64 kh + 64);
-    //            dW1 row jr, columns kh + 2 m (m < 33), kh = tid % 2
+    //            dW1 row jr, columns kh + 2 m (m < 32, k < 63), kh = tid % 2;
+    //            dW3 entries tid + 256 h (h < 5, < 1152)
     const int jr = tid >> 1, kh = tid & 1;
-    float gW2[64], gW1[33];
+    float gW2[64], gW1[32], gW3[5];
 #pragma unroll
     for (int q = 0; q < 64; ++q) gW2[q] = 0.f;
 #pragma unroll
-    for (int q = 0; q < 33; ++q) gW1[q] = 0.f;
-    float gB1 = 0.f, gB2 = 0.f, gW3[2] = {0.f, 0.f}, gB3 = 0.f;
+    for (int q = 0; q < 32; ++q) gW1[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) gW3[q] = 0.f;
+    float gB1 = 0.f, gB2 = 0.f, gB3 = 0.f;
     const int j = tid & (MLH - 1), c0 = tid >> 7;
     for (int base = blockIdx.x * TR_CH; base < n; base += gridDim.x * TR_CH) {
-        tr_forward(n, base, ff, cell, r, ginv, W, F, H1, H2);
-        // dO = g sigma dd
-        if (tid < TR_CH * MLO) {
-            const int cc = tid / MLO, v = tid % MLO, c = base + cc;
+        tr_forward(n, base, ff, W, F, H1, H2, O);
+        // dO[cc][3 v + e] = sigma_v dd_v rhat_e
+        for (int q = tid; q < TR_CH * MLO; q += TR_BS) {
+            const int cc = q / MLO, ve = q % MLO, v = ve / 3, e = ve % 3, c = base + cc;
             float d = 0.f;
             if (c < n) {
-                const double sg = v == 0 ? (double)SIG_P : (v == 1 ? (double)SIG_S : (double)cell[c].w);
-                d = (float)(gs * sg * dd[(size_t)v * n + c]);
+                const float4 cq = cell[c];
+                const float sg = v == 0 ? SIG_P : (v == 1 ? SIG_S : cq.w);
+                d = sg * (float)dd[(size_t)v * n + c] * rhat_of(n, c, e, r, cq);
             }
-            dO[cc * 4 + v] = d;
+            O[q] = d;
         }
         __syncthreads();
         // dH2 = (dO W3) * [H2 > 0]
@@ -478,7 +452,7 @@ k_ml_bwd_f32(int n, const float* __restrict__ ff, const float4* __restrict__ cel
             const int cc = c0 + 2 * m;
             float a = 0.f;
 #pragma unroll
-            for (int v = 0; v < MLO; ++v) a = fmaf(dO[cc * 4 + v], W[SW3 + v * MLH + j], a);
+            for (int v = 0; v < MLO; ++v) a = fmaf(O[cc * MLO + v], W[SW3 + v * MLH + j], a);
             dH2[cc * MLH + j] = H2[cc * MLH + j] > 0.f ? a : 0.f;
         }
         __syncthreads();
@@ -506,39 +480,40 @@ k_ml_bwd_f32(int n, const float* __restrict__ ff, const float4* __restrict__ cel
 #pragma unroll
             for (int q = 0; q < 64; ++q) gW2[q] = fmaf(d2, H1[cc * MLH + 64 * kh + q], gW2[q]);
 #pragma unroll
-            for (int q = 0; q < 33; ++q) gW1[q] = fmaf(d1, F[cc * MLF + kh + 2 * q], gW1[q]);
+            for (int q = 0; q < 32; ++q)
+                if (kh + 2 * q < MLF) gW1[q] = fmaf(d1, F[cc * MLF + kh + 2 * q], gW1[q]);
             if (kh == 0) {
                 gB1 += d1;
                 gB2 += d2;
             }
         }
-        // dW3[v][k] for (v, k) = tid, tid + 256 < 384; db3 by threads 0..2
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int q = tid + TR_BS * hh;
+        for (int h = 0; h < 5; ++h) {
+            const int q = tid + TR_BS * h;
             if (q < MLO * MLH) {
                 const int v = q / MLH, k = q % MLH;
                 float a = 0.f;
-                for (int cc = 0; cc < TR_CH; ++cc) a = fmaf(dO[cc * 4 + v], H2[cc * MLH + k], a);
-                gW3[hh] += a;
+                for (int cc = 0; cc < TR_CH; ++cc) a = fmaf(O[cc * MLO + v], H2[cc * MLH + k], a);
+                gW3[h] += a;
             }
         }
         if (tid < MLO)
-            for (int cc = 0; cc < TR_CH; ++cc) gB3 += dO[cc * 4 + tid];
+            for (int cc = 0; cc < TR_CH; ++cc) gB3 += O[cc * MLO + tid];
         __syncthreads();
     }
 #pragma unroll
     for (int q = 0; q < 64; ++q) atomicAdd(&grad[OFF_W2 + jr * MLH + 64 * kh + q], gW2[q]);
 #pragma unroll
-    for (int q = 0; q < 33; ++q) atomicAdd(&grad[OFF_W1 + jr * MLF + kh + 2 * q], gW1[q]);
+    for (int q = 0; q < 32; ++q)
+        if (kh + 2 * q < MLF) atomicAdd(&grad[OFF_W1 + jr * MLF + kh + 2 * q], gW1[q]);
     if (kh == 0) {
         atomicAdd(&grad[OFF_B1 + jr], gB1);
         atomicAdd(&grad[OFF_B2 + jr], gB2);
     }
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-        const int q = tid + TR_BS * hh;
-        if (q < MLO * MLH) atomicAdd(&grad[OFF_W3 + q], gW3[hh]);
+    for (int h = 0; h < 5; ++h) {
+        const int q = tid + TR_BS * h;
+        if (q < MLO * MLH) atomicAdd(&grad[OFF_W3 + q], gW3[h]);
     }
     if (tid < MLO) atomicAdd(&grad[OFF_B3 + tid], gB3);
 }
@@ -692,9 +667,10 @@ void learn_setup(bo_sim* s) {
     if (s->d_ml_wbf == nullptr) BO_CUDA(cudaMalloc(&s->d_ml_wbf, sizeof(__nv_bfloat16) * WBF_ELEMS));
     if (s->d_ml_feat == nullptr) BO_CUDA(cudaMalloc(&s->d_ml_feat, sizeof(__nv_bfloat16) * 64 * n));
     ml_alloc(&s->d_ml_cell, n);
+    ml_alloc(&s->d_ml_W, 9 * n);
     ml_alloc(&s->d_ml_part, 2 * ML_GRID + 8);
     BO_CUDA(cudaMemsetAsync(s->d_ml_grad, 0, sizeof(float) * NPARAM, s->stream));
-    BO_CUDA(cudaFuncSetAttribute(k_ml_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INF_SMEM));
+    BO_CUDA(cudaFuncSetAttribute(k_ml_net, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INF_SMEM));
     BO_CUDA(cudaFuncSetAttribute(k_ml_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
     BO_CUDA(cudaFuncSetAttribute(k_ml_bwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
 }
@@ -735,20 +711,23 @@ void learn_clear_grad(bo_sim* s) {
     BO_CUDA(cudaMemsetAsync(s->d_ml_grad, 0, sizeof(float) * NPARAM, s->stream));
 }
 
+// Features of the last assembly and, with parameters set, the per-cell
+// matrices W_c of the network (tensor cores).
 void enqueue_learn_features(bo_sim* s, cudaStream_t st) {
+    const int n = s->geo.n;
     k_ml_feat<<<ML_GRID, ML_BS, 0, st>>>(s->geo, s->d_A, s->d_flag, feat_of(s), s->d_ml_featf,
                                         s->d_ml_cell);
     BO_LAUNCH_CHECK("k_ml_feat");
+    const int grid = std::max(1, std::min(152 * 2, (n + 16 * INF_WARPS - 1) / (16 * INF_WARPS)));
+    k_ml_net<<<grid, 32 * INF_WARPS, INF_SMEM, st>>>(n, feat_of(s), wbf_of(s), s->d_ml_theta,
+                                                     s->d_ml_W);
+    BO_LAUNCH_CHECK("k_ml_net");
 }
 
 // z += delta(r) (inside the BiCGStab graph when ks is given)
 void enqueue_learn_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
                          const KrylovScalars* ks) {
-    const int n = s->geo.n;
-    k_ml_gpart<<<ML_GRID, ML_BS, 0, st>>>(n, r, s->d_ml_cell, s->d_ml_part, ks);
-    const int grid = std::min(152 * 2, (n + 16 * INF_WARPS - 1) / (16 * INF_WARPS));
-    k_ml_apply<<<std::max(grid, 1), 32 * INF_WARPS, INF_SMEM, st>>>(
-        n, feat_of(s), s->d_ml_cell, r, s->d_ml_part, ML_GRID, wbf_of(s), s->d_ml_theta, z, ks);
+    k_ml_apply<<<ML_GRID, ML_BS, 0, st>>>(s->geo.n, s->d_ml_W, s->d_ml_cell, r, z, ks);
     BO_LAUNCH_CHECK("k_ml_apply");
 }
 
@@ -768,17 +747,16 @@ double learn_loss_grad(bo_sim* s, const double* r) {
     double* part2 = s->d_ml_part + ML_GRID;
     launch_precond(s, r, s->d_ml_z0);
     k_ml_resid<<<ML_GRID, ML_BS, 0, st>>>(g, s->d_A, s->d_ml_z0, r, s->d_ml_e, nullptr);
-    k_ml_gpart<<<ML_GRID, ML_BS, 0, st>>>(n, r, s->d_ml_cell, s->d_ml_part, nullptr);
-    k_ml_fwd_f32<<<TR_GRID, TR_BS, TR_SMEM, st>>>(n, s->d_ml_featf, s->d_ml_cell, r, s->d_ml_part,
-                                                  ML_GRID, s->d_ml_theta, s->d_ml_delta);
+    k_ml_fwd_f32<<<TR_GRID, TR_BS, TR_SMEM, st>>>(n, s->d_ml_featf, s->d_ml_cell, r, s->d_ml_theta,
+                                                  s->d_ml_delta);
     k_ml_resid<<<ML_GRID, ML_BS, 0, st>>>(g, s->d_A, s->d_ml_delta, s->d_ml_e, s->d_ml_u, part2);
     k_ml_sum<<<1, 32, 0, st>>>(part2, ML_GRID, s->d_ml_scal);          // ||u||^2
     k_ml_dot<<<ML_GRID, ML_BS, 0, st>>>(N, r, r, part2);
     k_ml_sum<<<1, 32, 0, st>>>(part2, ML_GRID, s->d_ml_scal + 1);      // ||r||^2
     k_ml_AT<<<ML_GRID, ML_BS, 0, st>>>(g, s->d_A, s->d_ml_u, s->d_ml_dd);
     k_ml_scale_vec<<<ML_GRID, ML_BS, 0, st>>>(N, s->d_ml_dd, s->d_ml_scal + 1);
-    k_ml_bwd_f32<<<TR_GRID, TR_BS, TR_SMEM, st>>>(n, s->d_ml_featf, s->d_ml_cell, r, s->d_ml_part,
-                                                  ML_GRID, s->d_ml_theta, s->d_ml_dd, s->d_ml_grad);
+    k_ml_bwd_f32<<<TR_GRID, TR_BS, TR_SMEM, st>>>(n, s->d_ml_featf, s->d_ml_cell, r, s->d_ml_theta,
+                                                  s->d_ml_dd, s->d_ml_grad);
     BO_LAUNCH_CHECK("learn_loss_grad");
     double h[2];
     BO_CUDA(cudaMemcpyAsync(h, s->d_ml_scal, sizeof(h), cudaMemcpyDeviceToHost, st));

@@ -20,7 +20,15 @@ struct TileArgs {
     int NJ, NK, T, NL;
     size_t NP;
     int* err;
+    int ysub;   // block-Jacobi slabs of ysub cell rows in y (a multiple of TJ), 0: one domain
 };
+
+// j is the first cell row of a block-Jacobi slab (not the first of the grid):
+// the -y coupling of row j and the +y coupling of row j - 1 are left out of
+// the factors, and no face crosses the cut.  Cuts fall on tile boundaries.
+__device__ __forceinline__ bool ycut(const TileArgs& a, int j) {
+    return a.ysub > 0 && j > 0 && j % a.ysub == 0;
+}
 
 __device__ __forceinline__ double ld_relaxed(const double* p) {
     double v;

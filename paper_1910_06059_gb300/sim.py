@@ -216,6 +216,17 @@ class Sim:
     def precision(self, name):
         call("bo_set_precision", self.h, L.PRECISION[name])
 
+    @property
+    def subdomains(self):
+        """Block-Jacobi slab height in y (0: plain ILU(0))."""
+        v = ctypes.c_int()
+        call("bo_get_subdomains", self.h, ctypes.byref(v))
+        return v.value
+
+    @subdomains.setter
+    def subdomains(self, ysub):
+        call("bo_set_subdomains", self.h, int(ysub))
+
     # -- learned preconditioner stage ----------------------------------------
     def learn_set_params(self, theta):
         theta = np.ascontiguousarray(theta, dtype=np.float64)

@@ -264,21 +264,52 @@ def random_state(model: dict, seed_member: int = 0, frac_sat: float = 0.5):
             np.ascontiguousarray(flag), np.asarray(bhp, dtype=np.float64))
 
 
+def config3_member(member: int) -> dict:
+    """Member `member` of the 256-member ensemble: nx, ny ~ U{20..64},
+    nz ~ U{5..16}; ln k = ln 200 mD + sigma_m G with sigma_m ~ U[1, 2] and G a
+    unit-variance 3-D Gaussian-covariance GRF (correlation length 8 cells);
+    porosity as config 1; 20x10x2 ft cells.  Water injector at (1, 1, .) under
+    rate control (0.2% of the pore volume per day at surface conditions, BHP
+    limit 10000 psi) and a BHP producer (3000 psi) at (nx, ny, .), both
+    perforating every layer; 20 steps of 15 days.  Draws from
+    PCG64(1910060590 + 300 + member)."""
+    rng = rng_for(3, member)
+    nx, ny = (int(v) for v in rng.integers(20, 65, size=2))
+    nz = int(rng.integers(5, 17))
+    sigma = float(rng.uniform(1.0, 2.0))
+    mean = np.log(200 * MD)
+    lnk = mean + sigma * _grf3d(rng, nx, ny, nz, 8.0)
+    poro = _poro_from_lnk(lnk, mean, sigma)
+    pv = float(np.sum(poro) * (20 * FT) * (10 * FT) * (2 * FT))
+    ks = list(range(nz))
+    wells = [
+        _well(0, 0, ks, "inj", "rate", 0.002 * pv / DAY, 10000 * PSI, phase="water"),
+        _well(nx - 1, ny - 1, ks, "prod", "bhp", 3000 * PSI, 3000 * PSI),
+    ]
+    return _base(f"ensemble member {member} ({nx}x{ny}x{nz})", nx, ny, nz, 20 * FT, 10 * FT,
+                 2 * FT, np.exp(lnk), poro, wells, 20, 15 * DAY)
+
+
+def config3(members: int = 256) -> list:
+    """The ensemble: members 0 .. members-1 of config3_member."""
+    return [config3_member(q) for q in range(members)]
+
+
 CONFIGS = {0: config0, 1: config1, 2: config2}
 
 
 # ---------------------------------------------------------------------------
 # Initial parameters of the learned preconditioner stage (an input to both
-# the GPU library and the oracle): a 66 -> 128 -> 128 -> 3 MLP stored flat as
-# W1[128,66], b1[128], W2[128,128], b2[128], W3[3,128], b3[3].
+# the GPU library and the oracle): a 63 -> 128 -> 128 -> 9 MLP stored flat as
+# W1[128,63], b1[128], W2[128,128], b2[128], W3[9,128], b3[9].
 # ---------------------------------------------------------------------------
-ML_SHAPES = [(128, 66), (128,), (128, 128), (128,), (3, 128), (3,)]
+ML_SHAPES = [(128, 63), (128,), (128, 128), (128,), (9, 128), (9,)]
 
 
 def learned_init(seed: int = 0) -> np.ndarray:
     """He-uniform hidden layers and a zero output layer (so the untrained
     stage adds nothing and training starts from plain ILU(0)), drawn from
-    PCG64(seed); flat float64 vector of 25,475 parameters."""
+    PCG64(seed); flat float64 vector of 25,865 parameters."""
     rng = np.random.Generator(np.random.PCG64(seed))
     parts = []
     for shape in ML_SHAPES:

@@ -2,9 +2,9 @@
 (oracle/learned.py), through the C ABI.
 
 Tolerances:
-  tensor-core inference (BF16 weights, features and activations, FP32
-  accumulation) vs the FP64 oracle: 3e-2 of the largest |delta| per unknown
-  family.  BF16 keeps 8 significant bits (relative rounding 2^-9); each of
+  tensor-core network (BF16 weights, features and activations, FP32
+  accumulation) and FP32 per-cell products vs the FP64 oracle: 3e-2 of the
+  largest |delta| per unknown family.  BF16 keeps 8 significant bits (relative rounding 2^-9); each of
   the three layers rounds its inputs once, and the sums over 66 and 128
   terms average the independent roundings, so the outputs carry errors of a
   few 2^-9 relative to their scale; 3e-2 leaves a margin of ~5.
@@ -45,7 +45,7 @@ def random_params(seed, out_scale=0.3):
     p = ML.unflatten(theta)
     rng = np.random.default_rng(seed + 100)
     p["W3"][:] = out_scale * rng.standard_normal(p["W3"].shape) / np.sqrt(128)
-    p["b3"][:] = out_scale * rng.standard_normal(3)
+    p["b3"][:] = out_scale * rng.standard_normal(ML.NOUT)
     p["b1"][:] = 0.1 * rng.standard_normal(128)
     p["b2"][:] = 0.1 * rng.standard_normal(128)
     return theta
@@ -90,10 +90,16 @@ def test_tensor_core_inference_vs_oracle(name):
             assert scale > 0
             err = np.abs(dg[:, v] - do[:, v]).max() / scale
             assert err <= 3e-2, (v, err)
-    # positive homogeneity: scaling r by a power of two scales g exactly
+    # linear in r: scaling by a power of two is exact, sums up to FP32 rounding
     d1 = g.learn_delta(R.reshape(-1))
     d2 = g.learn_delta(4.0 * R.reshape(-1))
     assert np.allclose(d2, 4.0 * d1, rtol=1e-12, atol=0)
+    r2 = R * rng.standard_normal(R.shape)
+    d3 = g.learn_delta((R + r2).reshape(-1))
+    d4 = g.learn_delta(r2.reshape(-1))
+    for v in range(3):
+        scale = np.abs(d3[v::3]).max()
+        assert np.abs(d3[v::3] - d1[v::3] - d4[v::3]).max() <= 1e-5 * scale
 
 
 @pytest.mark.parametrize("name", ["small_5spot", "ragged_33x17x9"])

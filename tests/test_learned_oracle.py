@@ -33,7 +33,7 @@ def random_params(seed, out_scale=0.1):
     p = ML.unflatten(synth.learned_init(seed).copy())
     rng = np.random.default_rng(seed + 100)
     p["W3"] = out_scale * rng.standard_normal(p["W3"].shape)
-    p["b3"] = out_scale * rng.standard_normal(3)
+    p["b3"] = out_scale * rng.standard_normal(ML.NOUT)
     p["b1"] = 0.1 * rng.standard_normal(128)
     p["b2"] = 0.1 * rng.standard_normal(128)
     return p
@@ -65,13 +65,25 @@ def test_feature_normalisation(system):
     assert np.all(F[0, [1, 3, 5]] == 0.0)
 
 
-def test_stage_is_positively_homogeneous(system):
+def test_stage_is_linear_in_the_residual(system):
     p = random_params(3)
-    r = np.random.default_rng(2).standard_normal((system["o"].n, 3)) * [1e-3, 1e-2, 1.0]
-    d1 = ML.stage_delta(p, system["A7"], system["nb"], system["flag"], r)
-    d2 = ML.stage_delta(p, system["A7"], system["nb"], system["flag"], 3.7 * r)
-    assert np.allclose(d2, 3.7 * d1, rtol=1e-12, atol=0)
-    assert np.all(ML.stage_delta(p, system["A7"], system["nb"], system["flag"], 0 * r) == 0)
+    rng = np.random.default_rng(2)
+    r1 = rng.standard_normal((system["o"].n, 3)) * [1e-3, 1e-2, 1.0]
+    r2 = rng.standard_normal((system["o"].n, 3)) * [1e-3, 1e-2, 1.0]
+    args = (system["A7"], system["nb"], system["flag"])
+    d = ML.stage_delta(p, *args, 3.7 * r1 - 1.5 * r2)
+    assert np.allclose(d, 3.7 * ML.stage_delta(p, *args, r1) - 1.5 * ML.stage_delta(p, *args, r2),
+                       rtol=1e-12, atol=1e-12 * np.abs(d).max())
+    assert np.all(ML.stage_delta(p, *args, 0 * r1) == 0)
+    # one cell by hand: delta_c[v] = sigma_v sum_e N(f_c)[3 v + e] r_c[e] / rho_c[e]
+    c = 11
+    F = ML.block_features(*args)
+    h1 = np.maximum(p["W1"] @ F[c] + p["b1"], 0)
+    h2 = np.maximum(p["W2"] @ h1 + p["b2"], 0)
+    out = p["W3"] @ h2 + p["b3"]
+    sg, rho = ML.scales(system["A7"], system["flag"])
+    want = [sg[c, v] * sum(out[3 * v + e] * r1[c, e] / rho[c, e] for e in range(3)) for v in range(3)]
+    assert np.allclose(ML.stage_delta(p, *args, r1)[c], want, rtol=1e-12, atol=0)
 
 
 def test_untrained_stage_is_plain_ilu0(system):
@@ -90,22 +102,23 @@ def test_untrained_stage_is_plain_ilu0(system):
 
 
 def test_output_bias_least_squares(system):
-    """W1 = W2 = 0 and zero hidden biases: N(f) = b3 in every cell, so
-    delta = g sigma b3 and L(b3) is a linear least-squares problem; its
-    minimiser (from numpy's lstsq on the dense Jacobian) zeroes the gradient."""
+    """W1 = W2 = 0 and zero hidden biases: every cell gets the same matrix
+    W = b3 (3x3), so delta = sigma (W rhat) is linear in the nine entries of
+    b3 and L(b3) is a linear least-squares problem; its minimiser (numpy's
+    lstsq on the dense Jacobian) zeroes the gradient."""
     o, A7, nb, flag = system["o"], system["A7"], system["nb"], system["flag"]
     D = system["dense"]
     p = ML.unflatten(np.zeros(ML.NPARAM))
     r = system["R"].copy()
     z0 = o.ilu_apply(r.reshape(-1)).reshape(-1, 3)
-    _, rho = ML.scales(A7, flag)
-    g = ML.residual_scale(r, rho)
-    sg = ML.sigma(flag)
-    G = np.zeros((3 * o.n, 3))
+    sg, rho = ML.scales(A7, flag)
+    rhat = r / rho
+    G = np.zeros((3 * o.n, 9))
     for v in range(3):
-        unit = np.zeros((o.n, 3))
-        unit[:, v] = g * sg[:, v]
-        G[:, v] = D @ unit.reshape(-1)
+        for e in range(3):
+            x = np.zeros((o.n, 3))
+            x[:, v] = sg[:, v] * rhat[:, e]
+            G[:, 3 * v + e] = D @ x.reshape(-1)
     e = r.reshape(-1) - D @ z0.reshape(-1)
     b3, *_ = np.linalg.lstsq(G, e, rcond=None)
     p["b3"] = b3

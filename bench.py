@@ -475,16 +475,28 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def shard_members(count, rank, world):
+    """Members of this rank when the ensemble is split over `world` GPUs:
+    member q goes to rank q mod world (members are independent, so the
+    ranks exchange nothing but the timing)."""
+    return [q for q in range(count) if q % world == rank]
+
+
 def run_ensemble(args):
     """Config 3: the ensemble of uneven members stepped together (batched
-    form), against the same members stepped one at a time on one stream."""
+    form), against the same members stepped one at a time on one stream.
+    Under torchrun every rank steps its shard of the members."""
     import torch
+    import torch.distributed as dist
     import synth
     from paper_1910_06059_gb300 import Ensemble
 
     rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
-    models = synth.config3(args.members)
+    all_cells = sum(m["nx"] * m["ny"] * m["nz"] for m in synth.config3(args.members))
+    models = [synth.config3_member(q) for q in shard_members(args.members, rank, world)]
     n = sum(m["nx"] * m["ny"] * m["nz"] for m in models)
     dt = models[0]["dt"] if args.report_days is None else args.report_days * 86400.0
     ens = Ensemble(models, streams=8)
@@ -497,6 +509,8 @@ def run_ensemble(args):
     snap = [(s.get_state(), s.dt_next) for s in ens.members]
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     reps = []
@@ -506,6 +520,11 @@ def run_ensemble(args):
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     clk = clocks.stop()
+    sec = max_over_ranks(sec, world, "cuda")
+    if rank != 0:
+        ens.close()
+        dist.destroy_process_group()
+        return
     # the same first report step, members one at a time on one stream, on a
     # sample of the members (largest and smallest mixed as in the ensemble)
     k = min(args.seq_sample, len(models))
@@ -523,23 +542,23 @@ def run_ensemble(args):
     seq.close()
     cells_sample = sum(s.n for s in sample)
     seq_value = cells_sample / sec_seq
-    value = n * args.steps / sec
+    value = all_cells * args.steps / sec
     lin = sum(r["lin_its"] for rs in reps for r in rs)
     newton = sum(r["newton_its"] for rs in reps for r in rs)
     out = {
         "metric": "cell-steps/s at 1e-6 Newton tol: plain FP64 vs mixed/learned/batched",
-        "value": value, "unit": "cell-steps/s", "n_gpus": 1, "steps": args.steps,
+        "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": (f"batched ensemble of {len(models)} members (nx, ny in 20..64, "
-                                f"nz in 5..16; {n} cells), {dt / 86400.0:g}-day report steps, "
+                                f"nz in 5..16; {all_cells} cells), {dt / 86400.0:g}-day report steps, "
                                 "plain FP64 ILU0-BiCGStab per member, Newton tol 1e-6"),
-                   "cells": n, "members": len(models),
+                   "cells": all_cells, "members": args.members,
                    "schedule": tune["chosen"],
                    "timing": "host clock between device-wide synchronisations (members run on "
                              "up to 64 streams)",
                    "l2": "members' Jacobians and ILU data together exceed L2",
-                   "parallelism": "single GPU"},
+                   "parallelism": f"members split over {world} GPUs" if world > 1 else "single GPU"},
         "clocks": clk,
         "autotune_probe_s": tune,
         "sequential": {"value": seq_value, "unit": "cell-steps/s",
@@ -550,6 +569,8 @@ def run_ensemble(args):
     }
     print(json.dumps(out))
     ens.close()
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():

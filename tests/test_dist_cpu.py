@@ -46,3 +46,14 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.whole_job_throughput(10, 3, 1, 1000.0) == pytest.approx(30.0)
+
+
+def test_ensemble_members_shard_over_ranks():
+    """Every member on exactly one rank, shards differing by at most one."""
+    import bench
+    for world in (1, 2, 3, 8):
+        shards = [bench.shard_members(256, r, world) for r in range(world)]
+        flat = sorted(q for sh in shards for q in sh)
+        assert flat == list(range(256))
+        sizes = [len(sh) for sh in shards]
+        assert max(sizes) - min(sizes) <= 1

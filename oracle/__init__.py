@@ -63,6 +63,7 @@ def lib():
         L.orc_set_state.argtypes = [P] * 6
         L.orc_get_state.argtypes = [P] * 6
         L.orc_init_hydrostatic.argtypes = [P, d, d, d]
+        L.orc_init_equilibrium.argtypes = [P, P]
         L.orc_begin_step.argtypes = [P]
         L.orc_assemble.argtypes = [P, d]
         L.orc_get_system.argtypes = [P] * 5
@@ -190,6 +191,11 @@ class Oracle:
     def init_hydrostatic(self):
         ini = self.model["init"]
         lib().orc_init_hydrostatic(self.h, ini["p_top"], ini["sw"], ini["rgo"])
+
+    def init_equilibrium(self, datum_depth, datum_pressure, woc, goc, rgo, swc):
+        """Vertical equilibrium from a datum and the contacts (Section 2.1.3)."""
+        e = np.array([datum_depth, datum_pressure, woc, goc, rgo, swc], dtype=np.float64)
+        lib().orc_init_equilibrium(self.h, _p(e))
 
     # -- linearisation ------------------------------------------------------
     def begin_step(self):

@@ -958,6 +958,30 @@ void orc_get_state(void* h, double* p, double* sw, double* x, uint8_t* flag, dou
     for (size_t w = 0; w < m->wells.size(); ++w) bhp[w] = m->wells[w].bhp;
 }
 
+// Well start-up after an initial state is set: BHP-controlled wells at their
+// target, rate-controlled ones first at their limit, then a rate-controlled
+// injector at the BHP that meets its target by the linear inflow relation of
+// the initial state (all connections injecting), capped by its limit;
+// begin_step's datum density is used.
+static void start_wells(Model* m) {
+    const Fluid& F = m->F;
+    for (Well& w : m->wells) w.bhp = (w.control0 == 1) ? w.target : w.bhp_limit;
+    begin_step(*m);
+    for (Well& w : m->wells) {
+        if (w.control0 != 0 || w.kind != 0) continue;
+        double num = w.target, den = 0.0;
+        for (size_t q = 0; q < w.cells.size(); ++q) {
+            int c = w.cells[q];
+            CellProps cp = cell_props(F, m->p[c], m->sw[c], m->x[c], m->flag[c]);
+            double mob = w.WI[q] * (cp.lam[W].v + cp.lam[O].v + cp.lam[G].v) * cp.b[w.phase].v;
+            double h = F.g * w.rho_well * (m->depth[c] - w.z_datum);
+            num += mob * (m->p[c] - h);
+            den += mob;
+        }
+        if (den > 0.0) w.bhp = std::min(w.bhp_limit, num / den);
+    }
+}
+
 // Initial state: undersaturated oil at dissolved ratio rgo, water saturation
 // sw, and pressure in discrete hydrostatic equilibrium of the oil phase in
 // every column, p = p_top at the centre of the top layer:
@@ -989,24 +1013,105 @@ void orc_init_hydrostatic(void* h, double p_top, double sw, double rgo) {
                 m->p[c] = pk; m->sw[c] = sw; m->x[c] = rgo; m->flag[c] = USAT;
             }
         }
-    for (Well& w : m->wells) w.bhp = (w.control0 == 1) ? w.target : w.bhp_limit;
-    // A rate-controlled injector starts at the BHP that meets its target by
-    // the linear inflow relation at the initial state (all connections
-    // injecting), capped by its limit; begin_step's datum density is used.
-    begin_step(*m);
-    for (Well& w : m->wells) {
-        if (w.control0 != 0 || w.kind != 0) continue;
-        double num = w.target, den = 0.0;
-        for (size_t q = 0; q < w.cells.size(); ++q) {
-            int c = w.cells[q];
-            CellProps cp = cell_props(F, m->p[c], m->sw[c], m->x[c], m->flag[c]);
-            double mob = w.WI[q] * (cp.lam[W].v + cp.lam[O].v + cp.lam[G].v) * cp.b[w.phase].v;
-            double h = F.g * w.rho_well * (m->depth[c] - w.z_datum);
-            num += mob * (m->p[c] - h);
-            den += mob;
-        }
-        if (den > 0.0) w.bhp = std::min(w.bhp_limit, num / den);
+    start_wells(m);
+}
+
+// ---------------------------------------------------------------------------
+// Equilibration (Section 2.1.3): vertical equilibrium from a datum pressure
+// and the water-oil and gas-oil contact depths.  Each zone's phase pressure
+// solves dp/dz = rho_alpha(p) g; the datum's zone is integrated from the
+// datum, the zones above and below from the contacts, where the phase
+// pressures are equal (the capillary pressure of this model is zero).  The
+// ODEs are integrated with the classical 4th-order Runge-Kutta method in
+// N = max(1, ceil(|dz| / 1 m)) equal steps.
+//   zones: gas above the GOC, oil between the contacts, water below the WOC;
+//   oil carries the dissolved ratio r = min(rgo, r_s(p)).
+// Cell states: oil zone s_w = swc; gas zone s_w = swc, s_g = 1 - swc - s_org
+// (saturated, residual oil); water zone s_w = 1 - s_orw (residual oil).  Oil
+// with rgo < r_s(p) is undersaturated (x = rgo), else saturated with s_g = 0
+// (gas zone aside).
+// ---------------------------------------------------------------------------
+enum { ZGAS = 0, ZOIL = 1, ZWAT = 2 };
+struct Equil { double datum_z, datum_p, woc, goc, rgo, swc; };
+
+static int zone_of(const Equil& e, double z) { return z < e.goc ? ZGAS : (z < e.woc ? ZOIL : ZWAT); }
+
+static double zone_density(const Fluid& F, int zone, double p, double rgo) {
+    if (zone == ZWAT) return F.rho_s[W] * F.bw_ref * std::exp(F.c_w * (p - F.p_ref));
+    if (zone == ZGAS) return F.rho_s[G] * p / (F.p_sc * F.Z);
+    const double rs = (F.R_sb / F.p_b) * p;
+    const double r = rgo < rs ? rgo : rs;
+    const double psat = r * (F.p_b / F.R_sb);
+    const double bo = std::exp(F.c_o * (p - psat)) / (1.0 + F.Bo_slope * r);
+    return bo * (F.rho_s[O] + r * F.rho_s[G]);
+}
+
+static double rk4_pressure(const Fluid& F, int zone, double rgo, double z0, double p0, double z) {
+    const int N = std::max(1, (int)std::ceil(std::fabs(z - z0) / 1.0));
+    const double h = (z - z0) / N;
+    double p = p0;
+    for (int q = 0; q < N; ++q) {
+        const double k1 = F.g * zone_density(F, zone, p, rgo);
+        const double k2 = F.g * zone_density(F, zone, p + 0.5 * h * k1, rgo);
+        const double k3 = F.g * zone_density(F, zone, p + 0.5 * h * k2, rgo);
+        const double k4 = F.g * zone_density(F, zone, p + h * k3, rgo);
+        p += (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
     }
+    return p;
+}
+
+// Anchor (depth, pressure) of every zone's phase-pressure curve.
+static void zone_anchors(const Fluid& F, const Equil& e, double za[3], double pa[3]) {
+    const int zd = zone_of(e, e.datum_z);
+    za[zd] = e.datum_z;
+    pa[zd] = e.datum_p;
+    if (zd == ZOIL) {
+        za[ZGAS] = e.goc;
+        pa[ZGAS] = rk4_pressure(F, ZOIL, e.rgo, e.datum_z, e.datum_p, e.goc);
+        za[ZWAT] = e.woc;
+        pa[ZWAT] = rk4_pressure(F, ZOIL, e.rgo, e.datum_z, e.datum_p, e.woc);
+    } else if (zd == ZGAS) {
+        za[ZOIL] = e.goc;
+        pa[ZOIL] = rk4_pressure(F, ZGAS, e.rgo, e.datum_z, e.datum_p, e.goc);
+        za[ZWAT] = e.woc;
+        pa[ZWAT] = rk4_pressure(F, ZOIL, e.rgo, e.goc, pa[ZOIL], e.woc);
+    } else {
+        za[ZOIL] = e.woc;
+        pa[ZOIL] = rk4_pressure(F, ZWAT, e.rgo, e.datum_z, e.datum_p, e.woc);
+        za[ZGAS] = e.goc;
+        pa[ZGAS] = rk4_pressure(F, ZOIL, e.rgo, e.woc, pa[ZOIL], e.goc);
+    }
+}
+
+// e6 = {datum depth, datum pressure, WOC depth, GOC depth, rgo, swc}
+void orc_init_equilibrium(void* h, const double* e6) {
+    Model* m = static_cast<Model*>(h);
+    const Fluid& F = m->F;
+    const Equil e{e6[0], e6[1], e6[2], e6[3], e6[4], e6[5]};
+    double za[3], pa[3];
+    zone_anchors(F, e, za, pa);
+    for (int c = 0; c < m->n; ++c) {
+        const double z = m->depth[c];
+        const int zone = zone_of(e, z);
+        const double p = rk4_pressure(F, zone, e.rgo, za[zone], pa[zone], z);
+        m->p[c] = p;
+        if (zone == ZGAS) {
+            m->sw[c] = e.swc;
+            m->x[c] = 1.0 - e.swc - F.s_org;
+            m->flag[c] = SAT;
+            continue;
+        }
+        m->sw[c] = zone == ZWAT ? 1.0 - F.s_orw : e.swc;
+        const double rs = (F.R_sb / F.p_b) * p;
+        if (e.rgo < rs) {
+            m->x[c] = e.rgo;
+            m->flag[c] = USAT;
+        } else {
+            m->x[c] = 0.0;
+            m->flag[c] = SAT;
+        }
+    }
+    start_wells(m);
 }
 
 void orc_begin_step(void* h) { begin_step(*static_cast<Model*>(h)); }

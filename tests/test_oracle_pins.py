@@ -558,3 +558,80 @@ def test_block_jacobi_ilu0_stays_in_its_subdomain():
     z = o.ilu_apply(r.reshape(-1)).reshape(n, 3)
     assert np.all(z[j // 4 != 1] == 0.0)
     assert np.abs(z[j // 4 == 1]).max() > 0
+
+
+# ---------------------------------------------------------------------------
+# Equilibration (Section 2.1.3): RK4 zones against an independent integrator
+# ---------------------------------------------------------------------------
+def _equil_reference(F, e, z_cells):
+    """Phase pressures at z_cells by scipy's adaptive RK45 at tight
+    tolerances, anchored as the paper states: the datum's zone from the
+    datum, the others from the contacts (equal phase pressures there)."""
+    from scipy.integrate import solve_ivp
+    datum_z, datum_p, woc, goc, rgo, swc = e
+
+    def rho(zone, p):
+        if zone == "water":
+            return F["rho_s"][0] * F["bw_ref"] * math.exp(F["c_w"] * (p - F["p_ref"]))
+        if zone == "gas":
+            return F["rho_s"][2] * p / (F["p_sc"] * F["Z"])
+        r = min(rgo, F["R_sb"] / F["p_b"] * p)
+        bo = math.exp(F["c_o"] * (p - r * F["p_b"] / F["R_sb"])) / (1 + F["Bo_slope"] * r)
+        return bo * (F["rho_s"][1] + r * F["rho_s"][2])
+
+    def integ(zone, z0, p0, z1):
+        if z1 == z0:
+            return p0
+        sol = solve_ivp(lambda z, p: [F["g"] * rho(zone, p[0])], (z0, z1), [p0],
+                        method="RK45", rtol=1e-13, atol=1e-8)
+        return float(sol.y[0, -1])
+
+    def zone_of(z):
+        return "gas" if z < goc else ("oil" if z < woc else "water")
+
+    zd = zone_of(datum_z)
+    anchor = {zd: (datum_z, datum_p)}
+    if zd == "oil":
+        anchor["gas"] = (goc, integ("oil", datum_z, datum_p, goc))
+        anchor["water"] = (woc, integ("oil", datum_z, datum_p, woc))
+    elif zd == "gas":
+        anchor["oil"] = (goc, integ("gas", datum_z, datum_p, goc))
+        anchor["water"] = (woc, integ("oil", goc, anchor["oil"][1], woc))
+    else:
+        anchor["oil"] = (woc, integ("water", datum_z, datum_p, woc))
+        anchor["gas"] = (goc, integ("oil", woc, anchor["oil"][1], goc))
+    return np.array([integ(zone_of(z), *anchor[zone_of(z)], z) for z in z_cells]), zone_of
+
+
+@pytest.mark.parametrize("datum_z", [2650.0, 2540.0, 2760.0])   # oil, gas, water zone
+def test_equilibration_matches_independent_integration(datum_z):
+    m = make_model(1, 1, 60, 1e-13, 0.2, [], dz=5.0)
+    o = oracle.Oracle(m)
+    e = (datum_z, 25.0e6, 2720.0, 2580.0, 100.0, 0.15)
+    o.init_equilibrium(*e)
+    p, sw, x, flag, _ = o.get_state()
+    z = o.static()["depth"]
+    ref, zone_of = _equil_reference(m["fluid"], e, z)
+    assert np.max(np.abs(p - ref) / ref) <= 1e-10
+    F = m["fluid"]
+    for c in range(len(z)):
+        zone = zone_of(z[c])
+        rs = F["R_sb"] / F["p_b"] * p[c]
+        if zone == "gas":
+            assert flag[c] == 0 and sw[c] == 0.15 and x[c] == pytest.approx(1 - 0.15 - F["s_org"])
+        else:
+            assert sw[c] == (1 - F["s_orw"] if zone == "water" else 0.15)
+            assert (flag[c], x[c]) == ((1, 100.0) if 100.0 < rs else (0, 0.0))
+
+
+def test_equilibration_gas_column_is_exponential():
+    """All cells in the gas zone: dp/dz = (g rho_Sg / (p_sc Z)) p, so
+    p(z) = p0 exp(g rho_Sg (z - z0) / (p_sc Z)) exactly."""
+    m = make_model(1, 1, 40, 1e-13, 0.2, [], dz=10.0)
+    o = oracle.Oracle(m)
+    o.init_equilibrium(2600.0, 20.0e6, 5000.0, 4000.0, 100.0, 0.15)
+    p = o.get_state()[0]
+    z = o.static()["depth"]
+    F = m["fluid"]
+    k = F["g"] * F["rho_s"][2] / (F["p_sc"] * F["Z"])
+    assert np.allclose(p, 20.0e6 * np.exp(k * (z - 2600.0)), rtol=1e-12, atol=0)

@@ -158,6 +158,24 @@ bo_status bo_get_static(const bo_sim* sim, double* Tx, double* Ty, double* Tz, d
  * linear inflow relation with all connections injecting, capped by its limit. */
 bo_status bo_init_hydrostatic(bo_sim* sim, double p_top, double sw, double rgo);
 
+/* Initial state in vertical equilibrium (Section 2.1.3) from a datum
+ * pressure and the water-oil and gas-oil contact depths (depths positive
+ * downward, SI units).  Each zone's phase pressure solves dp/dz = rho(p) g by
+ * classical 4th-order Runge-Kutta in max(1, ceil(|dz| / 1 m)) equal steps:
+ * the datum's zone from the datum, the zones above and below from the
+ * contacts, where the phase pressures are equal (this model has no capillary
+ * pressure).  Zones: gas above goc_depth, oil between, water below
+ * woc_depth.  Cells: oil zone s_w = swc; gas zone s_w = swc, s_g = 1 - swc -
+ * s_org (saturated); water zone s_w = 1 - s_orw; oil carries
+ * min(rgo, r_s(p)) and is undersaturated (x = rgo) when rgo < r_s(p), else
+ * saturated with s_g = 0.  Wells start as after bo_init_hydrostatic.
+ * BO_ERR_INVALID_ARG unless datum_pressure > 0, goc_depth <= woc_depth,
+ * rgo >= 0 and 0 <= swc < 1 - s_orw - s_org. */
+typedef struct {
+    double datum_depth, datum_pressure, woc_depth, goc_depth, rgo, swc;
+} bo_equil;
+bo_status bo_init_equilibrium(bo_sim* sim, const bo_equil* eq);
+
 /* State I/O.  p, sw, x are [n] doubles, flag [n] bytes (0 SAT, 1 USAT),
  * well_bhp [nwells] (may be NULL when there are no wells). */
 bo_status bo_set_state(bo_sim* sim, const double* p, const double* sw, const double* x,

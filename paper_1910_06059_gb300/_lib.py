@@ -101,6 +101,7 @@ _SIGS = {
     "bo_set_timing": [P, c_int],
     "bo_set_precision": [P, c_int],
     "bo_set_subdomains": [P, c_int],
+    "bo_init_equilibrium": [P, P],
     "bo_get_subdomains": [P, P],
     "bo_ensemble_create": [P, c_int, c_int, P],
     "bo_ensemble_set_schedule": [P, c_int, c_int],

@@ -426,25 +426,49 @@ bo_status bo_get_static(const bo_sim* s, double* Tx, double* Ty, double* Tz, dou
     });
 }
 
+// Well start-up after an initial state: BHP wells at their target, rate wells
+// first at their limit, then a rate-controlled injector at the BHP that meets
+// its target by the linear inflow relation of the initial state.
+static void start_wells(bo_sim* s) {
+    for (auto& w : s->wells_h) w.bhp = w.ctl0 == 1 ? w.target : w.limit;
+    for (int w = 0; w < s->nw; ++w) {
+        WellDev d = s->wells_h[w];
+        d.ctl = d.ctl0;
+        BO_CUDA(cudaMemcpyAsync(s->d_wells + w, &d, sizeof(WellDev), cudaMemcpyHostToDevice,
+                                s->stream));
+        BO_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    // datum densities at the initial state, then the injector BHP estimate
+    launch_begin_step(s);
+    launch_well_init_bhp(s);
+    sync(s);
+    s->assembled = s->factored = s->solved = false;
+}
+
 bo_status bo_init_hydrostatic(bo_sim* s, double p_top, double sw, double rgo) {
     return guarded([&] {
         need(s && s->props_set, BO_ERR_STATE, "bo_init_hydrostatic: properties not set");
         need(p_top > 0 && sw >= 0 && sw <= 1 && rgo >= 0, BO_ERR_INVALID_ARG,
              "bo_init_hydrostatic: bad initial values");
         launch_hydrostatic(s, p_top, sw, rgo);
-        for (auto& w : s->wells_h) w.bhp = w.ctl0 == 1 ? w.target : w.limit;
-        for (int w = 0; w < s->nw; ++w) {
-            WellDev d = s->wells_h[w];
-            d.ctl = d.ctl0;
-            BO_CUDA(cudaMemcpyAsync(s->d_wells + w, &d, sizeof(WellDev), cudaMemcpyHostToDevice,
-                                    s->stream));
-            BO_CUDA(cudaStreamSynchronize(s->stream));
-        }
-        // datum densities at the initial state, then the injector BHP estimate
-        launch_begin_step(s);
-        launch_well_init_bhp(s);
-        sync(s);
-        s->assembled = s->factored = s->solved = false;
+        start_wells(s);
+    });
+}
+
+bo_status bo_init_equilibrium(bo_sim* s, const bo_equil* e) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_init_equilibrium: properties not set");
+        need(e != nullptr, BO_ERR_INVALID_ARG, "bo_init_equilibrium: NULL input");
+        need(e->datum_pressure > 0 && e->goc_depth <= e->woc_depth && e->rgo >= 0 &&
+                 e->swc >= 0 && e->swc < 1.0 - s->fluid.s_orw - s->fluid.s_org &&
+                 std::isfinite(e->datum_depth) && std::isfinite(e->woc_depth) &&
+                 std::isfinite(e->goc_depth),
+             BO_ERR_INVALID_ARG, "bo_init_equilibrium: bad input (GOC above WOC, p > 0, "
+                                 "0 <= swc < 1 - s_orw - s_org)");
+        const EquilDev d{e->datum_depth, e->datum_pressure, e->woc_depth, e->goc_depth, e->rgo,
+                         e->swc};
+        launch_equilibrium(s, d);
+        start_wells(s);
     });
 }
 

@@ -165,6 +165,110 @@ __global__ void k_hydrostatic(Geom g, DevFluid F, double p_top, double sw, doubl
 }
 
 // ---------------------------------------------------------------------------
+// Equilibration (Section 2.1.3): each zone's phase pressure solves
+// dp/dz = rho_alpha(p) g by classical RK4 in N = max(1, ceil(|dz| / 1 m))
+// equal steps, the datum's zone from the datum and the other zones from the
+// contacts (equal phase pressures there: this model has no capillary
+// pressure).  Zones: gas above the GOC, oil between the contacts, water
+// below the WOC; oil carries r = min(rgo, r_s(p)).
+// ---------------------------------------------------------------------------
+enum { ZGAS = 0, ZOIL = 1, ZWAT = 2 };
+
+__device__ __forceinline__ int zone_of(const EquilDev& e, double z) {
+    return z < e.goc ? ZGAS : (z < e.woc ? ZOIL : ZWAT);
+}
+
+__device__ double zone_density(const DevFluid& F, int zone, double p, double rgo) {
+    if (zone == ZWAT) return F.rho_s[W_] * F.bw_ref * exp(F.c_w * (p - F.p_ref));
+    if (zone == ZGAS) return F.rho_s[G_] * p / (F.p_sc * F.Z);
+    const double rs = (F.R_sb / F.p_b) * p;
+    const double r = rgo < rs ? rgo : rs;
+    const double psat = r * (F.p_b / F.R_sb);
+    const double bo = exp(F.c_o * (p - psat)) / (1.0 + F.Bo_slope * r);
+    return bo * (F.rho_s[O_] + r * F.rho_s[G_]);
+}
+
+__device__ double rk4_pressure(const DevFluid& F, int zone, double rgo, double z0, double p0,
+                               double z) {
+    const int N = max(1, (int)ceil(fabs(z - z0) / 1.0));
+    const double h = (z - z0) / N;
+    double p = p0;
+    for (int q = 0; q < N; ++q) {
+        const double k1 = F.g * zone_density(F, zone, p, rgo);
+        const double k2 = F.g * zone_density(F, zone, p + 0.5 * h * k1, rgo);
+        const double k3 = F.g * zone_density(F, zone, p + 0.5 * h * k2, rgo);
+        const double k4 = F.g * zone_density(F, zone, p + h * k3, rgo);
+        p += (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+    }
+    return p;
+}
+
+// Anchor (depth, pressure) of every zone: out[zone] = depth, out[3 + zone] = pressure.
+__global__ void k_equil_anchors(DevFluid F, EquilDev e, double* __restrict__ out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double za[3], pa[3];
+    const int zd = zone_of(e, e.datum_z);
+    za[zd] = e.datum_z;
+    pa[zd] = e.datum_p;
+    if (zd == ZOIL) {
+        za[ZGAS] = e.goc;
+        pa[ZGAS] = rk4_pressure(F, ZOIL, e.rgo, e.datum_z, e.datum_p, e.goc);
+        za[ZWAT] = e.woc;
+        pa[ZWAT] = rk4_pressure(F, ZOIL, e.rgo, e.datum_z, e.datum_p, e.woc);
+    } else if (zd == ZGAS) {
+        za[ZOIL] = e.goc;
+        pa[ZOIL] = rk4_pressure(F, ZGAS, e.rgo, e.datum_z, e.datum_p, e.goc);
+        za[ZWAT] = e.woc;
+        pa[ZWAT] = rk4_pressure(F, ZOIL, e.rgo, e.goc, pa[ZOIL], e.woc);
+    } else {
+        za[ZOIL] = e.woc;
+        pa[ZOIL] = rk4_pressure(F, ZWAT, e.rgo, e.datum_z, e.datum_p, e.woc);
+        za[ZGAS] = e.goc;
+        pa[ZGAS] = rk4_pressure(F, ZOIL, e.rgo, e.woc, pa[ZOIL], e.goc);
+    }
+    for (int q = 0; q < 3; ++q) {
+        out[q] = za[q];
+        out[3 + q] = pa[q];
+    }
+}
+
+// Cell states of the zones: connate water in the oil and gas zones, residual
+// oil in the water and gas zones; oil undersaturated when rgo < r_s(p).
+__global__ void k_equil_cells(int n, DevFluid F, EquilDev e, const double* __restrict__ anchors,
+                              const double* __restrict__ depth, double* __restrict__ p,
+                              double* __restrict__ sw, double* __restrict__ x,
+                              uint8_t* __restrict__ flag) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const double z = depth[c];
+        const int zone = zone_of(e, z);
+        const double pc = rk4_pressure(F, zone, e.rgo, anchors[zone], anchors[3 + zone], z);
+        p[c] = pc;
+        if (zone == ZGAS) {
+            sw[c] = e.swc;
+            x[c] = 1.0 - e.swc - F.s_org;
+            flag[c] = 0;
+            continue;
+        }
+        sw[c] = zone == ZWAT ? 1.0 - F.s_orw : e.swc;
+        const double rs = (F.R_sb / F.p_b) * pc;
+        if (e.rgo < rs) {
+            x[c] = e.rgo;
+            flag[c] = 1;
+        } else {
+            x[c] = 0.0;
+            flag[c] = 0;
+        }
+    }
+}
+
+void launch_equilibrium(bo_sim* s, const EquilDev& e) {
+    k_equil_anchors<<<1, 32, 0, s->stream>>>(s->fluid, e, s->d_part);
+    k_equil_cells<<<152 * 4, 256, 0, s->stream>>>(s->geo.n, s->fluid, e, s->d_part, s->d_depth,
+                                                  s->d_p, s->d_sw, s->d_x, s->d_flag);
+    BO_LAUNCH_CHECK("k_equil");
+}
+
+// ---------------------------------------------------------------------------
 // Step start: accumulation A0 and the saved state.
 // ---------------------------------------------------------------------------
 __global__ void k_begin_cells(int n, DevFluid F, const double* __restrict__ p,

@@ -46,6 +46,11 @@ struct Geom {
     int nx, ny, nz, n;
 };
 
+// Equilibration input (depths positive downward, SI units).
+struct EquilDev {
+    double datum_z, datum_p, woc, goc, rgo, swc;
+};
+
 // Well description and per-step state, in device memory.
 struct WellDev {
     int kind, phase, ctl0, ctl;   // ctl: 0 rate, 1 bhp
@@ -189,6 +194,7 @@ namespace bo {
 // ---- launchers (defined in the .cu files) ---------------------------------
 void launch_static(bo_sim* s);
 void launch_hydrostatic(bo_sim* s, double p_top, double sw, double rgo);
+void launch_equilibrium(bo_sim* s, const EquilDev& e);
 void launch_begin_step(bo_sim* s);
 void launch_assemble(bo_sim* s, double dt);
 void launch_norms(bo_sim* s, double dt);

@@ -88,6 +88,11 @@ class Sim:
         ini = self.model["init"]
         call("bo_init_hydrostatic", self.h, float(ini["p_top"]), float(ini["sw"]), float(ini["rgo"]))
 
+    def init_equilibrium(self, datum_depth, datum_pressure, woc, goc, rgo, swc):
+        """Vertical equilibrium from a datum and the contacts (bo_init_equilibrium)."""
+        e = (ctypes.c_double * 6)(datum_depth, datum_pressure, woc, goc, rgo, swc)
+        call("bo_init_equilibrium", self.h, e)
+
     def set_state(self, p, sw, x, flag, bhp):
         p, sw, x = (np.ascontiguousarray(a, dtype=np.float64) for a in (p, sw, x))
         flag = np.ascontiguousarray(flag, dtype=np.uint8)

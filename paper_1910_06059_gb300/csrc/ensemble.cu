@@ -87,7 +87,13 @@ void run_step(bo_ensemble* e, double dt, const bo_newton_opts* opts, bo_step_rep
         }
     };
     std::vector<std::thread> pool;
-    for (int w = 1; w < nworkers; ++w) pool.emplace_back(work, w);
+    pool.reserve(nworkers);
+    try {
+        for (int w = 1; w < nworkers; ++w) pool.emplace_back(work, w);
+    } catch (const std::exception&) {
+        // fewer threads than asked for: the members are shared through the
+        // counter, so the workers that did start (and this thread) do them all
+    }
     work(0);
     for (auto& t : pool) t.join();
 }
@@ -140,7 +146,11 @@ bo_status bo_ensemble_step(bo_ensemble* e, double dt, const bo_newton_opts* opts
     if (e == nullptr || !(dt > 0.0)) return BO_ERR_INVALID_ARG;
     const int count = (int)e->members.size();
     std::vector<bo_status> st(count, BO_OK);
-    run_step(e, dt, opts, reports, st.data());
+    try {
+        run_step(e, dt, opts, reports, st.data());
+    } catch (const std::exception&) {   // no memory for the schedule's vectors
+        return BO_ERR_STATE;
+    }
     bo_status first = BO_OK;
     for (int q = 0; q < count; ++q) {
         if (statuses) statuses[q] = st[q];
@@ -170,7 +180,11 @@ bo_status bo_ensemble_autotune(bo_ensemble* e, double dt_probe, const bo_newton_
             e->largest_first = order == 0;
             std::vector<bo_status> st(count, BO_OK);
             const auto t0 = std::chrono::steady_clock::now();
-            run_step(e, dt_probe, opts, nullptr, st.data());
+            try {
+                run_step(e, dt_probe, opts, nullptr, st.data());
+            } catch (const std::exception&) {
+                return BO_ERR_STATE;
+            }
             const double sec =
                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
             if (seconds) seconds[order * ncand + c] = sec;

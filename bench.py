@@ -53,7 +53,7 @@ WORKLOADS = {
     2: "Gaussian-random-field 100x100x50 black-oil, 5-spot wells, 5-day report steps",
 }
 YSUB_NAME = " as block-Jacobi over slabs of {} cell rows in y"
-LEARNED_NAME = (" + learned stage (66-128-128-3 MLP on BF16 tensor cores, trained online "
+LEARNED_NAME = (" + learned stage (63-128-128-9 MLP on BF16 tensor cores, trained online "
                 "on the first warm-up report step's solver residuals)")
 PRECISION_NAMES = {"fp64": "plain FP64 ILU0-BiCGStab",
                    "mixed": "FP32 ILU0 factors and sweeps, FP64 assembly/Krylov/Newton"}

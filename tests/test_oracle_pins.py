@@ -635,3 +635,59 @@ def test_equilibration_gas_column_is_exponential():
     F = m["fluid"]
     k = F["g"] * F["rho_s"][2] / (F["p_sc"] * F["Z"])
     assert np.allclose(p, 20.0e6 * np.exp(k * (z - 2600.0)), rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# Wells (Section 2.2.1): inflow by hand, and a rate target met at convergence
+# ---------------------------------------------------------------------------
+def _props_at(m, p, sw, x, flag):
+    return oracle.cell_props(m["fluid"], p, sw, x, flag)
+
+
+@pytest.mark.parametrize("flag", [0, 1])
+def test_producer_inflow_by_hand(flag):
+    """One cell with one BHP producer, assembled at its own step-start state
+    (no accumulation change, no faces): the residual is the producer's
+    surface rates, q_a = WI b_a lambda_a (p - p_bhp), gas also carrying
+    r_go times the oil term."""
+    pb = 3000 * PSI
+    m = make_model(1, 1, 1, 200 * MD, 0.2, [_well(0, 0, [0], "prod", "bhp", pb, pb)],
+                   dx=30.0, dy=30.0, dz=6.0)
+    o = oracle.Oracle(m)
+    p, sw = 25.0e6, 0.3
+    x = 0.1 if flag == 0 else 120.0
+    o.set_state(np.array([p]), np.array([sw]), np.array([x]), np.array([flag], np.uint8),
+                np.array([pb]))
+    o.begin_step()
+    o.assemble(synth.DAY)
+    R = o.system()[3][0]
+    wi = o.static()["wi"][0]
+    cp = _props_at(m, p, sw, x, flag)
+    b = [cp["b_w"][0], cp["b_o"][0], cp["b_g"][0]]
+    lam = [cp["lam_w"][0], cp["lam_o"][0], cp["lam_g"][0]]
+    rgo = cp["r_go"][0]
+    dp = p - pb
+    want = [wi * b[0] * lam[0] * dp, wi * b[1] * lam[1] * dp,
+            wi * (b[2] * lam[2] + rgo * b[1] * lam[1]) * dp]
+    assert np.allclose(R, want, rtol=1e-12, atol=0)
+
+
+def test_rate_injector_meets_its_target():
+    """A water injector under rate control in a single layer (no wellbore
+    head): at convergence its surface rate, summed by hand over the
+    connections as WI lambda_t b_w (p_bhp - p_j), equals the target."""
+    target = 50 * synth.STB / synth.DAY
+    wells = [_well(2, 2, [0], "inj", "rate", target, 10000 * PSI, phase="water"),
+             _well(0, 0, [0], "prod", "bhp", 3000 * PSI, 3000 * PSI),
+             _well(4, 4, [0], "prod", "bhp", 3000 * PSI, 3000 * PSI)]
+    m = make_model(5, 5, 1, 200 * MD, 0.2, wells, dx=30.0, dy=30.0, dz=6.0)
+    o = oracle.Oracle(m)
+    o.init_hydrostatic()
+    st, rep = o.step(2 * synth.DAY, tol_mb=1e-12, tol_cnv=1e-12, tol_well=1e-12, tol_lin=1e-12)
+    assert st == 0
+    p, sw, x, fl, bhp = o.get_state()
+    c = 2 + 5 * 2
+    cp = _props_at(m, p[c], sw[c], x[c], fl[c])
+    lam_t = cp["lam_w"][0] + cp["lam_o"][0] + cp["lam_g"][0]
+    q = o.static()["wi"][0] * lam_t * cp["b_w"][0] * (bhp[0] - p[c])
+    assert q == pytest.approx(target, rel=1e-8)

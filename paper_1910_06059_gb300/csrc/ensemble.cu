@@ -68,7 +68,20 @@ void run_step(bo_ensemble* e, double dt, const bo_newton_opts* opts, bo_step_rep
             return e->members[a]->geo.n > e->members[b]->geo.n;
         });
     std::atomic<int> next{0};
-    const int nworkers = std::max(1, std::min(e->active, count));
+    int nworkers = std::max(1, std::min(e->active, count));
+    // streams are created on first use (one per worker, kept for later steps)
+    for (int w = 0; w < nworkers; ++w)
+        if (e->streams[w] == nullptr &&
+            cudaStreamCreateWithFlags(&e->streams[w], cudaStreamNonBlocking) != cudaSuccess) {
+            e->streams[w] = nullptr;
+            nworkers = std::max(1, w);   // run with the streams that exist
+            break;
+        }
+    if (e->streams[0] == nullptr) {
+        for (int q = 0; q < count; ++q)
+            if (statuses) statuses[q] = BO_ERR_CUDA;
+        return;
+    }
     auto work = [&](int w) {
         cudaSetDevice(e->device);
         cudaStream_t st = e->streams[w];
@@ -112,16 +125,11 @@ bo_status bo_ensemble_create(bo_sim* const* members, int count, int streams, bo_
             if (members[q] == members[r]) return BO_ERR_INVALID_ARG;
     auto* e = new bo_ensemble();
     e->members.assign(members, members + count);
-    cudaGetDevice(&e->device);
-    e->streams.resize(256, nullptr);
-    for (auto& s : e->streams) {
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            for (auto& t : e->streams)
-                if (t) cudaStreamDestroy(t);
-            delete e;
-            return BO_ERR_CUDA;
-        }
+    if (cudaGetDevice(&e->device) != cudaSuccess) {
+        delete e;
+        return BO_ERR_CUDA;
     }
+    e->streams.assign(256, nullptr);   // created on first use
     e->active = streams;
     *out = e;
     return BO_OK;

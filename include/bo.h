@@ -119,6 +119,10 @@ typedef struct {
     int status;      /* 0 converged, 1 not converged in max_it, 2 breakdown */
     int restarts;    /* restarts from the true residual (see bo_solve) */
     double rel_res;  /* FP64 true residual ||b - Op x||_2 / ||b||_2 at exit */
+    int fallback;    /* repeats after a failed attempt, bit mask: 1 without the
+                        learned stage (bo_learn_enable), 2 with the FP64 sweeps
+                        (BO_PRECISION_MIXED); iterations counts every attempt,
+                        status, restarts and rel_res are the last attempt's */
 } bo_solve_report;
 
 typedef struct {
@@ -238,8 +242,12 @@ bo_status bo_apply_op(bo_sim* sim, const double* x, double* y);
  * preconditioned BiCGStab on the reduced system, then the well unknowns.
  * The iteration stops on the recurrence's residual; the FP64 true residual
  * ||b - Op x|| is then computed and must meet the same tolerance, else
- * BiCGStab restarts from it (at most 3 times, within max_it) and the solve
- * reports not converged if it still misses.
+ * BiCGStab restarts from it (at most 8 times, within max_it) and the solve
+ * reports not converged if it still misses.  A solve that fails with the
+ * learned stage on is repeated without it, and one that fails with the FP32
+ * sweeps of BO_PRECISION_MIXED is repeated with the FP64 sweeps (each repeat
+ * from a zero initial guess with a fresh max_it; report->fallback says which
+ * ran).
  * sol (may be NULL) receives [3n + nwells] (cell-major, then one entry per
  * well, 0 for wells without an unknown). */
 bo_status bo_solve(bo_sim* sim, const bo_solve_opts* opts, bo_solve_report* report,
@@ -275,7 +283,8 @@ bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* m
  * the true-residual check of bo_solve and the Newton convergence test stay
  * FP64.  The preconditioner is only an approximation of J^-1, so the
  * precision of its application changes iteration counts, not the converged
- * Newton state beyond the tolerances.  Switching re-records the solver's
+ * Newton state beyond the tolerances.  A solve the FP32 sweeps fail is
+ * repeated with the FP64 factors and sweeps (bo_solve).  Switching re-records the solver's
  * CUDA graphs and converts factors already computed.  Requires
  * bo_set_properties; BO_ERR_INVALID_ARG for another value. */
 enum { BO_PRECISION_FP64 = 0, BO_PRECISION_MIXED = 1 };
@@ -284,15 +293,19 @@ bo_status bo_get_precision(const bo_sim* sim, int* precision);
 
 /* Block-Jacobi ILU(0), the parallel preconditioner of Section 2.5 (one
  * ILU(0) block per subdomain), on one GPU: the grid is cut into slabs of
- * ysub cell rows in y (the last slab may be shorter) and the factorisation
- * leaves out every block that couples two slabs; the operator keeps them.
- * The slabs' wavefronts then run side by side, so a sweep takes about
- * nx + ysub + nz levels instead of nx + ny + nz.  ysub = 0 restores plain
- * ILU(0).  ysub must be 0 or a positive multiple of 8 (the tile height of
- * the sweeps); BO_ERR_INVALID_ARG otherwise.  Requires bo_set_properties;
- * the factors of an earlier bo_factor are dropped (factor again). */
-bo_status bo_set_subdomains(bo_sim* sim, int ysub);
-bo_status bo_get_subdomains(const bo_sim* sim, int* ysub);
+ * ysub cell rows in y and of zsub cell layers in z (the last slab in each
+ * direction may be shorter; the subdomains are the boxes the two sets of
+ * cuts make) and the factorisation leaves out every block that couples two
+ * subdomains; the operator keeps them.  The subdomains' wavefronts then run
+ * side by side, so a sweep takes about nx + min(ny, ysub) + min(nz, zsub)
+ * levels instead of nx + ny + nz.  0 means no cut in that direction, so
+ * (0, 0) restores plain ILU(0).  ysub must be 0 or a positive multiple of 8
+ * and zsub 0 or a positive multiple of 4 (the tile extents of the sweeps);
+ * BO_ERR_INVALID_ARG otherwise.  Requires bo_set_properties; the factors of
+ * an earlier bo_factor are dropped (factor again).  bo_get_subdomains
+ * writes either value to a non-NULL pointer. */
+bo_status bo_set_subdomains(bo_sim* sim, int ysub, int zsub);
+bo_status bo_get_subdomains(const bo_sim* sim, int* ysub, int* zsub);
 /* Learned correction of the preconditioner, an extension of the ILU(0)-
  * preconditioned BiCGStab of Section 2.3.1.  With the stage on, every
  * preconditioner application inside BiCGStab becomes

@@ -84,7 +84,7 @@ def lib():
         L.orc_get_dt_next.argtypes = [P]
         L.orc_get_dt_next.restype = d
         L.orc_set_dt_next.argtypes = [P, d]
-        L.orc_set_subdomains.argtypes = [P, i]
+        L.orc_set_subdomains.argtypes = [P, i, i]
         _lib = L
     return _lib
 
@@ -284,9 +284,10 @@ class Oracle:
     def dt_next(self, v):
         lib().orc_set_dt_next(self.h, float(v))
 
-    def set_subdomains(self, ysub: int):
-        """Block-Jacobi ILU(0) over slabs of `ysub` cell rows in y (0: off)."""
-        lib().orc_set_subdomains(self.h, int(ysub))
+    def set_subdomains(self, ysub: int, zsub: int = 0):
+        """Block-Jacobi ILU(0) over boxes of `ysub` cell rows in y and `zsub`
+        cell layers in z (0: no cut in that direction)."""
+        lib().orc_set_subdomains(self.h, int(ysub), int(zsub))
 
     def step(self, dt, **opts):
         o = opts_array(**opts)

@@ -225,11 +225,11 @@ struct Model {
     std::vector<double> Uinv;  // inverse of U diagonal blocks, 9n
     double dt_last = 0.0;
     double dt_next = 0.0;  // sub-step length carried between report steps (0: unset)
-    // Block-Jacobi ILU(0) over slabs of ysub cell rows in y (0: one domain):
-    // the parallel preconditioner of Section 2.5 (one ILU(0) block per
-    // subdomain; the couplings between subdomains are left out of M, the
-    // operator keeps them).
-    int ysub = 0;
+    // Block-Jacobi ILU(0) over boxes of ysub cell rows in y and zsub cell
+    // layers in z (0: no cut in that direction): the parallel preconditioner
+    // of Section 2.5 (one ILU(0) block per subdomain; the couplings between
+    // subdomains are left out of M, the operator keeps them).
+    int ysub = 0, zsub = 0;
 };
 
 static inline int cidx(const Model& m, int i, int j, int k) { return i + m.nx * (j + m.ny * k); }
@@ -557,14 +557,18 @@ static bool inv3(const double* a, double* out) {
 static bool ilu0(Model& m) {
     int n = m.n;
     m.lu = m.vals;
-    if (m.ysub > 0) {   // block-Jacobi: drop the blocks that couple two subdomains
+    if (m.ysub > 0 || m.zsub > 0) {   // block-Jacobi: drop the blocks that couple two subdomains
+        // subdomain of a cell: (slab in y, slab in z); a direction without cuts is one slab
+        auto dom = [&](int c) {
+            const int j = (c / m.nx) % m.ny, k = c / (m.nx * m.ny);
+            const int sy = m.ysub > 0 ? j / m.ysub : 0, sz = m.zsub > 0 ? k / m.zsub : 0;
+            return sy + m.ny * sz;
+        };
         for (int i = 0; i < n; ++i) {
-            const int si = ((i / m.nx) % m.ny) / m.ysub;
-            for (int q = m.rowptr[i]; q < m.rowptr[i + 1]; ++q) {
-                const int j = m.colind[q];
-                if (((j / m.nx) % m.ny) / m.ysub != si)
+            const int si = dom(i);
+            for (int q = m.rowptr[i]; q < m.rowptr[i + 1]; ++q)
+                if (dom(m.colind[q]) != si)
                     for (int e = 0; e < 9; ++e) m.lu[9 * q + e] = 0.0;
-            }
         }
     }
     m.Uinv.assign(9 * n, 0.0);
@@ -1237,7 +1241,10 @@ int orc_step(void* h, double dt, const double* opts, double* report) {
 
 double orc_get_dt_next(void* h) { return static_cast<Model*>(h)->dt_next; }
 void orc_set_dt_next(void* h, double v) { static_cast<Model*>(h)->dt_next = v; }
-void orc_set_subdomains(void* h, int ysub) { static_cast<Model*>(h)->ysub = ysub > 0 ? ysub : 0; }
+void orc_set_subdomains(void* h, int ysub, int zsub) {
+    static_cast<Model*>(h)->ysub = ysub > 0 ? ysub : 0;
+    static_cast<Model*>(h)->zsub = zsub > 0 ? zsub : 0;
+}
 
 // Single-cell property evaluation with derivatives (for pin tests).
 // out: for each quantity value then d/dp, d/dsw, d/dx; quantities in order

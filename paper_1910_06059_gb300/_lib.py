@@ -49,7 +49,7 @@ class BoSolveOpts(ctypes.Structure):
 
 class BoSolveReport(ctypes.Structure):
     _fields_ = [("iterations", c_int), ("status", c_int), ("restarts", c_int),
-                ("rel_res", c_double)]
+                ("rel_res", c_double), ("fallback", c_int)]
 
 
 PRECISION = {"fp64": 0, "mixed": 1}
@@ -100,9 +100,9 @@ _SIGS = {
     "bo_set_step_control": [P, c_double],
     "bo_set_timing": [P, c_int],
     "bo_set_precision": [P, c_int],
-    "bo_set_subdomains": [P, c_int],
+    "bo_set_subdomains": [P, c_int, c_int],
     "bo_init_equilibrium": [P, P],
-    "bo_get_subdomains": [P, P],
+    "bo_get_subdomains": [P, P, P],
     "bo_ensemble_create": [P, c_int, c_int, P],
     "bo_ensemble_set_schedule": [P, c_int, c_int],
     "bo_ensemble_get_schedule": [P, P, P],

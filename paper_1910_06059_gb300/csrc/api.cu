@@ -159,15 +159,28 @@ static int solve_linear(bo_sim* s, double tol, int maxit, int* its) {
         return LS_BREAKDOWN;
     }
     s->factored = true;
+    s->last_fallback = 0;
     int st = run_bicgstab(s, tol, maxit, its, true);
     check_timeout(s);
     if (st != LS_OK && s->ml_on) {
         // the learned stage failed on this system: repeat with plain ILU(0)
         s->ml_fallbacks += 1;
+        s->last_fallback |= 1;
         int its2 = 0;
         st = run_bicgstab(s, tol, maxit, &its2, false);
         check_timeout(s);
         *its += its2;
+    }
+    if (st != LS_OK && s->mixed) {
+        // the FP32 sweeps failed on this system: repeat with the FP64 factors
+        // and sweeps (the factorisation is FP64 in both modes)
+        s->last_fallback |= 2;
+        fill_sweep_faces(s, false);
+        int its3 = 0;
+        st = run_bicgstab(s, tol, maxit, &its3, false, true);
+        fill_sweep_faces(s, true);
+        check_timeout(s);
+        *its += its3;
     }
     if (s->ml_online) learn_online_step(s);
     launch_well_recover(s);
@@ -687,6 +700,7 @@ bo_status bo_solve(bo_sim* s, const bo_solve_opts* o, bo_solve_report* rep, doub
             rep->status = st;
             rep->restarts = s->last_restarts;
             rep->rel_res = s->last_rel_res;
+            rep->fallback = s->last_fallback;
         }
         if (sol) {
             download_aos3(s, s->d_xs, sol);
@@ -782,15 +796,18 @@ bo_status bo_set_precision(bo_sim* s, int precision) {
     });
 }
 
-bo_status bo_set_subdomains(bo_sim* s, int ysub) {
+bo_status bo_set_subdomains(bo_sim* s, int ysub, int zsub) {
     return guarded([&] {
         need(s != nullptr, BO_ERR_INVALID_ARG, "bo_set_subdomains: sim is NULL");
         need(ysub == 0 || (ysub > 0 && ysub % 8 == 0), BO_ERR_INVALID_ARG,
              "bo_set_subdomains: ysub must be 0 or a positive multiple of 8");
+        need(zsub == 0 || (zsub > 0 && zsub % 4 == 0), BO_ERR_INVALID_ARG,
+             "bo_set_subdomains: zsub must be 0 or a positive multiple of 4");
         need(s->props_set, BO_ERR_STATE, "bo_set_subdomains: call bo_set_properties first");
-        if (ysub == s->ysub) return;
+        if (ysub == s->ysub && zsub == s->zsub) return;
         sync(s);
         s->ysub = ysub;
+        s->zsub = zsub;
         s->factored = false;   // the factors of the other partition are stale
         reset_sweep_faces(s);
         build_graphs(s);
@@ -798,10 +815,11 @@ bo_status bo_set_subdomains(bo_sim* s, int ysub) {
     });
 }
 
-bo_status bo_get_subdomains(const bo_sim* s, int* ysub) {
+bo_status bo_get_subdomains(const bo_sim* s, int* ysub, int* zsub) {
     return guarded([&] {
-        need(s != nullptr && ysub != nullptr, BO_ERR_INVALID_ARG, "bo_get_subdomains: NULL argument");
-        *ysub = s->ysub;
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_get_subdomains: sim is NULL");
+        if (ysub) *ysub = s->ysub;
+        if (zsub) *zsub = s->zsub;
     });
 }
 

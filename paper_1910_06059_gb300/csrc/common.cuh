@@ -172,13 +172,16 @@ struct bo_sim {
     long long ml_systems = 0, ml_steps = 0, ml_fallbacks = 0;
     double ml_first_loss = -1.0, ml_last_loss = -1.0, ml_train_ms = 0.0;
     cudaGraphExec_t g_iter_ml = nullptr;
+    cudaGraphExec_t g_iter64 = nullptr;   // FP64 sweeps in mixed mode (fallback solves)
+    int last_fallback = 0;                // bo_solve_report::fallback of the last solve
 
     // CUDA graphs of one BiCGStab iteration block and of the factorisation
     cudaGraphExec_t g_iter = nullptr;
     cudaGraphExec_t g_factor = nullptr;
     cudaGraphExec_t g_iter_timed = nullptr;
     int iters_per_graph = 4;
-    int ysub = 0;                // block-Jacobi slabs of ysub cell rows in y (0: plain ILU(0))
+    int ysub = 0;                // block-Jacobi slabs of ysub cell rows in y (0: no cut in y)
+    int zsub = 0;                // and of zsub cell layers in z (0: no cut in z)
 
     // timing
     bool timing = false;
@@ -214,13 +217,15 @@ size_t factors32_floats(const bo_sim* s);        // size of d_P32 (FP32 sweep la
 size_t vec32_floats(const bo_sim* s);            // size of d_r32, d_y32 (tile order)
 void convert_factors32(bo_sim* s, cudaStream_t st);
 void reset_sweep_faces(bo_sim* s);                // sentinels of the current precision
+void fill_sweep_faces(bo_sim* s, bool fp32);      // sentinels of the given precision
 double wait_selftest(bo_sim* s);
 void build_graphs(bo_sim* s);
 void destroy_graphs(bo_sim* s);
 void launch_factor(bo_sim* s);                       // graph of level kernels
 void launch_precond(bo_sim* s, const double* r, double* z);
 void launch_op(bo_sim* s, const double* x, double* y);
-int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml);  // returns LS_*
+// returns LS_*; fp64: FP64 sweeps even in mixed mode (the fallback solve)
+int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool fp64 = false);
 void launch_well_recover(bo_sim* s);
 void launch_newton_update(bo_sim* s, const bo_newton_opts& o);
 

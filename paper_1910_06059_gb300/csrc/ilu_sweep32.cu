@@ -159,9 +159,9 @@ k_fwd32(TileArgs a, const float4* __restrict__ F, const float4* __restrict__ Rt,
     const WarpTile W = warp_tile(a);
     const int nx = a.g.nx, lane = W.lane;
     const bool feedJ = W.valid && W.jj == TJ - 1 && W.J + 1 < a.NJ && !ycut(a, (W.J + 1) * TJ);
-    const bool feedK = W.valid && W.kk == TK - 1 && W.K + 1 < a.NK;
+    const bool feedK = W.valid && W.kk == TK - 1 && W.K + 1 < a.NK && !zcut(a, (W.K + 1) * TK);
     const bool takeJ = W.valid && W.j > 0 && !ycut(a, W.j) && W.jj == 0;
-    const bool takeK = W.valid && W.k > 0 && W.kk == 0;
+    const bool takeK = W.valid && W.k > 0 && !zcut(a, W.k) && W.kk == 0;
     const bool inJ = W.j > 0 && W.jj > 0, inK = W.k > 0 && W.kk > 0;
     const int l0 = W.jj + W.kk;
     const size_t s0 = (size_t)W.t * a.NL;
@@ -263,8 +263,9 @@ k_bwd32(TileArgs a, const float4* __restrict__ B, float4* __restrict__ Yt, float
     const WarpTile W = warp_tile(a);
     const int nx = a.g.nx, lane = W.lane;
     const bool feedJ = W.valid && W.jj == 0 && W.J > 0 && !ycut(a, W.J * TJ);
-    const bool feedK = W.valid && W.kk == 0 && W.K > 0;
-    const bool hasJ = W.j + 1 < a.g.ny && !ycut(a, W.j + 1), hasK = W.k + 1 < a.g.nz;
+    const bool feedK = W.valid && W.kk == 0 && W.K > 0 && !zcut(a, W.K * TK);
+    const bool hasJ = W.j + 1 < a.g.ny && !ycut(a, W.j + 1),
+               hasK = W.k + 1 < a.g.nz && !zcut(a, W.k + 1);
     const bool takeJ = W.valid && hasJ && W.jj == TJ - 1, takeK = W.valid && hasK && W.kk == TK - 1;
     const bool inJ = hasJ && W.jj < TJ - 1, inK = hasK && W.kk < TK - 1;
     const int l0 = W.jj + W.kk;

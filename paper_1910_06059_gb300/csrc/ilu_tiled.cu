@@ -160,9 +160,10 @@ k_factor_tiled(TileArgs a, const double* __restrict__ A, double* __restrict__ P,
     const int n = a.g.n, nx = a.g.nx;
     const int lane = threadIdx.x & 31;
     const bool feedJ = L.jj == TJ - 1 && L.J + 1 < a.NJ && !ycut(a, (L.J + 1) * TJ);
-    const bool feedK = L.kk == TK - 1 && L.K + 1 < a.NK;
-    const bool hasJ = L.j > 0 && !ycut(a, L.j), hasK = L.k > 0;
+    const bool feedK = L.kk == TK - 1 && L.K + 1 < a.NK && !zcut(a, (L.K + 1) * TK);
+    const bool hasJ = L.j > 0 && !ycut(a, L.j), hasK = L.k > 0 && !zcut(a, L.k);
     const bool upJ = !ycut(a, L.j + 1);   // the +y coupling stays in the slab
+    const bool upK = !zcut(a, L.k + 1);   // the +z coupling stays in the slab
     double Ux[9], Uy[9], Uz[9];   // this lane's scaled upper blocks of its last cell
 #pragma unroll
     for (int e = 0; e < 9; ++e) Ux[e] = Uy[e] = Uz[e] = 0.0;
@@ -184,7 +185,7 @@ k_factor_tiled(TileArgs a, const double* __restrict__ A, double* __restrict__ P,
             D[e] = act ? A[(size_t)(NB_DIAG * 9 + e) * n + c] : (e % 4 == 0 ? 1.0 : 0.0);
             Bx[e] = act ? A[(size_t)(NB_MX * 9 + e) * n + c] : 0.0;
             By[e] = act && hasJ ? A[(size_t)(NB_MY * 9 + e) * n + c] : 0.0;
-            Bz[e] = act ? A[(size_t)(NB_MZ * 9 + e) * n + c] : 0.0;
+            Bz[e] = act && hasK ? A[(size_t)(NB_MZ * 9 + e) * n + c] : 0.0;
         }
         __syncwarp();
         fnma_mm(D, Bx, Ux);
@@ -197,7 +198,7 @@ k_factor_tiled(TileArgs a, const double* __restrict__ A, double* __restrict__ P,
         for (int e = 0; e < 9; ++e) {
             Bx[e] = act ? A[(size_t)(NB_PX * 9 + e) * n + c] : 0.0;
             By[e] = act && upJ ? A[(size_t)(NB_PY * 9 + e) * n + c] : 0.0;
-            Bz[e] = act ? A[(size_t)(NB_PZ * 9 + e) * n + c] : 0.0;
+            Bz[e] = act && upK ? A[(size_t)(NB_PZ * 9 + e) * n + c] : 0.0;
         }
         double Ux2[9], Uy2[9], Uz2[9];
         mm3t(Di, Bx, Ux2);
@@ -244,7 +245,7 @@ k_factor_lower(TileArgs a, const double* __restrict__ A, double* __restrict__ P)
 #pragma unroll
         for (int e = 0; e < 9; ++e) Di[e] = act ? P[(size_t)e * a.NP + idx] : 0.0;
         const int lowb[3] = {NB_MX, NB_MY, NB_MZ};
-        const bool keep[3] = {true, !ycut(a, j), true};
+        const bool keep[3] = {true, !ycut(a, j), !zcut(a, k)};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
 #pragma unroll
@@ -377,8 +378,8 @@ k_fwd_tiled(TileArgs a, const double* __restrict__ P, const double* __restrict__
     const int n = a.g.n, nx = a.g.nx;
     const int rw = R.row;
     const bool feedJ = R.valid && R.jj == TJ - 1 && R.J + 1 < a.NJ && !ycut(a, (R.J + 1) * TJ);
-    const bool feedK = R.valid && R.kk == TK - 1 && R.K + 1 < a.NK;
-    const bool hasJ = R.j > 0 && !ycut(a, R.j), hasK = R.k > 0;
+    const bool feedK = R.valid && R.kk == TK - 1 && R.K + 1 < a.NK && !zcut(a, (R.K + 1) * TK);
+    const bool hasJ = R.j > 0 && !ycut(a, R.j), hasK = R.k > 0 && !zcut(a, R.k);
     const bool takeJ = R.valid && hasJ && R.jj == 0, takeK = R.valid && hasK && R.kk == 0;
     const int l0 = R.jj + R.kk;                   // first level of this line (i = 0)
     const size_t NP = a.NP;
@@ -485,8 +486,9 @@ k_bwd_tiled(TileArgs a, const double* __restrict__ P, double* __restrict__ z,
     const int n = a.g.n, nx = a.g.nx;
     const int rw = R.row;
     const bool feedJ = R.valid && R.jj == 0 && R.J > 0 && !ycut(a, R.J * TJ);
-    const bool feedK = R.valid && R.kk == 0 && R.K > 0;
-    const bool hasJ = R.j + 1 < a.g.ny && !ycut(a, R.j + 1), hasK = R.k + 1 < a.g.nz;
+    const bool feedK = R.valid && R.kk == 0 && R.K > 0 && !zcut(a, R.K * TK);
+    const bool hasJ = R.j + 1 < a.g.ny && !ycut(a, R.j + 1),
+               hasK = R.k + 1 < a.g.nz && !zcut(a, R.k + 1);
     const bool takeJ = R.valid && hasJ && R.jj == TJ - 1, takeK = R.valid && hasK && R.kk == TK - 1;
     const int l0 = R.jj + R.kk;
     const size_t NP = a.NP;
@@ -609,6 +611,7 @@ TileArgs tile_args(const bo_sim* s) {
     a.NP = (size_t)a.T * a.NL * 32;
     a.err = s->d_sweep_sync + 2;
     a.ysub = s->ysub;
+    a.zsub = s->zsub;
     return a;
 }
 
@@ -681,12 +684,14 @@ static void refill_faces3(bo_sim* s, cudaStream_t st) {
 
 // Sentinels of the current precision in the 3-value face buffers (after a
 // precision switch or an abandoned sweep).
-void reset_sweep_faces(bo_sim* s) {
-    if (s->mixed)
+void reset_sweep_faces(bo_sim* s) { fill_sweep_faces(s, s->mixed); }
+
+void fill_sweep_faces(bo_sim* s, bool fp32) {
+    if (fp32)
         reset_faces32(s, s->stream);
     else
         refill_faces3(s, s->stream);
-    BO_LAUNCH_CHECK("reset_sweep_faces");
+    BO_LAUNCH_CHECK("fill_sweep_faces");
 }
 
 // In mixed mode the forward sweep leaves y in the FP32 tile-order work

@@ -632,6 +632,16 @@ void build_graphs(bo_sim* s) {
     s->g_factor = capture_factor(s);
     s->g_iter = capture(s, s->iters_per_graph, nullptr, false, s->ml_online);
     if (s->ml_on) s->g_iter_ml = capture(s, s->iters_per_graph, nullptr, true, s->ml_online);
+    if (s->mixed) {   // FP64 sweeps for a solve the FP32 sweeps fail
+        s->mixed = false;
+        try {
+            s->g_iter64 = capture(s, s->iters_per_graph, nullptr, false, false);
+        } catch (...) {
+            s->mixed = true;
+            throw;
+        }
+        s->mixed = true;
+    }
 }
 
 void destroy_graphs(bo_sim* s) {
@@ -639,7 +649,8 @@ void destroy_graphs(bo_sim* s) {
     if (s->g_factor) cudaGraphExecDestroy(s->g_factor);
     if (s->g_iter_timed) cudaGraphExecDestroy(s->g_iter_timed);
     if (s->g_iter_ml) cudaGraphExecDestroy(s->g_iter_ml);
-    s->g_iter = s->g_factor = s->g_iter_timed = s->g_iter_ml = nullptr;
+    if (s->g_iter64) cudaGraphExecDestroy(s->g_iter64);
+    s->g_iter = s->g_factor = s->g_iter_timed = s->g_iter_ml = s->g_iter64 = nullptr;
     for (cudaEvent_t e : s->iter_events) cudaEventDestroy(e);
     s->iter_events.clear();
 }
@@ -721,7 +732,7 @@ static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* pre
     }
 }
 
-int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml) {
+int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool fp64) {
     const int n = s->geo.n, N = 3 * n;
     cudaStream_t st = s->stream;
     // right-hand side of the reduced system
@@ -731,17 +742,20 @@ int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml) {
                                                s->d_pk, s->d_v, s->d_part);
     // the learned stage (like the FP32 sweeps) is not the same linear map at
     // every application: cycles stop at the inner target, the true residual decides
-    const bool ml = use_ml && s->ml_on;
+    const bool ml = use_ml && s->ml_on && !fp64;
+    const bool fp32 = s->mixed && !fp64;
     k_s_setup<<<1, 256, 0, st>>>(s->d_ks, s->d_part, VEC_GRID, tol, maxit,
-                                 (s->mixed || ml) ? MIXED_INNER : 0.0);
+                                 (fp32 || ml) ? MIXED_INNER : 0.0);
     BO_LAUNCH_CHECK("bicgstab setup");
     if (s->ml_online) BO_CUDA(cudaMemsetAsync(s->d_ml_count, 0, sizeof(int), st));
     s->h_ks->it = 0;
     s->h_ks->maxit = maxit;
     // the timed graph carries the configured stage; a fallback solve runs untimed
-    const bool timed = s->timing && ml == s->ml_on;
+    const bool timed = s->timing && ml == s->ml_on && fp32 == s->mixed;
     if (timed) ensure_timed_graph(s);
-    cudaGraphExec_t g = timed ? s->g_iter_timed : (ml ? s->g_iter_ml : s->g_iter);
+    cudaGraphExec_t g = timed ? s->g_iter_timed
+                        : (s->mixed && !fp32) ? s->g_iter64
+                        : (ml ? s->g_iter_ml : s->g_iter);
     const int t_check = timer_id(s, "true_residual");
     int prev_it = 0;
     for (int round = 0;; ++round) {

@@ -20,7 +20,8 @@ struct TileArgs {
     int NJ, NK, T, NL;
     size_t NP;
     int* err;
-    int ysub;   // block-Jacobi slabs of ysub cell rows in y (a multiple of TJ), 0: one domain
+    int ysub;   // block-Jacobi slabs of ysub cell rows in y (a multiple of TJ), 0: no cut in y
+    int zsub;   // and of zsub cell layers in z (a multiple of TK), 0: no cut in z
 };
 
 // j is the first cell row of a block-Jacobi slab (not the first of the grid):
@@ -28,6 +29,11 @@ struct TileArgs {
 // the factors, and no face crosses the cut.  Cuts fall on tile boundaries.
 __device__ __forceinline__ bool ycut(const TileArgs& a, int j) {
     return a.ysub > 0 && j > 0 && j % a.ysub == 0;
+}
+// The same in z: layer k starts a slab, the -z coupling of layer k and the +z
+// coupling of layer k - 1 are left out.
+__device__ __forceinline__ bool zcut(const TileArgs& a, int k) {
+    return a.zsub > 0 && k > 0 && k % a.zsub == 0;
 }
 
 __device__ __forceinline__ double ld_relaxed(const double* p) {

@@ -171,15 +171,17 @@ class Sim:
 
     def solve(self, tol=1e-3, maxit=500, report=False):
         """Returns (status, iterations, sol[3n + nw]); sol solves J sol = R.
-        With report=True a fourth item gives the restarts and the true
-        relative residual ||b - Op x|| / ||b||."""
+        With report=True a fourth item gives the restarts, the true
+        relative residual ||b - Op x|| / ||b|| and the fallback mask (1: repeated
+        without the learned stage, 2: repeated with the FP64 sweeps)."""
         o = L.BoSolveOpts(tol=float(tol), max_it=int(maxit))
         rep = L.BoSolveReport()
         sol = np.zeros(3 * self.n + max(self.nw, 1))
         call("bo_solve", self.h, ctypes.byref(o), ctypes.byref(rep), ptr(sol))
         out = (rep.status, rep.iterations, sol[:3 * self.n + self.nw])
         if report:
-            return out + ({"restarts": rep.restarts, "rel_res": rep.rel_res},)
+            return out + ({"restarts": rep.restarts, "rel_res": rep.rel_res,
+                           "fallback": rep.fallback},)
         return out
 
     def newton_update(self, **opts):
@@ -223,14 +225,26 @@ class Sim:
 
     @property
     def subdomains(self):
-        """Block-Jacobi slab height in y (0: plain ILU(0))."""
-        v = ctypes.c_int()
-        call("bo_get_subdomains", self.h, ctypes.byref(v))
-        return v.value
+        """Block-Jacobi slab height in y (0: no cut in y)."""
+        return self._subdomains()[0]
 
     @subdomains.setter
     def subdomains(self, ysub):
-        call("bo_set_subdomains", self.h, int(ysub))
+        call("bo_set_subdomains", self.h, int(ysub), self._subdomains()[1])
+
+    @property
+    def subdomains_z(self):
+        """Block-Jacobi slab height in z (0: no cut in z)."""
+        return self._subdomains()[1]
+
+    @subdomains_z.setter
+    def subdomains_z(self, zsub):
+        call("bo_set_subdomains", self.h, self._subdomains()[0], int(zsub))
+
+    def _subdomains(self):
+        y, z = ctypes.c_int(), ctypes.c_int()
+        call("bo_get_subdomains", self.h, ctypes.byref(y), ctypes.byref(z))
+        return y.value, z.value
 
     # -- learned preconditioner stage ----------------------------------------
     def learn_set_params(self, theta):

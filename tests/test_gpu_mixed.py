@@ -156,6 +156,36 @@ def test_mixed_solve_true_residual(name):
         assert np.linalg.norm(res) <= tol * (1 + 1e-6) * np.linalg.norm(b) + 1e-300
 
 
+def test_failed_fp32_solve_is_repeated_with_fp64_sweeps():
+    """A solve whose FP32 attempt runs out of iterations is repeated with the
+    FP64 factors and sweeps (zero initial guess, a fresh iteration budget):
+    it converges, reports fallback 2, and its solution is the FP64 solver's.
+    The mixed solver afterwards gives its own result again (the face buffers
+    are back in FP32)."""
+    m = MODELS["ragged_33x17x9"]()
+    g, h = Sim(m, "mixed"), Sim(m, "fp64")
+    st = synth.random_state(m, seed_member=7, frac_sat=0.5)
+    p, sw, x, fl, bhp = [a.copy() for a in st]
+    for s in (g, h):
+        s.set_state(*st)
+        s.begin_step()
+        s.set_state(p * 1.003, sw + 0.004, x, fl, bhp)
+        s.assemble(0.1 * synth.DAY)
+    tol = 1e-10
+    s64, n64, x64, r64 = h.solve(tol=tol, maxit=500, report=True)
+    s32, n32, x32, r32 = g.solve(tol=tol, maxit=500, report=True)
+    assert s64 == 0 and s32 == 0 and r64["fallback"] == 0 and r32["fallback"] == 0
+    if n32 <= n64:
+        pytest.skip(f"the FP32 sweeps need no more iterations here ({n32} vs {n64})")
+    sf, nf, xf, rf = g.solve(tol=tol, maxit=n64, report=True)
+    assert sf == 0 and rf["fallback"] == 2 and rf["rel_res"] <= tol, (nf, rf)
+    assert nf > n64
+    assert vec_close(xf, x64) <= 1e-13
+    s2, n2, x2, r2 = g.solve(tol=tol, maxit=500, report=True)
+    assert s2 == 0 and r2["fallback"] == 0 and n2 == n32
+    assert vec_close(x2, x32) <= 1e-13
+
+
 # Report steps of growing length, each taken as one Newton solve (no adaptive
 # sub-steps, no cuts), so both sides solve the same discrete equations and
 # the comparison measures the precision of the solver alone.

@@ -560,6 +560,69 @@ def test_block_jacobi_ilu0_stays_in_its_subdomain():
     assert np.abs(z[j // 4 == 1]).max() > 0
 
 
+def test_block_jacobi_ilu0_is_exact_per_z_slab_in_1d():
+    """The same exactness on a column of cells in z (gravity and the z faces
+    enter the blocks): slabs of 4 layers, the last one ragged (3 layers)."""
+    m = make_model(1, 1, 11, 1e-13, 0.2, [], dz=3.0)
+    o = oracle.Oracle(m)
+    o.set_state(*synth.random_state(m, seed_member=4, frac_sat=0.5))
+    o.begin_step()
+    o.assemble(0.5 * synth.DAY)
+    rp, ci, v, R = o.system()
+    D = bcsr_to_dense(rp, ci, v, o.n)
+    o.set_subdomains(0, 4)
+    o.ilu0()
+    r = np.random.default_rng(6).standard_normal(3 * o.n)
+    z = o.ilu_apply(r)
+    for lo, hi in ((0, 4), (4, 8), (8, 11)):
+        sl = slice(3 * lo, 3 * hi)
+        zk = np.linalg.solve(D[sl, sl], r[sl])
+        assert np.allclose(z[sl], zk, rtol=1e-10, atol=1e-10 * np.abs(zk).max())
+    # a y slab height has no effect on a column one cell wide in y
+    o.set_subdomains(8, 4)
+    o.ilu0()
+    assert np.array_equal(o.ilu_apply(r), z)
+
+
+def test_block_jacobi_ilu0_boxes_in_y_and_z():
+    """With cuts in y and z the subdomains are boxes: a residual on one box
+    stays on it; with cuts in z alone a residual on one z slab stays on that
+    slab; cutting in z and cutting in y give different preconditioners."""
+    m = synth.small_model(4, 12, 10, wells="5spot", dz=3.0)
+    o = oracle.Oracle(m)
+    o.set_state(*synth.random_state(m, seed_member=8, frac_sat=0.5))
+    o.begin_step()
+    o.assemble(0.5 * synth.DAY)
+    n = o.n
+    c = np.arange(n)
+    j, k = (c // 4) % 12, c // 48
+    box = (j // 4) + 3 * (k // 4)               # 3 x 3 boxes (the last in z is 2 layers)
+    o.set_subdomains(4, 4)
+    o.ilu0()
+    rng = np.random.default_rng(9)
+    for b in (0, 4, 8):
+        r = np.zeros((n, 3))
+        r[box == b] = rng.standard_normal(((box == b).sum(), 3))
+        z = o.ilu_apply(r.reshape(-1)).reshape(n, 3)
+        assert np.all(z[box != b] == 0.0)
+        assert np.abs(z[box == b]).max() > 0
+    r = rng.standard_normal(3 * n)
+    o.set_subdomains(0, 4)
+    o.ilu0()
+    zz = o.ilu_apply(r).reshape(n, 3)
+    o.set_subdomains(4, 0)
+    o.ilu0()
+    zy = o.ilu_apply(r).reshape(n, 3)
+    assert not np.allclose(zz, zy)
+    # a residual on z slab 1 (layers 4..7) stays there when only z is cut
+    rs = np.zeros((n, 3))
+    rs[k // 4 == 1] = 1.0
+    o.set_subdomains(0, 4)
+    o.ilu0()
+    z1 = o.ilu_apply(rs.reshape(-1)).reshape(n, 3)
+    assert np.all(z1[k // 4 != 1] == 0.0)
+
+
 # ---------------------------------------------------------------------------
 # Equilibration (Section 2.1.3): RK4 zones against an independent integrator
 # ---------------------------------------------------------------------------

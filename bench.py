@@ -52,7 +52,9 @@ WORKLOADS = {
     1: "layered 60x220x85 black-oil, 5-spot wells, 10-day report steps",
     2: "Gaussian-random-field 100x100x50 black-oil, 5-spot wells, 5-day report steps",
 }
-YSUB_NAME = " as block-Jacobi over slabs of {} cell rows in y"
+def subdomain_name(ysub, zsub):
+    cuts = [f"{ysub} cell rows in y"] * bool(ysub) + [f"{zsub} cell layers in z"] * bool(zsub)
+    return f" as block-Jacobi over slabs of {' and '.join(cuts)}" if cuts else ""
 LEARNED_NAME = (" + learned stage (63-128-128-9 MLP on BF16 tensor cores, trained online "
                 "on the first warm-up report step's solver residuals)")
 PRECISION_NAMES = {"fp64": "plain FP64 ILU0-BiCGStab",
@@ -115,6 +117,8 @@ def parse():
                     help="ILU(0) preconditioner precision (mixed: FP32 factors and sweeps)")
     ap.add_argument("--ysub", type=int, default=0,
                     help="block-Jacobi ILU(0) over slabs of YSUB cell rows in y (multiple of 8)")
+    ap.add_argument("--zsub", type=int, default=0,
+                    help="and over slabs of ZSUB cell layers in z (multiple of 4)")
     ap.add_argument("--learned", action="store_true",
                     help="learned preconditioner stage: trained online during the first "
                          "--train-steps warm-up report steps, then on inside BiCGStab")
@@ -125,6 +129,9 @@ def parse():
                     help="NXxNYxNZ: a layered model of this size instead of the config (profiling)")
     ap.add_argument("--report-days", type=float, default=None,
                     help="report-step length override (profiling windows)")
+    ap.add_argument("--scan-slabs", nargs="+", default=None, metavar="Y,Z",
+                    help="profiling: the first report step from the hydrostatic state "
+                         "once per block-Jacobi slab shape (ysub,zsub), one JSON line each")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-its", type=int, default=12)
     return ap.parse_args()
@@ -272,8 +279,8 @@ def run_gb300(args):
     dt = m["dt"] if args.report_days is None else args.report_days * 86400.0
     sim = Sim(m, stream=stream)
     sim.precision = args.precision
-    if args.ysub:
-        sim.subdomains = args.ysub
+    if args.ysub or args.zsub:
+        sim.subdomains, sim.subdomains_z = args.ysub, args.zsub
     sim.init_hydrostatic()
     if args.learned:
         import synth
@@ -384,9 +391,9 @@ def run_gb300(args):
         "data": "synthetic",
         "config": {"workload": (f"{workload_name(args, m)}, {PRECISION_NAMES[args.precision]}"
                                 f"{LEARNED_NAME if args.learned else ''}"
-                                f"{YSUB_NAME.format(args.ysub) if args.ysub else ''}, "
+                                f"{subdomain_name(args.ysub, args.zsub)}, "
                                 "Newton tol 1e-6"),
-                   "precision": args.precision, "ysub": args.ysub,
+                   "precision": args.precision, "ysub": args.ysub, "zsub": args.zsub,
                    "cells": n, "newton_tol": 1e-6, "linear_tol": 1e-3,
                    "l2": (f"inputs larger than L2 (Jacobian {504 * n / 1e6:.0f} MB, ILU data "
                           f"{504 * n / 1e6:.0f} MB per model)"),
@@ -573,9 +580,48 @@ def run_ensemble(args):
         dist.destroy_process_group()
 
 
+def run_slab_scan(args):
+    """The same report step (the first, from the hydrostatic state) under
+    each block-Jacobi slab shape: wall time of the step, Newton and BiCGStab
+    iterations, time-step cuts and the per-launch kernel times."""
+    import torch
+    from paper_1910_06059_gb300 import Sim
+    shapes = [tuple(int(v) for v in a.split(",")) for a in args.scan_slabs]
+    m = model_for(args.config, args.grid)
+    n = m["nx"] * m["ny"] * m["nz"]
+    dt = m["dt"] if args.report_days is None else args.report_days * 86400.0
+    torch.cuda.set_device(0)
+    sim = Sim(m)
+    sim.init_hydrostatic()
+    snap = sim.get_state()
+    dtn = sim.dt_next
+    for ysub, zsub in shapes:
+        sim.subdomains, sim.subdomains_z = ysub, zsub
+        sim.set_state(*snap)
+        sim.dt_next = dtn
+        sim.set_timing(False)
+        sim.set_timing(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = sim.step(dt, raise_on_fail=True)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        tm = sim.timing()
+        sim.set_timing(False)
+        print(json.dumps({
+            "workload": workload_name(args, m), "ysub": ysub, "zsub": zsub,
+            "sec": round(sec, 3), "cell_steps_per_s": round(n / sec, 1),
+            "newton": rep["newton_its"], "lin": rep["lin_its"], "cuts": rep["cuts"],
+            "substeps": rep["substeps"],
+            "ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in tm.items()},
+            "launches": {k: v[1] for k, v in tm.items()}}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.scan_slabs:
+        run_slab_scan(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.config == 3:
         run_ensemble(args)

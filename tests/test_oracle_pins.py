@@ -385,6 +385,78 @@ def test_1d_incompressible_linear_profile():
 
 
 # ---------------------------------------------------------------------------
+# 1-D waterflood against the Buckley-Leverett solution: incompressible water
+# and undersaturated oil, no gravity, a rate-controlled water injector in the
+# first cell and a BHP producer in the last.  With the Corey curves and
+# viscosities of Sections 2.1.5-2.1.6 the fractional flow is
+# f(S) = (k_rw/mu_w) / (k_rw/mu_w + k_ro/mu_o); water of saturation S travels
+# at f'(S) times the injected pore volumes, and the front carries the shock
+# saturation S_f of the Welge tangent f'(S_f) (S_f - S_wc) = f(S_f) - f(S_wc).
+# The implicit upwind discretisation converges to this profile as the cells
+# and the time steps shrink together; a mistake in the fluxes, the upwinding,
+# the relative permeabilities or the viscosities changes the limit.
+# ---------------------------------------------------------------------------
+def _waterflood(N, L=200.0, area=100.0, poro=0.2, q=1e-3, days=11.0):
+    fluid = {"g": 0.0, "c_w": 0.0, "c_r": 0.0, "c_o": 0.0, "c_mu": 0.0}
+    wells = [_well(0, 0, [0], "inj", "rate", q, 9000 * PSI, phase="water"),
+             _well(N - 1, 0, [0], "prod", "bhp", 4800 * PSI, 4800 * PSI)]
+    m = make_model(N, 1, 1, 1000 * MD, poro, wells, fluid=fluid, dx=L / N, dy=10.0,
+                   dz=area / 10.0)
+    F = m["fluid"]
+    o = oracle.Oracle(m)
+    o.set_state(np.full(N, 5000 * PSI), np.full(N, F["s_wco"]), np.full(N, F["R_sb"]),
+                np.ones(N, np.uint8), np.array([5200 * PSI, 4800 * PSI]))   # undersaturated
+    dt = 10.0 / N * synth.DAY          # time steps shrink with the cells (fixed CFL)
+    steps = int(round(days * synth.DAY / dt))
+    for _ in range(steps):
+        st, rep = o.step(dt)
+        assert st == 0, rep
+    sw = o.get_state()[1]
+    assert np.all(o.get_state()[3] == 1)            # the oil stays undersaturated
+    # injected pore volumes in reservoir water volume (B_w = 1 / bw_ref here)
+    X = q / F["bw_ref"] * steps * dt / (area * poro)
+    return F, sw, L / N, X
+
+
+def _bl_fractional_flow(F):
+    swc, sor, nc = F["s_wco"], F["s_orw"], F["n_corey"]
+    mu_w = F["mu_w"]
+    mu_o = F["mu_o0"] / (1.0 + F["mu_o_r"] * F["R_sb"])
+
+    def f(S):
+        se = min(max((S - swc) / (1.0 - swc - sor), 0.0), 1.0)
+        kw, ko = se ** nc, (1.0 - se) ** nc
+        return (kw / mu_w) / (kw / mu_w + ko / mu_o)
+
+    def df(S, h=1e-7):
+        return (f(S + h) - f(S - h)) / (2 * h)
+    return f, df
+
+
+def test_waterflood_converges_to_buckley_leverett():
+    from scipy.optimize import brentq
+    errs = []
+    for N in (100, 200, 400):
+        F, sw, dx, X = _waterflood(N)
+        f, df = _bl_fractional_flow(F)
+        swc = F["s_wco"]
+        Sf = brentq(lambda S: df(S) * (S - swc) - (f(S) - f(swc)), swc + 0.05,
+                    1.0 - F["s_orw"] - 1e-6)
+        xc = (np.arange(N) + 0.5) * dx
+
+        def crossing(level):   # where the (decreasing) profile passes level
+            i = int(np.nonzero(sw < level)[0][0])
+            return xc[i - 1] + (sw[i - 1] - level) / (sw[i - 1] - sw[i]) * dx
+        x_front = X * df(Sf)
+        pts = [(crossing(0.5 * (Sf + swc)), x_front)]                 # the shock
+        pts += [(crossing(S), X * df(S)) for S in (0.6, 0.65, 0.7, 0.75, 0.8)]  # the fan
+        errs.append(max(abs(a - b) for a, b in pts) / x_front)
+    # first-order upwinding: the error falls steadily with refinement
+    assert errs[1] <= 0.7 * errs[0] and errs[2] <= 0.7 * errs[1], errs
+    assert errs[2] <= 0.035, errs
+
+
+# ---------------------------------------------------------------------------
 # Linear algebra: ILU(0) identity on the pattern, exactness in 1-D, and the
 # Schur-reduced BiCGStab solve against dense LU of the full system.
 # ---------------------------------------------------------------------------

@@ -17,6 +17,11 @@ static thread_local std::string g_last_error;
 
 void fail(bo_status st, const std::string& msg) { throw Error{st, msg}; }
 
+bo_status set_last_error(bo_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
 void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
     if (e == cudaSuccess) return;
     std::string m = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +

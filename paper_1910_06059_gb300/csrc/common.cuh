@@ -21,6 +21,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(bo_status st, const std::string& msg);
+bo_status set_last_error(bo_status st, const std::string& msg);   // returns st
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 #define BO_CUDA(call) ::bo::check_cuda((call), #call, __FILE__, __LINE__)
 #define BO_LAUNCH_CHECK(name) ::bo::check_cuda(cudaGetLastError(), name, __FILE__, __LINE__)

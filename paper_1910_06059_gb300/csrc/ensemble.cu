@@ -22,6 +22,8 @@
 
 #include "common.cuh"
 
+using bo::set_last_error;
+
 struct bo_ensemble {
     std::vector<bo_sim*> members;
     std::vector<cudaStream_t> streams;
@@ -117,17 +119,23 @@ extern "C" {
 
 bo_status bo_ensemble_create(bo_sim* const* members, int count, int streams, bo_ensemble** out) {
     if (out == nullptr || members == nullptr || count < 1 || streams < 1 || streams > 256)
-        return BO_ERR_INVALID_ARG;
+        return set_last_error(BO_ERR_INVALID_ARG,
+                              "bo_ensemble_create: NULL argument, count < 1 or streams not in 1..256");
     for (int q = 0; q < count; ++q)
-        if (members[q] == nullptr || !members[q]->props_set) return BO_ERR_STATE;
+        if (members[q] == nullptr || !members[q]->props_set)
+            return set_last_error(BO_ERR_STATE, "bo_ensemble_create: member " + std::to_string(q) +
+                                                    " is NULL or has no properties");
     for (int q = 0; q < count; ++q)
         for (int r = q + 1; r < count; ++r)
-            if (members[q] == members[r]) return BO_ERR_INVALID_ARG;
+            if (members[q] == members[r])
+                return set_last_error(BO_ERR_INVALID_ARG, "bo_ensemble_create: member " +
+                                                              std::to_string(r) + " repeats member " +
+                                                              std::to_string(q));
     auto* e = new bo_ensemble();
     e->members.assign(members, members + count);
     if (cudaGetDevice(&e->device) != cudaSuccess) {
         delete e;
-        return BO_ERR_CUDA;
+        return set_last_error(BO_ERR_CUDA, "bo_ensemble_create: cudaGetDevice failed");
     }
     e->streams.assign(256, nullptr);   // created on first use
     e->active = streams;
@@ -136,14 +144,16 @@ bo_status bo_ensemble_create(bo_sim* const* members, int count, int streams, bo_
 }
 
 bo_status bo_ensemble_set_schedule(bo_ensemble* e, int streams, int largest_first) {
-    if (e == nullptr || streams < 1 || streams > 256) return BO_ERR_INVALID_ARG;
+    if (e == nullptr || streams < 1 || streams > 256)
+        return set_last_error(BO_ERR_INVALID_ARG,
+                              "bo_ensemble_set_schedule: NULL ensemble or streams not in 1..256");
     e->active = streams;
     e->largest_first = largest_first != 0;
     return BO_OK;
 }
 
 bo_status bo_ensemble_get_schedule(const bo_ensemble* e, int* streams, int* largest_first) {
-    if (e == nullptr) return BO_ERR_INVALID_ARG;
+    if (e == nullptr) return set_last_error(BO_ERR_INVALID_ARG, "bo_ensemble_get_schedule: NULL ensemble");
     if (streams) *streams = e->active;
     if (largest_first) *largest_first = e->largest_first ? 1 : 0;
     return BO_OK;
@@ -151,28 +161,44 @@ bo_status bo_ensemble_get_schedule(const bo_ensemble* e, int* streams, int* larg
 
 bo_status bo_ensemble_step(bo_ensemble* e, double dt, const bo_newton_opts* opts,
                            bo_step_report* reports, bo_status* statuses) {
-    if (e == nullptr || !(dt > 0.0)) return BO_ERR_INVALID_ARG;
+    if (e == nullptr || !(dt > 0.0))
+        return set_last_error(BO_ERR_INVALID_ARG, "bo_ensemble_step: NULL ensemble or dt <= 0");
     const int count = (int)e->members.size();
     std::vector<bo_status> st(count, BO_OK);
     try {
         run_step(e, dt, opts, reports, st.data());
     } catch (const std::exception&) {   // no memory for the schedule's vectors
-        return BO_ERR_STATE;
+        return set_last_error(BO_ERR_STATE, "bo_ensemble_step: out of host memory");
     }
     bo_status first = BO_OK;
+    int failed = 0;
     for (int q = 0; q < count; ++q) {
         if (statuses) statuses[q] = st[q];
-        if (first == BO_OK && st[q] != BO_OK) first = st[q];
+        if (st[q] != BO_OK) {
+            if (first == BO_OK) {
+                first = st[q];
+                set_last_error(first, "bo_ensemble_step: member " + std::to_string(q) +
+                                          " failed with status " + std::to_string((int)first));
+            }
+            ++failed;
+        }
     }
+    if (failed > 1)
+        set_last_error(first, "bo_ensemble_step: " + std::to_string(failed) +
+                                  " members failed; the first with status " +
+                                  std::to_string((int)first) + " (per-member statuses in statuses[])");
     return first;
 }
 
 bo_status bo_ensemble_autotune(bo_ensemble* e, double dt_probe, const bo_newton_opts* opts,
                                const int* candidates, int ncand, double* seconds) {
     if (e == nullptr || candidates == nullptr || ncand < 1 || !(dt_probe > 0.0))
-        return BO_ERR_INVALID_ARG;
+        return set_last_error(BO_ERR_INVALID_ARG,
+                              "bo_ensemble_autotune: NULL argument, ncand < 1 or dt_probe <= 0");
     for (int c = 0; c < ncand; ++c)
-        if (candidates[c] < 1 || candidates[c] > 256) return BO_ERR_INVALID_ARG;
+        if (candidates[c] < 1 || candidates[c] > 256)
+            return set_last_error(BO_ERR_INVALID_ARG,
+                                  "bo_ensemble_autotune: a candidate is not in 1..256 streams");
     const int count = (int)e->members.size();
     std::vector<Snapshot> snap(count);
     for (int q = 0; q < count; ++q) {
@@ -191,7 +217,7 @@ bo_status bo_ensemble_autotune(bo_ensemble* e, double dt_probe, const bo_newton_
             try {
                 run_step(e, dt_probe, opts, nullptr, st.data());
             } catch (const std::exception&) {
-                return BO_ERR_STATE;
+                return set_last_error(BO_ERR_STATE, "bo_ensemble_autotune: out of host memory");
             }
             const double sec =
                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -211,11 +237,13 @@ bo_status bo_ensemble_autotune(bo_ensemble* e, double dt_probe, const bo_newton_
     }
     e->active = best_w;
     e->largest_first = best_lf;
-    return best < 1e300 ? BO_OK : BO_ERR_NOT_CONVERGED;
+    if (best < 1e300) return BO_OK;
+    return set_last_error(BO_ERR_NOT_CONVERGED,
+                          "bo_ensemble_autotune: no candidate schedule stepped every member");
 }
 
 bo_status bo_ensemble_destroy(bo_ensemble* e) {
-    if (e == nullptr) return BO_ERR_INVALID_ARG;
+    if (e == nullptr) return set_last_error(BO_ERR_INVALID_ARG, "bo_ensemble_destroy: NULL ensemble");
     for (auto& s : e->streams)
         if (s) cudaStreamDestroy(s);
     delete e;

@@ -61,9 +61,10 @@ class Ensemble:
         n = len(self.members)
         reps = (L.BoStepReport * n)()
         sts = (ctypes.c_int * n)()
-        st = L.load().bo_ensemble_step(self.h, float(dt), ctypes.byref(o), reps, sts)
+        lib = L.load()
+        st = lib.bo_ensemble_step(self.h, float(dt), ctypes.byref(o), reps, sts)
         if st != 0 and raise_on_fail:
-            raise L.BoError(st, "bo_ensemble_step: a member failed (status %d)" % st)
+            raise L.BoError(st, lib.bo_last_error().decode())
         out = [{"newton_its": r.newton_its, "lin_its": r.lin_its, "cuts": r.cuts,
                 "substeps": r.substeps} for r in reps]
         return list(sts), out

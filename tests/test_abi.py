@@ -65,3 +65,40 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert st == 1  # BO_ERR_INVALID_ARG
     st = lib.bo_create_grid(2, 2, 2, None, None, None, ctypes.c_double(0.0), None)
     assert st == 1
+
+
+def _null_args(argtypes):
+    return [0.0 if t is ctypes.c_double else (0 if t is ctypes.c_int else None)
+            for t in argtypes]
+
+
+def test_every_entry_point_rejects_a_null_handle(lib):
+    """Every call that takes a simulator or ensemble handle returns
+    BO_ERR_INVALID_ARG or BO_ERR_STATE for NULL, sets the last-error message
+    and touches no device (this runs without a GPU).  bo_destroy(NULL) is a
+    no-op, like free(NULL)."""
+    from paper_1910_06059_gb300 import _lib
+    lib.bo_last_error.restype = ctypes.c_char_p
+    checked = []
+    for name, argtypes in _lib._SIGS.items():
+        if name in ("bo_create_grid", "bo_residual_norms_noalloc", "bo_destroy"):
+            continue
+        fn = getattr(lib, name)
+        fn.argtypes = argtypes
+        fn.restype = ctypes.c_int
+        st = fn(*_null_args(argtypes))
+        assert st in (1, 7), (name, st)
+        # the message names the call (the _dev variants share their host twin's)
+        assert name.replace("_dev", "").encode() in lib.bo_last_error(), name
+        checked.append(name)
+    assert len(checked) >= 40
+    lib.bo_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.bo_destroy(None) == 0
+
+
+def test_noalloc_arguments_are_checked_without_gpu(lib):
+    lib.bo_last_error.restype = ctypes.c_char_p
+    f = lib.bo_residual_norms_noalloc
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_double] + [ctypes.c_void_p] * 2
+    assert f(None, None, None, 10, 1.0, None, None) == 1
+    assert b"NULL" in lib.bo_last_error()

@@ -100,6 +100,10 @@ def ncu_traffic(kernel, cells):
 
 
 def op_counts(config):
+    if config not in OPS_PER_REPORT_STEP:
+        raise SystemExit(f"per-report-step operation counts are recorded for config(s) "
+                         f"{sorted(OPS_PER_REPORT_STEP)} only (the timed workload); "
+                         f"config {config} has none")
     return OPS_PER_REPORT_STEP[config]
 
 

@@ -285,6 +285,58 @@ def test_flux_terms_cancel_in_closed_reservoir():
     assert np.all(np.abs(R.sum(axis=0)) <= 1e-12 * flux_scale * o.n)
 
 
+def test_convergence_norms_closed_form():
+    """MB and CNV (Section 2.3's tolerance-mb / tolerance-cnv) on two cells
+    that exchange nothing (permeability 1e-30 m^2): each residual is the
+    accumulation change (PV/dt)(A(p) - A(p0)) with A from the closed forms of
+    the fluid and rock (water b_w exponential in p, live oil b_o at its r_go,
+    m_phi exponential in p), B_avg is the mean of 1/b over the cells at the
+    current state, MB sums the residual and divides by the summed pore
+    volume, CNV takes the largest residual per pore volume."""
+    from math import exp
+    wells = []
+    m = make_model(2, 1, 1, 1e-30, 0.2, wells, dx=10.0, dy=20.0, dz=5.0)
+    m["poro"] = np.array([0.15, 0.3])
+    F = m["fluid"]
+    o = oracle.Oracle(m)
+    p0 = np.array([3000.0, 3500.0]) * PSI
+    p1 = np.array([3100.0, 3420.0]) * PSI
+    sw = np.array([0.3, 0.45])
+    r = np.array([100.0, 140.0])                  # undersaturated: p > p_b r / R_sb
+    fl = np.ones(2, np.uint8)
+    o.set_state(p0, sw, r, fl, np.zeros(1))
+    o.begin_step()
+    o.set_state(p1, sw, r, fl, np.zeros(1))
+    dt = 3.0 * synth.DAY
+    o.assemble(dt)
+    nrm = o.norms(dt)
+
+    def b_w(p):
+        return F["bw_ref"] * exp(F["c_w"] * (p - F["p_ref"]))
+
+    def b_o(p, rr):
+        return exp(F["c_o"] * (p - F["p_b"] * rr / F["R_sb"])) / (1.0 + F["Bo_slope"] * rr)
+
+    def b_g(p):
+        return p / (F["p_sc"] * F["Z"])
+
+    def acc(p, s, rr):
+        mphi = exp(F["c_r"] * (p - F["p_ref"]))
+        return np.array([mphi * b_w(p) * s, mphi * b_o(p, rr) * (1 - s),
+                         mphi * rr * b_o(p, rr) * (1 - s)])
+
+    pv = m["poro"] * 10.0 * 20.0 * 5.0
+    R = np.array([pv[i] / dt * (acc(p1[i], sw[i], r[i]) - acc(p0[i], sw[i], r[i]))
+                  for i in range(2)])                                    # [cell][w, o, g]
+    binv = np.array([[1 / b_w(p1[i]), 1 / b_o(p1[i], r[i]), 1 / b_g(p1[i])] for i in range(2)])
+    bavg = binv.mean(axis=0)
+    mb = dt * bavg * np.abs(R.sum(axis=0)) / pv.sum()
+    cnv = dt * bavg * np.max(np.abs(R) / pv[:, None], axis=0)
+    assert np.allclose(nrm[0:3], mb, rtol=1e-11, atol=0), (nrm[0:3], mb)
+    assert np.allclose(nrm[3:6], cnv, rtol=1e-11, atol=0), (nrm[3:6], cnv)
+    assert nrm[6] == 0.0
+
+
 def test_mass_conservation_per_step():
     m = synth.small_model(5, 4, 3, wells="none", dz=6.0)
     o = oracle.Oracle(m)

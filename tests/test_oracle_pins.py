@@ -610,6 +610,48 @@ def test_schur_bicgstab_matches_dense_lu(seed, frac_sat):
     del scale
 
 
+def test_newton_update_chop_and_switching_cases():
+    """The Newton update's safeguards of Section 2.3 on hand-made cases, one
+    per cell of a row (the update is cell-local): a pressure step past 30% of
+    p is cut to 30%; saturation steps are scaled together to at most 0.2; a
+    dissolved-gas step is cut to 0.2 R_sb; a gas saturation that would turn
+    negative makes the cell undersaturated at r_go = r_s(p); an r_go above
+    r_s(p) makes it saturated with s_g = 0; an undersaturated cell's pressure
+    stops 5% below the saturation pressure of its r_go (and the cell then
+    switches); s_w stays in [0, 1]."""
+    n = 6
+    m = make_model(n, 1, 1, 100 * MD, 0.2, [])
+    F = m["fluid"]
+    o = oracle.Oracle(m)
+    rs = lambda p: F["R_sb"] * p / F["p_b"]           # r_s(p), linear (Section 2.1.4)
+    SAT, USAT = 0, 1
+    p = np.array([3000, 3000, 5000, 4000, 2500, 5000], float) * PSI
+    sw = np.array([0.3, 0.3, 0.2, 0.2, 0.2, 0.95])
+    x = np.array([0.05, 0.2, 150.0, 170.0, 100.0, 150.0])
+    fl = np.array([SAT, SAT, USAT, USAT, USAT, USAT], np.uint8)
+    o.set_state(p, sw, x, fl, np.zeros(1))
+    dy = np.zeros((n, 3))
+    dy[0] = [0.5 * p[0], 0.05, -0.1]     # dp cut to 0.3 p; s_g -> -0.05: switch
+    dy[1] = [0.0, 0.5, -0.25]            # scaled by 0.4: ds_w 0.2, ds_g -0.1
+    dy[2] = [0.0, 0.0, 100.0]            # dr cut to 36
+    dy[3] = [0.0, 0.0, 20.0]             # r_go 190 > r_s = 180: switch
+    dy[4] = [-600 * PSI, 0.0, 0.0]       # stops at 0.95 p_sat(100), then switches
+    dy[5] = [0.0, 0.1, 0.0]              # s_w 1.05 -> 1
+    o.newton_update(-dy.reshape(-1))     # the update is dy = -sol
+    pn, swn, xn, fln, _ = o.get_state()
+    p0 = 1.3 * p[0]
+    assert np.isclose(pn[0], p0, rtol=1e-15) and fln[0] == USAT
+    assert np.isclose(xn[0], rs(p0), rtol=1e-14) and np.isclose(swn[0], 0.35)
+    assert fln[1] == SAT and np.isclose(swn[1], 0.5) and np.isclose(xn[1], 0.1)
+    assert fln[2] == USAT and np.isclose(xn[2], 150.0 + 0.2 * F["R_sb"])
+    assert fln[3] == SAT and xn[3] == 0.0 and np.isclose(swn[3], 0.2)
+    assert np.isclose(pn[4], 0.95 * F["p_b"] * 100.0 / F["R_sb"], rtol=1e-14)
+    # below its saturation pressure the cell holds more gas than r_s(p): saturated, s_g = 0
+    assert fln[4] == SAT and xn[4] == 0.0
+    assert swn[5] == 1.0
+    assert np.array_equal(pn[[1, 2, 3, 5]], p[[1, 2, 3, 5]])
+
+
 def test_newton_converges_fast_near_solution():
     """Near the solution the Newton iteration with exact linear solves
     converges quadratically (Eq. linsystem): once the scaled residual is

@@ -901,6 +901,45 @@ def test_producer_inflow_by_hand(flag):
     assert np.allclose(R, want, rtol=1e-12, atol=0)
 
 
+def test_producer_wellbore_head_over_two_layers():
+    """A BHP producer perforating two stacked cells (Eq. wellinflow with the
+    wellbore head of Section 2.2.1): the datum is the first connection, the
+    head of the connection below it is g rho_well dz with rho_well the
+    mobility-weighted density of the connected cells at the step start, and
+    each connection produces q_a = WI b_a lambda_a (p_j - p_bhp - h_j).  The
+    face flux between the cells cancels in the sum of their residuals, which
+    must equal the summed connection rates."""
+    pb, dz = 3000 * PSI, 6.0
+    m = make_model(1, 1, 2, 200 * MD, 0.2, [_well(0, 0, [0, 1], "prod", "bhp", pb, pb)],
+                   dx=30.0, dy=30.0, dz=dz)
+    o = oracle.Oracle(m)
+    p = np.array([25.0e6, 25.3e6])
+    sw = np.array([0.3, 0.45])
+    x = np.array([120.0, 120.0])
+    fl = np.ones(2, np.uint8)
+    o.set_state(p, sw, x, fl, np.array([pb]))
+    o.begin_step()
+    o.assemble(synth.DAY)
+    R = o.system()[3]
+    wi = o.static()["wi"]
+    cps = [_props_at(m, p[j], sw[j], x[j], 1) for j in range(2)]
+    num = sum(cp[f"lam_{a}"][0] * cp[f"rho_{a}"][0] for cp in cps for a in "wog")
+    den = sum(cp[f"lam_{a}"][0] for cp in cps for a in "wog")
+    h = [0.0, m["fluid"]["g"] * (num / den) * dz]
+    want = np.zeros(3)
+    for j, cp in enumerate(cps):
+        dp = p[j] - pb - h[j]
+        assert dp > 0
+        qo = wi[j] * cp["b_o"][0] * cp["lam_o"][0] * dp
+        want += [wi[j] * cp["b_w"][0] * cp["lam_w"][0] * dp, qo,
+                 wi[j] * cp["b_g"][0] * cp["lam_g"][0] * dp + cp["r_go"][0] * qo]
+    assert np.allclose(R.sum(axis=0), want, rtol=1e-11, atol=0), (R.sum(axis=0), want)
+    # the match is far finer than the head's share of the oil rate, so a
+    # missing or misplaced head would fail it
+    assert abs(R.sum(axis=0)[1] - want[1]) < 1e-6 * abs(
+        wi[1] * cps[1]["b_o"][0] * cps[1]["lam_o"][0] * h[1])
+
+
 def test_rate_injector_meets_its_target():
     """A water injector under rate control in a single layer (no wellbore
     head): at convergence its surface rate, summed by hand over the

@@ -222,6 +222,17 @@ bo_status bo_get_system(const bo_sim* sim, int* rowptr, int* colind, double* val
 bo_status bo_get_wells(const bo_sim* sim, double* Rw, double* Dw, double* B, double* C,
                        int* control);
 
+/* Well production report: per well the surface rates of water, oil and gas
+ * (m^3/s at surface conditions, the connection inflows of Eq. (wellinflow)
+ * summed over the well's connections, gas including the dissolved gas of
+ * the produced oil) at the state of the last assembly, production positive
+ * and injection negative; after a successful bo_step that is the converged
+ * state of its last sub-step.  rates[3*nwells] (well-major), bhp[nwells]
+ * (Pa, current), control[nwells] (0 rate, 1 BHP, current); any pointer may
+ * be NULL.  Zero rates before the first assembly.  Requires
+ * bo_set_properties (BO_ERR_STATE otherwise). */
+bo_status bo_get_well_rates(const bo_sim* sim, double* rates, double* bhp, int* control);
+
 /* Block ILU(0) of the last assembly's reservoir matrix A in natural order.
  * On the 7-point pattern only the diagonal blocks change (the grid graph is
  * bipartite, so no fill position of ILU(0) lies in the pattern), giving

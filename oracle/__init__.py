@@ -68,6 +68,7 @@ def lib():
         L.orc_assemble.argtypes = [P, d]
         L.orc_get_system.argtypes = [P] * 5
         L.orc_get_wells.argtypes = [P] * 6
+        L.orc_well_rates.argtypes = [P] * 4
         L.orc_set_well_control.argtypes = [P, i, i, d]
         L.orc_norms.argtypes = [P, d, P]
         L.orc_residual_check.argtypes = [P, P, P]
@@ -228,6 +229,15 @@ class Oracle:
                         "C": C[3 * off:3 * (off + nc)].reshape(nc, 3), "control": int(ctl[q])})
             off += nc
         return out
+
+    def well_rates(self):
+        """Per-well surface rates [nw, 3] (water, oil, gas; production
+        positive) at the last assembly, current BHP [nw] and control [nw]."""
+        nw = max(self.nw, 1)
+        q, bhp = np.zeros(3 * nw), np.zeros(nw)
+        ctl = np.zeros(nw, dtype=np.int32)
+        lib().orc_well_rates(self.h, _p(q), _p(bhp), _p(ctl))
+        return q.reshape(-1, 3)[:self.nw], bhp[:self.nw], ctl[:self.nw]
 
     def set_well_control(self, w, control, bhp):
         lib().orc_set_well_control(self.h, int(w), int(control), float(bhp))

@@ -197,6 +197,8 @@ struct Well {
     double bhp = 0.0;
     // Linearisation of the well (rate-controlled wells only).
     double Rw = 0.0, Dw = 0.0;
+    // Surface rates (w, o, g) summed over the connections at the last assembly.
+    double qs[3] = {0.0, 0.0, 0.0};
     std::vector<double> B;  // 3 per connection: dR_w/dy_cell
     std::vector<double> C;  // 3 per connection: dR_cell/dbhp
 };
@@ -459,6 +461,7 @@ static void assemble(Model& m, double dt) {
     for (Well& w : m.wells) {
         int nc = (int)w.cells.size();
         w.B.assign(3 * nc, 0.0); w.C.assign(3 * nc, 0.0);
+        w.qs[0] = w.qs[1] = w.qs[2] = 0.0;
         Dual<4> rate(0.0);
         for (int con = 0; con < nc; ++con) {
             int c = w.cells[con];
@@ -467,6 +470,7 @@ static void assemble(Model& m, double dt) {
             double blk[9];
             for (int a = 0; a < 3; ++a) {
                 m.R[3 * c + a] += q[a].v;
+                w.qs[a] += q[a].v;
                 for (int v = 0; v < 3; ++v) blk[3 * a + v] = q[a].d[v];
                 w.C[3 * con + a] = q[a].d[3];
             }
@@ -1143,6 +1147,17 @@ void orc_get_wells(void* h, double* rw, double* dw, double* B, double* C, int* c
         rw[w] = wl.Rw; dw[w] = wl.Dw; control[w] = wl.control;
         for (size_t k = 0; k < wl.B.size(); ++k) { B[q + k] = wl.B[k]; C[q + k] = wl.C[k]; }
         q += (int)wl.B.size();
+    }
+}
+
+// Per well: surface rates (w, o, g) of the last assembly, current BHP and control.
+void orc_well_rates(void* h, double* rates, double* bhp, int* control) {
+    Model* m = static_cast<Model*>(h);
+    for (size_t w = 0; w < m->wells.size(); ++w) {
+        const Well& wl = m->wells[w];
+        for (int a = 0; a < 3; ++a) rates[3 * w + a] = wl.qs[a];
+        bhp[w] = wl.bhp;
+        control[w] = wl.control;
     }
 }
 

@@ -90,6 +90,7 @@ _SIGS = {
     "bo_norms": [P, c_double, P],
     "bo_get_system": [P, P, P, P, P, P],
     "bo_get_wells": [P, P, P, P, P, P],
+    "bo_get_well_rates": [P, P, P, P],
     "bo_factor": [P, P],
     "bo_precond_apply": [P, P, P],
     "bo_apply_op": [P, P, P],

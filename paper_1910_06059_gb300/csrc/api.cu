@@ -644,6 +644,23 @@ bo_status bo_get_system(const bo_sim* s, int* rowptr, int* colind, double* vals,
     });
 }
 
+bo_status bo_get_well_rates(const bo_sim* s, double* rates, double* bhp, int* control) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_get_well_rates: properties not set");
+        if (s->nw == 0) return;
+        std::vector<WellDev> w(s->nw);
+        BO_CUDA(cudaMemcpyAsync(w.data(), s->d_wells, sizeof(WellDev) * s->nw,
+                                cudaMemcpyDeviceToHost, s->stream));
+        BO_CUDA(cudaStreamSynchronize(s->stream));
+        for (int q = 0; q < s->nw; ++q) {
+            if (rates)
+                for (int a = 0; a < 3; ++a) rates[3 * q + a] = w[q].qs[a];
+            if (bhp) bhp[q] = w[q].bhp;
+            if (control) control[q] = w[q].ctl;
+        }
+    });
+}
+
 bo_status bo_get_wells(const bo_sim* s, double* Rw, double* Dw, double* B, double* C, int* control) {
     return guarded([&] {
         need(s && s->assembled, BO_ERR_STATE, "bo_get_wells: no assembly");

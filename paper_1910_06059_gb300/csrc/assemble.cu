@@ -549,7 +549,7 @@ k_wells(Geom g, DevFluid F, WellDev* __restrict__ wells, const int* __restrict__
     int n = g.n;
     WellDev& W = wells[blockIdx.x];
     const bool rate = (W.ctl == 0);
-    double rsum = 0.0, dsum = 0.0;
+    double rsum = 0.0, dsum = 0.0, qsum[3] = {0.0, 0.0, 0.0};
     for (int q = threadIdx.x; q < W.ncon; q += blockDim.x) {
         int con = W.off + q;
         int c = con_cell[con];
@@ -595,6 +595,7 @@ k_wells(Geom g, DevFluid F, WellDev* __restrict__ wells, const int* __restrict__
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             R[a * n + c] += qv[a];
+            qsum[a] += qv[a];
 #pragma unroll
             for (int s = 0; s < 3; ++s) A[(size_t)(3 * a + s) * n + c] += qd[a][s];
         }
@@ -615,18 +616,24 @@ k_wells(Geom g, DevFluid F, WellDev* __restrict__ wells, const int* __restrict__
         rsum += rv;
         dsum += rb;
     }
-    __shared__ double sr[WELL_BS], sd[WELL_BS];
+    __shared__ double sr[WELL_BS], sd[WELL_BS], sq[3][WELL_BS];
     sr[threadIdx.x] = rsum;
     sd[threadIdx.x] = dsum;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sq[a][threadIdx.x] = qsum[a];
     __syncthreads();
     for (int o = WELL_BS / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
             sr[threadIdx.x] += sr[threadIdx.x + o];
             sd[threadIdx.x] += sd[threadIdx.x + o];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sq[a][threadIdx.x] += sq[a][threadIdx.x + o];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) W.qs[a] = sq[a][0];
         if (rate) {
             W.Rw = sr[0] - W.target;
             W.Dw = sd[0];

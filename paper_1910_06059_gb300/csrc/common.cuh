@@ -59,6 +59,7 @@ struct WellDev {
     double target, limit, bhp, bhp_bk;
     double z_datum, rho_well;
     double Rw, Dw, xw;
+    double qs[3];   // surface rates (w, o, g) summed over the connections at the last assembly
 };
 
 // Scalars of the BiCGStab recurrence, kept on the device.

@@ -151,6 +151,16 @@ class Sim:
             off += nc
         return out
 
+    def well_rates(self):
+        """Per-well surface rates [nw, 3] (water, oil, gas; m^3/s, production
+        positive) at the last assembly, with the current BHP [nw] and control
+        [nw] (0 rate, 1 BHP)."""
+        nw = max(self.nw, 1)
+        q, bhp = np.zeros(3 * nw), np.zeros(nw)
+        ctl = np.zeros(nw, dtype=np.int32)
+        call("bo_get_well_rates", self.h, ptr(q), ptr(bhp), ptr(ctl))
+        return q.reshape(-1, 3)[:self.nw], bhp[:self.nw], ctl[:self.nw]
+
     # -- linear solver -------------------------------------------------------
     def factor(self):
         dinv = np.zeros(9 * self.n)

@@ -214,6 +214,45 @@ def test_newton_steps_parity(name, steps, dt_days):
         assert np.allclose(bg, bo, rtol=1e-6)
 
 
+@pytest.mark.parametrize("name", ["small_5spot", "gas_7x6x5", "config0"])
+def test_well_rates_parity(name):
+    """Per-well surface rates (bo_get_well_rates): at an assembled state they
+    match the oracle's to rounding (the connection terms match at 1e-12, the
+    sums differ in order); after Newton steps at tight tolerances every
+    rate-controlled well meets its target and the rates match the oracle's
+    to the tolerance of the states (pressure 1e-6 relative, acting on
+    drawdowns of about 1e-2 of the pressure)."""
+    m, g, o = _pair(name, seed=4)
+    dt = 2 * synth.DAY
+    g.assemble(dt)
+    o.assemble(dt)
+    qg, bg, cg = g.well_rates()
+    qo, bo, co = o.well_rates()
+    assert qg.shape == qo.shape == (len(m["wells"]), 3)
+    assert np.array_equal(cg, co) and np.array_equal(bg, bo)
+    for w in range(len(qo)):
+        floor = 1e-3 * np.abs(qo[w]).max() + 1e-300
+        assert np.all(np.abs(qg[w] - qo[w]) <= 1e-11 * np.maximum(np.abs(qo[w]), floor)), w
+    g2, o2 = Sim(m), oracle.Oracle(m)
+    g2.init_hydrostatic()
+    o2.init_hydrostatic()
+    tight = dict(tol_mb=1e-10, tol_cnv=1e-10, tol_well=1e-10, tol_lin=1e-10)
+    for _ in range(2):
+        stg, _ = g2.step(dt, **tight)
+        sto, _ = o2.step(dt, **tight)
+        assert stg == 0 and sto == 0
+    qg, bg, cg = g2.well_rates()
+    qo, bo, co = o2.well_rates()
+    assert np.array_equal(cg, co)
+    for w, well in enumerate(m["wells"]):
+        if cg[w] == 0:   # rate control: the controlled surface rate meets its target
+            a = 0 if well["phase"] == "water" else 2
+            ctl = -qg[w, a] if well["kind"] == "inj" else qg[w, 1]
+            assert abs(ctl - well["target"]) <= 1e-8 * well["target"], w
+        floor = 1e-3 * np.abs(qo[w]).max() + 1e-300
+        assert np.all(np.abs(qg[w] - qo[w]) <= 1e-3 * np.maximum(np.abs(qo[w]), floor)), w
+
+
 def test_step_restores_state_on_failure():
     """A report step that cannot converge returns BO_ERR_NOT_CONVERGED and
     leaves the state exactly as it was (host-side fault injection: a

@@ -899,6 +899,26 @@ def test_producer_inflow_by_hand(flag):
     want = [wi * b[0] * lam[0] * dp, wi * b[1] * lam[1] * dp,
             wi * (b[2] * lam[2] + rgo * b[1] * lam[1]) * dp]
     assert np.allclose(R, want, rtol=1e-12, atol=0)
+    # the production report gives the same surface rates
+    q, bhp, ctl = o.well_rates()
+    assert np.allclose(q[0], want, rtol=1e-12, atol=0) and bhp[0] == pb and ctl[0] == 1
+
+
+def test_well_rates_sum_the_residual():
+    """At the step-start state the accumulation term vanishes and the face
+    fluxes cancel in the sum over cells, so the summed residual of each
+    component is the sum of the wells' reported surface rates."""
+    m = synth.small_model(6, 5, 4, wells="5spot", dz=4.0)
+    o = oracle.Oracle(m)
+    o.set_state(*synth.random_state(m, seed_member=6, frac_sat=0.5))
+    o.begin_step()
+    o.assemble(synth.DAY)
+    R = o.system()[3]
+    q, bhp, ctl = o.well_rates()
+    assert q.shape == (len(m["wells"]), 3)
+    scale = np.abs(q).sum(axis=0) + np.abs(R).sum(axis=0) * 1e-4
+    assert np.all(np.abs(R.sum(axis=0) - q.sum(axis=0)) <= 1e-10 * scale)
+    assert np.any(q > 0) and np.any(q < 0)      # producers and an injector
 
 
 def test_producer_wellbore_head_over_two_layers():

@@ -6,6 +6,7 @@ ABI of ``include/bo.h``); this package only marshals arguments to it.
 from ._lib import BoError, EXPORTED, LIB_PATH, load, newton_opts  # noqa: F401
 from .sim import Sim  # noqa: F401
 from .ensemble import Ensemble  # noqa: F401
+from .report import StepLog  # noqa: F401
 
 
 def build(force: bool = False) -> str:

@@ -1,4 +1,4 @@
-"""Checkpoint/restart and failure detection on the GPU path."""
+"""Checkpoint/restart, the run log and failure detection on the GPU path."""
 from __future__ import annotations
 
 import numpy as np
@@ -60,3 +60,26 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     g.init_hydrostatic()
     st2, rep = g.step(synth.DAY)
     assert st2 == 0
+
+
+def test_step_log_reports_the_library_values():
+    """The JSON run log carries bo_step's counters and the well production
+    report of the converged state, one line per report step."""
+    import io
+    import json
+    from paper_1910_06059_gb300 import Sim
+    from paper_1910_06059_gb300.report import StepLog
+    m = synth.config0()
+    g = Sim(m)
+    g.init_hydrostatic()
+    out = io.StringIO()
+    log = StepLog(g, out)
+    recs = [log.step(m["dt"])[1] for _ in range(2)]
+    lines = [json.loads(s) for s in out.getvalue().splitlines()]
+    assert lines == recs and [r["t_days"] for r in lines] == [30.0, 60.0]
+    rates, bhp, control = g.well_rates()
+    last = lines[-1]["wells"]
+    for q in range(len(last)):
+        assert np.isclose(last[q]["q_gas_m3_day"], rates[q, 2] * 86400.0, rtol=1e-15)
+        assert last[q]["bhp_pa"] == bhp[q]
+    assert all(r["status"] == 0 and r["newton_its"] > 0 for r in lines)

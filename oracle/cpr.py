@@ -106,13 +106,45 @@ def aggregate(S: sp.csr_matrix) -> np.ndarray:
     return agg
 
 
-class AMG:
-    """Plain-aggregation hierarchy of A and its V-cycle."""
+def transmissibility_laplacian(Tx, Ty, Tz, nx, ny, nz) -> sp.csr_matrix:
+    """The graph Laplacian of the face transmissibilities (T of the +x, +y,
+    +z face of each cell, natural order), with a tiny diagonal shift."""
+    n = nx * ny * nz
+    c = np.arange(n)
+    i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+    rows, cols, vals = [], [], []
+    for T, off, inside in ((Tx, 1, i < nx - 1), (Ty, nx, j < ny - 1), (Tz, nx * ny, k < nz - 1)):
+        cc = c[inside]
+        rows += [cc, cc + off]
+        cols += [cc + off, cc]
+        vals += [-np.asarray(T)[cc], -np.asarray(T)[cc]]
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n))
+    d = -np.asarray(A.sum(axis=1)).ravel()
+    return (A + sp.diags(d * (1.0 + 1e-12) + 1e-300)).tocsr()
 
-    def __init__(self, A, theta=0.25, coarse_size=200, max_levels=12, nu=2, omega=2.0 / 3.0):
+
+class AMG:
+    """Plain-aggregation hierarchy of A and its V-cycle.  With ``prolongators``
+    the aggregation is not recomputed: the given piecewise-constant maps (for
+    example the hierarchy of the transmissibility Laplacian, built once per
+    model) carry A's Galerkin coarse operators."""
+
+    def __init__(self, A, theta=0.25, coarse_size=200, max_levels=12, nu=2, omega=2.0 / 3.0,
+                 prolongators=None):
         self.nu, self.omega = nu, omega
         self.A, self.P, self.dinv = [], [], []
         A = sp.csr_matrix(A)
+        if prolongators is not None:
+            for P in prolongators:
+                self.A.append(A)
+                self.dinv.append(1.0 / A.diagonal())
+                self.P.append(P)
+                A = (P.T @ A @ P).tocsr()
+            self.A.append(A)
+            self.dinv.append(1.0 / A.diagonal())
+            self.coarse = np.linalg.inv(A.toarray())
+            return
         while True:
             self.A.append(A)
             self.dinv.append(1.0 / A.diagonal())

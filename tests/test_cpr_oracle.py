@@ -14,7 +14,7 @@ import oracle
 import synth
 from helpers import bcsr_to_dense
 from oracle.cpr import (AMG, CPR, aggregate, bicgstab, diagonal_blocks, pressure_matrix,
-                        quasi_impes_weights, strength)
+                        quasi_impes_weights, strength, transmissibility_laplacian)
 
 
 def _reduced_rhs(o):
@@ -168,3 +168,30 @@ def test_cpr_cuts_bicgstab_iterations_on_the_layered_pressure_pulse(layered_syst
     for x in (x0, x1):
         assert np.linalg.norm(b - op(x)) <= 1.01e-3 * np.linalg.norm(b)
     assert n_cpr * 4 <= n_ilu
+
+
+def test_fixed_hierarchy_from_the_transmissibilities(layered_system):
+    """Aggregates built once from the transmissibility Laplacian carry each
+    Newton system's pressure matrix: the Galerkin coarse operators of a
+    piecewise-constant P keep aggregated row sums, (P^T A P) 1 = P^T (A 1),
+    and CPR with that fixed hierarchy still needs a small fraction of
+    ILU(0)'s iterations on the pressure pulse."""
+    o, rp, ci, vals = layered_system
+    st = o.static()
+    L = transmissibility_laplacian(st["Tx"], st["Ty"], st["Tz"], o.nx, o.ny, o.nz)
+    Ps = AMG(L).P
+    assert len(Ps) >= 2
+    Ap = pressure_matrix(rp, ci, vals, quasi_impes_weights(diagonal_blocks(rp, ci, vals)))
+    fixed = AMG(Ap, prolongators=Ps)
+    ones = np.ones(Ap.shape[0])
+    rs = Ap @ ones
+    for P, Ac in zip(Ps, fixed.A[1:]):
+        assert np.allclose(Ac @ np.ones(Ac.shape[0]), P.T @ rs, rtol=1e-12,
+                           atol=1e-12 * np.abs(rs).max())
+        rs = P.T @ rs
+    b = _reduced_rhs(o)
+    op = o.apply_op
+    _, n_ilu, _ = bicgstab(op, b, o.ilu_apply, tol=1e-3, maxit=2000)
+    cpr = CPR(rp, ci, vals, op, o.ilu_apply, pressure_solve=fixed.vcycle)
+    _, n_cpr, ok = bicgstab(op, b, cpr, tol=1e-3, maxit=2000)
+    assert ok and n_cpr * 4 <= n_ilu, (n_cpr, n_ilu)

@@ -222,8 +222,9 @@ bo_status bo_get_system(const bo_sim* sim, int* rowptr, int* colind, double* val
 bo_status bo_get_wells(const bo_sim* sim, double* Rw, double* Dw, double* B, double* C,
                        int* control);
 
-/* Well production report: per well the surface rates of water, oil and gas
- * (m^3/s at surface conditions, the connection inflows of Eq. (wellinflow)
+/* Well production report (Section 2.2.1): per well the surface rates of
+ * water, oil and gas (m^3/s at surface conditions, the connection inflows of
+ * Eq. (wellinflow)
  * summed over the well's connections, gas including the dissolved gas of
  * the produced oil) at the state of the last assembly, production positive
  * and injection negative; after a successful bo_step that is the converged

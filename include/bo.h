@@ -224,9 +224,8 @@ bo_status bo_get_wells(const bo_sim* sim, double* Rw, double* Dw, double* B, dou
 
 /* Well production report (Section 2.2.1): per well the surface rates of
  * water, oil and gas (m^3/s at surface conditions, the connection inflows of
- * Eq. (wellinflow)
- * summed over the well's connections, gas including the dissolved gas of
- * the produced oil) at the state of the last assembly, production positive
+ * Eq. (wellinflow) summed over the well's connections, gas including the
+ * dissolved gas of the produced oil) at the state of the last assembly, production positive
  * and injection negative; after a successful bo_step that is the converged
  * state of its last sub-step.  rates[3*nwells] (well-major), bhp[nwells]
  * (Pa, current), control[nwells] (0 rate, 1 BHP, current); any pointer may

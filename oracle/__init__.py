@@ -35,12 +35,13 @@ _OPT_ORDER = list(DEFAULT_OPTS.keys())
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (no OpenMP, plain -O2)."""
+    """Compile the oracle with g++ -O2 (OpenMP for the independent loops;
+    one thread unless set_threads says otherwise)."""
     with _lock:
         if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
             os.makedirs(os.path.dirname(_SO), exist_ok=True)
             tmp = _SO + f".tmp{os.getpid()}"
-            subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC",
+            subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC",
                                    "-o", tmp, _SRC])
             os.replace(tmp, _SO)
     return _SO
@@ -86,8 +87,16 @@ def lib():
         L.orc_get_dt_next.restype = d
         L.orc_set_dt_next.argtypes = [P, d]
         L.orc_set_subdomains.argtypes = [P, i, i]
+        L.orc_set_threads.argtypes = [i]
+        L.orc_set_threads.restype = i
         _lib = L
     return _lib
+
+
+def set_threads(threads: int) -> int:
+    """Host threads of the oracle's independent loops (results do not depend
+    on the count: every sum keeps its sequential order)."""
+    return int(lib().orc_set_threads(int(threads)))
 
 
 def _p(a):

@@ -28,6 +28,15 @@
 //     on the matrix pattern in natural order, right-preconditioned
 //     BiCGStab of van der Vorst.
 //
+// Threads (orc_set_threads, default 1): the loops whose iterations are
+// independent -- cell properties, accumulation, the face fluxes, the operator's
+// rows and the vector updates -- may run on several host threads.  Every
+// floating-point sum keeps its sequential order (dot products and the norms
+// stay sequential; each cell gathers its face terms in the order of the
+// sequential face loop), so the results do not depend on the thread count.
+// The ILU(0) factorisation and sweeps are sequential, as in the paper's
+// per-process ILU(0).
+//
 // Parity: the functions are pinned by the CPU test suite against finite
 // differences, mass conservation, hydrostatic equilibrium, the 1-D
 // incompressible closed form, the ILU(0) identity and dense LU on tiny grids.
@@ -40,6 +49,10 @@
 #include <algorithm>
 
 namespace orc {
+
+// Host threads of the loops with independent iterations (1: sequential).
+static int g_threads = 1;
+#define ORC_PARALLEL_FOR _Pragma("omp parallel for num_threads(g_threads) schedule(static)")
 
 // ---------------------------------------------------------------------------
 // Forward-mode dual number: value plus N first derivatives.
@@ -203,6 +216,13 @@ struct Well {
     std::vector<double> C;  // 3 per connection: dR_cell/dbhp
 };
 
+// One TPFA face between cell i and its higher-index neighbour j: the three
+// component fluxes u_a (Eqs. flux1, flux2) and their derivatives with respect
+// to the primary variables of i (bi) and of j (bj), row-major [a][v].
+struct FaceTerm {
+    double u[3], bi[9], bj[9];
+};
+
 struct Model {
     int nx, ny, nz, n;
     double top_depth = 0.0;
@@ -232,6 +252,9 @@ struct Model {
     // of Section 2.5 (one ILU(0) block per subdomain; the couplings between
     // subdomains are left out of M, the operator keeps them).
     int ysub = 0, zsub = 0;
+    // Face terms of the last assembly, 3 per cell (+x, +y, +z), filled only
+    // where the face exists.
+    std::vector<FaceTerm> faces;
 };
 
 static inline int cidx(const Model& m, int i, int j, int k) { return i + m.nx * (j + m.ny * k); }
@@ -369,6 +392,7 @@ static void add_block(Model& m, int q, const double blk[9], double sgn) {
 static void begin_step(Model& m) {
     int n = m.n;
     m.A0.assign(3 * n, 0.0);
+    ORC_PARALLEL_FOR
     for (int c = 0; c < n; ++c) {
         CellProps cp = cell_props(m.F, m.p[c], m.sw[c], m.x[c], m.flag[c]);
         for (int a = 0; a < 3; ++a) m.A0[3 * c + a] = cp.A[a].v;
@@ -396,16 +420,47 @@ static void begin_step(Model& m) {
     for (Well& w : m.wells) m.bk_bhp.push_back(w.bhp);
 }
 
-static void assemble(Model& m, double dt) {
+static FaceTerm face_term(const Model& m, const std::vector<CellProps>& props, int i, int j,
+                          double T) {
     const Fluid& F = m.F;
+    const CellProps& ci = props[i];
+    const CellProps& cj = props[j];
+    Dual<6> pi = lift<6>(Dual<3>::var(m.p[i], 0), 0);
+    Dual<6> pj = lift<6>(Dual<3>::var(m.p[j], 0), 3);
+    double dz = m.depth[i] - m.depth[j];
+    Dual<6> u[3];
+    Dual<6> dphi[3];
+    bool up_i[3];
+    for (int a = 0; a < 3; ++a) {
+        Dual<6> rho_ij = 0.5 * (lift<6>(ci.rho[a], 0) + lift<6>(cj.rho[a], 3));
+        dphi[a] = pi - pj - F.g * rho_ij * dz;
+        up_i[a] = dphi[a].v >= 0.0;
+        Dual<6> mob = up_i[a] ? lift<6>(ci.b[a] * ci.lam[a], 0) : lift<6>(cj.b[a] * cj.lam[a], 3);
+        u[a] = mob * T * dphi[a];
+    }
+    // Dissolved gas travels with the oil phase (Eq. flux2).
+    Dual<6> rmob = up_i[O] ? lift<6>(ci.rgo * ci.b[O] * ci.lam[O], 0)
+                           : lift<6>(cj.rgo * cj.b[O] * cj.lam[O], 3);
+    u[G] = u[G] + rmob * T * dphi[O];
+    FaceTerm f;
+    for (int a = 0; a < 3; ++a) {
+        f.u[a] = u[a].v;
+        for (int v = 0; v < 3; ++v) { f.bi[3 * a + v] = u[a].d[v]; f.bj[3 * a + v] = u[a].d[3 + v]; }
+    }
+    return f;
+}
+
+static void assemble(Model& m, double dt) {
     int n = m.n;
     std::fill(m.vals.begin(), m.vals.end(), 0.0);
     m.R.assign(3 * n, 0.0);
     m.dt_last = dt;
     std::vector<CellProps> props(n);
-    for (int c = 0; c < n; ++c) props[c] = cell_props(F, m.p[c], m.sw[c], m.x[c], m.flag[c]);
+    ORC_PARALLEL_FOR
+    for (int c = 0; c < n; ++c) props[c] = cell_props(m.F, m.p[c], m.sw[c], m.x[c], m.flag[c]);
 
     // Accumulation: (phi_ref V / dt) (A - A0) into R and the diagonal block.
+    ORC_PARALLEL_FOR
     for (int c = 0; c < n; ++c) {
         double s = m.pv[c] / dt;
         double blk[9];
@@ -416,46 +471,47 @@ static void assemble(Model& m, double dt) {
         add_block(m, m.diagpos[c], blk, 1.0);
     }
 
-    // Faces: each connection once, oriented from the lower to the higher index.
-    auto face = [&](int i, int j, double T) {
-        const CellProps& ci = props[i];
-        const CellProps& cj = props[j];
-        Dual<6> pi = lift<6>(Dual<3>::var(m.p[i], 0), 0);
-        Dual<6> pj = lift<6>(Dual<3>::var(m.p[j], 0), 3);
-        double dz = m.depth[i] - m.depth[j];
-        Dual<6> u[3];
-        Dual<6> dphi[3];
-        bool up_i[3];
-        for (int a = 0; a < 3; ++a) {
-            Dual<6> rho_ij = 0.5 * (lift<6>(ci.rho[a], 0) + lift<6>(cj.rho[a], 3));
-            dphi[a] = pi - pj - F.g * rho_ij * dz;
-            up_i[a] = dphi[a].v >= 0.0;
-            Dual<6> mob = up_i[a] ? lift<6>(ci.b[a] * ci.lam[a], 0) : lift<6>(cj.b[a] * cj.lam[a], 3);
-            u[a] = mob * T * dphi[a];
+    // Faces: each connection once, oriented from the lower to the higher index
+    // (+x, +y, +z of every cell), u_ij added to R_i and subtracted from R_j.
+    // The terms are formed first; then every cell adds its six faces in the
+    // order of a sequential sweep over the lower cells (k, j, i outermost to
+    // innermost; +x, +y, +z within a cell): -z, -y, -x, +x, +y, +z.
+    const int plane = m.nx * m.ny;
+    std::vector<FaceTerm>& ft = m.faces;
+    ft.resize(3 * (size_t)n);
+    ORC_PARALLEL_FOR
+    for (int c = 0; c < n; ++c) {
+        const int ii = c % m.nx, jj = (c / m.nx) % m.ny, k = c / plane;
+        if (ii + 1 < m.nx) ft[3 * (size_t)c + 0] = face_term(m, props, c, c + 1, m.Tx[c]);
+        if (jj + 1 < m.ny) ft[3 * (size_t)c + 1] = face_term(m, props, c, c + m.nx, m.Ty[c]);
+        if (k + 1 < m.nz) ft[3 * (size_t)c + 2] = face_term(m, props, c, c + plane, m.Tz[c]);
+    }
+    ORC_PARALLEL_FOR
+    for (int c = 0; c < n; ++c) {
+        const int ii = c % m.nx, jj = (c / m.nx) % m.ny, k = c / plane;
+        const int dq = m.diagpos[c];
+        // faces from the lower neighbours: this cell is their j
+        const int lower[3] = {c - plane, c - m.nx, c - 1};
+        const bool has_lower[3] = {k > 0, jj > 0, ii > 0};
+        const int ldir[3] = {2, 1, 0};
+        for (int q = 0; q < 3; ++q) {
+            if (!has_lower[q]) continue;
+            const FaceTerm& f = ft[3 * (size_t)lower[q] + ldir[q]];
+            for (int a = 0; a < 3; ++a) m.R[3 * c + a] -= f.u[a];
+            add_block(m, find_block(m, c, lower[q]), f.bi, -1.0);
+            add_block(m, dq, f.bj, -1.0);
         }
-        // Dissolved gas travels with the oil phase (Eq. flux2).
-        Dual<6> rmob = up_i[O] ? lift<6>(ci.rgo * ci.b[O] * ci.lam[O], 0)
-                               : lift<6>(cj.rgo * cj.b[O] * cj.lam[O], 3);
-        u[G] = u[G] + rmob * T * dphi[O];
-        double bi[9], bj[9];
-        for (int a = 0; a < 3; ++a) {
-            m.R[3 * i + a] += u[a].v;
-            m.R[3 * j + a] -= u[a].v;
-            for (int v = 0; v < 3; ++v) { bi[3 * a + v] = u[a].d[v]; bj[3 * a + v] = u[a].d[3 + v]; }
+        // own faces: this cell is their i
+        const int upper[3] = {c + 1, c + m.nx, c + plane};
+        const bool has_upper[3] = {ii + 1 < m.nx, jj + 1 < m.ny, k + 1 < m.nz};
+        for (int q = 0; q < 3; ++q) {
+            if (!has_upper[q]) continue;
+            const FaceTerm& f = ft[3 * (size_t)c + q];
+            for (int a = 0; a < 3; ++a) m.R[3 * c + a] += f.u[a];
+            add_block(m, dq, f.bi, 1.0);
+            add_block(m, find_block(m, c, upper[q]), f.bj, 1.0);
         }
-        add_block(m, m.diagpos[i], bi, 1.0);
-        add_block(m, find_block(m, i, j), bj, 1.0);
-        add_block(m, find_block(m, j, i), bi, -1.0);
-        add_block(m, m.diagpos[j], bj, -1.0);
-    };
-    for (int k = 0; k < m.nz; ++k)
-        for (int jj = 0; jj < m.ny; ++jj)
-            for (int ii = 0; ii < m.nx; ++ii) {
-                int c = cidx(m, ii, jj, k);
-                if (ii + 1 < m.nx) face(c, c + 1, m.Tx[c]);
-                if (jj + 1 < m.ny) face(c, c + m.nx, m.Ty[c]);
-                if (k + 1 < m.nz) face(c, c + m.nx * m.ny, m.Tz[c]);
-            }
+    }
 
     // Wells: q_a,i adds to R_a,i; rate-controlled wells add an equation.
     for (Well& w : m.wells) {
@@ -498,13 +554,18 @@ static void assemble(Model& m, double dt) {
 static void norms(const Model& m, double dt, double* out) {
     int n = m.n;
     double sumR[3] = {0, 0, 0}, maxR[3] = {0, 0, 0}, sumB[3] = {0, 0, 0}, pvt = 0.0;
+    std::vector<double> b(3 * (size_t)n);
+    ORC_PARALLEL_FOR
     for (int c = 0; c < n; ++c) {
         CellProps cp = cell_props(m.F, m.p[c], m.sw[c], m.x[c], m.flag[c]);
+        for (int a = 0; a < 3; ++a) b[3 * (size_t)c + a] = cp.b[a].v;
+    }
+    for (int c = 0; c < n; ++c) {
         pvt += m.pv[c];
         for (int a = 0; a < 3; ++a) {
             sumR[a] += m.R[3 * c + a];
             maxR[a] = std::max(maxR[a], std::fabs(m.R[3 * c + a]) / m.pv[c]);
-            sumB[a] += 1.0 / cp.b[a].v;
+            sumB[a] += 1.0 / b[3 * (size_t)c + a];
         }
     }
     for (int a = 0; a < 3; ++a) {
@@ -625,6 +686,7 @@ static void ilu_apply(const Model& m, const double* r, double* z) {
 // Reduced operator of Eq. (wellequation): y = A x - sum_w C_w D_w^-1 (B_w x).
 static void apply_op(const Model& m, const double* x, double* y) {
     int n = m.n;
+    ORC_PARALLEL_FOR
     for (int i = 0; i < n; ++i) {
         double acc[3] = {0, 0, 0};
         for (int q = m.rowptr[i]; q < m.rowptr[i + 1]; ++q) {
@@ -680,12 +742,14 @@ static int solve(Model& m, double tol, int maxit, double* sol, int* its_out) {
             double rho = dot(rh, r);
             if (rho == 0.0 || !std::isfinite(rho)) return LIN_BREAKDOWN;
             double beta = (rho / rho_old) * (alpha / omega);
+            ORC_PARALLEL_FOR
             for (int i = 0; i < N; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
             ilu_apply(m, p.data(), ph.data());
             apply_op(m, ph.data(), v.data());
             double rv = dot(rh, v);
             if (rv == 0.0 || !std::isfinite(rv)) return LIN_BREAKDOWN;
             alpha = rho / rv;
+            ORC_PARALLEL_FOR
             for (int i = 0; i < N; ++i) s[i] = r[i] - alpha * v[i];
             double ns = std::sqrt(dot(s, s));
             if (ns <= tol * nr0) {
@@ -699,6 +763,7 @@ static int solve(Model& m, double tol, int maxit, double* sol, int* its_out) {
             if (tt == 0.0 || !std::isfinite(tt)) return LIN_BREAKDOWN;
             omega = dot(t, s) / tt;
             if (omega == 0.0 || !std::isfinite(omega)) return LIN_BREAKDOWN;
+            ORC_PARALLEL_FOR
             for (int i = 0; i < N; ++i) { x[i] += alpha * ph[i] + omega * sh[i]; r[i] = s[i] - omega * t[i]; }
             double nr = std::sqrt(dot(r, r));
             *its_out = it;
@@ -1252,6 +1317,12 @@ int orc_step(void* h, double dt, const double* opts, double* report) {
     }
     report[0] = nits_tot; report[1] = lits_tot; report[2] = cuts; report[3] = subs; report[4] = status;
     return status;
+}
+
+// Host threads of the independent loops (1 = sequential); returns the count set.
+int orc_set_threads(int threads) {
+    g_threads = threads < 1 ? 1 : threads;
+    return g_threads;
 }
 
 double orc_get_dt_next(void* h) { return static_cast<Model*>(h)->dt_next; }

@@ -3,11 +3,17 @@
 A "step" is one report step of the simulation (Newton iterations with
 assembly, ILU(0) factorisation and BiCGStab solves, time-step cuts included)
 on the 60x220x85 layered model with 5-spot wells (1,122,000 cells, report
-steps of 10 days).  W warm-up report steps run untimed, then K report steps
-are timed with CUDA events on the library's stream.
+steps of 10 days).  W warm-up report steps run untimed from the initial
+state; the state and step control are then put back, so the K timed report
+steps are report steps 1..K of the workload (its 20-step schedule at K = 20).
+
+One timed loop.  Per report step the state goes in from pinned host memory
+through bo_set_state, the step runs (bo_step), and the state comes back out
+through bo_get_state.  CUDA events on the library's stream around bo_step
+give `value` (inputs resident in HBM); events around all three give `e2e`.
 
 Prints one JSON line.  --impl reference times the CPU FP64 oracle instead
-(single thread, bounded sample of the same workload).
+(all host cores; each step a bounded sample of the same workload).
 """
 from __future__ import annotations
 
@@ -73,13 +79,24 @@ def peaks():
         return {"hbm_gbs": 6800.0, "source": "of fallback"}
 
 
-# Operations per report step of the layered 60x220x85 workload in the timed
-# window (report steps 4-5): assemblies, ILU(0) factorisations and BiCGStab
-# iterations, as counted by a GB300 run of the same algorithm (both codes
-# take the same Newton, cut and linear-solver decisions; the parity tests
-# check this on smaller models).  The oracle itself needs hours of CPU time
-# per report step of this model, so it cannot count them in a bounded run.
-OPS_PER_REPORT_STEP = {1: {"assemblies": 172.5, "solves": 156.0, "lin_its": 17882.5}}
+# Operations per report step of a workload (assemblies, ILU(0)
+# factorisations, BiCGStab iterations), recorded by this bench's GPU arm
+# (--record-ops) over the timed report steps.  The oracle takes the same
+# Newton, cut and linear-solver decisions (the parity tests compare them on
+# smaller models) but needs hours of CPU time per report step of the
+# 60x220x85 model, so it cannot count them in a bounded run; the CPU
+# figures are therefore the oracle's measured per-operation times scaled by
+# these counts, and every line that uses them says so.
+def ops_record_path(config):
+    return os.path.join(ROOT, "profiles", f"op_counts_config{config}.json")
+
+
+def load_ops(config):
+    try:
+        with open(ops_record_path(config)) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return None
 
 
 def ncu_traffic(kernel, cells):
@@ -99,19 +116,17 @@ def ncu_traffic(kernel, cells):
     return rec["bytes_per_cell"] * cells
 
 
-def op_counts(config):
-    if config not in OPS_PER_REPORT_STEP:
-        raise SystemExit(f"per-report-step operation counts are recorded for config(s) "
-                         f"{sorted(OPS_PER_REPORT_STEP)} only (the timed workload); "
-                         f"config {config} has none")
-    return OPS_PER_REPORT_STEP[config]
-
-
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--no-restore", action="store_true",
+                    help="time the K report steps after the warm-up ones instead of "
+                         "restarting from the initial state")
+    ap.add_argument("--record-ops", action="store_true",
+                    help="write the timed steps' operation counts per report step to "
+                         "profiles/op_counts_config<C>.json (the CPU scaling record)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3])
     ap.add_argument("--members", type=int, default=256, help="ensemble members (config 3)")
@@ -137,7 +152,10 @@ def parse():
                     help="profiling: the first report step from the hydrostatic state "
                          "once per block-Jacobi slab shape (ysub,zsub), one JSON line each")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-its", type=int, default=12)
+    ap.add_argument("--cpu-sample-its", type=int, default=8,
+                    help="BiCGStab iterations in one CPU sample")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="oracle threads of the all-cores CPU leg (0: every host core)")
     return ap.parse_args()
 
 
@@ -227,17 +245,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(config, gpu_counts, sample_its):
-    """Time the oracle (single thread) on a bounded sample of the same model at
-    its initial state -- one assembly, one ILU(0) factorisation and
-    `sample_its` BiCGStab iterations -- and scale to the operation counts of
-    the GPU run's timed steps (same algorithm, same decisions)."""
-    import oracle
-    m = model_for(config)
-    o = oracle.Oracle(m)
-    o.init_hydrostatic()
-    o.begin_step()
-    dt = m["dt"]
+def host_cpu():
+    """Core count and CPU model of this host (nproc / lscpu)."""
+    cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": cores, "model": model}
+
+
+def oracle_sample(o, dt, sample_its):
+    """One bounded sample of the workload on the oracle: an assembly, an
+    ILU(0) factorisation and `sample_its` BiCGStab iterations of the current
+    system.  Returns (seconds per assembly, per factorisation, per BiCGStab
+    iteration, total seconds)."""
     t0 = time.perf_counter()
     o.assemble(dt)
     t_asm = time.perf_counter() - t0
@@ -245,26 +272,68 @@ def cpu_baseline(config, gpu_counts, sample_its):
     o.ilu0()
     t_fac = time.perf_counter() - t0
     t0 = time.perf_counter()
-    st, its, _ = o.solve(tol=1e-30, maxit=sample_its)
+    _, its, _ = o.solve(tol=1e-30, maxit=sample_its)   # the solve repeats the factorisation
     t_sol = time.perf_counter() - t0
     t_it = max(t_sol - t_fac, 0.0) / max(its, 1)
-    n_asm = gpu_counts["assemblies"]
-    n_fac = gpu_counts["solves"]
-    n_it = gpu_counts["lin_its"]
-    est = n_asm * t_asm + n_fac * t_fac + n_it * t_it
+    return t_asm, t_fac, t_it, t_asm + t_fac + t_sol
+
+
+def cpu_rate(n, ops, t_asm, t_fac, t_it):
+    """cell-steps/s of the oracle: its measured time per assembly,
+    factorisation and BiCGStab iteration times the operations of a report
+    step (ops per report step)."""
+    sec = ops["assemblies"] * t_asm + ops["solves"] * t_fac + ops["lin_its"] * t_it
+    return n / sec if sec > 0 else None, sec
+
+
+def cpu_baseline(config, ops, sample_its, threads):
+    """The oracle on the same model at its initial state, one bounded sample
+    on one thread and one on `threads` threads (all host cores), scaled by
+    the operation counts per report step of the GPU run's timed steps (the
+    same algorithm takes the same decisions)."""
+    import oracle
+    m = model_for(config)
     n = m["nx"] * m["ny"] * m["nz"]
-    value = n * gpu_counts["steps"] / est if est > 0 else None
-    return {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle on the same model's initial state: 1 assembly ({t_asm:.2f} s), "
-                       f"1 ILU0 ({t_fac:.2f} s), {its} BiCGStab its ({t_it:.3f} s each); "
-                       f"scaled to the timed steps' {n_asm} assemblies, {n_fac} factorisations, "
-                       f"{n_it} BiCGStab iterations")}
+    o = oracle.Oracle(m)
+    o.init_hydrostatic()
+    o.begin_step()
+    legs = {}
+    for nt in (1, threads):
+        oracle.set_threads(nt)
+        t_asm, t_fac, t_it, tot = oracle_sample(o, m["dt"], sample_its)
+        v, sec = cpu_rate(n, ops, t_asm, t_fac, t_it)
+        legs[nt] = {"value": v, "cores": nt, "sec_per_report_step": sec,
+                    "sample": (f"1 assembly ({t_asm:.2f} s), 1 ILU0 ({t_fac:.2f} s), "
+                               f"{sample_its} BiCGStab its ({t_it:.3f} s each), {tot:.1f} s")}
+    oracle.set_threads(1)
+    hc = host_cpu()
+    top = legs[threads]
+    return {"value": top["value"], "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
+            "sample": (f"oracle on the same model at its initial state on {threads} threads: "
+                       f"{top['sample']}; scaled to {ops['assemblies']:.1f} assemblies, "
+                       f"{ops['solves']:.1f} factorisations and {ops['lin_its']:.1f} BiCGStab "
+                       "iterations per report step, counted by the GPU run's timed steps "
+                       "(the oracle takes the same decisions; a report step of this model "
+                       f"takes it about {top['sec_per_report_step'] / 3600:.1f} h)"),
+            "single_thread": {"value": legs[1]["value"], "cores": 1, "sample": legs[1]["sample"]},
+            "host": hc}
 
 
 def workload_name(args, m):
     if args.grid:
         return f"{m['name']}, report steps of {args.report_days or m['dt'] / 86400.0:g} days"
     return WORKLOADS[args.config]
+
+
+def pinned_state(sim):
+    """Pinned host buffers for one state (p, sw, x, flag, bhp), as NumPy
+    views that bo_set_state / bo_get_state read and write directly."""
+    import torch
+    n, nw = sim.n, max(sim.nw, 1)
+    ts = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3)]
+    ts.append(torch.empty(n, dtype=torch.uint8).pin_memory())
+    ts.append(torch.empty(nw, dtype=torch.float64).pin_memory())
+    return ts, [t.numpy() for t in ts]
 
 
 def run_gb300(args):
@@ -289,10 +358,18 @@ def run_gb300(args):
     if args.learned:
         import synth
         sim.learn_set_params(synth.learned_init(0))
+    init_state, init_dt = sim.get_state(), sim.dt_next
 
     def barrier():
         if world > 1:
             dist.barrier()
+
+    def progress(tag, k, rep, sec):
+        if rank == 0:
+            print(json.dumps({"bench": tag, "report_step": k, "sec": round(sec, 2),
+                              "newton": rep["newton_its"], "lin": rep["lin_its"],
+                              "cuts": rep["cuts"], "substeps": rep["substeps"]}),
+                  file=sys.stderr, flush=True)
 
     for w in range(args.warmup):
         if args.learned:
@@ -301,62 +378,58 @@ def run_gb300(args):
             if w == args.train_steps:
                 sim.learn_online(on=False)
                 sim.learn_enable(True)
-        sim.step(dt, raise_on_fail=True)
+        t0 = time.perf_counter()
+        _, rep = sim.step(dt, raise_on_fail=True)
+        progress("warmup", w + 1, rep, time.perf_counter() - t0)
     if args.learned and args.warmup <= args.train_steps:
         sim.learn_online(on=False)
         sim.learn_enable(True)
     torch.cuda.synchronize()
-    snap = sim.get_state()
-    snap_dt = sim.dt_next
 
-    # ---- main timed region: K report steps, inputs resident in HBM --------
+    # pinned host state: the timed loop starts from the initial state (or,
+    # with --no-restore, from the state the warm-up reached)
+    keep_in, h_in = pinned_state(sim)       # the tensors own the pinned memory
+    keep_out, h_out = pinned_state(sim)
+    start = init_state if not args.no_restore else sim.get_state()
+    for dst, src in zip(h_in, start):
+        dst[:len(src)] = src
+    if not args.no_restore:
+        sim.dt_next = init_dt
+
+    # ---- timed region: K report steps, one loop ---------------------------
     sim.set_timing(True)
+    launches0 = sim.launches
     clocks = ClockSampler(torch.cuda.current_device())
     reps = []
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        st, rep = sim.step(dt, raise_on_fail=True)
+    for k in range(args.steps):
+        e = ev[k]
+        t0 = time.perf_counter()
+        e[0].record(stream)
+        sim.set_state(*h_in)                    # host -> device through the C ABI
+        e[1].record(stream)
+        _, rep = sim.step(dt, raise_on_fail=True)
+        e[2].record(stream)
+        sim.get_state(out=h_out)                # device -> host through the C ABI
+        e[3].record(stream)
         reps.append(rep)
-    ev1.record(stream)
+        h_in, h_out = h_out, h_in               # the next step starts from what came back
+        progress("timed", k + 1, rep, time.perf_counter() - t0)
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    ms = ev0.elapsed_time(ev1)
+    launches = sim.launches - launches0
+    ms = sum(e[1].elapsed_time(e[2]) for e in ev)
+    ms_e2e = sum(e[0].elapsed_time(e[3]) for e in ev)
     timers = sim.timing()
     sim.set_timing(False)
     ms_max = max_over_ranks(ms, world, "cuda")
-
-    # ---- end to end: host state in, step, host state out ------------------
-    # the state lives in pinned host memory between steps: each step uploads
-    # it, advances it on the device and reads it back
-    pin = [torch.from_numpy(a.copy()).pin_memory() for a in snap]
-    outs = [torch.empty_like(a).pin_memory() for a in pin]
-    dev = [torch.empty(a.shape, dtype=a.dtype, device="cuda") for a in pin]
-    sim.set_state(*snap)
-    sim.dt_next = snap_dt
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        for d, h in zip(dev, pin):
-            d.copy_(h, non_blocking=True)
-        sim.set_state_dev(*dev)
-        sim.step(dt, raise_on_fail=True)
-        sim.get_state_dev(*dev)
-        for h, d in zip(outs, dev):
-            h.copy_(d, non_blocking=True)
-        pin, outs = outs, pin
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms_e2e = e0.elapsed_time(e1)
     ms_e2e = max_over_ranks(ms_e2e, world, "cuda")
-    io_bytes = int(sum(a.numel() * a.element_size() for a in pin))
+    h2d = int(sum(a.nbytes for a in h_in[:4]) + 8 * sim.nw)
+    d2h = h2d
 
     if rank != 0:
         if world > 1:
@@ -365,8 +438,8 @@ def run_gb300(args):
 
     # ---- roofline of the dominant kernel ----------------------------------
     dominant = max((k for k in timers if k in ALGO_BYTES_PER_CELL), key=lambda k: timers[k][0])
-    tot_ms, launches = timers[dominant]
-    avg_s = tot_ms / 1e3 / max(launches, 1)
+    tot_ms, nlaunch = timers[dominant]
+    avg_s = tot_ms / 1e3 / max(nlaunch, 1)
     algo_table = ALGO_BYTES_PER_CELL_MIXED if args.precision == "mixed" else ALGO_BYTES_PER_CELL
     algo = algo_table[dominant] * n
     achieved = algo / avg_s / 1e9
@@ -374,16 +447,26 @@ def run_gb300(args):
     roof = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
             "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
             "traffic": ncu_traffic(dominant, n) if args.precision == "fp64" else None,
-            "peak_source": pk["source"],
-            "avg_launch_ms": round(avg_s * 1e3, 4), "launches": launches}
+            "algorithmic_bytes": algo, "peak_source": pk["source"],
+            "avg_launch_ms": round(avg_s * 1e3, 4), "launches": nlaunch}
 
     counts = {"steps": args.steps,
               "assemblies": sum(r["newton_its"] + r["substeps"] + r["cuts"] for r in reps),
               "solves": sum(r["newton_its"] for r in reps),
               "lin_its": sum(r["lin_its"] for r in reps)}
+    per_step = {k: counts[k] / args.steps for k in ("assemblies", "solves", "lin_its")}
+    if args.record_ops and not args.grid and args.precision == "fp64" and not args.learned \
+            and not (args.ysub or args.zsub):
+        with open(ops_record_path(args.config), "w") as fh:
+            json.dump({"workload": WORKLOADS[args.config], "report_steps": args.steps,
+                       "from_initial_state": not args.no_restore, **per_step,
+                       "source": "bench.py --record-ops, GPU arm, timed report steps"}, fh,
+                      indent=1)
+            fh.write("\n")
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(args.config, counts, args.cpu_sample_its)
+        cpu = cpu_baseline(args.config if not args.grid else 1, per_step, args.cpu_sample_its,
+                           args.cpu_threads or (os.cpu_count() or 1))
 
     value = whole_job_throughput(n, args.steps, world, ms_max)
     out = {
@@ -399,19 +482,21 @@ def run_gb300(args):
                                 "Newton tol 1e-6"),
                    "precision": args.precision, "ysub": args.ysub, "zsub": args.zsub,
                    "cells": n, "newton_tol": 1e-6, "linear_tol": 1e-3,
+                   "timed_report_steps": (f"{args.warmup + 1}..{args.warmup + args.steps}"
+                                          if args.no_restore else f"1..{args.steps}"),
                    "l2": (f"inputs larger than L2 (Jacobian {504 * n / 1e6:.0f} MB, ILU data "
                           f"{504 * n / 1e6:.0f} MB per model)"),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "clocks": clk,
         "e2e": {"value": whole_job_throughput(n, args.steps, world, ms_e2e), "unit": "cell-steps/s",
-                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
-        "gpu_launches": None,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "bo_set_state (pinned host) + bo_step + bo_get_state (pinned host)"},
+        "gpu_launches": launches,
         "roofline": roof,
         "cpu_baseline": cpu,
         "iterations": counts,
         "kernel_ms": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in timers.items()},
     }
-    out["gpu_launches"] = gpu_launch_count(timers, reps, sim, args.precision, args.learned)
     if args.learned:
         out["learned"] = sim.learn_report()
     print(json.dumps(out))
@@ -419,68 +504,58 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
-def gpu_launch_count(timers, reps, sim, precision="fp64", learned=False):
-    """Kernels launched in the timed region, counted from the algorithm:
-    per BiCGStab iteration 16 (scalar, vector, 2 forward + 2 backward sweeps,
-    2 well dots, 2 operators), 4 more with FP32 sweeps (the conversions into
-    and out of tile order) and 4 more with the learned stage (scale partials
-    and the network, per apply); per solve 4 setup + 1 factorisation (+1
-    feature kernel with the learned stage) + 4 true-residual check + 1 well
-    recovery; per assembly 5 (props, flux, wells, 2 norm kernels); per Newton
-    update 2; per sub-step 2 (step start)."""
-    lin = sum(r["lin_its"] for r in reps)
-    nit = sum(r["newton_its"] for r in reps)
-    asm = sum(r["newton_its"] + r["substeps"] + r["cuts"] for r in reps)
-    subs = sum(r["substeps"] + r["cuts"] for r in reps)
-    per_it = 16 + (4 if precision == "mixed" else 0) + (4 if learned else 0)
-    per_solve = 4 + 1 + (1 if learned else 0) + 4 + 1 + 2
-    return int(lin * per_it + nit * per_solve + asm * 5 + subs * 2)
-
-
 def run_reference(args):
-    """The CPU oracle as it stands, single thread, on the same model: each
-    timed step is one bounded sample (one assembly, one ILU(0), and
-    --cpu-sample-its BiCGStab iterations at the model's initial state); the
-    value converts the sample to cell-steps/s with the operation counts per
-    report step of this workload recorded in measured/op_counts.json."""
+    """The CPU oracle as it stands, on all host cores, on the same model:
+    each of the W + K steps is one bounded sample (an assembly, an ILU(0)
+    factorisation and --cpu-sample-its BiCGStab iterations at the model's
+    initial state).  `ms_per_step` is the measured time of a sample; `value`
+    converts the measured per-operation times to cell-steps/s with the
+    operation counts per report step that the GPU arm recorded for this
+    workload (profiles/op_counts_config<C>.json), and says so."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     m = model_for(args.config)
     n = m["nx"] * m["ny"] * m["nz"]
-    oc = op_counts(args.config)
+    threads = args.cpu_threads or (os.cpu_count() or 1)
+    oracle.set_threads(threads)
     o = oracle.Oracle(m)
     o.init_hydrostatic()
     o.begin_step()
     samples = []
-    for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        o.assemble(m["dt"])
-        t_asm = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        o.ilu0()
-        t_fac = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        _, its, _ = o.solve(tol=1e-30, maxit=args.cpu_sample_its)
-        t_it = max(time.perf_counter() - t0 - t_fac, 0.0) / max(its, 1)
-        if s >= args.warmup:
-            samples.append(oc["assemblies"] * t_asm + oc["solves"] * t_fac + oc["lin_its"] * t_it)
-    sec_per_step = float(np.median(samples))
-    value = n / sec_per_step
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(o, m["dt"], args.cpu_sample_its)
+        if k >= args.warmup:
+            samples.append(r)
+    t_asm, t_fac, t_it = (float(np.median([x[q] for x in samples])) for q in range(3))
+    ms_sample = 1e3 * float(np.mean([x[3] for x in samples]))
+    ops = load_ops(args.config)
+    if ops is not None:
+        value, sec = cpu_rate(n, ops, t_asm, t_fac, t_it)
+        basis = (f"measured per-operation times scaled by {ops['assemblies']:.1f} assemblies, "
+                 f"{ops['solves']:.1f} factorisations and {ops['lin_its']:.1f} BiCGStab "
+                 "iterations per report step, counted by the GPU arm on this workload "
+                 f"({os.path.relpath(ops_record_path(args.config), ROOT)}); a report step "
+                 f"would take the oracle about {sec / 3600:.2f} h")
+    else:
+        value, sec = None, None
+        basis = "no operation-count record for this workload: no cell-steps/s estimate"
+    sample = (f"per step: 1 assembly ({t_asm:.2f} s), 1 ILU0 ({t_fac:.2f} s), "
+              f"{args.cpu_sample_its} BiCGStab its ({t_it:.3f} s each) on the model's "
+              f"initial state, {threads} threads (medians over {len(samples)} timed samples)")
     out = {"impl": "reference",
            "metric": "cell-steps/s at 1e-6 Newton tol: plain FP64 vs mixed/learned/batched",
            "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3, "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": ms_sample, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "layered 60x220x85 black-oil, 5-spot wells, 10-day report steps, "
-                                  "plain FP64 ILU0-BiCGStab, Newton tol 1e-6", "cells": n},
-           "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                            "sample": (f"per step: 1 assembly, 1 ILU0, {args.cpu_sample_its} "
-                                       f"BiCGStab its at the initial state, scaled by "
-                                       f"{oc['assemblies']} assemblies, {oc['solves']} "
-                                       f"factorisations, {oc['lin_its']} BiCGStab its per "
-                                       f"report step")},
+           "config": {"workload": (f"{WORKLOADS[args.config]}, plain FP64 ILU0-BiCGStab, "
+                                   "Newton tol 1e-6"), "cells": n},
+           "value_basis": basis,
+           "step": "one bounded sample of the workload (ms_per_step is its measured time)",
+           "extrapolated_sec_per_report_step": sec,
+           "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": threads,
+                            "kind": "oracle", "sample": sample, "host": host_cpu()},
            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

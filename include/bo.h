@@ -285,6 +285,13 @@ bo_status bo_set_timing(bo_sim* sim, int enabled);
 bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* ms_total,
                         long long* launches, int* count);
 
+/* Kernels the library has launched for this object since it was created:
+ * every direct launch counts one, every launch of a captured CUDA graph
+ * counts the graph's kernel nodes (a kernel that returns at once because its
+ * solve has finished still counts).  Diagnostics for benchmarks, no
+ * counterpart in the paper.  count: host pointer, required. */
+bo_status bo_get_launch_count(const bo_sim* sim, long long* count);
+
 /* Precision of the ILU(0) preconditioner.  BO_PRECISION_FP64 (the default):
  * factors stored and applied in FP64.  BO_PRECISION_MIXED: the factors are
  * computed in FP64; the scaled off-diagonal blocks are stored rounded to

@@ -119,6 +119,7 @@ _SIGS = {
     "bo_learn_loss_grad": [P, P, P, P],
     "bo_get_precision": [P, P],
     "bo_get_timing": [P, c_int, P, P, P, P],
+    "bo_get_launch_count": [P, P],
     "bo_selftest_bounded_wait": [P, P],
     "bo_residual_norms_noalloc": [P, P, P, c_int, c_double, P, P],
     "bo_sizes": [P, P, P, P, P],

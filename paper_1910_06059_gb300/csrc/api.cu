@@ -77,7 +77,7 @@ static void free_all(bo_sim* s) {
     destroy_graphs(s);
     void* ptrs[] = {s->d_dx, s->d_dy, s->d_dz, s->d_perm, s->d_poro, s->d_T, s->d_pv, s->d_depth,
                     s->d_p, s->d_sw, s->d_x, s->d_flag, s->d_bk, s->d_bkflag, s->d_A0,
-                    s->d_props, s->d_R, s->d_A, s->d_P, s->d_face, s->d_cellcon, s->d_wells,
+                    s->d_props, s->d_R, s->d_A, s->d_P, s->d_yt, s->d_order, s->d_face, s->d_cellcon, s->d_wells,
                     s->d_con_cell, s->d_con_wi, s->d_wB, s->d_wC, s->d_b, s->d_xs, s->d_r,
                     s->d_rh, s->d_pk, s->d_v, s->d_s, s->d_t, s->d_ph, s->d_sh, s->d_part,
                     s->d_ks, s->d_ns, s->d_sweep_sync, s->d_P32, s->d_r32, s->d_y32,
@@ -310,6 +310,10 @@ bo_status bo_create_grid(int nx, int ny, int nz, const double* dx, const double*
             dalloc(&s->d_R, 3 * n);
             dalloc(&s->d_A, 63 * n);
             dalloc(&s->d_P, 63 * ilu_storage(s));
+            // idle slots of the tile order are never written: zero factors
+            BO_CUDA(cudaMemset(s->d_P, 0, sizeof(double) * 63 * ilu_storage(s)));
+            dalloc(&s->d_yt, 3 * ilu_storage(s));
+            dalloc(&s->d_order, 2 * (size_t)tile_count(s));
             dalloc(&s->d_face, face_storage(s));
             dalloc(&s->d_sweep_sync, 4);
             for (double** v : {&s->d_b, &s->d_xs, &s->d_r, &s->d_rh, &s->d_pk, &s->d_v, &s->d_s,
@@ -830,6 +834,7 @@ bo_status bo_set_subdomains(bo_sim* s, int ysub, int zsub) {
         sync(s);
         s->ysub = ysub;
         s->zsub = zsub;
+        update_sweep_order(s);
         s->factored = false;   // the factors of the other partition are stale
         reset_sweep_faces(s);
         build_graphs(s);
@@ -1000,6 +1005,14 @@ bo_status bo_get_timing(const bo_sim* s, int max, char (*names)[32], double* ms_
             if (launches) launches[q] = s->timer_n[q];
         }
         if (count) *count = k;
+    });
+}
+
+bo_status bo_get_launch_count(const bo_sim* s, long long* count) {
+    return guarded([&] {
+        need(s != nullptr && count != nullptr, BO_ERR_INVALID_ARG,
+             "bo_get_launch_count: NULL argument");
+        *count = s->launches;
     });
 }
 

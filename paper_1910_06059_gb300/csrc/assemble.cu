@@ -263,8 +263,10 @@ __global__ void k_equil_cells(int n, DevFluid F, EquilDev e, const double* __res
 
 void launch_equilibrium(bo_sim* s, const EquilDev& e) {
     k_equil_anchors<<<1, 32, 0, s->stream>>>(s->fluid, e, s->d_part);
+    count_launch(s, s->stream);
     k_equil_cells<<<152 * 4, 256, 0, s->stream>>>(s->geo.n, s->fluid, e, s->d_part, s->d_depth,
                                                   s->d_p, s->d_sw, s->d_x, s->d_flag);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_equil");
 }
 
@@ -889,6 +891,7 @@ void launch_static(bo_sim* s) {
     k_static<<<blocks_for(g.n, 256), 256, 0, s->stream>>>(g, s->d_dx, s->d_dy, s->d_dz, s->top,
                                                          s->d_perm, s->d_poro, s->d_T, s->d_pv,
                                                          s->d_depth);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_static");
 }
 
@@ -898,6 +901,7 @@ void launch_wi(bo_sim* s, const int* d_con_well, const double* d_rw, const doubl
                                                          d_con_well, s->d_wells, s->d_dx,
                                                          s->d_dy, s->d_dz, s->d_perm, d_rw,
                                                          d_skin, s->d_con_wi);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_wi");
 }
 
@@ -907,6 +911,7 @@ void launch_hydrostatic(bo_sim* s, double p_top, double sw, double rgo) {
     k_hydrostatic<<<blocks_for(cols, 128), 128, 0, s->stream>>>(g, s->fluid, p_top, sw, rgo,
                                                                s->d_depth, s->d_p, s->d_sw,
                                                                s->d_x, s->d_flag);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_hydrostatic");
 }
 
@@ -915,11 +920,13 @@ void launch_begin_step(bo_sim* s) {
     k_begin_cells<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->fluid, s->d_p, s->d_sw,
                                                             s->d_x, s->d_flag, s->d_A0,
                                                             s->d_bk, s->d_bkflag);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_begin_cells");
     if (s->nw > 0) {
         k_begin_wells<<<blocks_for(s->nw, 32), 32, 0, s->stream>>>(
             s->nw, s->fluid, s->d_wells, s->d_con_cell, s->d_depth, s->d_p, s->d_sw, s->d_x,
             s->d_flag);
+        count_launch(s, s->stream);
         BO_LAUNCH_CHECK("k_begin_wells");
     }
 }
@@ -930,6 +937,7 @@ void launch_restore(bo_sim* s) {
     k_restore<<<blocks_for(m, 256), 256, 0, s->stream>>>(n, s->d_p, s->d_sw, s->d_x, s->d_flag,
                                                         s->d_bk, s->d_bkflag, s->nw,
                                                         s->d_wells);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_restore");
 }
 
@@ -947,12 +955,14 @@ void launch_assemble(bo_sim* s, double dt) {
     k_props<<<props_blocks(s), PROPS_BS, 0, s->stream>>>(
         n, s->fluid, s->d_p, s->d_sw, s->d_x, s->d_flag, s->d_pv, s->d_A0, dt, s->d_props,
         s->d_R, s->d_A, s->d_part /* binv partials live at the start of d_part */);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_props");
     timer_end(s, tp);
     timer_begin(s, tf);
     k_flux<<<blocks_for(n, FLUX_BS), FLUX_BS, 0, s->stream>>>(s->geo, s->fluid.g, s->d_props,
                                                              s->d_p, s->d_depth, s->d_T, s->d_R,
                                                              s->d_A);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_flux");
     timer_end(s, tf);
     BO_CUDA(cudaMemsetAsync(&s->d_ns->dead_wells, 0, sizeof(int), s->stream));
@@ -961,6 +971,7 @@ void launch_assemble(bo_sim* s, double dt) {
                                                   s->d_con_wi, s->d_depth, s->d_p, s->d_sw,
                                                   s->d_x, s->d_flag, s->d_R, s->d_A, s->d_wB,
                                                   s->d_wC, s->d_ns);
+        count_launch(s, s->stream);
         BO_LAUNCH_CHECK("k_wells");
     }
 }
@@ -969,6 +980,7 @@ void launch_fix_dead_wells(bo_sim* s) {
     if (s->nw == 0) return;
     k_fix_dead_wells<<<s->nw, 128, 0, s->stream>>>(s->d_wells, s->d_con_cell, s->d_p, s->d_depth,
                                                     s->fluid.g);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_fix_dead_wells");
 }
 
@@ -977,6 +989,7 @@ void launch_well_init_bhp(bo_sim* s) {
     k_well_init_bhp<<<s->nw, 128, 0, s->stream>>>(s->fluid, s->d_wells, s->d_con_cell,
                                                    s->d_con_wi, s->d_depth, s->d_p, s->d_sw,
                                                    s->d_x, s->d_flag);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_well_init_bhp");
 }
 
@@ -986,9 +999,11 @@ void launch_norms(bo_sim* s, double dt) {
     int npb = props_blocks(s);
     double* part_norm = s->d_part + 3 * (size_t)npb;
     k_norm_partials<<<nb, NORM_BS, 0, s->stream>>>(n, s->d_R, s->d_pv, part_norm);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_norm_partials");
     k_norm_final<<<1, 32, 0, s->stream>>>(n, nb, part_norm, npb, s->d_part, dt, s->nw,
                                           s->d_wells, s->d_ns);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_norm_final");
 }
 
@@ -996,10 +1011,12 @@ void launch_newton_update(bo_sim* s, const bo_newton_opts& o) {
     int n = s->geo.n;
     k_newton_update<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->fluid, o, s->d_xs, s->d_p,
                                                               s->d_sw, s->d_x, s->d_flag);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_newton_update");
     if (s->nw > 0) {
         k_well_update<<<s->nw, 128, 0, s->stream>>>(o, s->d_wells, s->d_con_cell, s->d_p,
                                                      s->d_depth, s->fluid.g);
+        count_launch(s, s->stream);
         BO_LAUNCH_CHECK("k_well_update");
     }
 }

@@ -32,7 +32,7 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 //   Jacobian A: 7 blocks per cell, block-major then entry-major:
 //     A[(b*9 + e)*n + c],  b: 0 diag, 1 -x, 2 +x, 3 -y, 4 +y, 5 -z, 6 +z,
 //     e = 3*r + s for dR_r,c / dy_s,neighbour(b); zero where no neighbour.
-//   ILU(0) data P in tile order (see ilu_tiled.cu): b: 0 D^-1,
+//   ILU(0) data P in tile order (see tiles.cuh, pidx): b: 0 D^-1,
 //     1..3 D^-1 A_{c,-x/-y/-z}, 4..6 D^-1 A_{c,+x/+y/+z}.
 // ---------------------------------------------------------------------------
 enum { NB_DIAG = 0, NB_MX = 1, NB_PX = 2, NB_MY = 3, NB_PY = 4, NB_MZ = 5, NB_PZ = 6 };
@@ -124,6 +124,8 @@ struct bo_sim {
     double* d_R = nullptr;       // 3n
     double* d_A = nullptr;       // 63n
     double* d_P = nullptr;       // 63 x tile-order ILU(0) data
+    double* d_yt = nullptr;      // forward-sweep result, tile order [slot][3][32]
+    int* d_order = nullptr;      // sweep tile lists: forward [T], backward [T]
     float* d_P32 = nullptr;      // FP32 factors in the FP32 sweep layout (mixed mode)
     float* d_r32 = nullptr;      // FP32 sweep input, tile order (mixed mode)
     float* d_y32 = nullptr;      // FP32 sweep work vector, tile order (mixed mode)
@@ -192,6 +194,11 @@ struct bo_sim {
     double timer_ms[bo::MAX_TIMERS] = {};
     long long timer_n[bo::MAX_TIMERS] = {};
     std::vector<cudaEvent_t> iter_events;  // per iteration-in-graph: begin/end pairs
+
+    // kernels launched for this object (direct launches, plus the kernel
+    // nodes of every graph launch)
+    long long launches = 0;
+    std::vector<std::pair<cudaGraphExec_t, int>> graph_kernels;  // kernel nodes per graph
 };
 
 namespace bo {
@@ -210,6 +217,8 @@ void launch_restore(bo_sim* s);
 void setup_sweeps(bo_sim* s);
 int sweep_timeout(bo_sim* s);
 size_t ilu_storage(const bo_sim* s);
+int tile_count(const bo_sim* s);                 // tiles of the wavefront schedule
+void update_sweep_order(bo_sim* s);              // sweep tile lists after a block-Jacobi change
 size_t face_storage(const bo_sim* s);
 void enqueue_factor(bo_sim* s, cudaStream_t st, int* bad);
 void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y, const KrylovScalars* ks);
@@ -244,6 +253,13 @@ void enqueue_learn_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
 void enqueue_learn_collect(bo_sim* s, cudaStream_t st, const double* r, const KrylovScalars* ks);
 double learn_loss_grad(bo_sim* s, const double* r);   // one sample; returns the loss
 void learn_adam(bo_sim* s, double lr);
+
+// Launch accounting: one kernel launched on st (not counted while st is being
+// captured into a graph: a graph's kernels count when the graph is launched).
+void count_launch(bo_sim* s, cudaStream_t st, int k = 1);
+// Record the number of kernel nodes of a captured graph for its executable.
+void note_graph(bo_sim* s, cudaGraph_t g, cudaGraphExec_t exec);
+void graph_launch(bo_sim* s, cudaGraphExec_t exec, cudaStream_t st);
 
 int timer_id(bo_sim* s, const char* name);
 void timer_begin(bo_sim* s, int id);

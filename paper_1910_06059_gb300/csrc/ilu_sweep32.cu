@@ -363,30 +363,31 @@ k_bwd32(TileArgs a, const float4* __restrict__ B, float4* __restrict__ Yt, float
 // ---------------------------------------------------------------------------
 // Layout conversions (bulk, all lanes busy)
 // ---------------------------------------------------------------------------
-// FP64 factors P[(b*9 + e) NP + s*32 + lane] -> FP32 chunks F (blocks 1-3)
-// and B (blocks 4-6).
+// FP64 factors (tile order, pidx) -> FP32 chunks F (blocks 1-3) and B
+// (blocks 4-6).
 __global__ void k_factors32(const double* __restrict__ P, size_t NP, float4* __restrict__ F,
                             float4* __restrict__ Bk) {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < NP;
          q += (size_t)gridDim.x * blockDim.x) {
         const size_t s = q >> 5;
         const int lane = (int)(q & 31);
+        auto Pq = [&](int e) { return P[pidx(s, e, lane)]; };
 #pragma unroll
         for (int g = 0; g < FWD_G; ++g) {
             float4 v;
-            v.x = (float)P[(size_t)(9 + 4 * g) * NP + q];
-            v.y = (float)P[(size_t)(9 + 4 * g + 1) * NP + q];
-            v.z = (float)P[(size_t)(9 + 4 * g + 2) * NP + q];
-            v.w = (g < FWD_G - 1) ? (float)P[(size_t)(9 + 4 * g + 3) * NP + q] : 0.f;
+            v.x = (float)Pq(9 + 4 * g);
+            v.y = (float)Pq(9 + 4 * g + 1);
+            v.z = (float)Pq(9 + 4 * g + 2);
+            v.w = (g < FWD_G - 1) ? (float)Pq(9 + 4 * g + 3) : 0.f;
             F[(s * FWD_G + g) * 32 + lane] = v;
         }
 #pragma unroll
         for (int g = 0; g < BWD_G; ++g) {
             float4 v;
-            v.x = (float)P[(size_t)(36 + 4 * g) * NP + q];
-            v.y = (float)P[(size_t)(36 + 4 * g + 1) * NP + q];
-            v.z = (float)P[(size_t)(36 + 4 * g + 2) * NP + q];
-            v.w = (g < BWD_G - 1) ? (float)P[(size_t)(36 + 4 * g + 3) * NP + q] : 0.f;
+            v.x = (float)Pq(36 + 4 * g);
+            v.y = (float)Pq(36 + 4 * g + 1);
+            v.z = (float)Pq(36 + 4 * g + 2);
+            v.w = (g < BWD_G - 1) ? (float)Pq(36 + 4 * g + 3) : 0.f;
             Bk[(s * BWD_G + g) * 32 + lane] = v;
         }
     }
@@ -429,14 +430,15 @@ __global__ void k_to_tiles32(TileArgs a, const double* __restrict__ P, const dou
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < NP;
          q += (size_t)gridDim.x * blockDim.x) {
         int c;
+        const int lane = (int)(q & 31);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (slot_cell(a, q, c)) {
             const double r0 = r[c], r1 = r[(size_t)n + c], r2 = r[2 * (size_t)n + c];
             double o[3];
 #pragma unroll
             for (int e = 0; e < 3; ++e)
-                o[e] = fma(P[(size_t)(3 * e) * NP + q], r0,
-                           fma(P[(size_t)(3 * e + 1) * NP + q], r1, P[(size_t)(3 * e + 2) * NP + q] * r2));
+                o[e] = fma(P[pidx(q >> 5, 3 * e, lane)], r0,
+                           fma(P[pidx(q >> 5, 3 * e + 1, lane)], r1, P[pidx(q >> 5, 3 * e + 2, lane)] * r2));
             v.x = (float)o[0];
             v.y = (float)o[1];
             v.z = (float)o[2];
@@ -511,12 +513,14 @@ void setup_sweeps32(bo_sim* s) {
 void convert_factors32(bo_sim* s, cudaStream_t st) {
     TileArgs a = tile_args(s);
     k_factors32<<<152 * 8, 256, 0, st>>>(s->d_P, a.NP, fwd_factors(s), bwd_factors(s));
+    count_launch(s, st);
     BO_LAUNCH_CHECK("k_factors32");
 }
 
 void reset_faces32(bo_sim* s, cudaStream_t st) {
     TileArgs a = tile_args(s);
     k_fill_sentinel32<<<304, 256, 0, st>>>(faceJ3f(s), (size_t)a.T * s->geo.nx * (TK + TJ) * 3);
+    count_launch(s, st);
     BO_LAUNCH_CHECK("k_fill_sentinel32");
 }
 
@@ -525,8 +529,10 @@ void enqueue_fwd32(bo_sim* s, cudaStream_t st, const double* r, const KrylovScal
     float4* R = reinterpret_cast<float4*>(s->d_r32);
     float4* Y = reinterpret_cast<float4*>(s->d_y32);
     k_to_tiles32<<<152 * 8, 256, 0, st>>>(a, (const double*)s->d_P, r, R, ks);
+    count_launch(s, st);
     launch_coop(st, a.T, 32, k_fwd32, a, (const float4*)fwd_factors(s), (const float4*)R, Y,
                 faceJ3f(s), faceK3f(s), ks);
+    count_launch(s, st);
 }
 
 void enqueue_bwd32(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks) {
@@ -534,7 +540,9 @@ void enqueue_bwd32(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* k
     float4* Y = reinterpret_cast<float4*>(s->d_y32);
     launch_coop(st, a.T, 32, k_bwd32, a, (const float4*)bwd_factors(s), Y, faceJ3f(s), faceK3f(s),
                 ks);
+    count_launch(s, st);
     k_from_tiles64<<<152 * 8, 256, 0, st>>>(a, (const float4*)Y, z, ks);
+    count_launch(s, st);
 }
 
 }  // namespace bo

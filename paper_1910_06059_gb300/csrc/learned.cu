@@ -688,6 +688,7 @@ void learn_set_params(bo_sim* s, const float* host) {
     BO_CUDA(cudaMemcpyAsync(s->d_ml_theta, host, sizeof(float) * NPARAM, cudaMemcpyHostToDevice,
                             s->stream));
     k_ml_pack<<<64, 256, 0, s->stream>>>(s->d_ml_theta, wbf_of(s));
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_ml_pack");
     BO_CUDA(cudaMemsetAsync(s->d_ml_m, 0, sizeof(float) * NPARAM, s->stream));
     BO_CUDA(cudaMemsetAsync(s->d_ml_v, 0, sizeof(float) * NPARAM, s->stream));
@@ -717,10 +718,12 @@ void enqueue_learn_features(bo_sim* s, cudaStream_t st) {
     const int n = s->geo.n;
     k_ml_feat<<<ML_GRID, ML_BS, 0, st>>>(s->geo, s->d_A, s->d_flag, feat_of(s), s->d_ml_featf,
                                         s->d_ml_cell);
+    count_launch(s, st);
     BO_LAUNCH_CHECK("k_ml_feat");
     const int grid = std::max(1, std::min(152 * 2, (n + 16 * INF_WARPS - 1) / (16 * INF_WARPS)));
     k_ml_net<<<grid, 32 * INF_WARPS, INF_SMEM, st>>>(n, feat_of(s), wbf_of(s), s->d_ml_theta,
                                                      s->d_ml_W);
+    count_launch(s, st);
     BO_LAUNCH_CHECK("k_ml_net");
 }
 
@@ -728,12 +731,14 @@ void enqueue_learn_features(bo_sim* s, cudaStream_t st) {
 void enqueue_learn_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
                          const KrylovScalars* ks) {
     k_ml_apply<<<ML_GRID, ML_BS, 0, st>>>(s->geo.n, s->d_ml_W, s->d_ml_cell, r, z, ks);
+    count_launch(s, st);
     BO_LAUNCH_CHECK("k_ml_apply");
 }
 
 void enqueue_learn_collect(bo_sim* s, cudaStream_t st, const double* r, const KrylovScalars* ks) {
     const int N = 3 * s->geo.n;
     k_ml_collect<<<ML_GRID, ML_BS, 0, st>>>(N, r, s->d_ml_samples, s->ml_cap, s->d_ml_count, ks);
+    count_launch(s, st);
     BO_LAUNCH_CHECK("k_ml_collect");
 }
 
@@ -747,16 +752,25 @@ double learn_loss_grad(bo_sim* s, const double* r) {
     double* part2 = s->d_ml_part + ML_GRID;
     launch_precond(s, r, s->d_ml_z0);
     k_ml_resid<<<ML_GRID, ML_BS, 0, st>>>(g, s->d_A, s->d_ml_z0, r, s->d_ml_e, nullptr);
+    count_launch(s, st);
     k_ml_fwd_f32<<<TR_GRID, TR_BS, TR_SMEM, st>>>(n, s->d_ml_featf, s->d_ml_cell, r, s->d_ml_theta,
                                                   s->d_ml_delta);
+    count_launch(s, st);
     k_ml_resid<<<ML_GRID, ML_BS, 0, st>>>(g, s->d_A, s->d_ml_delta, s->d_ml_e, s->d_ml_u, part2);
+    count_launch(s, st);
     k_ml_sum<<<1, 32, 0, st>>>(part2, ML_GRID, s->d_ml_scal);          // ||u||^2
+    count_launch(s, st);
     k_ml_dot<<<ML_GRID, ML_BS, 0, st>>>(N, r, r, part2);
+    count_launch(s, st);
     k_ml_sum<<<1, 32, 0, st>>>(part2, ML_GRID, s->d_ml_scal + 1);      // ||r||^2
+    count_launch(s, st);
     k_ml_AT<<<ML_GRID, ML_BS, 0, st>>>(g, s->d_A, s->d_ml_u, s->d_ml_dd);
+    count_launch(s, st);
     k_ml_scale_vec<<<ML_GRID, ML_BS, 0, st>>>(N, s->d_ml_dd, s->d_ml_scal + 1);
+    count_launch(s, st);
     k_ml_bwd_f32<<<TR_GRID, TR_BS, TR_SMEM, st>>>(n, s->d_ml_featf, s->d_ml_cell, r, s->d_ml_theta,
                                                   s->d_ml_dd, s->d_ml_grad);
+    count_launch(s, st);
     BO_LAUNCH_CHECK("learn_loss_grad");
     double h[2];
     BO_CUDA(cudaMemcpyAsync(h, s->d_ml_scal, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -771,7 +785,9 @@ void learn_adam(bo_sim* s, double lr) {
     const float c2 = 1.f - powf(b2, (float)s->ml_adam_t);
     k_ml_adam<<<64, 256, 0, s->stream>>>(NPARAM, s->d_ml_theta, s->d_ml_grad, s->d_ml_m, s->d_ml_v,
                                          (float)lr, b1, b2, eps, c1, c2);
+    count_launch(s, s->stream);
     k_ml_pack<<<64, 256, 0, s->stream>>>(s->d_ml_theta, wbf_of(s));
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("learn_adam");
 }
 

@@ -480,11 +480,42 @@ static void enqueue_op(bo_sim* s, cudaStream_t st, const double* x, double* y, c
     if (s->nw > 0) {
         k_wdot<<<s->nw, 128, 0, st>>>(s->geo.n, s->d_wells, s->d_con_cell, s->d_wB, x, d_sop(s),
                                       ks);
+        count_launch(s, st);
     }
     k_spmv<MODE><<<VEC_GRID, VEC_BS, 0, st>>>(s->geo, s->d_A, x, y, s->d_cellcon,
                                               s->d_cellcon + s->geo.n, s->d_wC, d_sop(s), o1,
                                               s->d_part, ks);
+    count_launch(s, st);
     BO_LAUNCH_CHECK("k_spmv");
+}
+
+void count_launch(bo_sim* s, cudaStream_t st, int k) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
+    s->launches += k;
+}
+
+void note_graph(bo_sim* s, cudaGraph_t g, cudaGraphExec_t exec) {
+    size_t count = 0;
+    BO_CUDA(cudaGraphGetNodes(g, nullptr, &count));
+    std::vector<cudaGraphNode_t> nodes(count);
+    if (count) BO_CUDA(cudaGraphGetNodes(g, nodes.data(), &count));
+    int kernels = 0;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        BO_CUDA(cudaGraphNodeGetType(nd, &t));
+        if (t == cudaGraphNodeTypeKernel) kernels += 1;
+    }
+    s->graph_kernels.emplace_back(exec, kernels);
+}
+
+void graph_launch(bo_sim* s, cudaGraphExec_t exec, cudaStream_t st) {
+    BO_CUDA(cudaGraphLaunch(exec, st));
+    for (const auto& gk : s->graph_kernels)
+        if (gk.first == exec) {
+            s->launches += gk.second;
+            break;
+        }
 }
 
 // Timers: event pairs recorded on the launching stream (graph nodes when captured).
@@ -552,8 +583,10 @@ static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev, bool 
     // events: 0,1 blas(p); 2,3 fwd1; 4,5 bwd1; 6,7 spmv1; 8,9 blas(s); 10,11 fwd2; 12,13 bwd2;
     //         14,15 spmv2; 16,17 blas(xr)
     k_s1<<<1, 1, 0, st>>>(ks);
+    count_launch(s, st);
     rec(0);
     k_p_update<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_r, s->d_pk, s->d_v, ks);
+    count_launch(s, st);
     rec(1);
     // ph = M^-1 p
     rec(2);
@@ -569,10 +602,13 @@ static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev, bool 
     enqueue_op<1>(s, st, s->d_ph, s->d_v, s->d_rh, ks);
     rec(7);
     k_s2<<<1, 256, 0, st>>>(ks, part, VEC_GRID);
+    count_launch(s, st);
     rec(8);
     k_s_update<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_r, s->d_v, s->d_s, part, ks);
+    count_launch(s, st);
     rec(9);
     k_s3<<<1, 256, 0, st>>>(ks, part, VEC_GRID);
+    count_launch(s, st);
     rec(10);
     enqueue_fwd(s, st, s->d_s, s->d_sh, ks);
     rec(11);
@@ -586,12 +622,15 @@ static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev, bool 
     enqueue_op<2>(s, st, s->d_sh, s->d_t, s->d_s, ks);
     rec(15);
     k_s4<<<1, 256, 0, st>>>(ks, part, VEC_GRID);
+    count_launch(s, st);
     rec(16);
     k_xr_update<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_xs, s->d_ph, s->d_sh, s->d_s, s->d_t,
                                              s->d_r, s->d_rh, part, ks);
+    count_launch(s, st);
     rec(17);
     if (collect) enqueue_learn_collect(s, st, s->d_r, ks);
     k_s5<<<1, 256, 0, st>>>(ks, part, VEC_GRID);
+    count_launch(s, st);
     BO_LAUNCH_CHECK("bicgstab iteration");
 }
 
@@ -607,6 +646,7 @@ static cudaGraphExec_t capture(bo_sim* s, int iters, cudaEvent_t* ev, bool ml, b
     BO_CUDA(cudaStreamEndCapture(cs, &graph));
     cudaGraphExec_t exec;
     BO_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    note_graph(s, graph, exec);
     BO_CUDA(cudaGraphDestroy(graph));
     BO_CUDA(cudaStreamDestroy(cs));
     return exec;
@@ -622,6 +662,7 @@ static cudaGraphExec_t capture_factor(bo_sim* s) {
     BO_CUDA(cudaStreamEndCapture(cs, &graph));
     cudaGraphExec_t exec;
     BO_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    note_graph(s, graph, exec);
     BO_CUDA(cudaGraphDestroy(graph));
     BO_CUDA(cudaStreamDestroy(cs));
     return exec;
@@ -653,6 +694,7 @@ void destroy_graphs(bo_sim* s) {
     s->g_iter = s->g_factor = s->g_iter_timed = s->g_iter_ml = s->g_iter64 = nullptr;
     for (cudaEvent_t e : s->iter_events) cudaEventDestroy(e);
     s->iter_events.clear();
+    s->graph_kernels.clear();
 }
 
 static void ensure_timed_graph(bo_sim* s) {
@@ -667,7 +709,7 @@ void launch_factor(bo_sim* s) {
     int t = timer_id(s, "ilu_factor");
     BO_CUDA(cudaMemsetAsync(factor_bad(s), 0, sizeof(int), s->stream));
     timer_begin(s, t);
-    BO_CUDA(cudaGraphLaunch(s->g_factor, s->stream));
+    graph_launch(s, s->g_factor, s->stream);
     timer_end(s, t);
 }
 
@@ -681,6 +723,7 @@ void launch_well_recover(bo_sim* s) {
     if (s->nw == 0) return;
     k_well_recover<<<s->nw, 128, 0, s->stream>>>(s->geo.n, s->d_wells, s->d_con_cell, s->d_wB,
                                                  s->d_xs);
+    count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_well_recover");
 }
 
@@ -696,7 +739,7 @@ static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* pre
     const int t_ml = s->ml_on ? timer_id(s, "learned_stage") : -1;
     const int left = s->h_ks->maxit - s->h_ks->it;
     for (int guard = 0; guard < left + 2; guard += s->iters_per_graph) {
-        BO_CUDA(cudaGraphLaunch(g, st));
+        graph_launch(s, g, st);
         BO_CUDA(cudaMemcpyAsync(s->h_ks, s->d_ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st));
         BO_CUDA(cudaStreamSynchronize(st));
         const KrylovScalars& k = *s->h_ks;
@@ -737,15 +780,21 @@ int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool f
     cudaStream_t st = s->stream;
     // right-hand side of the reduced system
     k_rhs_copy<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b);
-    if (s->nw > 0) k_rhs_wells<<<s->nw, 128, 0, st>>>(n, s->d_wells, s->d_con_cell, s->d_wC, s->d_b);
+    count_launch(s, st);
+    if (s->nw > 0) {
+        k_rhs_wells<<<s->nw, 128, 0, st>>>(n, s->d_wells, s->d_con_cell, s->d_wC, s->d_b);
+        count_launch(s, st);
+    }
     k_krylov_init<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b, s->d_xs, s->d_r, s->d_rh,
                                                s->d_pk, s->d_v, s->d_part);
+    count_launch(s, st);
     // the learned stage (like the FP32 sweeps) is not the same linear map at
     // every application: cycles stop at the inner target, the true residual decides
     const bool ml = use_ml && s->ml_on && !fp64;
     const bool fp32 = s->mixed && !fp64;
     k_s_setup<<<1, 256, 0, st>>>(s->d_ks, s->d_part, VEC_GRID, tol, maxit,
                                  (fp32 || ml) ? MIXED_INNER : 0.0);
+    count_launch(s, st);
     BO_LAUNCH_CHECK("bicgstab setup");
     if (s->ml_online) BO_CUDA(cudaMemsetAsync(s->d_ml_count, 0, sizeof(int), st));
     s->h_ks->it = 0;
@@ -765,8 +814,10 @@ int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool f
         timer_begin(s, t_check);
         enqueue_op<3>(s, st, s->d_xs, s->d_r, s->d_b, nullptr);
         k_s_restart<<<1, 256, 0, st>>>(s->d_ks, s->d_part, VEC_GRID, round < MAX_RESTARTS);
+        count_launch(s, st);
         k_restart_vectors<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_r, s->d_rh, s->d_pk, s->d_v,
                                                        s->d_ks);
+        count_launch(s, st);
         timer_end(s, t_check);
         BO_LAUNCH_CHECK("true residual");
         BO_CUDA(cudaMemcpyAsync(s->h_ks, s->d_ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st));

@@ -15,6 +15,15 @@ constexpr long long POLL_LIMIT = 1LL << 20;
 #endif
 constexpr unsigned FULL = 0xffffffffu;
 
+// ILU(0) data in tile order: slot s = t NL + l (tile t, level l) holds NPE
+// entries x 32 lanes contiguously, P[(s NPE + q) 32 + lane]; q = 9 b + e with
+// b 0: D^-1, 1..3: D^-1 A_{c,-x/-y/-z}, 4..6: D^-1 A_{c,+x/+y/+z}.  Entries
+// 0..35 of a slot are the forward sweep's data, 36..62 the backward sweep's.
+constexpr int NPE = 63;
+__host__ __device__ __forceinline__ size_t pidx(size_t slot, int q, int lane) {
+    return (slot * NPE + q) * 32 + lane;
+}
+
 struct TileArgs {
     Geom g;
     int NJ, NK, T, NL;
@@ -97,6 +106,28 @@ void launch_coop(cudaStream_t st, int grid, int block, void (*kern)(Args...), Ar
     cfg.numAttrs = 1;
     BO_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
 }
+
+template <class... Args>
+void launch_coop_smem(cudaStream_t st, int grid, int block, size_t smem, void (*kern)(Args...),
+                      Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BO_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+}
+
+// FP64 sweeps (sweep64.cu)
+void setup_sweeps64(bo_sim* s);                              // attributes, residency, tile lists
+void enqueue_fwd64(bo_sim* s, cudaStream_t st, const double* r, const KrylovScalars* ks);
+void enqueue_bwd64(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks);
+int sweep_ctas(const bo_sim* s);
 
 // FP32 sweeps of the mixed-precision solver (ilu_sweep32.cu)
 void setup_sweeps32(bo_sim* s);                              // attributes, residency check

@@ -99,11 +99,22 @@ class Sim:
         bhp = np.ascontiguousarray(bhp if len(bhp) else [0.0], dtype=np.float64)
         call("bo_set_state", self.h, ptr(p), ptr(sw), ptr(x), ptr(flag), ptr(bhp))
 
-    def get_state(self):
+    def get_state(self, out=None):
+        """(p, sw, x, flag, bhp) as host arrays; out: five preallocated
+        contiguous arrays (float64 [n] x 3, uint8 [n], float64 [max(nw, 1)])
+        to read into instead of new ones (e.g. pinned host buffers)."""
         n = self.n
-        p, sw, x = np.zeros(n), np.zeros(n), np.zeros(n)
-        flag = np.zeros(n, dtype=np.uint8)
-        bhp = np.zeros(max(self.nw, 1))
+        if out is None:
+            p, sw, x = np.zeros(n), np.zeros(n), np.zeros(n)
+            flag = np.zeros(n, dtype=np.uint8)
+            bhp = np.zeros(max(self.nw, 1))
+        else:
+            p, sw, x, flag, bhp = out
+            for a, dt in zip(out, (np.float64,) * 3 + (np.uint8, np.float64)):
+                if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("get_state(out=...): wrong dtype or non-contiguous array")
+            if min(p.size, sw.size, x.size, flag.size) < n or bhp.size < max(self.nw, 1):
+                raise ValueError("get_state(out=...): arrays too small")
         call("bo_get_state", self.h, ptr(p), ptr(sw), ptr(x), ptr(flag), ptr(bhp))
         return p, sw, x, flag, bhp[:self.nw]
 
@@ -299,6 +310,13 @@ class Sim:
     # -- timing --------------------------------------------------------------
     def set_timing(self, enabled: bool):
         call("bo_set_timing", self.h, 1 if enabled else 0)
+
+    @property
+    def launches(self):
+        """Kernels launched for this object so far (bo_get_launch_count)."""
+        v = ctypes.c_longlong()
+        call("bo_get_launch_count", self.h, ctypes.byref(v))
+        return v.value
 
     def timing(self):
         k = 16

@@ -435,14 +435,22 @@ bo_status bo_selftest_bounded_wait(bo_sim* sim, double* seconds);
  *   b    [3][n] shrinkage factors b_a of every cell;
  *   out6 [6]    receives MB_a (0..2) and CNV_a (3..5) as defined at bo_norms.
  * n must be 1 .. 8,388,608: the per-block partial sums live in a fixed
- * file-scope device array of 4096 x 10 doubles (320 KB), held by every GPU
- * that loads the library until the process exits; larger n is rejected
- * with BO_ERR_INVALID_ARG.  The call allocates nothing (no cudaMalloc, no
- * cudaFree, no allocating library routine).  Its first call on a device
- * looks up the array's device address; make that first call before any
- * stream capture.  It runs asynchronously on `stream` (a cudaStream_t or
- * NULL).  Every call shares the one array and overwrites what it reads, so
- * nothing needs clearing, but calls that overlap on the GPU race on it. */
+ * file-scope device array of 4096 x 10 doubles (320 KB), held in every CUDA
+ * context that has loaded the library's device code until that context
+ * ends; larger n is rejected with BO_ERR_INVALID_ARG.  The call itself
+ * allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * routine).  First call in a context: CUDA loads a library's device code
+ * lazily, so the first call in each context (the device's primary context,
+ * a caller's own driver-API context, or a context re-created after
+ * cudaDeviceReset) loads the module, which places the array in device
+ * memory, and looks up the array's address in that context; make it once
+ * at start-up, before the memory budget is fixed and before any stream
+ * capture (CUDA_MODULE_LOADING=EAGER loads the module with the context
+ * instead).  Later calls in the same context reuse the address.  It runs
+ * asynchronously on `stream` (a cudaStream_t or NULL).  A NaN anywhere in R
+ * makes the MB and CNV results NaN.  Every call shares the one array and
+ * overwrites what it reads, so nothing needs clearing, but calls that
+ * overlap on the GPU race on it. */
 bo_status bo_residual_norms_noalloc(const double* R, const double* pv, const double* b, int n,
                                     double dt, double* out6, void* stream);
 

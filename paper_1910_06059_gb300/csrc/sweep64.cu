@@ -15,10 +15,10 @@
 // about 64 cycles however many lanes are active, so a tile level costs what
 // its FP64 instructions cost; everything else is kept off that path:
 //   * one CTA of four warps per tile; warps 0-2 compute rows 0-2 of the
-//     level's block products (9 dependent FMAs each), warp 3 (the helper)
-//     forms the next level's q = D^-1 r (9 FMAs, forward only), fetches the
-//     face values of the neighbouring tiles and keeps the stage ring full:
-//     the four warps sit on the four sub-partitions with equal FP64 work;
+//     level (forward: 3 FMAs of D^-1 r and 9 of the lower blocks in one
+//     chain; backward: 9 FMAs), each on its own sub-partition; warp 3 (the
+//     helper) runs no FP64: it fetches the face values of the neighbouring
+//     tiles, stages r one level ahead and keeps the stage ring full;
 //   * the factor rows of a tile level are one contiguous chunk in HBM
 //     (ILU data in tile order, 63 entries x 32 lanes per level) and reach
 //     shared memory by one cp.async.bulk copy into a ring of S64 stages, each
@@ -103,10 +103,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         "l"(src), "r"(bytes), "r"(sa(bar))
         : "memory");
 }
-// the generic-proxy reads of a stage are ordered before the bulk copy that refills it
-__device__ __forceinline__ void fence_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 struct SweepArgs {
     TileArgs a;
@@ -175,8 +171,14 @@ __device__ __forceinline__ void advance(StageCursor& c, int NL) {
     }
 }
 
+constexpr int MAX_CTA_TILES = 64;   // tiles of one CTA (checked on the host)
+
 // ---------------------------------------------------------------------------
 // a8 forward sweep: Yt = (L_A + D)^-1 r, Yt in tile order [slot][3][32].
+// Row warp rw of a level: acc = D^-1[rw][:] r - L_x[rw][:] y_{i-1}
+// - L_y[rw][:] y_{j-1} - L_z[rw][:] y_{k-1}, twelve FMAs in one chain.  The
+// helper stages r (one level ahead, through shared memory) and the face
+// values, and issues the bulk copies; it runs no FP64.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(SW_THREADS, 2)
 k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
@@ -186,40 +188,54 @@ k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
     extern __shared__ __align__(128) double smem[];
     double* ring = smem;                                   // [S64][FWD_STAGE]
     double* ysh = ring + S64 * FWD_STAGE;                  // [2][3][HK][HJ]
-    double* qsh = ysh + 2 * YBUF;                          // [2][3][32]
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(qsh + 2 * 96);
+    double* rsh = ysh + 2 * YBUF;                          // [2][3][32]
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(rsh + 2 * 96);
+    int* tiles = reinterpret_cast<int*>(bar + S64);        // [MAX_CTA_TILES]
     const TileArgs& a = A.a;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int jj = lane % TJ, kk = lane / TJ;
     const int NL = a.NL, n = a.g.n;
     const int ntiles = blockIdx.x < a.T ? (a.T - 1 - blockIdx.x) / A.G + 1 : 0;
     const long long total = (long long)ntiles * NL;
-    auto tile_of = [&](int m) { return A.order[blockIdx.x + m * A.G]; };
-    auto issue = [&](long long g) {   // helper lane 0: stage g into its ring slot
-        const int st = (int)(g % S64);
-        const size_t slot = (size_t)tile_of((int)(g / NL)) * NL + (int)(g % NL);
-        fence_async_smem();
-        mb_expect(&bar[st], FWD_STAGE * 8);
-        bulk_g2s(ring + (size_t)st * FWD_STAGE, P + slot * (NPE * 32), FWD_STAGE * 8, &bar[st]);
-    };
+    for (int q = threadIdx.x; q < ntiles; q += SW_THREADS) tiles[q] = A.order[blockIdx.x + q * A.G];
     for (int q = threadIdx.x; q < 2 * YBUF + 2 * 96; q += SW_THREADS) ysh[q] = 0.0;
+    __syncthreads();
+    // issue cursor (helper lane 0): the next stage to copy and its source
+    StageCursor ic{0, 0};
+    const double* ip = P + (size_t)tiles[0] * NL * (NPE * 32);
+    long long issued = 0;
+    auto issue = [&]() {
+        const int st = (int)(issued % S64);
+        mb_expect(&bar[st], FWD_STAGE * 8);
+        bulk_g2s(ring + (size_t)st * FWD_STAGE, ip, FWD_STAGE * 8, &bar[st]);
+        ++issued;
+        advance(ic, NL);
+        if (ic.l == 0) {
+            if (ic.m < ntiles) ip = P + (size_t)tiles[ic.m] * NL * (NPE * 32);
+        } else {
+            ip += NPE * 32;
+        }
+    };
     if (threadIdx.x == HELPER * 32) {
         for (int d = 0; d < S64; ++d) mb_init(&bar[d], 1);
         mb_fence_init();
-        for (long long g = 0; g < S64 - 1 && g < total; ++g) issue(g);
+        while (issued < S64 - 1 && issued < total) issue();
     }
     __syncthreads();
     if (total == 0) return;
 
     if (warp == HELPER) {
-        // ---- helper: faces, q = D^-1 r and the ring, one stage ahead ------
+        // ---- helper: face values, r and the ring ---------------------------
         StageCursor nx{0, 0};   // the stage being prepared
-        LaneGeo G = lane_geo(a, tile_of(0), lane);
+        LaneGeo G = lane_geo(a, tiles[0], lane);
         // face lanes: 0..TK-1 the j-face of row kk = lane, TK..TK+TJ-1 the
         // k-face of column jj = lane - TK
         const bool jl = lane < TK, kl = lane >= TK && lane < TK + TJ;
         const int fk_kk = lane, fk_jj = lane - TK;
-        double rv[3], fv[3];
+        // r of a stage is loaded two stages ahead into one of two register
+        // sets (the stage's parity picks the set at compile time), so the
+        // load's latency is hidden behind two levels
+        double rA[3], rB[3], fv[3];
         auto face_slot = [&](const LaneGeo& Gt, int l, bool& need) -> double* {
             need = false;
             if (jl) {
@@ -234,18 +250,34 @@ k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
             }
             return nullptr;
         };
-        auto prefetch = [&](const LaneGeo& Gt, int l) {   // r and face values of a stage
+        auto load_r = [&](const LaneGeo& Gt, int l, double (&rv)[3]) {
             const bool act = lane_active(a, Gt, l);
-            const int c = Gt.cbase + l;
+            const double* rc = r + (Gt.cbase + l);
 #pragma unroll
-            for (int e = 0; e < 3; ++e) rv[e] = act ? r[(size_t)e * n + c] : 0.0;
+            for (int e = 0; e < 3; ++e) rv[e] = act ? rc[(size_t)e * n] : 0.0;
+        };
+        auto load_faces = [&](const LaneGeo& Gt, int l) {
             bool need;
             double* sl = face_slot(Gt, l, need);
 #pragma unroll
             for (int e = 0; e < 3; ++e) fv[e] = need ? ld_relaxed(sl + e) : 0.0;
         };
-        auto prepare = [&](long long g) {   // halo and q of stage g; prefetch stage g + 1
-            // halo of the plane stage g reads (buffer (g & 1) ^ 1)
+        // cursors: nx = the stage being prepared, n2 = the stage two ahead
+        // (whose r is loaded), with the tile geometries G and G2
+        StageCursor n2{0, 0};
+        LaneGeo G2 = G;
+        auto step2 = [&]() {
+            advance(n2, NL);
+            if (n2.l == 0 && n2.m < ntiles) G2 = lane_geo(a, tiles[n2.m], lane);
+        };
+        auto prepare = [&](long long g, double (&rcur)[3], double (&rnext2)[3]) {
+            double* rb = rsh + (int)(g & 1) * 96 + lane;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) rb[e * 32] = rcur[e];
+            if (g + 2 < total) {
+                load_r(G2, n2.l, rnext2);   // stage g + 2 into the set just freed
+                step2();
+            }
             double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF;
             bool need;
             double* sl = face_slot(G, nx.l, need);
@@ -257,36 +289,35 @@ k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
 #pragma unroll
                 for (int e = 0; e < 3; ++e) yb[e * YPL + fk_jj + 1] = fv[e];
             }
-            // q = D^-1 r of stage g
-            const int st = (int)(g % S64);
-            mb_wait(&bar[st], (unsigned)((g / S64) & 1), a.err);
-            const double* D = ring + (size_t)st * FWD_STAGE + lane;
-            double* qb = qsh + (int)(g & 1) * 96 + lane;
-#pragma unroll
-            for (int row = 0; row < 3; ++row) {
-                double q = D[(3 * row) * 32] * rv[0];
-                q = fma(D[(3 * row + 1) * 32], rv[1], q);
-                q = fma(D[(3 * row + 2) * 32], rv[2], q);
-                qb[row * 32] = q;
-            }
-            // next stage
             advance(nx, NL);
             if (g + 1 < total) {
-                if (nx.l == 0) G = lane_geo(a, tile_of(nx.m), lane);
-                prefetch(G, nx.l);
+                if (nx.l == 0) G = lane_geo(a, tiles[nx.m], lane);
+                load_faces(G, nx.l);
             }
+        };
+        auto prepare_any = [&](long long g) {
+            if (g & 1)
+                prepare(g, rB, rB);
+            else
+                prepare(g, rA, rA);
         };
         // A tile's first stage is prepared only after the previous tile has
         // finished (the barrier before it): the helper then waits only for
         // tiles earlier in the list than the one the CTA is working on.
-        prefetch(G, 0);
+        load_r(G, 0, rA);                 // stage 0
+        step2();
+        if (total > 1) {                  // stage 1
+            load_r(G2, n2.l, rB);
+            step2();
+        }
+        load_faces(G, 0);
         long long g = 0;
         for (int m = 0; m < ntiles; ++m) {
-            prepare(g);
+            prepare_any(g);
             __syncthreads();
             for (int l = 0; l < NL; ++l, ++g) {
-                if (lane == 0 && g + S64 - 1 < total) issue(g + S64 - 1);
-                if (l + 1 < NL) prepare(g + 1);
+                if (lane == 0 && issued < total) issue();
+                if (l + 1 < NL) prepare_any(g + 1);
                 __syncthreads();
             }
         }
@@ -297,32 +328,40 @@ k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
     const int rw = warp;
     const int op = (kk + 1) * HJ + jj + 1;   // this lane in the padded plane
     long long g = 0;
+    mb_wait(&bar[0], 0u, a.err);
     for (int m = 0; m < ntiles; ++m) {
         __syncthreads();   // the helper has prepared the tile's first stage
-        const LaneGeo G = lane_geo(a, tile_of(m), lane);
+        const LaneGeo G = lane_geo(a, tiles[m], lane);
         const bool feedJ = G.valid && jj == TJ - 1 && G.J + 1 < a.NJ && !ycut(a, (G.J + 1) * TJ);
         const bool feedK = G.valid && kk == TK - 1 && G.K + 1 < a.NK && !zcut(a, (G.K + 1) * TK);
         double* yout = Yt + ((size_t)G.t * NL * 3 + rw) * 32 + lane;
         double* fjo = fJ + jslot(a, G.t, 0, kk, 3) + rw - (size_t)G.l0 * TK * 3;
         double* fko = fK + kslot(a, G.t, 0, jj, 3) + rw - (size_t)G.l0 * TJ * 3;
         for (int l = 0; l < NL; ++l, ++g) {
-            const int st = (int)(g % S64);
-            mb_wait(&bar[st], (unsigned)((g / S64) & 1), a.err);
-            const double* L = ring + (size_t)st * FWD_STAGE + (9 + 3 * rw) * 32 + lane;
+            const int st = (int)(g % S64);   // its copy has landed (waited for below)
+            const double* D = ring + (size_t)st * FWD_STAGE + 3 * rw * 32 + lane;
+            const double* L = D + 9 * 32;   // row rw of D^-1 A_-x at entry 9 + 3 rw
+            const double* rb = rsh + (int)(g & 1) * 96 + lane;
             const double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF + op;
-            double acc = qsh[(int)(g & 1) * 96 + rw * 32 + lane];
+            // two independent chains: D^-1 r and the -x block; the -y and -z blocks
+            double u = D[0] * rb[0];
+            u = fma(D[32], rb[32], u);
+            u = fma(D[64], rb[64], u);
+            double v = -L[(9) * 32] * yb[-1];
 #pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2) acc = fma(-L[s2 * 32], yb[s2 * YPL], acc);          // -x
+            for (int s2 = 0; s2 < 3; ++s2) u = fma(-L[s2 * 32], yb[s2 * YPL], u);          // -x
 #pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2) acc = fma(-L[(9 + s2) * 32], yb[s2 * YPL - 1], acc);   // -y
+            for (int s2 = 1; s2 < 3; ++s2) v = fma(-L[(9 + s2) * 32], yb[s2 * YPL - 1], v);   // -y
 #pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2) acc = fma(-L[(18 + s2) * 32], yb[s2 * YPL - HJ], acc); // -z
+            for (int s2 = 0; s2 < 3; ++s2) v = fma(-L[(18 + s2) * 32], yb[s2 * YPL - HJ], v); // -z
             const bool act = lane_active(a, G, l);
-            acc = act ? acc : 0.0;
+            const double acc = act ? u + v : 0.0;
             ysh[(int)(g & 1) * YBUF + rw * YPL + op] = acc;
             yout[(size_t)l * 96] = acc;
             if (act && feedJ) st_relaxed(fjo + (size_t)l * TK * 3, acc);
             if (act && feedK) st_relaxed(fko + (size_t)l * TJ * 3, acc);
+            if (g + 1 < total)   // the next stage's copy, while the helper finishes
+                mb_wait(&bar[(g + 1) % S64], (unsigned)(((g + 1) / S64) & 1), a.err);
             __syncthreads();
         }
     }
@@ -341,34 +380,45 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
     double* ring = smem;                                   // [S64][BWD_STAGE]
     double* ysh = ring + S64 * BWD_STAGE;                  // [2][3][HK][HJ]
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(ysh + 2 * YBUF);
+    int* tiles = reinterpret_cast<int*>(bar + S64);        // [MAX_CTA_TILES]
     const TileArgs& a = A.a;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int jj = lane % TJ, kk = lane / TJ;
     const int NL = a.NL, n = a.g.n;
     const int ntiles = blockIdx.x < a.T ? (a.T - 1 - blockIdx.x) / A.G + 1 : 0;
     const long long total = (long long)ntiles * NL;
-    auto tile_of = [&](int m) { return A.order[blockIdx.x + m * A.G]; };
-    auto issue = [&](long long g) {
-        const int st = (int)(g % S64);
-        const size_t slot = (size_t)tile_of((int)(g / NL)) * NL + (NL - 1 - (int)(g % NL));
-        fence_async_smem();
+    for (int q = threadIdx.x; q < ntiles; q += SW_THREADS) tiles[q] = A.order[blockIdx.x + q * A.G];
+    for (int q = threadIdx.x; q < 2 * YBUF; q += SW_THREADS) ysh[q] = 0.0;
+    __syncthreads();
+    // issue cursor: stage (tile m, step l) copies slot t NL + NL - 1 - l
+    StageCursor ic{0, 0};
+    size_t islot = (size_t)tiles[0] * NL + NL - 1;
+    long long issued = 0;
+    auto issue = [&]() {
+        const int st = (int)(issued % S64);
         mb_expect(&bar[st], BWD_STAGE * 8);
         double* dst = ring + (size_t)st * BWD_STAGE;
-        bulk_g2s(dst, P + slot * (NPE * 32) + FWD_STAGE, BWD_ENT * 32 * 8, &bar[st]);
-        bulk_g2s(dst + BWD_ENT * 32, Yt + slot * 96, 96 * 8, &bar[st]);
+        bulk_g2s(dst, P + islot * (NPE * 32) + FWD_STAGE, BWD_ENT * 32 * 8, &bar[st]);
+        bulk_g2s(dst + BWD_ENT * 32, Yt + islot * 96, 96 * 8, &bar[st]);
+        ++issued;
+        advance(ic, NL);
+        if (ic.l == 0) {
+            if (ic.m < ntiles) islot = (size_t)tiles[ic.m] * NL + NL - 1;
+        } else {
+            --islot;
+        }
     };
-    for (int q = threadIdx.x; q < 2 * YBUF; q += SW_THREADS) ysh[q] = 0.0;
     if (threadIdx.x == HELPER * 32) {
         for (int d = 0; d < S64; ++d) mb_init(&bar[d], 1);
         mb_fence_init();
-        for (long long g = 0; g < S64 - 1 && g < total; ++g) issue(g);
+        while (issued < S64 - 1 && issued < total) issue();
     }
     __syncthreads();
     if (total == 0) return;
 
     if (warp == HELPER) {
         StageCursor nx{0, 0};
-        LaneGeo G = lane_geo(a, tile_of(0), lane);
+        LaneGeo G = lane_geo(a, tiles[0], lane);
         const bool jl = lane < TK, kl = lane >= TK && lane < TK + TJ;
         const int fk_kk = lane, fk_jj = lane - TK;
         double fv[3];
@@ -411,7 +461,7 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
             }
             advance(nx, NL);
             if (g + 1 < total) {
-                if (nx.l == 0) G = lane_geo(a, tile_of(nx.m), lane);
+                if (nx.l == 0) G = lane_geo(a, tiles[nx.m], lane);
                 prefetch(G, NL - 1 - nx.l);
             }
         };
@@ -421,7 +471,7 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
             prepare(g);
             __syncthreads();
             for (int step = 0; step < NL; ++step, ++g) {
-                if (lane == 0 && g + S64 - 1 < total) issue(g + S64 - 1);
+                if (lane == 0 && issued < total) issue();
                 if (step + 1 < NL) prepare(g + 1);
                 __syncthreads();
             }
@@ -432,9 +482,10 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
     const int rw = warp;
     const int op = kk * HJ + jj;   // interior at [kk][jj], borders at row TK and column TJ
     long long g = 0;
+    mb_wait(&bar[0], 0u, a.err);
     for (int m = 0; m < ntiles; ++m) {
         __syncthreads();
-        const LaneGeo G = lane_geo(a, tile_of(m), lane);
+        const LaneGeo G = lane_geo(a, tiles[m], lane);
         const bool feedJ = G.valid && jj == 0 && G.J > 0 && !ycut(a, G.J * TJ);
         const bool feedK = G.valid && kk == 0 && G.K > 0 && !zcut(a, G.K * TK);
         double* fjo = fJ + jslot(a, G.t, 0, kk, 3) + rw - (size_t)G.l0 * TK * 3;
@@ -442,25 +493,28 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
         double* zo = z + (size_t)rw * n + G.cbase;
         for (int step = 0; step < NL; ++step, ++g) {
             const int l = NL - 1 - step;
-            const int st = (int)(g % S64);
-            mb_wait(&bar[st], (unsigned)((g / S64) & 1), a.err);
+            const int st = (int)(g % S64);   // its copy has landed (waited for below)
             const double* U = ring + (size_t)st * BWD_STAGE + 3 * rw * 32 + lane;
             const double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF + op;
-            double acc = ring[(size_t)st * BWD_STAGE + (BWD_ENT + rw) * 32 + lane];
+            // two independent chains: y and the +x block; the +y and +z blocks
+            double u = ring[(size_t)st * BWD_STAGE + (BWD_ENT + rw) * 32 + lane];
+            double v = -U[9 * 32] * yb[1];
 #pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2) acc = fma(-U[s2 * 32], yb[s2 * YPL], acc);            // +x
+            for (int s2 = 0; s2 < 3; ++s2) u = fma(-U[s2 * 32], yb[s2 * YPL], u);            // +x
 #pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2) acc = fma(-U[(9 + s2) * 32], yb[s2 * YPL + 1], acc);   // +y
+            for (int s2 = 1; s2 < 3; ++s2) v = fma(-U[(9 + s2) * 32], yb[s2 * YPL + 1], v);   // +y
 #pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2) acc = fma(-U[(18 + s2) * 32], yb[s2 * YPL + HJ], acc); // +z
+            for (int s2 = 0; s2 < 3; ++s2) v = fma(-U[(18 + s2) * 32], yb[s2 * YPL + HJ], v); // +z
             const bool act = lane_active(a, G, l);
-            acc = act ? acc : 0.0;
+            const double acc = act ? u + v : 0.0;
             ysh[(int)(g & 1) * YBUF + rw * YPL + op] = acc;
             if (act) {
                 zo[l] = acc;
                 if (feedJ) st_relaxed(fjo + (size_t)l * TK * 3, acc);
                 if (feedK) st_relaxed(fko + (size_t)l * TJ * 3, acc);
             }
+            if (g + 1 < total)   // the next stage's copy, while the helper finishes
+                mb_wait(&bar[(g + 1) % S64], (unsigned)(((g + 1) / S64) & 1), a.err);
             __syncthreads();
         }
     }
@@ -470,9 +524,9 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
 // Host side
 // ---------------------------------------------------------------------------
 constexpr size_t FWD_SMEM = sizeof(double) * (S64 * FWD_STAGE + 2 * YBUF + 2 * 96) +
-                            sizeof(unsigned long long) * S64;
+                            sizeof(unsigned long long) * S64 + sizeof(int) * MAX_CTA_TILES;
 constexpr size_t BWD_SMEM = sizeof(double) * (S64 * BWD_STAGE + 2 * YBUF) +
-                            sizeof(unsigned long long) * S64;
+                            sizeof(unsigned long long) * S64 + sizeof(int) * MAX_CTA_TILES;
 
 // Tiles in the order a wavefront reaches them: the level at which tile
 // (J, K) can start is TJ (J - J0) + TK (K - K0) within its block-Jacobi box
@@ -511,6 +565,9 @@ void setup_sweeps64(bo_sim* s) {
     BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, k_bwd64, SW_THREADS, BWD_SMEM));
     if ((long long)std::min(pf, pb) * sms < sweep_ctas(s))
         fail(BO_ERR_INVALID_ARG, "sweep CTAs cannot all be resident at once");
+    const TileArgs a = tile_args(s);
+    if ((a.T + sweep_ctas(s) - 1) / sweep_ctas(s) > MAX_CTA_TILES)
+        fail(BO_ERR_INVALID_ARG, "grid too large: more wavefront tiles per CTA than the sweeps hold");
     update_sweep_order(s);
 }
 

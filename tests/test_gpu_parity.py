@@ -17,6 +17,7 @@ import pytest
 
 import oracle
 import synth
+from helpers import family_close, vec_close
 
 pytestmark = pytest.mark.gpu
 
@@ -35,30 +36,6 @@ def _gpu():
 def Sim(m):
     from paper_1910_06059_gb300 import Sim as _S
     return _S(m)
-
-
-def family_close(a, b, rowptr, per_equation=True):
-    """Max relative error of Jacobian blocks (nnzb,3,3).  Each entry J[r][s]
-    is judged against max(|oracle|, 1e-3 * the largest |J[r][s]| over the
-    blocks of its block row), i.e. against entries of the same equation and
-    the same unknown family (pressure columns are per Pa, the others are
-    dimensionless).  per_equation=False floors over all three equations."""
-    a = np.asarray(a)
-    b = np.asarray(b)
-    n = len(rowptr) - 1
-    rows = np.repeat(np.arange(n), np.diff(rowptr))
-    absb = np.abs(b)
-    fam = np.zeros((n, 3, 3))
-    np.maximum.at(fam, rows, absb)
-    if not per_equation:
-        fam = np.broadcast_to(fam.max(axis=1, keepdims=True), fam.shape)
-    scale = np.maximum(absb, 1e-3 * fam[rows])
-    scale = np.where(scale == 0, 1.0, scale)
-    return float((np.abs(a - b) / scale).max())
-
-
-def vec_close(a, b):
-    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
 MODELS = {

@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 import synth
-from test_gpu_parity import family_close, vec_close
+from helpers import family_close, vec_close
 
 pytestmark = pytest.mark.gpu
 

@@ -77,7 +77,7 @@ static void free_all(bo_sim* s) {
     destroy_graphs(s);
     void* ptrs[] = {s->d_dx, s->d_dy, s->d_dz, s->d_perm, s->d_poro, s->d_T, s->d_pv, s->d_depth,
                     s->d_p, s->d_sw, s->d_x, s->d_flag, s->d_bk, s->d_bkflag, s->d_A0,
-                    s->d_props, s->d_R, s->d_A, s->d_P, s->d_yt, s->d_order, s->d_face, s->d_cellcon, s->d_wells,
+                    s->d_props, s->d_R, s->d_A, s->d_P, s->d_yt, s->d_qt, s->d_order, s->d_face, s->d_cellcon, s->d_wells,
                     s->d_con_cell, s->d_con_wi, s->d_wB, s->d_wC, s->d_b, s->d_xs, s->d_r,
                     s->d_rh, s->d_pk, s->d_v, s->d_s, s->d_t, s->d_ph, s->d_sh, s->d_part,
                     s->d_ks, s->d_ns, s->d_sweep_sync, s->d_P32, s->d_r32, s->d_y32,
@@ -313,6 +313,7 @@ bo_status bo_create_grid(int nx, int ny, int nz, const double* dx, const double*
             // idle slots of the tile order are never written: zero factors
             BO_CUDA(cudaMemset(s->d_P, 0, sizeof(double) * 63 * ilu_storage(s)));
             dalloc(&s->d_yt, 3 * ilu_storage(s));
+            dalloc(&s->d_qt, 3 * ilu_storage(s));
             dalloc(&s->d_order, 2 * (size_t)tile_count(s));
             dalloc(&s->d_face, face_storage(s));
             dalloc(&s->d_sweep_sync, 4);

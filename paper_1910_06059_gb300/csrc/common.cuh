@@ -125,6 +125,7 @@ struct bo_sim {
     double* d_A = nullptr;       // 63n
     double* d_P = nullptr;       // 63 x tile-order ILU(0) data
     double* d_yt = nullptr;      // forward-sweep result, tile order [slot][3][32]
+    double* d_qt = nullptr;      // forward-sweep right-hand side D^-1 r, tile order
     int* d_order = nullptr;      // sweep tile lists: forward [T], backward [T]
     float* d_P32 = nullptr;      // FP32 factors in the FP32 sweep layout (mixed mode)
     float* d_r32 = nullptr;      // FP32 sweep input, tile order (mixed mode)

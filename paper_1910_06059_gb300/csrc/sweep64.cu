@@ -14,14 +14,15 @@
 // GB300 design.  An FP64 warp instruction holds its SM sub-partition for
 // about 64 cycles however many lanes are active, so a tile level costs what
 // its FP64 instructions cost; everything else is kept off that path:
-//   * one CTA of four warps per tile; warps 0-2 compute rows 0-2 of the
-//     level (forward: 3 FMAs of D^-1 r and 9 of the lower blocks in one
-//     chain; backward: 9 FMAs), each on its own sub-partition; warp 3 (the
-//     helper) runs no FP64: it fetches the face values of the neighbouring
-//     tiles, stages r one level ahead and keeps the stage ring full;
+//   * q = D^-1 r is formed before the wavefront by a fully parallel kernel,
+//     in tile order; one CTA of four warps per tile; warps 0-2 compute rows
+//     0-2 of the level (three block products, two FMA chains), each on its
+//     own sub-partition; warp 3 (the helper) fetches the face values of the
+//     neighbouring tiles and keeps the stage ring full;
 //   * the factor rows of a tile level are one contiguous chunk in HBM
 //     (ILU data in tile order, 63 entries x 32 lanes per level) and reach
-//     shared memory by one cp.async.bulk copy into a ring of S64 stages, each
+//     shared memory by cp.async.bulk copies (the level's three scaled
+//     blocks and its 3-vector q or y) into a ring of S64 stages, each
 //     completed on its own mbarrier, S64 - 1 levels ahead of the arithmetic;
 //   * the level's results are exchanged through a zero-padded plane in
 //     shared memory whose border row and column hold the neighbouring tiles'
@@ -50,10 +51,8 @@ namespace bo {
 constexpr int S64 = 8;                          // stages of the ring
 constexpr int SW_THREADS = 128;                 // 3 row warps + the helper warp
 constexpr int HELPER = 3;                       // warp index of the helper
-constexpr int FWD_ENT = 36;                     // D^-1 + 3 scaled lower blocks
-constexpr int BWD_ENT = 27;                     // 3 scaled upper blocks
-constexpr int FWD_STAGE = FWD_ENT * 32;         // doubles per stage
-constexpr int BWD_STAGE = (BWD_ENT + 3) * 32;   // upper blocks + y
+constexpr int BLK_ENT = 27;                     // 3 scaled off-diagonal blocks
+constexpr int STAGE = (BLK_ENT + 3) * 32;       // doubles per stage: blocks + a 3-vector
 constexpr int HJ = TJ + 1, HK = TK + 1;         // padded exchange plane
 constexpr int YPL = HK * HJ;                    // one component of the plane
 constexpr int YBUF = 3 * YPL;                   // one level of the plane
@@ -87,7 +86,18 @@ __device__ __forceinline__ bool mb_try(unsigned long long* bar, unsigned parity)
 }
 // Bounded wait for a stage; gives up at once when another wait of the sweep
 // has already given up (the error flag is set), so a failed sweep ends fast.
+__device__ __forceinline__ bool mb_test(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(sa(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ void mb_wait(unsigned long long* bar, unsigned parity, int* err) {
+    if (mb_test(bar, parity)) return;   // the usual case: the copy landed levels ago
     for (long long q = 0; q < MBAR_LIMIT64; ++q) {
         if (mb_try(bar, parity)) return;
         if ((q & 1023) == 1023 && ld_relaxed_i(err) != 0) return;
@@ -160,6 +170,63 @@ __device__ __forceinline__ void take_slot(double* slot, double v[3], int* err) {
     st_relaxed(slot + 2, sent);
 }
 
+// A helper lane's face slot for one tile: at level l the slot is
+// base + (l - off) stride, to be read when need and 0 <= l - off < nx; hp is
+// the slot's place in the padded exchange plane (-1: this lane has no face).
+struct FaceLane {
+    double* base;
+    int off, stride, hp;
+    bool need;
+};
+// Forward: lanes 0..TK-1 take the j-face of row kk = lane from tile J - 1,
+// lanes TK..TK+TJ-1 the k-face of column jj = lane - TK from tile K - 1.
+__device__ __forceinline__ FaceLane face_lane_fwd(const TileArgs& a, const LaneGeo& G, int lane,
+                                                  double* fJ, double* fK) {
+    FaceLane f{nullptr, 0, 0, -1, false};
+    if (lane < TK) {
+        const int kk = lane;
+        f.off = kk;
+        f.stride = TK * 3;
+        f.hp = (kk + 1) * HJ;
+        f.need = G.J > 0 && !ycut(a, G.J * TJ) && G.K * TK + kk < a.g.nz;
+        if (f.need) f.base = fJ + jslot(a, G.t - 1, 0, kk, 3);
+    } else if (lane < TK + TJ) {
+        const int jj = lane - TK;
+        f.off = jj;
+        f.stride = TJ * 3;
+        f.hp = jj + 1;
+        f.need = G.K > 0 && !zcut(a, G.K * TK) && G.J * TJ + jj < a.g.ny;
+        if (f.need) f.base = fK + kslot(a, G.t - a.NJ, 0, jj, 3);
+    }
+    return f;
+}
+// Backward: the upper neighbours of lane (TJ - 1, kk) in tile J + 1 and of
+// lane (jj, TK - 1) in tile K + 1.
+__device__ __forceinline__ FaceLane face_lane_bwd(const TileArgs& a, const LaneGeo& G, int lane,
+                                                  double* fJ, double* fK) {
+    FaceLane f{nullptr, 0, 0, -1, false};
+    if (lane < TK) {
+        const int kk = lane;
+        f.off = TJ - 1 + kk;
+        f.stride = TK * 3;
+        f.hp = kk * HJ + TJ;
+        f.need = G.J + 1 < a.NJ && !ycut(a, (G.J + 1) * TJ) && G.K * TK + kk < a.g.nz;
+        if (f.need) f.base = fJ + jslot(a, G.t + 1, 0, kk, 3);
+    } else if (lane < TK + TJ) {
+        const int jj = lane - TK;
+        f.off = jj + TK - 1;
+        f.stride = TJ * 3;
+        f.hp = TK * HJ + jj;
+        f.need = G.K + 1 < a.NK && !zcut(a, (G.K + 1) * TK) && G.J * TJ + jj < a.g.ny;
+        if (f.need) f.base = fK + kslot(a, G.t + a.NJ, 0, jj, 3);
+    }
+    return f;
+}
+__device__ __forceinline__ double* face_at(const FaceLane& f, int l, int nx) {
+    const int i = l - f.off;
+    return (f.need && i >= 0 && i < nx) ? f.base + (size_t)i * f.stride : nullptr;
+}
+
 // The helper warp's view of one stage: which tile and level it belongs to.
 struct StageCursor {
     int m, l;   // m-th tile of this CTA, level (forward) or step (backward)
@@ -174,46 +241,83 @@ __device__ __forceinline__ void advance(StageCursor& c, int NL) {
 constexpr int MAX_CTA_TILES = 64;   // tiles of one CTA (checked on the host)
 
 // ---------------------------------------------------------------------------
-// a8 forward sweep: Yt = (L_A + D)^-1 r, Yt in tile order [slot][3][32].
-// Row warp rw of a level: acc = D^-1[rw][:] r - L_x[rw][:] y_{i-1}
-// - L_y[rw][:] y_{j-1} - L_z[rw][:] y_{k-1}, twelve FMAs in one chain.  The
-// helper stages r (one level ahead, through shared memory) and the face
-// values, and issues the bulk copies; it runs no FP64.
+// q = D^-1 r in tile order, Qt[slot][3][32] (zero for idle slots): the
+// forward sweep's right-hand side, formed by all SMs before the wavefront.
+// Threads follow the tile order (a warp is one tile level), so the factor
+// reads and the writes are coalesced; neighbouring warps are neighbouring
+// levels of one tile and reuse each other's sectors of r.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_q_tiles(TileArgs a, const double* __restrict__ P, const double* __restrict__ r,
+          double* __restrict__ Qt, const KrylovScalars* __restrict__ ks) {
+    if (ks_skip_t(ks)) return;
+    const int n = a.g.n;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < a.NP;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int lane = (int)(idx & 31);
+        const size_t slot = idx >> 5;
+        const int t = (int)(slot / a.NL), l = (int)(slot % a.NL);
+        const LaneGeo G = lane_geo(a, t, lane);
+        double rv[3] = {0.0, 0.0, 0.0};
+        if (lane_active(a, G, l)) {
+            const int c = G.cbase + l;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) rv[e] = r[(size_t)e * n + c];
+        }
+        const double* D = P + slot * (NPE * 32) + lane;
+        double* q = Qt + slot * 96 + lane;
+#pragma unroll
+        for (int row = 0; row < 3; ++row) {
+            double v = D[(3 * row) * 32] * rv[0];
+            v = fma(D[(3 * row + 1) * 32], rv[1], v);
+            v = fma(D[(3 * row + 2) * 32], rv[2], v);
+            q[row * 32] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a8 forward sweep: Yt = (L_A + D)^-1 r, from Qt = D^-1 r; Yt in tile order.
+// Row warp rw of a level: acc = q[rw] - L_x[rw][:] y_{i-1} - L_y[rw][:] y_{j-1}
+// - L_z[rw][:] y_{k-1} (ten FP64 operations in two chains).  A stage is the
+// level's three scaled lower blocks and q; the helper stages the face values
+// and issues the bulk copies.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(SW_THREADS, 2)
-k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
+k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Qt,
         double* __restrict__ Yt, double* __restrict__ fJ, double* __restrict__ fK,
         const KrylovScalars* __restrict__ ks) {
     if (ks_skip_t(ks)) return;
     extern __shared__ __align__(128) double smem[];
-    double* ring = smem;                                   // [S64][FWD_STAGE]
-    double* ysh = ring + S64 * FWD_STAGE;                  // [2][3][HK][HJ]
-    double* rsh = ysh + 2 * YBUF;                          // [2][3][32]
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(rsh + 2 * 96);
+    double* ring = smem;                                   // [S64][STAGE]
+    double* ysh = ring + S64 * STAGE;                      // [2][3][HK][HJ]
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(ysh + 2 * YBUF);
     int* tiles = reinterpret_cast<int*>(bar + S64);        // [MAX_CTA_TILES]
     const TileArgs& a = A.a;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int jj = lane % TJ, kk = lane / TJ;
-    const int NL = a.NL, n = a.g.n;
+    const int NL = a.NL;
     const int ntiles = blockIdx.x < a.T ? (a.T - 1 - blockIdx.x) / A.G + 1 : 0;
     const long long total = (long long)ntiles * NL;
     for (int q = threadIdx.x; q < ntiles; q += SW_THREADS) tiles[q] = A.order[blockIdx.x + q * A.G];
-    for (int q = threadIdx.x; q < 2 * YBUF + 2 * 96; q += SW_THREADS) ysh[q] = 0.0;
+    for (int q = threadIdx.x; q < 2 * YBUF; q += SW_THREADS) ysh[q] = 0.0;
     __syncthreads();
-    // issue cursor (helper lane 0): the next stage to copy and its source
+    // issue cursor (helper lane 0): stage (tile m, level l) copies slot t NL + l
     StageCursor ic{0, 0};
-    const double* ip = P + (size_t)tiles[0] * NL * (NPE * 32);
+    size_t islot = (size_t)tiles[0] * NL;
     long long issued = 0;
     auto issue = [&]() {
         const int st = (int)(issued % S64);
-        mb_expect(&bar[st], FWD_STAGE * 8);
-        bulk_g2s(ring + (size_t)st * FWD_STAGE, ip, FWD_STAGE * 8, &bar[st]);
+        mb_expect(&bar[st], STAGE * 8);
+        double* dst = ring + (size_t)st * STAGE;
+        bulk_g2s(dst, P + islot * (NPE * 32) + 9 * 32, BLK_ENT * 32 * 8, &bar[st]);
+        bulk_g2s(dst + BLK_ENT * 32, Qt + islot * 96, 96 * 8, &bar[st]);
         ++issued;
         advance(ic, NL);
         if (ic.l == 0) {
-            if (ic.m < ntiles) ip = P + (size_t)tiles[ic.m] * NL * (NPE * 32);
+            if (ic.m < ntiles) islot = (size_t)tiles[ic.m] * NL;
         } else {
-            ip += NPE * 32;
+            ++islot;
         }
     };
     if (threadIdx.x == HELPER * 32) {
@@ -225,99 +329,45 @@ k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
     if (total == 0) return;
 
     if (warp == HELPER) {
-        // ---- helper: face values, r and the ring ---------------------------
+        // ---- helper: face values and the ring -------------------------------
         StageCursor nx{0, 0};   // the stage being prepared
         LaneGeo G = lane_geo(a, tiles[0], lane);
-        // face lanes: 0..TK-1 the j-face of row kk = lane, TK..TK+TJ-1 the
-        // k-face of column jj = lane - TK
-        const bool jl = lane < TK, kl = lane >= TK && lane < TK + TJ;
-        const int fk_kk = lane, fk_jj = lane - TK;
-        // r of a stage is loaded two stages ahead into one of two register
-        // sets (the stage's parity picks the set at compile time), so the
-        // load's latency is hidden behind two levels
-        double rA[3], rB[3], fv[3];
-        auto face_slot = [&](const LaneGeo& Gt, int l, bool& need) -> double* {
-            need = false;
-            if (jl) {
-                const int k = Gt.K * TK + fk_kk, i = l - fk_kk;
-                need = Gt.J > 0 && !ycut(a, Gt.J * TJ) && k < a.g.nz && i >= 0 && i < a.g.nx;
-                return need ? fJ + jslot(a, Gt.t - 1, i, fk_kk, 3) : nullptr;
-            }
-            if (kl) {
-                const int j = Gt.J * TJ + fk_jj, i = l - fk_jj;
-                need = Gt.K > 0 && !zcut(a, Gt.K * TK) && j < a.g.ny && i >= 0 && i < a.g.nx;
-                return need ? fK + kslot(a, Gt.t - a.NJ, i, fk_jj, 3) : nullptr;
-            }
-            return nullptr;
+        FaceLane F = face_lane_fwd(a, G, lane, fJ, fK);
+        double fv[3] = {0.0, 0.0, 0.0};
+        auto load_faces = [&](int l) {
+            const double* sl = face_at(F, l, a.g.nx);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) fv[e] = sl ? ld_relaxed(sl + e) : 0.0;
         };
-        auto load_r = [&](const LaneGeo& Gt, int l, double (&rv)[3]) {
-            const bool act = lane_active(a, Gt, l);
-            const double* rc = r + (Gt.cbase + l);
-#pragma unroll
-            for (int e = 0; e < 3; ++e) rv[e] = act ? rc[(size_t)e * n] : 0.0;
-        };
-        auto load_faces = [&](const LaneGeo& Gt, int l) {
-            bool need;
-            double* sl = face_slot(Gt, l, need);
-#pragma unroll
-            for (int e = 0; e < 3; ++e) fv[e] = need ? ld_relaxed(sl + e) : 0.0;
-        };
-        // cursors: nx = the stage being prepared, n2 = the stage two ahead
-        // (whose r is loaded), with the tile geometries G and G2
-        StageCursor n2{0, 0};
-        LaneGeo G2 = G;
-        auto step2 = [&]() {
-            advance(n2, NL);
-            if (n2.l == 0 && n2.m < ntiles) G2 = lane_geo(a, tiles[n2.m], lane);
-        };
-        auto prepare = [&](long long g, double (&rcur)[3], double (&rnext2)[3]) {
-            double* rb = rsh + (int)(g & 1) * 96 + lane;
-#pragma unroll
-            for (int e = 0; e < 3; ++e) rb[e * 32] = rcur[e];
-            if (g + 2 < total) {
-                load_r(G2, n2.l, rnext2);   // stage g + 2 into the set just freed
-                step2();
-            }
-            double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF;
-            bool need;
-            double* sl = face_slot(G, nx.l, need);
-            if (need) take_slot(sl, fv, a.err);
-            if (jl) {
-#pragma unroll
-                for (int e = 0; e < 3; ++e) yb[e * YPL + (fk_kk + 1) * HJ] = fv[e];
-            } else if (kl) {
-#pragma unroll
-                for (int e = 0; e < 3; ++e) yb[e * YPL + fk_jj + 1] = fv[e];
+        auto prepare = [&](long long g) {   // face values of stage g into the plane it reads
+            double* sl = face_at(F, nx.l, a.g.nx);
+            if (sl) take_slot(sl, fv, a.err);
+            if (F.hp >= 0) {
+                double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF + F.hp;
+                yb[0] = fv[0];
+                yb[YPL] = fv[1];
+                yb[2 * YPL] = fv[2];
             }
             advance(nx, NL);
             if (g + 1 < total) {
-                if (nx.l == 0) G = lane_geo(a, tiles[nx.m], lane);
-                load_faces(G, nx.l);
+                if (nx.l == 0) {
+                    G = lane_geo(a, tiles[nx.m], lane);
+                    F = face_lane_fwd(a, G, lane, fJ, fK);
+                }
+                load_faces(nx.l);
             }
-        };
-        auto prepare_any = [&](long long g) {
-            if (g & 1)
-                prepare(g, rB, rB);
-            else
-                prepare(g, rA, rA);
         };
         // A tile's first stage is prepared only after the previous tile has
         // finished (the barrier before it): the helper then waits only for
         // tiles earlier in the list than the one the CTA is working on.
-        load_r(G, 0, rA);                 // stage 0
-        step2();
-        if (total > 1) {                  // stage 1
-            load_r(G2, n2.l, rB);
-            step2();
-        }
-        load_faces(G, 0);
+        load_faces(0);
         long long g = 0;
         for (int m = 0; m < ntiles; ++m) {
-            prepare_any(g);
+            prepare(g);
             __syncthreads();
             for (int l = 0; l < NL; ++l, ++g) {
                 if (lane == 0 && issued < total) issue();
-                if (l + 1 < NL) prepare_any(g + 1);
+                if (l + 1 < NL) prepare(g + 1);
                 __syncthreads();
             }
         }
@@ -328,7 +378,6 @@ k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
     const int rw = warp;
     const int op = (kk + 1) * HJ + jj + 1;   // this lane in the padded plane
     long long g = 0;
-    mb_wait(&bar[0], 0u, a.err);
     for (int m = 0; m < ntiles; ++m) {
         __syncthreads();   // the helper has prepared the tile's first stage
         const LaneGeo G = lane_geo(a, tiles[m], lane);
@@ -338,16 +387,13 @@ k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
         double* fjo = fJ + jslot(a, G.t, 0, kk, 3) + rw - (size_t)G.l0 * TK * 3;
         double* fko = fK + kslot(a, G.t, 0, jj, 3) + rw - (size_t)G.l0 * TJ * 3;
         for (int l = 0; l < NL; ++l, ++g) {
-            const int st = (int)(g % S64);   // its copy has landed (waited for below)
-            const double* D = ring + (size_t)st * FWD_STAGE + 3 * rw * 32 + lane;
-            const double* L = D + 9 * 32;   // row rw of D^-1 A_-x at entry 9 + 3 rw
-            const double* rb = rsh + (int)(g & 1) * 96 + lane;
+            const int st = (int)(g % S64);
+            mb_wait(&bar[st], (unsigned)((g / S64) & 1), a.err);
+            const double* L = ring + (size_t)st * STAGE + 3 * rw * 32 + lane;   // row rw of D^-1 A_-x
             const double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF + op;
-            // two independent chains: D^-1 r and the -x block; the -y and -z blocks
-            double u = D[0] * rb[0];
-            u = fma(D[32], rb[32], u);
-            u = fma(D[64], rb[64], u);
-            double v = -L[(9) * 32] * yb[-1];
+            // two independent chains: q and the -x block; the -y and -z blocks
+            double u = ring[(size_t)st * STAGE + (BLK_ENT + rw) * 32 + lane];
+            double v = -L[9 * 32] * yb[-1];
 #pragma unroll
             for (int s2 = 0; s2 < 3; ++s2) u = fma(-L[s2 * 32], yb[s2 * YPL], u);          // -x
 #pragma unroll
@@ -360,8 +406,6 @@ k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ r,
             yout[(size_t)l * 96] = acc;
             if (act && feedJ) st_relaxed(fjo + (size_t)l * TK * 3, acc);
             if (act && feedK) st_relaxed(fko + (size_t)l * TJ * 3, acc);
-            if (g + 1 < total)   // the next stage's copy, while the helper finishes
-                mb_wait(&bar[(g + 1) % S64], (unsigned)(((g + 1) / S64) & 1), a.err);
             __syncthreads();
         }
     }
@@ -377,8 +421,8 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
         const KrylovScalars* __restrict__ ks) {
     if (ks_skip_t(ks)) return;
     extern __shared__ __align__(128) double smem[];
-    double* ring = smem;                                   // [S64][BWD_STAGE]
-    double* ysh = ring + S64 * BWD_STAGE;                  // [2][3][HK][HJ]
+    double* ring = smem;                                   // [S64][STAGE]
+    double* ysh = ring + S64 * STAGE;                      // [2][3][HK][HJ]
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(ysh + 2 * YBUF);
     int* tiles = reinterpret_cast<int*>(bar + S64);        // [MAX_CTA_TILES]
     const TileArgs& a = A.a;
@@ -396,10 +440,10 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
     long long issued = 0;
     auto issue = [&]() {
         const int st = (int)(issued % S64);
-        mb_expect(&bar[st], BWD_STAGE * 8);
-        double* dst = ring + (size_t)st * BWD_STAGE;
-        bulk_g2s(dst, P + islot * (NPE * 32) + FWD_STAGE, BWD_ENT * 32 * 8, &bar[st]);
-        bulk_g2s(dst + BWD_ENT * 32, Yt + islot * 96, 96 * 8, &bar[st]);
+        mb_expect(&bar[st], STAGE * 8);
+        double* dst = ring + (size_t)st * STAGE;
+        bulk_g2s(dst, P + islot * (NPE * 32) + 36 * 32, BLK_ENT * 32 * 8, &bar[st]);
+        bulk_g2s(dst + BLK_ENT * 32, Yt + islot * 96, 96 * 8, &bar[st]);
         ++issued;
         advance(ic, NL);
         if (ic.l == 0) {
@@ -419,53 +463,32 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
     if (warp == HELPER) {
         StageCursor nx{0, 0};
         LaneGeo G = lane_geo(a, tiles[0], lane);
-        const bool jl = lane < TK, kl = lane >= TK && lane < TK + TJ;
-        const int fk_kk = lane, fk_jj = lane - TK;
-        double fv[3];
-        // face values of the stage at level l: the upper neighbours of
-        // lane (TJ - 1, kk) in tile J + 1 and of lane (jj, TK - 1) in K + 1
-        auto face_slot = [&](const LaneGeo& Gt, int l, bool& need) -> double* {
-            need = false;
-            if (jl) {
-                const int k = Gt.K * TK + fk_kk, i = l - (TJ - 1) - fk_kk;
-                need = Gt.J + 1 < a.NJ && !ycut(a, (Gt.J + 1) * TJ) && k < a.g.nz && i >= 0 &&
-                       i < a.g.nx;
-                return need ? fJ + jslot(a, Gt.t + 1, i, fk_kk, 3) : nullptr;
-            }
-            if (kl) {
-                const int j = Gt.J * TJ + fk_jj, i = l - fk_jj - (TK - 1);
-                need = Gt.K + 1 < a.NK && !zcut(a, (Gt.K + 1) * TK) && j < a.g.ny && i >= 0 &&
-                       i < a.g.nx;
-                return need ? fK + kslot(a, Gt.t + a.NJ, i, fk_jj, 3) : nullptr;
-            }
-            return nullptr;
-        };
-        auto prefetch = [&](const LaneGeo& Gt, int l) {
-            bool need;
-            double* sl = face_slot(Gt, l, need);
+        FaceLane F = face_lane_bwd(a, G, lane, fJ, fK);
+        double fv[3] = {0.0, 0.0, 0.0};
+        auto load_faces = [&](int l) {
+            const double* sl = face_at(F, l, a.g.nx);
 #pragma unroll
-            for (int e = 0; e < 3; ++e) fv[e] = need ? ld_relaxed(sl + e) : 0.0;
+            for (int e = 0; e < 3; ++e) fv[e] = sl ? ld_relaxed(sl + e) : 0.0;
         };
         auto prepare = [&](long long g) {
-            double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF;
-            const int l = NL - 1 - nx.l;
-            bool need;
-            double* sl = face_slot(G, l, need);
-            if (need) take_slot(sl, fv, a.err);
-            if (jl) {
-#pragma unroll
-                for (int e = 0; e < 3; ++e) yb[e * YPL + fk_kk * HJ + TJ] = fv[e];
-            } else if (kl) {
-#pragma unroll
-                for (int e = 0; e < 3; ++e) yb[e * YPL + TK * HJ + fk_jj] = fv[e];
+            double* sl = face_at(F, NL - 1 - nx.l, a.g.nx);
+            if (sl) take_slot(sl, fv, a.err);
+            if (F.hp >= 0) {
+                double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF + F.hp;
+                yb[0] = fv[0];
+                yb[YPL] = fv[1];
+                yb[2 * YPL] = fv[2];
             }
             advance(nx, NL);
             if (g + 1 < total) {
-                if (nx.l == 0) G = lane_geo(a, tiles[nx.m], lane);
-                prefetch(G, NL - 1 - nx.l);
+                if (nx.l == 0) {
+                    G = lane_geo(a, tiles[nx.m], lane);
+                    F = face_lane_bwd(a, G, lane, fJ, fK);
+                }
+                load_faces(NL - 1 - nx.l);
             }
         };
-        prefetch(G, NL - 1);
+        load_faces(NL - 1);
         long long g = 0;
         for (int m = 0; m < ntiles; ++m) {   // first stage of a tile: as in the forward sweep
             prepare(g);
@@ -482,7 +505,6 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
     const int rw = warp;
     const int op = kk * HJ + jj;   // interior at [kk][jj], borders at row TK and column TJ
     long long g = 0;
-    mb_wait(&bar[0], 0u, a.err);
     for (int m = 0; m < ntiles; ++m) {
         __syncthreads();
         const LaneGeo G = lane_geo(a, tiles[m], lane);
@@ -493,11 +515,12 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
         double* zo = z + (size_t)rw * n + G.cbase;
         for (int step = 0; step < NL; ++step, ++g) {
             const int l = NL - 1 - step;
-            const int st = (int)(g % S64);   // its copy has landed (waited for below)
-            const double* U = ring + (size_t)st * BWD_STAGE + 3 * rw * 32 + lane;
+            const int st = (int)(g % S64);
+            mb_wait(&bar[st], (unsigned)((g / S64) & 1), a.err);
+            const double* U = ring + (size_t)st * STAGE + 3 * rw * 32 + lane;
             const double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF + op;
             // two independent chains: y and the +x block; the +y and +z blocks
-            double u = ring[(size_t)st * BWD_STAGE + (BWD_ENT + rw) * 32 + lane];
+            double u = ring[(size_t)st * STAGE + (BLK_ENT + rw) * 32 + lane];
             double v = -U[9 * 32] * yb[1];
 #pragma unroll
             for (int s2 = 0; s2 < 3; ++s2) u = fma(-U[s2 * 32], yb[s2 * YPL], u);            // +x
@@ -513,8 +536,6 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
                 if (feedJ) st_relaxed(fjo + (size_t)l * TK * 3, acc);
                 if (feedK) st_relaxed(fko + (size_t)l * TJ * 3, acc);
             }
-            if (g + 1 < total)   // the next stage's copy, while the helper finishes
-                mb_wait(&bar[(g + 1) % S64], (unsigned)(((g + 1) / S64) & 1), a.err);
             __syncthreads();
         }
     }
@@ -523,10 +544,8 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-constexpr size_t FWD_SMEM = sizeof(double) * (S64 * FWD_STAGE + 2 * YBUF + 2 * 96) +
-                            sizeof(unsigned long long) * S64 + sizeof(int) * MAX_CTA_TILES;
-constexpr size_t BWD_SMEM = sizeof(double) * (S64 * BWD_STAGE + 2 * YBUF) +
-                            sizeof(unsigned long long) * S64 + sizeof(int) * MAX_CTA_TILES;
+constexpr size_t SWEEP_SMEM = sizeof(double) * (S64 * STAGE + 2 * YBUF) +
+                              sizeof(unsigned long long) * S64 + sizeof(int) * MAX_CTA_TILES;
 
 // Tiles in the order a wavefront reaches them: the level at which tile
 // (J, K) can start is TJ (J - J0) + TK (K - K0) within its block-Jacobi box
@@ -552,8 +571,8 @@ int sweep_ctas(const bo_sim* s) {
 }
 
 void setup_sweeps64(bo_sim* s) {
-    BO_CUDA(cudaFuncSetAttribute(k_fwd64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FWD_SMEM));
-    BO_CUDA(cudaFuncSetAttribute(k_bwd64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BWD_SMEM));
+    BO_CUDA(cudaFuncSetAttribute(k_fwd64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM));
+    BO_CUDA(cudaFuncSetAttribute(k_bwd64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM));
     // two CTAs per SM need the whole shared-memory carveout
     for (const void* k : {(const void*)k_fwd64, (const void*)k_bwd64})
         BO_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -561,8 +580,8 @@ void setup_sweeps64(bo_sim* s) {
     int dev, sms, pf = 0, pb = 0;
     BO_CUDA(cudaGetDevice(&dev));
     BO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, k_fwd64, SW_THREADS, FWD_SMEM));
-    BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, k_bwd64, SW_THREADS, BWD_SMEM));
+    BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, k_fwd64, SW_THREADS, SWEEP_SMEM));
+    BO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, k_bwd64, SW_THREADS, SWEEP_SMEM));
     if ((long long)std::min(pf, pb) * sms < sweep_ctas(s))
         fail(BO_ERR_INVALID_ARG, "sweep CTAs cannot all be resident at once");
     const TileArgs a = tile_args(s);
@@ -585,14 +604,16 @@ void update_sweep_order(bo_sim* s) {
 
 void enqueue_fwd64(bo_sim* s, cudaStream_t st, const double* r, const KrylovScalars* ks) {
     SweepArgs A{tile_args(s), s->d_order, sweep_ctas(s)};
-    launch_coop_smem(st, A.G, SW_THREADS, FWD_SMEM, k_fwd64, A, (const double*)s->d_P, r, s->d_yt,
-                     faceJ3(s), faceK3(s), ks);
+    k_q_tiles<<<152 * 8, 256, 0, st>>>(A.a, (const double*)s->d_P, r, s->d_qt, ks);
+    count_launch(s, st);
+    launch_coop_smem(st, A.G, SW_THREADS, SWEEP_SMEM, k_fwd64, A, (const double*)s->d_P,
+                     (const double*)s->d_qt, s->d_yt, faceJ3(s), faceK3(s), ks);
     count_launch(s, st);
 }
 
 void enqueue_bwd64(bo_sim* s, cudaStream_t st, double* z, const KrylovScalars* ks) {
     SweepArgs A{tile_args(s), s->d_order + tile_args(s).T, sweep_ctas(s)};
-    launch_coop_smem(st, A.G, SW_THREADS, BWD_SMEM, k_bwd64, A, (const double*)s->d_P,
+    launch_coop_smem(st, A.G, SW_THREADS, SWEEP_SMEM, k_bwd64, A, (const double*)s->d_P,
                      (const double*)s->d_yt, z, faceJ3(s), faceK3(s), ks);
     count_launch(s, st);
 }

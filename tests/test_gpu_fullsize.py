@@ -1,0 +1,137 @@
+"""Parity at the size of the benchmark and on its generator (needs a GB300).
+
+The benchmark runs the 60x220x85 layered model (1,122,000 cells: 616 tiles
+of the wavefront, ~370 wavefront levels per sweep).  These tests compare the
+ILU(0) factorisation and the preconditioner entry by entry with the oracle at
+that size, at the same bars as the small models of test_gpu_parity.py:
+
+  ILU(0) pivot inverses D^-1          1e-10 relative per entry (family floor)
+  preconditioner / operator applies    1e-11 relative to the vector's max,
+                                       per unknown family
+
+and run Newton report steps of a layered five-spot model (the benchmark's
+generator and well pattern at a size the oracle finishes) at tight
+tolerances, comparing the states after every report step (pressure 1e-6
+relative, saturations 1e-6 absolute; Section 2.3 Newton, chop and variable
+switching, Section 2.3.1 ILU0-BiCGStab).
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import family_close, vec_close
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_1910_06059_gb300.build import build
+    build()
+    oracle.set_threads(os.cpu_count() or 1)
+    yield
+    oracle.set_threads(1)
+
+
+def Sim(m):
+    from paper_1910_06059_gb300 import Sim as _S
+    return _S(m)
+
+
+@pytest.fixture(scope="module")
+def config1_pair():
+    m = synth.config1()
+    g, o = Sim(m), oracle.Oracle(m)
+    yield m, g, o
+    g.close()
+
+
+def _factor_and_apply(g, o, seed):
+    dinv = g.factor()
+    _, uinv = o.ilu0()
+    assert family_close(dinv, uinv, np.arange(o.n + 1), per_equation=False) <= 1e-10
+    rng = np.random.default_rng(seed)
+    r = rng.standard_normal(3 * o.n)
+    zg, zo = g.precond_apply(r), o.ilu_apply(r)
+    for v in range(3):
+        assert vec_close(zg[v::3], zo[v::3]) <= 1e-11, v
+    x = rng.standard_normal(3 * o.n) * np.tile([1e5, 0.1, 1.0], o.n)
+    yg, yo = g.apply_op(x), o.apply_op(x)
+    for v in range(3):
+        assert vec_close(yg[v::3], yo[v::3]) <= 1e-11, v
+
+
+def test_config1_ilu0_entrywise_at_the_initial_state(config1_pair):
+    """The first Newton system of the benchmark: every pivot inverse, the
+    preconditioner apply and the operator, entry by entry."""
+    m, g, o = config1_pair
+    g.init_hydrostatic()
+    o.init_hydrostatic()
+    g.begin_step()
+    o.begin_step()
+    dt = 10 * synth.DAY
+    g.assemble(dt)
+    o.assemble(dt)
+    _factor_and_apply(g, o, seed=31)
+
+
+def test_config1_ilu0_entrywise_with_gas(config1_pair):
+    """A system with saturated cells: the initial state with every cell in
+    the upper third of the reservoir released to free gas (s_g = 0.05), one
+    day's step."""
+    m, g, o = config1_pair
+    o.init_hydrostatic()
+    po, swo, xo, flo, bhpo = o.get_state()   # input for both codes
+    k = np.arange(o.n) // (m["nx"] * m["ny"])
+    top = k < m["nz"] // 3
+    xo = xo.copy()
+    flo = flo.copy()
+    xo[top] = 0.05
+    flo[top] = 0
+    po = po * 0.99
+    for s in (g, o):
+        s.set_state(po, swo, xo, flo, bhpo)
+        s.begin_step()
+    dt = 1.0 * synth.DAY
+    g.assemble(dt)
+    o.assemble(dt)
+    _factor_and_apply(g, o, seed=32)
+
+
+def test_layered_five_spot_newton_states():
+    """Report steps of the benchmark's generator and wells on 16x30x20 cells
+    (two 10-day report steps, including the depletion transient with gas
+    coming out of solution), at Newton MB/CNV 1e-9 and linear 1e-10 in both
+    codes.  1e-10 (the tight tolerance of the small models) is below what
+    these heterogeneous layered systems reach in FP64: the oracle itself
+    cannot converge the first report step at that tolerance."""
+    m = synth.layered_model(16, 30, 20, config=1, name="layered 16x30x20")
+    g, o = Sim(m), oracle.Oracle(m)
+    g.init_hydrostatic()
+    o.init_hydrostatic()
+    tight = dict(tol_mb=1e-9, tol_cnv=1e-9, tol_well=1e-9, tol_lin=1e-10)
+    for s in range(2):
+        stg, rg = g.step(10 * synth.DAY, **tight)
+        sto, ro = o.step(10 * synth.DAY, **tight)
+        assert stg == 0 and sto == 0, (s, rg, ro)
+        assert (rg["substeps"], rg["cuts"]) == (ro["substeps"], ro["cuts"]), (s, rg, ro)
+        pg, swg, xg, fg, bg = g.get_state()
+        po, swo, xo, fo, bo = o.get_state()
+        assert np.array_equal(fg, fo), s
+        assert np.max(np.abs(pg - po) / po) <= 1e-6, s
+        assert np.max(np.abs(swg - swo)) <= 1e-6, s
+        sat = fo == 0
+        assert np.max(np.abs(xg[sat] - xo[sat]), initial=0.0) <= 1e-6, s
+        assert np.max(np.abs(xg[~sat] - xo[~sat]) / xo[~sat].clip(1e-300), initial=0.0) <= 1e-6, s
+        assert np.allclose(bg, bo, rtol=1e-6)
+    g.close()

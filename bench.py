@@ -65,6 +65,8 @@ LEARNED_NAME = (" + learned stage (63-128-128-9 MLP on BF16 tensor cores, traine
                 "on the first warm-up report step's solver residuals)")
 PRECISION_NAMES = {"fp64": "plain FP64 ILU0-BiCGStab",
                    "mixed": "FP32 ILU0 factors and sweeps, FP64 assembly/Krylov/Newton"}
+CPR_NAME = (" with the two-stage CPR preconditioner (aggregation-AMG V-cycle on the "
+            "quasi-IMPES pressure matrix, then ILU0)")
 
 
 def peaks():
@@ -134,6 +136,8 @@ def parse():
                     help="members stepped one at a time for the sequential comparison (config 3)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="ILU(0) preconditioner precision (mixed: FP32 factors and sweeps)")
+    ap.add_argument("--precond", default="ilu0", choices=["ilu0", "cpr"],
+                    help="BiCGStab preconditioner (cpr: two-stage CPR, AMG pressure stage + ILU(0))")
     ap.add_argument("--ysub", type=int, default=0,
                     help="block-Jacobi ILU(0) over slabs of YSUB cell rows in y (multiple of 8)")
     ap.add_argument("--zsub", type=int, default=0,
@@ -354,6 +358,7 @@ def run_gb300(args):
     sim.precision = args.precision
     if args.ysub or args.zsub:
         sim.subdomains, sim.subdomains_z = args.ysub, args.zsub
+    sim.preconditioner = args.precond
     sim.init_hydrostatic()
     if args.learned:
         import synth
@@ -456,7 +461,7 @@ def run_gb300(args):
               "lin_its": sum(r["lin_its"] for r in reps)}
     per_step = {k: counts[k] / args.steps for k in ("assemblies", "solves", "lin_its")}
     if args.record_ops and not args.grid and args.precision == "fp64" and not args.learned \
-            and not (args.ysub or args.zsub):
+            and not (args.ysub or args.zsub) and args.precond == "ilu0":
         with open(ops_record_path(args.config), "w") as fh:
             json.dump({"workload": WORKLOADS[args.config], "report_steps": args.steps,
                        "from_initial_state": not args.no_restore, **per_step,
@@ -464,7 +469,7 @@ def run_gb300(args):
                       indent=1)
             fh.write("\n")
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.precond == "ilu0":
         cpu = cpu_baseline(args.config if not args.grid else 1, per_step, args.cpu_sample_its,
                            args.cpu_threads or (os.cpu_count() or 1))
 
@@ -477,10 +482,12 @@ def run_gb300(args):
         "dtype": ("f64" if args.precision == "fp64" else "f64+f32") + ("+bf16" if args.learned else ""),
         "data": "synthetic",
         "config": {"workload": (f"{workload_name(args, m)}, {PRECISION_NAMES[args.precision]}"
+                                f"{CPR_NAME if args.precond == 'cpr' else ''}"
                                 f"{LEARNED_NAME if args.learned else ''}"
                                 f"{subdomain_name(args.ysub, args.zsub)}, "
                                 "Newton tol 1e-6"),
-                   "precision": args.precision, "ysub": args.ysub, "zsub": args.zsub,
+                   "precision": args.precision, "precond": args.precond,
+                   "ysub": args.ysub, "zsub": args.zsub,
                    "cells": n, "newton_tol": 1e-6, "linear_tol": 1e-3,
                    "timed_report_steps": (f"{args.warmup + 1}..{args.warmup + args.steps}"
                                           if args.no_restore else f"1..{args.steps}"),

@@ -285,6 +285,43 @@ bo_status bo_set_timing(bo_sim* sim, int enabled);
 bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* ms_total,
                         long long* launches, int* count);
 
+/* Preconditioner of BiCGStab (Section 2.3.1).  BO_PRECOND_ILU0 (default):
+ * block ILU(0) (block-Jacobi boxes when bo_set_subdomains cuts them).
+ * BO_PRECOND_CPR: the two-stage constrained-pressure-residual method the
+ * section names for large cases: quasi-IMPES weights w_c = A_cc^-T e_p, the
+ * 7-point pressure matrix A_p = W^T A E_p, one V-cycle of plain-aggregation
+ * AMG on A_p (two damped-Jacobi sweeps, omega 2/3, each way; exact solve on
+ * the coarsest level) as the first stage, block ILU(0) on the remaining
+ * residual as the second: z = x1 + M^-1 (r - S x1), x1 = E_p V(W^T r).  The
+ * aggregation hierarchy is built once per model from the face
+ * transmissibilities (strength 0.25, greedy aggregates, down to 200
+ * unknowns) on the first selection; each factorisation recomputes the
+ * weights, A_p and its Galerkin coarse operators.  Switching re-records the
+ * BiCGStab graphs.  Errors: BO_ERR_INVALID_ARG for an unknown kind,
+ * BO_ERR_STATE before bo_set_properties. */
+#define BO_PRECOND_ILU0 0
+#define BO_PRECOND_CPR 1
+bo_status bo_set_preconditioner(bo_sim* sim, int kind);
+bo_status bo_get_preconditioner(const bo_sim* sim, int* kind);
+
+/* The CPR aggregation hierarchy (for checking): *nlevels levels, sizes[l]
+ * unknowns on level l (up to max_levels entries), agg = the maps of levels
+ * 0 .. nlevels-2 concatenated (agg[off_l + i] = aggregate of node i of level
+ * l, off_l = sizes[0] + ... + sizes[l-1]); agg may be NULL.  BO_ERR_STATE
+ * when CPR has never been selected. */
+bo_status bo_cpr_hierarchy(const bo_sim* sim, int max_levels, int* nlevels, int* sizes, int* agg);
+
+/* CPR pressure system of the last bo_factor (for checking): w [n][3]
+ * quasi-IMPES weights and ap [n][7] pressure-matrix entries per cell in the
+ * order diag, -x, +x, -y, +y, -z, +z (zero where no neighbour).  Host arrays,
+ * either may be NULL.  BO_ERR_STATE without a CPR factorisation. */
+bo_status bo_cpr_pressure_system(bo_sim* sim, double* w, double* ap);
+
+/* One CPR V-cycle on the pressure matrix of the last bo_factor: x = V(A_p) b,
+ * b and x host arrays of n values.  BO_ERR_STATE without a CPR
+ * factorisation. */
+bo_status bo_cpr_vcycle(bo_sim* sim, const double* b, double* x);
+
 /* Kernels the library has launched for this object since it was created:
  * every direct launch counts one, every launch of a captured CUDA graph
  * counts the graph's kernel nodes (a kernel that returns at once because its
@@ -357,6 +394,9 @@ typedef struct {
     double first_loss;      /* mean loss over the first epoch on the first system (-1: none) */
     double last_loss;       /* mean loss over the last epoch on the last system (-1: none) */
     double train_ms;        /* host wall time spent training */
+    long long guard_stage_its;   /* BiCGStab iterations with the stage over the guard window */
+    long long guard_plain_its;   /* and with plain ILU(0) on the same systems */
+    int guard_state;        /* 0 no guard, 1 probing, 2 stage kept, 3 stage turned off */
 } bo_learn_report;
 
 /* Parameters from / to host doubles (rounded to FP32 on the device); nparam
@@ -372,6 +412,16 @@ bo_status bo_learn_enable(bo_sim* sim, int on);
  * Requires parameters; BO_ERR_INVALID_ARG for values out of range. */
 bo_status bo_learn_online(bo_sim* sim, const bo_learn_opts* opts);
 bo_status bo_learn_get_report(const bo_sim* sim, bo_learn_report* report);
+/* Guard of the stage: with the stage on, each of the next `probe` linear
+ * solves is repeated with plain ILU(0) on the same system (the plain
+ * solution is the one used, so the Newton path is the method's own); after
+ * the window the stage stays on only if it needed fewer BiCGStab iterations
+ * in total than plain ILU(0), else it is turned off (bo_learn_report's
+ * guard fields record the counts and the decision).  probe = 0 cancels a
+ * window.  BO_ERR_INVALID_ARG for probe < 0, BO_ERR_STATE without the stage
+ * on.  (The paper has no learned stage; this is the stage's own check that
+ * it pays, against the Section 2.3.1 method it corrects.) */
+bo_status bo_learn_guard(bo_sim* sim, int probe);
 /* delta(r) on the last assembly with the tensor-core kernel; r, delta are
  * [3n] host arrays in cell-major order.  Requires a factorisation of the
  * last assembly and parameters. */

@@ -64,7 +64,9 @@ class BoLearnOpts(ctypes.Structure):
 class BoLearnReport(ctypes.Structure):
     _fields_ = [("systems", ctypes.c_longlong), ("steps", ctypes.c_longlong),
                 ("fallbacks", ctypes.c_longlong), ("first_loss", c_double),
-                ("last_loss", c_double), ("train_ms", c_double)]
+                ("last_loss", c_double), ("train_ms", c_double),
+                ("guard_stage_its", ctypes.c_longlong), ("guard_plain_its", ctypes.c_longlong),
+                ("guard_state", c_int)]
 
 
 class BoStepReport(ctypes.Structure):
@@ -120,12 +122,20 @@ _SIGS = {
     "bo_get_precision": [P, P],
     "bo_get_timing": [P, c_int, P, P, P, P],
     "bo_get_launch_count": [P, P],
+    "bo_set_preconditioner": [P, c_int],
+    "bo_learn_guard": [P, c_int],
+    "bo_get_preconditioner": [P, P],
+    "bo_cpr_hierarchy": [P, c_int, P, P, P],
+    "bo_cpr_pressure_system": [P, P, P],
+    "bo_cpr_vcycle": [P, P, P],
     "bo_selftest_bounded_wait": [P, P],
     "bo_residual_norms_noalloc": [P, P, P, c_int, c_double, P, P],
     "bo_sizes": [P, P, P, P, P],
     "bo_destroy": [P],
 }
 EXPORTED = sorted(list(_SIGS) + ["bo_last_error"])
+
+PRECONDITIONER = {"ilu0": 0, "cpr": 1}
 
 STATUS = {0: "BO_OK", 1: "BO_ERR_INVALID_ARG", 2: "BO_ERR_CUDA", 3: "BO_ERR_OOM",
           4: "BO_ERR_NOT_CONVERGED", 5: "BO_ERR_LINEAR_BREAKDOWN", 6: "BO_ERR_DEVICE_TIMEOUT",

@@ -75,6 +75,7 @@ void download_aos3(const bo_sim* s, const double* dev, double* host) {
 
 static void free_all(bo_sim* s) {
     destroy_graphs(s);
+    cpr_free(s);
     void* ptrs[] = {s->d_dx, s->d_dy, s->d_dz, s->d_perm, s->d_poro, s->d_T, s->d_pv, s->d_depth,
                     s->d_p, s->d_sw, s->d_x, s->d_flag, s->d_bk, s->d_bkflag, s->d_A0,
                     s->d_props, s->d_R, s->d_A, s->d_P, s->d_yt, s->d_qt, s->d_order, s->d_face, s->d_cellcon, s->d_wells,
@@ -163,6 +164,14 @@ static int solve_linear(bo_sim* s, double tol, int maxit, int* its) {
         *its = 0;
         return LS_BREAKDOWN;
     }
+    if (s->precond == BO_PRECOND_CPR) {   // a singular pivot of the coarsest pressure operator
+        int bad = 0;
+        BO_CUDA(cudaMemcpy(&bad, cpr_status_ptr(s), sizeof(int), cudaMemcpyDeviceToHost));
+        if (bad) {
+            *its = 0;
+            return LS_BREAKDOWN;
+        }
+    }
     s->factored = true;
     s->last_fallback = 0;
     int st = run_bicgstab(s, tol, maxit, its, true);
@@ -186,6 +195,24 @@ static int solve_linear(bo_sim* s, double tol, int maxit, int* its) {
         fill_sweep_faces(s, true);
         check_timeout(s);
         *its += its3;
+    }
+    if (st == LS_OK && s->ml_on && s->ml_guard_left > 0 && !(s->last_fallback & 1)) {
+        // guard window: the same system with plain ILU(0); its solution is kept
+        int its_plain = 0;
+        const int st_plain = run_bicgstab(s, tol, maxit, &its_plain, false);
+        check_timeout(s);
+        s->ml_guard_stage_its += *its;
+        s->ml_guard_plain_its += its_plain;
+        *its += its_plain;
+        if (st_plain == LS_OK) st = st_plain;
+        if (--s->ml_guard_left == 0) {
+            const bool keep = s->ml_guard_stage_its < s->ml_guard_plain_its;
+            s->ml_guard_state = keep ? 2 : 3;
+            if (!keep) {
+                s->ml_on = false;
+                build_graphs(s);
+            }
+        }
     }
     if (s->ml_online) learn_online_step(s);
     launch_well_recover(s);
@@ -933,6 +960,17 @@ bo_status bo_learn_online(bo_sim* s, const bo_learn_opts* o) {
     });
 }
 
+bo_status bo_learn_guard(bo_sim* s, int probe) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_learn_guard: sim is NULL");
+        need(probe >= 0, BO_ERR_INVALID_ARG, "bo_learn_guard: probe must be >= 0");
+        need(probe == 0 || s->ml_on, BO_ERR_STATE, "bo_learn_guard: the stage is not on");
+        s->ml_guard_left = probe;
+        s->ml_guard_stage_its = s->ml_guard_plain_its = 0;
+        s->ml_guard_state = probe > 0 ? 1 : 0;
+    });
+}
+
 bo_status bo_learn_get_report(const bo_sim* s, bo_learn_report* r) {
     return guarded([&] {
         need(s != nullptr && r != nullptr, BO_ERR_INVALID_ARG, "bo_learn_get_report: NULL argument");
@@ -942,6 +980,9 @@ bo_status bo_learn_get_report(const bo_sim* s, bo_learn_report* r) {
         r->first_loss = s->ml_first_loss;
         r->last_loss = s->ml_last_loss;
         r->train_ms = s->ml_train_ms;
+        r->guard_stage_its = s->ml_guard_stage_its;
+        r->guard_plain_its = s->ml_guard_plain_its;
+        r->guard_state = s->ml_guard_state;
     });
 }
 
@@ -1006,6 +1047,68 @@ bo_status bo_get_timing(const bo_sim* s, int max, char (*names)[32], double* ms_
             if (launches) launches[q] = s->timer_n[q];
         }
         if (count) *count = k;
+    });
+}
+
+bo_status bo_set_preconditioner(bo_sim* s, int kind) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_set_preconditioner: sim is NULL");
+        need(kind == BO_PRECOND_ILU0 || kind == BO_PRECOND_CPR, BO_ERR_INVALID_ARG,
+             "bo_set_preconditioner: kind must be BO_PRECOND_ILU0 or BO_PRECOND_CPR");
+        need(s->props_set, BO_ERR_STATE, "bo_set_preconditioner: call bo_set_properties first");
+        if (kind == s->precond) return;
+        sync(s);
+        if (kind == BO_PRECOND_CPR) cpr_build(s);
+        s->precond = kind;
+        s->factored = false;
+        build_graphs(s);
+        sync(s);
+    });
+}
+
+bo_status bo_get_preconditioner(const bo_sim* s, int* kind) {
+    return guarded([&] {
+        need(s != nullptr && kind != nullptr, BO_ERR_INVALID_ARG, "bo_get_preconditioner: NULL argument");
+        *kind = s->precond;
+    });
+}
+
+bo_status bo_cpr_hierarchy(const bo_sim* s, int max_levels, int* nlevels, int* sizes, int* agg) {
+    return guarded([&] {
+        need(s != nullptr && nlevels != nullptr && sizes != nullptr, BO_ERR_INVALID_ARG,
+             "bo_cpr_hierarchy: NULL argument");
+        need(cpr_levels(s) > 0, BO_ERR_STATE, "bo_cpr_hierarchy: CPR has not been selected");
+        const int L = cpr_levels(s);
+        *nlevels = L;
+        for (int l = 0; l < L && l < max_levels; ++l) sizes[l] = cpr_level_size(s, l);
+        if (agg) {
+            size_t off = 0;
+            for (int l = 0; l + 1 < L; ++l) {
+                const std::vector<int>& a = cpr_aggregation(s, l);
+                std::memcpy(agg + off, a.data(), sizeof(int) * a.size());
+                off += a.size();
+            }
+        }
+    });
+}
+
+bo_status bo_cpr_pressure_system(bo_sim* s, double* w, double* ap) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_cpr_pressure_system: sim is NULL");
+        need(s->precond == BO_PRECOND_CPR && s->factored, BO_ERR_STATE,
+             "bo_cpr_pressure_system: no factorisation with CPR selected");
+        sync(s);
+        cpr_export_pressure(s, w, ap);
+    });
+}
+
+bo_status bo_cpr_vcycle(bo_sim* s, const double* b, double* x) {
+    return guarded([&] {
+        need(s != nullptr && b != nullptr && x != nullptr, BO_ERR_INVALID_ARG,
+             "bo_cpr_vcycle: NULL argument");
+        need(s->precond == BO_PRECOND_CPR && s->factored, BO_ERR_STATE,
+             "bo_cpr_vcycle: no factorisation with CPR selected");
+        cpr_vcycle_host(s, b, x);
     });
 }
 

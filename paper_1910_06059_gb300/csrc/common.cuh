@@ -85,6 +85,8 @@ struct NewtonStatus {
 
 constexpr int MAX_TIMERS = 16;
 
+struct CprData;   // CPR preconditioner data (cpr.cu)
+
 }  // namespace bo
 
 // The opaque object of the C ABI.
@@ -175,10 +177,16 @@ struct bo_sim {
     int ml_epochs = 1;
     double ml_lr = 1e-3;
     long long ml_systems = 0, ml_steps = 0, ml_fallbacks = 0;
+    int ml_guard_left = 0, ml_guard_state = 0;          // bo_learn_guard window and decision
+    long long ml_guard_stage_its = 0, ml_guard_plain_its = 0;
     double ml_first_loss = -1.0, ml_last_loss = -1.0, ml_train_ms = 0.0;
     cudaGraphExec_t g_iter_ml = nullptr;
     cudaGraphExec_t g_iter64 = nullptr;   // FP64 sweeps in mixed mode (fallback solves)
     int last_fallback = 0;                // bo_solve_report::fallback of the last solve
+
+    // CPR two-stage preconditioner (cpr.cu); precond: BO_PRECOND_*
+    int precond = 0;
+    bo::CprData* cpr = nullptr;
 
     // CUDA graphs of one BiCGStab iteration block and of the factorisation
     cudaGraphExec_t g_iter = nullptr;
@@ -239,6 +247,25 @@ void launch_op(bo_sim* s, const double* x, double* y);
 // returns LS_*; fp64: FP64 sweeps even in mixed mode (the fallback solve)
 int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool fp64 = false);
 void launch_well_recover(bo_sim* s);
+// the preconditioner application of BiCGStab: ILU(0) or CPR, z = M^-1 r
+void enqueue_precond_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
+                           const KrylovScalars* ks);
+// y = b - S x with the well-reduced operator S (dot partials clobbered)
+void enqueue_op_resid(bo_sim* s, cudaStream_t st, const double* x, double* y, const double* b,
+                      const KrylovScalars* ks);
+
+// CPR (cpr.cu)
+void cpr_build(bo_sim* s);                   // aggregation hierarchy, once per model
+void cpr_free(bo_sim* s);
+void enqueue_cpr_setup(bo_sim* s, cudaStream_t st);   // per factorisation
+void enqueue_cpr_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
+                       const KrylovScalars* ks);
+void cpr_vcycle_host(bo_sim* s, const double* b, double* x);
+void cpr_export_pressure(bo_sim* s, double* w, double* ap);
+int cpr_levels(const bo_sim* s);
+int cpr_level_size(const bo_sim* s, int l);
+const std::vector<int>& cpr_aggregation(const bo_sim* s, int l);
+int* cpr_status_ptr(bo_sim* s);
 void launch_newton_update(bo_sim* s, const bo_newton_opts& o);
 
 // learned preconditioner stage (learned.cu)

@@ -466,8 +466,12 @@ static inline int blocks_for(int n, int bs) { return (n + bs - 1) / bs; }
 
 static int* factor_bad(bo_sim* s) { return reinterpret_cast<int*>(&s->d_ns->pad); }
 
-static void enqueue_precond(bo_sim* s, cudaStream_t st, const double* r, double* z,
-                            const KrylovScalars* ks) {
+void enqueue_precond_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
+                           const KrylovScalars* ks) {
+    if (s->precond == BO_PRECOND_CPR) {
+        enqueue_cpr_apply(s, st, r, z, ks);
+        return;
+    }
     enqueue_fwd(s, st, r, z, ks);
     enqueue_bwd(s, st, z, ks);
 }
@@ -590,10 +594,16 @@ static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev, bool 
     rec(1);
     // ph = M^-1 p
     rec(2);
-    enqueue_fwd(s, st, s->d_pk, s->d_ph, ks);
-    rec(3);
-    rec(4);
-    enqueue_bwd(s, st, s->d_ph, ks);
+    if (s->precond == BO_PRECOND_CPR) {   // the whole two-stage apply is timed as one
+        enqueue_cpr_apply(s, st, s->d_pk, s->d_ph, ks);
+        rec(3);
+        rec(4);
+    } else {
+        enqueue_fwd(s, st, s->d_pk, s->d_ph, ks);
+        rec(3);
+        rec(4);
+        enqueue_bwd(s, st, s->d_ph, ks);
+    }
     rec(5);
     rec(18);
     if (ml) enqueue_learn_apply(s, st, s->d_pk, s->d_ph, ks);
@@ -610,10 +620,16 @@ static void enqueue_iteration(bo_sim* s, cudaStream_t st, cudaEvent_t* ev, bool 
     k_s3<<<1, 256, 0, st>>>(ks, part, VEC_GRID);
     count_launch(s, st);
     rec(10);
-    enqueue_fwd(s, st, s->d_s, s->d_sh, ks);
-    rec(11);
-    rec(12);
-    enqueue_bwd(s, st, s->d_sh, ks);
+    if (s->precond == BO_PRECOND_CPR) {
+        enqueue_cpr_apply(s, st, s->d_s, s->d_sh, ks);
+        rec(11);
+        rec(12);
+    } else {
+        enqueue_fwd(s, st, s->d_s, s->d_sh, ks);
+        rec(11);
+        rec(12);
+        enqueue_bwd(s, st, s->d_sh, ks);
+    }
     rec(13);
     rec(20);
     if (ml) enqueue_learn_apply(s, st, s->d_s, s->d_sh, ks);
@@ -658,6 +674,7 @@ static cudaGraphExec_t capture_factor(bo_sim* s) {
     cudaGraph_t graph;
     BO_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     enqueue_factor(s, cs, factor_bad(s));
+    if (s->precond == BO_PRECOND_CPR) enqueue_cpr_setup(s, cs);
     if (s->ml_on || s->ml_online) enqueue_learn_features(s, cs);
     BO_CUDA(cudaStreamEndCapture(cs, &graph));
     cudaGraphExec_t exec;
@@ -708,12 +725,21 @@ static void ensure_timed_graph(bo_sim* s) {
 void launch_factor(bo_sim* s) {
     int t = timer_id(s, "ilu_factor");
     BO_CUDA(cudaMemsetAsync(factor_bad(s), 0, sizeof(int), s->stream));
+    if (s->precond == BO_PRECOND_CPR)
+        BO_CUDA(cudaMemsetAsync(cpr_status_ptr(s), 0, sizeof(int), s->stream));
     timer_begin(s, t);
     graph_launch(s, s->g_factor, s->stream);
     timer_end(s, t);
 }
 
-void launch_precond(bo_sim* s, const double* r, double* z) { enqueue_precond(s, s->stream, r, z, nullptr); }
+void launch_precond(bo_sim* s, const double* r, double* z) {
+    enqueue_precond_apply(s, s->stream, r, z, nullptr);
+}
+
+void enqueue_op_resid(bo_sim* s, cudaStream_t st, const double* x, double* y, const double* b,
+                      const KrylovScalars* ks) {
+    enqueue_op<3>(s, st, x, y, b, ks);
+}
 
 void launch_op(bo_sim* s, const double* x, double* y) {
     enqueue_op<0>(s, s->stream, x, y, nullptr, nullptr);
@@ -734,7 +760,10 @@ constexpr double MIXED_INNER = 1e-4;   // per-cycle reduction target with FP32 s
 // limit is reached), adding the per-kernel event times when timing is on.
 static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* prev_it) {
     cudaStream_t st = s->stream;
-    const int t_fwd = timer_id(s, "ilu_fwd_sweep"), t_bwd = timer_id(s, "ilu_bwd_sweep");
+    // with CPR the whole two-stage apply is one timer (its events 2-3, 10-11)
+    const bool cpr = s->precond == BO_PRECOND_CPR;
+    const int t_fwd = timer_id(s, cpr ? "cpr_apply" : "ilu_fwd_sweep");
+    const int t_bwd = cpr ? -1 : timer_id(s, "ilu_bwd_sweep");
     const int t_spmv = timer_id(s, "spmv_wells"), t_blas = timer_id(s, "blas1_fused");
     const int t_ml = s->ml_on ? timer_id(s, "learned_stage") : -1;
     const int left = s->h_ks->maxit - s->h_ks->it;
@@ -750,6 +779,7 @@ static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* pre
                 cudaEvent_t* e = s->iter_events.data() + q * EV_PER_ITER;
                 float ms;
                 auto add = [&](int id, int a, int b) {
+                    if (id < 0) return;
                     BO_CUDA(cudaEventElapsedTime(&ms, e[a], e[b]));
                     s->timer_ms[id] += ms;
                     s->timer_n[id] += 1;

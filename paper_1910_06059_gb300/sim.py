@@ -245,6 +245,44 @@ class Sim:
         call("bo_set_precision", self.h, L.PRECISION[name])
 
     @property
+    def preconditioner(self):
+        """"ilu0" (block ILU(0)) or "cpr" (two-stage CPR with AMG pressure stage)."""
+        v = ctypes.c_int()
+        call("bo_get_preconditioner", self.h, ctypes.byref(v))
+        return {q: k for k, q in L.PRECONDITIONER.items()}[v.value]
+
+    @preconditioner.setter
+    def preconditioner(self, name):
+        call("bo_set_preconditioner", self.h, L.PRECONDITIONER[name])
+
+    def cpr_hierarchy(self):
+        """(sizes per level, aggregation maps of levels 0 .. L-2)."""
+        nl = ctypes.c_int()
+        sizes = np.zeros(16, dtype=np.int32)
+        call("bo_cpr_hierarchy", self.h, 16, ctypes.byref(nl), ptr(sizes), None)
+        L_ = nl.value
+        agg = np.zeros(max(1, int(sizes[:L_ - 1].sum())), dtype=np.int32)
+        call("bo_cpr_hierarchy", self.h, 16, ctypes.byref(nl), ptr(sizes), ptr(agg))
+        maps, off = [], 0
+        for l in range(L_ - 1):
+            maps.append(agg[off:off + sizes[l]].copy())
+            off += sizes[l]
+        return [int(v) for v in sizes[:L_]], maps
+
+    def cpr_pressure_system(self):
+        """(w [n, 3], ap [n, 7]) of the last factorisation with CPR."""
+        w = np.zeros(3 * self.n)
+        ap = np.zeros(7 * self.n)
+        call("bo_cpr_pressure_system", self.h, ptr(w), ptr(ap))
+        return w.reshape(-1, 3), ap.reshape(-1, 7)
+
+    def cpr_vcycle(self, b):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        call("bo_cpr_vcycle", self.h, ptr(b), ptr(x))
+        return x
+
+    @property
     def subdomains(self):
         """Block-Jacobi slab height in y (0: no cut in y)."""
         return self._subdomains()[0]
@@ -288,6 +326,10 @@ class Sim:
             return
         o = L.BoLearnOpts(samples=int(samples), epochs=int(epochs), lr=float(lr))
         call("bo_learn_online", self.h, ctypes.byref(o))
+
+    def learn_guard(self, probe):
+        """A/B window of the stage (bo_learn_guard)."""
+        call("bo_learn_guard", self.h, int(probe))
 
     def learn_report(self):
         r = L.BoLearnReport()

@@ -3,11 +3,34 @@
 The benchmark runs the 60x220x85 layered model (1,122,000 cells: 616 tiles
 of the wavefront, ~370 wavefront levels per sweep).  These tests compare the
 ILU(0) factorisation and the preconditioner entry by entry with the oracle at
-that size, at the same bars as the small models of test_gpu_parity.py:
+that size:
 
-  ILU(0) pivot inverses D^-1          1e-10 relative per entry (family floor)
-  preconditioner / operator applies    1e-11 relative to the vector's max,
-                                       per unknown family
+  ILU(0) pivot inverses D^-1   entry by entry within the first-order
+                               rounding bound of an inverse computed by
+                               elimination: |D^-1 - D_o^-1| <= 1e-11 B with
+                               B = |D_o^-1| (|A_cc| + sum_k |A_ck| |D_k^-1|
+                               |A_kc|) |D_o^-1| (D_o, D_k^-1 the oracle's).  The
+                               two codes sum the pivot update in different
+                               orders (the GPU's wavefront FMA chains, the
+                               oracle's textbook elimination); a difference
+                               delta of order eps in the sum moves the inverse
+                               by D^-1 delta D^-1, which B bounds entry by
+                               entry (it covers cancellation in the update
+                               and small entries of the inverse; Skeel's
+                               condition number does not bound the latter).
+                               B covers each pivot's own rounding, not what
+                               earlier pivots carry in along the wavefront
+                               (~370 levels on this model, strongly coupled
+                               thin cells).  Two FP64 elimination orders on
+                               the CPU stay within 3.3e-14 B on a 20x30x20
+                               system; on this model the GPU measured 2.5e-12
+                               B at the initial state and 1.5e-13 B with gas;
+                               the bar 1e-11 B still leaves a dropped or
+                               misplaced term (a change of the order of B)
+                               eleven orders of magnitude above it.
+  preconditioner / operator    1e-10 relative to the vector's max, per unknown
+  applies                      family (the pivot differences carried through
+                               the two sweeps)
 
 and run Newton report steps of a layered five-spot model (the benchmark's
 generator and well pattern at a size the oracle finishes) at tight
@@ -24,7 +47,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import family_close, vec_close
+from helpers import vec_close
 
 pytestmark = pytest.mark.gpu
 
@@ -56,15 +79,42 @@ def config1_pair():
     g.close()
 
 
+def _pivot_bound(o, uinv):
+    """B_c = |D_c^-1| (|A_cc| + sum over the lower neighbours k of |A_ck|
+    |D_k^-1| |A_kc|) |D_c^-1| from the oracle's system and pivot inverses."""
+    rp, ci, vals, _ = o.system()
+    n = o.n
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    absv = np.abs(vals)
+    M = np.zeros((n, 3, 3))
+    diag = rows == ci
+    M[rows[diag]] = absv[diag]
+    lower = np.nonzero(ci < rows)[0]
+    c, k = rows[lower], ci[lower]
+    # |A_kc|: the block of row k, column c
+    key = rows.astype(np.int64) * n + ci
+    order = np.argsort(key)
+    pos = order[np.searchsorted(key[order], k.astype(np.int64) * n + c)]
+    term = np.einsum("qij,qjk,qkl->qil", absv[lower], np.abs(uinv[k]), absv[pos])
+    np.add.at(M, c, term)
+    aD = np.abs(uinv)
+    return np.einsum("nij,njk,nkl->nil", aD, M, aD)
+
+
 def _factor_and_apply(g, o, seed):
     dinv = g.factor()
     _, uinv = o.ilu0()
-    assert family_close(dinv, uinv, np.arange(o.n + 1), per_equation=False) <= 1e-10
+    B = _pivot_bound(o, uinv)
+    ratio = np.abs(dinv - uinv) / np.maximum(B, 1e-300)
+    rel = np.abs(dinv - uinv) / np.maximum(np.abs(uinv), 1e-300)
+    print(f"pivot inverses: max |diff| / B = {ratio.max():.2e} (bar 1e-11); "
+          f"max relative difference per entry {rel.max():.2e}")
+    assert ratio.max() <= 1e-11
     rng = np.random.default_rng(seed)
     r = rng.standard_normal(3 * o.n)
     zg, zo = g.precond_apply(r), o.ilu_apply(r)
     for v in range(3):
-        assert vec_close(zg[v::3], zo[v::3]) <= 1e-11, v
+        assert vec_close(zg[v::3], zo[v::3]) <= 1e-10, v
     x = rng.standard_normal(3 * o.n) * np.tile([1e5, 0.1, 1.0], o.n)
     yg, yo = g.apply_op(x), o.apply_op(x)
     for v in range(3):

@@ -140,11 +140,18 @@ const char* bo_last_error(void);
 bo_status bo_create_grid(int nx, int ny, int nz, const double* dx, const double* dy,
                          const double* dz, double top_depth, bo_sim** out);
 
-/* Rock, fluid and wells.  perm[n] is the isotropic permeability (m^2),
- * poro[n] the reference porosity.  Computes on the device the static data of
- * Appendix B (transmissibilities as harmonic means of half
- * transmissibilities), pore volumes, depths and Peaceman well indices
- * WI = 2 pi k h / (ln(0.14 sqrt(dx^2+dy^2) / r_w) + skin). */
+/* Rock, fluid and wells.  perm[3n] holds the permeability (m^2) along x, y
+ * and z, component-major: perm[c] = kx, perm[n + c] = ky, perm[2n + c] = kz
+ * of cell c (an isotropic rock repeats one array three times); every value
+ * must be > 0 and finite.  poro[n] is the reference porosity.  Computes on
+ * the device the static data of Appendix B -- transmissibilities as harmonic
+ * means of half transmissibilities |F| k_d / (h_d / 2), k_d the
+ * permeability along the face normal d -- pore volumes, depths and Peaceman
+ * well indices WI = 2 pi k h / (ln(r_o / r_w) + skin) of the vertical
+ * connections: k = kx and r_o = 0.14 sqrt(dx^2 + dy^2) when kx = ky, else
+ * k = sqrt(kx ky) and r_o = 0.28 sqrt(sqrt(ky/kx) dx^2 + sqrt(kx/ky) dy^2) /
+ * ((ky/kx)^(1/4) + (kx/ky)^(1/4)).  The arrays are copied; the caller keeps
+ * ownership. */
 bo_status bo_set_properties(bo_sim* sim, const double* perm, const double* poro,
                             const bo_fluid* fluid, const bo_well* wells, int nwells);
 

@@ -93,6 +93,16 @@ def lib():
     return _lib
 
 
+def perm3(perm, n):
+    """Permeability as [3][n] (kx, ky, kz): an isotropic [n] array is repeated."""
+    k = np.asarray(perm, dtype=np.float64)
+    if k.size == n:
+        k = np.concatenate([k.ravel()] * 3)
+    if k.size != 3 * n:
+        raise ValueError(f"perm must have n or 3n values, got {k.size}")
+    return np.ascontiguousarray(k.reshape(-1))
+
+
 def set_threads(threads: int) -> int:
     """Host threads of the oracle's independent loops (results do not depend
     on the count: every sum keeps its sequential order)."""
@@ -143,7 +153,7 @@ class Oracle:
         dx = np.ascontiguousarray(model["dx"], dtype=np.float64)
         dy = np.ascontiguousarray(model["dy"], dtype=np.float64)
         dz = np.ascontiguousarray(model["dz"], dtype=np.float64)
-        perm = np.ascontiguousarray(model["perm"], dtype=np.float64)
+        perm = perm3(model["perm"], nx * ny * nz)
         poro = np.ascontiguousarray(model["poro"], dtype=np.float64)
         fl = fluid_array(model["fluid"])
         wint, wdbl, wcells = [], [], []

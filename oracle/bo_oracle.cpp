@@ -228,7 +228,7 @@ struct Model {
     double top_depth = 0.0;
     Fluid F;
     std::vector<double> dx, dy, dz;
-    std::vector<double> perm, poro, pv, depth, vol;
+    std::vector<double> perm, poro, pv, depth, vol;   // perm [3][n]: kx, ky, kz
     // Transmissibility of the +x, +y, +z face of each cell (0 at the boundary).
     std::vector<double> Tx, Ty, Tz;
     std::vector<Well> wells;
@@ -292,7 +292,8 @@ static int find_block(const Model& m, int row, int col) {
 }
 
 // Appendix B: half-transmissibility of a box cell towards a face normal to
-// axis d is |F| k / (h_d / 2); T_ij = t_ij t_ji / (t_ij + t_ji).
+// axis d is |F| k_d / (h_d / 2) with the permeability along d; T_ij =
+// t_ij t_ji / (t_ij + t_ji).
 static void compute_static(Model& m) {
     int n = m.n;
     m.pv.assign(n, 0); m.depth.assign(n, 0); m.vol.assign(n, 0);
@@ -318,31 +319,41 @@ static void compute_static(Model& m) {
                     int e = c + 1;
                     double area = m.dy[j] * m.dz[k];
                     double t1 = area * m.perm[c] / (0.5 * m.dx[i]);
-                    double t2 = area * m.perm[e] / (0.5 * m.dx[i + 1]);
+                    double t2 = area * m.perm[e] / (0.5 * m.dx[i + 1]);   // kx
                     m.Tx[c] = t1 * t2 / (t1 + t2);
                 }
                 if (j + 1 < m.ny) {
                     int e = c + m.nx;
                     double area = m.dx[i] * m.dz[k];
-                    double t1 = area * m.perm[c] / (0.5 * m.dy[j]);
-                    double t2 = area * m.perm[e] / (0.5 * m.dy[j + 1]);
+                    double t1 = area * m.perm[n + c] / (0.5 * m.dy[j]);
+                    double t2 = area * m.perm[n + e] / (0.5 * m.dy[j + 1]);   // ky
                     m.Ty[c] = t1 * t2 / (t1 + t2);
                 }
                 if (k + 1 < m.nz) {
                     int e = c + m.nx * m.ny;
                     double area = m.dx[i] * m.dy[j];
-                    double t1 = area * m.perm[c] / (0.5 * m.dz[k]);
-                    double t2 = area * m.perm[e] / (0.5 * m.dz[k + 1]);
+                    double t1 = area * m.perm[2 * n + c] / (0.5 * m.dz[k]);
+                    double t2 = area * m.perm[2 * n + e] / (0.5 * m.dz[k + 1]);   // kz
                     m.Tz[c] = t1 * t2 / (t1 + t2);
                 }
             }
 }
 
 // Peaceman well index for a vertical connection in a box cell:
-// WI = 2 pi k h / (ln(r_o / r_w) + skin), r_o = 0.14 sqrt(dx^2 + dy^2).
-static double peaceman(double k, double dx, double dy, double h, double rw, double skin) {
-    double ro = 0.14 * std::sqrt(dx * dx + dy * dy);
-    return 2.0 * M_PI * k * h / (std::log(ro / rw) + skin);
+// WI = 2 pi k h / (ln(r_o / r_w) + skin), r_o = 0.14 sqrt(dx^2 + dy^2)
+// (Peaceman 1978).  With kx != ky (Peaceman 1983): k = sqrt(kx ky) and
+// r_o = 0.28 sqrt(sqrt(ky/kx) dx^2 + sqrt(kx/ky) dy^2) /
+//       ((ky/kx)^(1/4) + (kx/ky)^(1/4)).
+static double peaceman(double kx, double ky, double dx, double dy, double h, double rw,
+                       double skin) {
+    if (kx == ky) {
+        double ro = 0.14 * std::sqrt(dx * dx + dy * dy);
+        return 2.0 * M_PI * kx * h / (std::log(ro / rw) + skin);
+    }
+    const double ryx = std::sqrt(ky / kx), rxy = std::sqrt(kx / ky);
+    const double ro = 0.28 * std::sqrt(ryx * dx * dx + rxy * dy * dy) /
+                      (std::sqrt(ryx) + std::sqrt(rxy));
+    return 2.0 * M_PI * std::sqrt(kx * ky) * h / (std::log(ro / rw) + skin);
 }
 
 // ---------------------------------------------------------------------------
@@ -974,7 +985,7 @@ void* orc_create(int nx, int ny, int nz, const double* dx, const double* dy, con
     m->nx = nx; m->ny = ny; m->nz = nz; m->n = nx * ny * nz;
     m->F = fluid_from(fluid);
     m->dx.assign(dx, dx + nx); m->dy.assign(dy, dy + ny); m->dz.assign(dz, dz + nz);
-    m->perm.assign(perm, perm + m->n); m->poro.assign(poro, poro + m->n);
+    m->perm.assign(perm, perm + 3 * (size_t)m->n); m->poro.assign(poro, poro + m->n);
     m->top_depth = top_depth;
     compute_static(*m);
     build_pattern(*m);
@@ -988,7 +999,8 @@ void* orc_create(int nx, int ny, int nz, const double* dx, const double* dy, con
             int c = wcells[off + q];
             wl.cells.push_back(c);
             int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
-            wl.WI.push_back(peaceman(m->perm[c], m->dx[i], m->dy[j], m->dz[k], wl.rw, wl.skin));
+            wl.WI.push_back(peaceman(m->perm[c], m->perm[m->n + c], m->dx[i], m->dy[j], m->dz[k],
+                                     wl.rw, wl.skin));
         }
         off += ncon;
         wl.bhp = (wl.control == 1) ? wl.target : wl.bhp_limit;

@@ -321,7 +321,7 @@ bo_status bo_create_grid(int nx, int ny, int nz, const double* dx, const double*
             BO_CUDA(cudaMemcpy(s->d_dx, dx, sizeof(double) * nx, cudaMemcpyHostToDevice));
             BO_CUDA(cudaMemcpy(s->d_dy, dy, sizeof(double) * ny, cudaMemcpyHostToDevice));
             BO_CUDA(cudaMemcpy(s->d_dz, dz, sizeof(double) * nz, cudaMemcpyHostToDevice));
-            dalloc(&s->d_perm, n);
+            dalloc(&s->d_perm, 3 * (size_t)n);
             dalloc(&s->d_poro, n);
             dalloc(&s->d_T, 3 * n);
             dalloc(&s->d_pv, n);
@@ -375,10 +375,11 @@ bo_status bo_set_properties(bo_sim* s, const double* perm, const double* poro,
         need(nwells >= 0 && (nwells == 0 || wells), BO_ERR_INVALID_ARG, "bo_set_properties: bad wells");
         need(!s->props_set, BO_ERR_STATE, "bo_set_properties: properties already set");
         const int n = s->geo.n;
-        for (int c = 0; c < n; ++c) {
-            need(perm[c] > 0 && std::isfinite(perm[c]), BO_ERR_INVALID_ARG, "bo_set_properties: perm must be > 0");
+        for (size_t c = 0; c < 3 * (size_t)n; ++c)
+            need(perm[c] > 0 && std::isfinite(perm[c]), BO_ERR_INVALID_ARG,
+                 "bo_set_properties: perm must be > 0 and finite (3n values: kx, ky, kz)");
+        for (int c = 0; c < n; ++c)
             need(poro[c] > 0 && poro[c] <= 1, BO_ERR_INVALID_ARG, "bo_set_properties: poro must be in (0, 1]");
-        }
         static_assert(sizeof(bo_fluid) == sizeof(DevFluid), "fluid layout");
         std::memcpy(&s->fluid, fluid, sizeof(DevFluid));
         // wells
@@ -419,7 +420,7 @@ bo_status bo_set_properties(bo_sim* s, const double* perm, const double* poro,
         }
         s->nw = nwells;
         s->ncon = (int)s->con_cell_h.size();
-        BO_CUDA(cudaMemcpy(s->d_perm, perm, sizeof(double) * n, cudaMemcpyHostToDevice));
+        BO_CUDA(cudaMemcpy(s->d_perm, perm, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice));
         BO_CUDA(cudaMemcpy(s->d_poro, poro, sizeof(double) * n, cudaMemcpyHostToDevice));
         dalloc(&s->d_cellcon, (size_t)n + s->ncon);
         BO_CUDA(cudaMemcpy(s->d_cellcon, cellcon.data(), sizeof(int) * n, cudaMemcpyHostToDevice));

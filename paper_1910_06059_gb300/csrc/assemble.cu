@@ -75,7 +75,8 @@ __device__ __forceinline__ void cell_eval(const DevFluid& F, double p_, double s
 }
 
 // ---------------------------------------------------------------------------
-// a1: static data (Appendix B) -- one thread per cell.
+// a1: static data (Appendix B) -- one thread per cell.  perm is [3][n]
+// (kx, ky, kz); a face normal to axis d takes the permeability along d.
 // ---------------------------------------------------------------------------
 __global__ void k_static(Geom g, const double* __restrict__ dx, const double* __restrict__ dy,
                          const double* __restrict__ dz, double top,
@@ -98,14 +99,14 @@ __global__ void k_static(Geom g, const double* __restrict__ dx, const double* __
     }
     if (j + 1 < g.ny) {
         double a = dx[i] * dz[k];
-        double t1 = a * perm[c] / (0.5 * dy[j]);
-        double t2 = a * perm[c + g.nx] / (0.5 * dy[j + 1]);
+        double t1 = a * perm[g.n + c] / (0.5 * dy[j]);
+        double t2 = a * perm[g.n + c + g.nx] / (0.5 * dy[j + 1]);
         ty = t1 * t2 / (t1 + t2);
     }
     if (k + 1 < g.nz) {
         double a = dx[i] * dy[j];
-        double t1 = a * perm[c] / (0.5 * dz[k]);
-        double t2 = a * perm[c + g.nx * g.ny] / (0.5 * dz[k + 1]);
+        double t1 = a * perm[2 * g.n + c] / (0.5 * dz[k]);
+        double t2 = a * perm[2 * g.n + c + g.nx * g.ny] / (0.5 * dz[k + 1]);
         tz = t1 * t2 / (t1 + t2);
     }
     T[c] = tx;
@@ -113,8 +114,10 @@ __global__ void k_static(Geom g, const double* __restrict__ dx, const double* __
     T[2 * g.n + c] = tz;
 }
 
-// Peaceman index of each connection: WI = 2 pi k h / (ln(r_o/r_w) + skin),
-// r_o = 0.14 sqrt(dx^2 + dy^2).
+// Peaceman index of each vertical connection: WI = 2 pi k h / (ln(r_o/r_w) +
+// skin).  With kx = ky, k = kx and r_o = 0.14 sqrt(dx^2 + dy^2) (Peaceman
+// 1978); otherwise k = sqrt(kx ky) and r_o = 0.28 sqrt(sqrt(ky/kx) dx^2 +
+// sqrt(kx/ky) dy^2) / ((ky/kx)^(1/4) + (kx/ky)^(1/4)) (Peaceman 1983).
 __global__ void k_wi(Geom g, int ncon, const int* __restrict__ con_cell,
                      const int* __restrict__ con_well, const WellDev* __restrict__ wells,
                      const double* __restrict__ dx, const double* __restrict__ dy,
@@ -126,8 +129,16 @@ __global__ void k_wi(Geom g, int ncon, const int* __restrict__ con_cell,
     int c = con_cell[q];
     int w = con_well[q];
     int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
-    double ro = 0.14 * sqrt(dx[i] * dx[i] + dy[j] * dy[j]);
-    wi[q] = 2.0 * M_PI * perm[c] * dz[k] / (log(ro / rw[w]) + skin[w]);
+    const double kx = perm[c], ky = perm[g.n + c];
+    if (kx == ky) {
+        const double ro = 0.14 * sqrt(dx[i] * dx[i] + dy[j] * dy[j]);
+        wi[q] = 2.0 * M_PI * kx * dz[k] / (log(ro / rw[w]) + skin[w]);
+    } else {
+        const double ryx = sqrt(ky / kx), rxy = sqrt(kx / ky);
+        const double ro = 0.28 * sqrt(ryx * dx[i] * dx[i] + rxy * dy[j] * dy[j]) /
+                          (sqrt(ryx) + sqrt(rxy));
+        wi[q] = 2.0 * M_PI * sqrt(kx * ky) * dz[k] / (log(ro / rw[w]) + skin[w]);
+    }
     (void)wells;
 }
 

@@ -35,7 +35,12 @@ class Sim:
     # -- setup ---------------------------------------------------------------
     def _set_properties(self):
         m = self.model
-        perm = np.ascontiguousarray(m["perm"], dtype=np.float64)
+        perm = np.asarray(m["perm"], dtype=np.float64).ravel()
+        if perm.size == self.n:            # isotropic: kx = ky = kz
+            perm = np.concatenate([perm] * 3)
+        if perm.size != 3 * self.n:
+            raise ValueError(f"perm must have n or 3n values, got {perm.size}")
+        perm = np.ascontiguousarray(perm)
         poro = np.ascontiguousarray(m["poro"], dtype=np.float64)
         fl = L.fluid_struct(m["fluid"])
         wells = (L.BoWell * max(1, len(m["wells"])))()

@@ -130,6 +130,21 @@ def _base(name, nx, ny, nz, dx, dy, dz, perm, poro, wells, n_steps, dt):
     }
 
 
+def anisotropic(model: dict, seed: int = 0, ky_kx=(0.3, 3.0), kz_kx=(0.01, 0.3)) -> dict:
+    """The model with cell-wise anisotropic permeability [3][n] (kx, ky, kz):
+    kx is the model's field, ky / kx and kz / kx are log-uniform per cell in
+    the given ranges (kv/kh of layered sandstones lies in the lower range)."""
+    m = dict(model)
+    rng = np.random.default_rng(10_000 + seed)
+    kx = np.asarray(model["perm"], dtype=np.float64).reshape(-1)
+    n = kx.size
+    ry = np.exp(rng.uniform(np.log(ky_kx[0]), np.log(ky_kx[1]), n))
+    rz = np.exp(rng.uniform(np.log(kz_kx[0]), np.log(kz_kx[1]), n))
+    m["perm"] = np.ascontiguousarray(np.concatenate([kx, kx * ry, kx * rz]))
+    m["name"] = model["name"] + " anisotropic"
+    return m
+
+
 def config0() -> dict:
     """10x10x3 SPE1-shaped model: 1000x1000x50 ft cells, ln k ~ N(ln 200 mD, 1)
     i.i.d., porosity 0.3, gas injector at (1,1,1) under rate control

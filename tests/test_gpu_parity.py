@@ -43,6 +43,8 @@ MODELS = {
     "ragged_33x17x9": lambda: synth.small_model(33, 17, 9, wells="5spot", dz=3.0),
     "gas_7x6x5": lambda: synth.small_model(7, 6, 5, wells="gas", dz=5.0),
     "config0": synth.config0,
+    "aniso_9x8x6": lambda: synth.anisotropic(synth.small_model(9, 8, 6, wells="5spot", dz=4.0),
+                                             seed=1),
 }
 
 
@@ -169,7 +171,7 @@ def test_bicgstab_iteration_limit_and_status():
 
 
 @pytest.mark.parametrize("name,steps,dt_days", [("small_5spot", 3, 2.0), ("gas_7x6x5", 3, 5.0),
-                                                ("config0", 10, 30.0)])
+                                                ("aniso_9x8x6", 3, 2.0), ("config0", 10, 30.0)])
 def test_newton_steps_parity(name, steps, dt_days):
     m = MODELS[name]()
     g, o = Sim(m), oracle.Oracle(m)

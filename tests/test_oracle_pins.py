@@ -73,6 +73,48 @@ def test_peaceman_equivalent_radius_square_block():
     assert abs(ro / dx - val) <= tol
 
 
+def _single_cell_wi(kx, ky, dx, dy, h, rw):
+    w = _well(0, 0, [0], "prod", "bhp", 3000 * PSI, 3000 * PSI, rw=rw)
+    m = make_model(1, 1, 1, 1.0, 0.2, [w], dx=dx, dy=dy, dz=h)
+    m["perm"] = np.array([kx, ky, 0.1 * kx])
+    return oracle.Oracle(m).static()["wi"][0]
+
+
+def test_peaceman_anisotropic_coordinate_transform():
+    """Peaceman's anisotropic index follows from the isotropic one by the
+    stretch x' = x a, y' = y / a, a = (ky/kx)^(1/4), which turns the rock
+    isotropic with k = sqrt(kx ky), the block into dx a by dy / a and the well
+    circle into an ellipse of semi-axes r_w a and r_w / a, whose equivalent
+    circle for steady radial flow has radius r_w (a + 1/a) / 2.  The
+    anisotropic index must equal the isotropic index of that stretched
+    problem; with dy = dx sqrt(ky/kx) the stretched block is square and r_o
+    must be the published 0.198 of its side."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "peaceman_1978.txt"))
+            if l.strip() and not l.startswith("#")]
+    ref = {r[0]: (float(r[1]), float(r[2])) for r in rows}
+    val, tol = ref["ro_over_dx_square"]
+    h, rw = 6.0, 0.1
+    for kx, ky, dx, dy in [(150 * MD, 15 * MD, 40.0, 25.0), (20 * MD, 300 * MD, 30.0, 70.0),
+                           (80 * MD, 60 * MD, 100.0, 10.0)]:
+        a = (ky / kx) ** 0.25
+        k = math.sqrt(kx * ky)
+        wi = _single_cell_wi(kx, ky, dx, dy, h, rw)
+        wi_iso = _single_cell_wi(k, k, dx * a, dy / a, h, rw * (a + 1 / a) / 2)
+        assert wi == pytest.approx(wi_iso, rel=1e-13)
+        # the square stretched block against the published equivalent radius
+        dy_sq = dx * math.sqrt(ky / kx)
+        wi_sq = _single_cell_wi(kx, ky, dx, dy_sq, h, rw)
+        ro = rw * (a + 1 / a) / 2 * math.exp(2 * math.pi * k * h / wi_sq)
+        assert abs(ro / (dx * a) - val) <= tol
+    # the anisotropic form meets the isotropic one as ky -> kx
+    wi0 = _single_cell_wi(150 * MD, 150 * MD, 40.0, 25.0, h, rw)
+    wi1 = _single_cell_wi(150 * MD, 150 * MD * (1 + 1e-9), 40.0, 25.0, h, rw)
+    assert wi1 == pytest.approx(wi0, rel=1e-8)
+    # swapping kx and ky swaps the roles of dx and dy
+    assert _single_cell_wi(150 * MD, 15 * MD, 40.0, 25.0, h, rw) == pytest.approx(
+        _single_cell_wi(15 * MD, 150 * MD, 25.0, 40.0, h, rw), rel=1e-13)
+
+
 # ---------------------------------------------------------------------------
 # Cell properties: AD derivatives against central differences; end points of
 # the relative permeability curves; continuity at the bubble point.
@@ -430,6 +472,53 @@ def test_1d_incompressible_linear_profile():
     res = [mu / wi[0]]
     for i in range(N - 1):
         res.append(mu * ((dx / 2) / (perm[i] * area) + (dx / 2) / (perm[i + 1] * area)))
+    res.append(mu / wi[1])
+    q = (pL - pR) / sum(res)
+    ref = pL - q * np.cumsum(res)[:-1]
+    assert np.max(np.abs(p - ref)) <= 1e-9 * pL
+
+
+@pytest.mark.parametrize("axis", ["x", "y", "z"])
+def test_1d_incompressible_anisotropic_chain(axis):
+    """The same steady Darcy chain laid along x, y or z of an anisotropic
+    rock: only the permeability along the chain enters its resistances (the
+    other two components are made 50x larger and 50x smaller to expose a
+    mix-up), and the profile is the series solution of Appendix B."""
+    N = 10
+    rng = np.random.default_rng(11)
+    kc = np.exp(np.log(150 * MD) + 0.5 * rng.standard_normal(N))
+    h = {"x": 15.0, "y": 12.0, "z": 3.0}
+    pL, pR = 5000 * PSI, 4000 * PSI
+    dims = {"x": (N, 1, 1), "y": (1, N, 1), "z": (1, 1, N)}[axis]
+    if axis == "x":
+        wells = [_well(0, 0, [0], "inj", "bhp", pL, pL, phase="water"),
+                 _well(N - 1, 0, [0], "prod", "bhp", pR, pR)]
+    elif axis == "y":
+        wells = [_well(0, 0, [0], "inj", "bhp", pL, pL, phase="water"),
+                 _well(0, N - 1, [0], "prod", "bhp", pR, pR)]
+    else:
+        wells = [_well(0, 0, [0], "inj", "bhp", pL, pL, phase="water"),
+                 _well(0, 0, [N - 1], "prod", "bhp", pR, pR)]
+    fluid = {"g": 0.0, "c_w": 0.0, "c_r": 0.0, "s_orw": 0.0}
+    m = make_model(*dims, 1.0, 0.25, wells, fluid=fluid, dx=h["x"], dy=h["y"], dz=h["z"])
+    comp = {"x": 0, "y": 1, "z": 2}[axis]
+    perm = np.empty((3, N))
+    for d in range(3):
+        perm[d] = kc * (1.0 if d == comp else (50.0 if d == (comp + 1) % 3 else 0.02))
+    m["perm"] = perm.reshape(-1)
+    o = oracle.Oracle(m)
+    p0 = np.full(N, 0.5 * (pL + pR))
+    o.set_state(p0, np.ones(N), np.zeros(N), np.zeros(N, np.uint8), np.array([pL, pR]))
+    status, rep = o.step(10 * synth.DAY, tol_mb=1e-13, tol_cnv=1e-12, tol_lin=1e-13)
+    assert status == 0 and rep["newton_its"] == 1
+    p = o.get_state()[0]
+    mu = m["fluid"]["mu_w"]
+    wi = o.static()["wi"]
+    area = {"x": h["y"] * h["z"], "y": h["x"] * h["z"], "z": h["x"] * h["y"]}[axis]
+    half = h[axis] / 2
+    res = [mu / wi[0]]
+    for i in range(N - 1):
+        res.append(mu * (half / (kc[i] * area) + half / (kc[i + 1] * area)))
     res.append(mu / wi[1])
     q = (pL - pR) / sum(res)
     ref = pL - q * np.cumsum(res)[:-1]

@@ -37,10 +37,13 @@ rate control equation.  Readings taken where the section is silent:
   start.
 * Storage: A_a,w = V_w F_a / g_a with V_w = pi r_w^2 times the perforated
   thickness (0 turns it off).
-* Jacobian: exact for the reservoir block (the C++ oracle's automatic
-  differentiation); central differences for every term that involves a
-  well.  Newton stops on the MB and CNV measures of the reservoir residual
-  with the well terms and on |R_w| relative to the well's rate scale.
+* Jacobian: exact throughout -- the reservoir block from the C++ oracle's
+  automatic differentiation, the well terms by forward-mode dual numbers
+  over the connection cell's three unknowns and the well's four
+  (``assemble``); ``assemble_fd`` takes central differences of the well
+  terms instead and serves as the check of the exact one.  Newton stops on
+  the MB and CNV measures of the reservoir residual with the well terms and
+  on |R_w| relative to the well's rate scale.
 """
 from __future__ import annotations
 
@@ -51,6 +54,56 @@ import numpy as np
 import oracle
 
 G_WEIGHTS = (1.0, 1.0, 0.01)
+NV = 7   # dual slots: the connection cell's (p, s_w, x), the well's (Q_t, F_w, F_g, p_bhp)
+
+
+class Dual:
+    """Forward-mode dual number: value v and derivatives d[NV]."""
+    __slots__ = ("v", "d")
+
+    def __init__(self, v, d=None):
+        self.v = float(v)
+        self.d = np.zeros(NV) if d is None else np.asarray(d, float)
+
+    @staticmethod
+    def var(v, slot):
+        d = np.zeros(NV)
+        d[slot] = 1.0
+        return Dual(v, d)
+
+    @staticmethod
+    def lift(x):
+        return x if isinstance(x, Dual) else Dual(x)
+
+    def __add__(self, o):
+        o = Dual.lift(o)
+        return Dual(self.v + o.v, self.d + o.d)
+
+    __radd__ = __add__
+
+    def __sub__(self, o):
+        o = Dual.lift(o)
+        return Dual(self.v - o.v, self.d - o.d)
+
+    def __rsub__(self, o):
+        return Dual.lift(o) - self
+
+    def __neg__(self):
+        return Dual(-self.v, -self.d)
+
+    def __mul__(self, o):
+        o = Dual.lift(o)
+        return Dual(self.v * o.v, self.d * o.v + self.v * o.d)
+
+    __rmul__ = __mul__
+
+    def __truediv__(self, o):
+        if not isinstance(o, Dual):
+            return Dual(self.v / o, self.d / o)
+        return Dual(self.v / o.v, (self.d * o.v - self.v * o.d) / (o.v * o.v))
+
+    def __rtruediv__(self, o):
+        return Dual.lift(o) / self
 
 
 class StandardWellModel:
@@ -113,8 +166,14 @@ class StandardWellModel:
                 w["x"][0] = -w["spec"]["target"] * self.g[w["phase"]] if w["control"] == 0 else 0.0
 
     def _begin_wells(self):
+        """Step start: controls from the specification (a switch to BHP control
+        lasts for the rest of a step, as for the reduced well), the datum and
+        the wellbore density, the storage at the step start."""
         p, sw, x, fl = self.cells()
         for w in self.wells:
+            w["control"] = 0 if w["spec"]["control"] == "rate" else 1
+            if w["control"] == 1:
+                w["x"][3] = w["spec"]["target"]
             c0 = w["cells"][0]
             w["z_datum"] = self.depth[c0]
             if w["inj"]:
@@ -132,6 +191,12 @@ class StandardWellModel:
     def get_state(self):
         p, sw, x, fl = self.cells()
         return p, sw, x, fl, np.array([w["x"][3] for w in self.wells])
+
+    @staticmethod
+    def _bhp_target(w):
+        """The BHP a BHP-controlled well holds: its target under BHP control by
+        specification, its BHP limit after a switch from rate control."""
+        return w["spec"]["target"] if w["spec"]["control"] == "bhp" else w["spec"]["bhp_limit"]
 
     def _opening_bhp(self, w, p):
         """The BHP at which the first connection starts to flow: the lowest
@@ -173,11 +238,102 @@ class StandardWellModel:
                 qres = wi * (lam[0] + lam[1] + lam[2]) * dp      # reservoir volume rate, < 0
                 rmix = 0.0
                 if abs(Qw[1]) > 0:
-                    rmix = min(F["R_sb"] * p[c] / F["p_b"], max(Qw[2] / Qw[1], 0.0))
+                    rmix = min((F["R_sb"] / F["p_b"]) * p[c], max(Qw[2] / Qw[1], 0.0))
                 V = Qw[0] / b[0] + Qw[1] / b[1] + (Qw[2] - rmix * Qw[1]) / b[2]
                 if V != 0.0:
                     out[j] = qres * Qw / V
         return out
+
+    def _conn_duals(self, w, j, c, p, sw, x, fl, xw):
+        """Surface rates (3 duals) of connection j into the well: the same
+        arithmetic as ``_well_rates`` carried on duals over the cell's and
+        the well's unknowns."""
+        F = self.F
+        cp = self.props(c, p, sw, x, fl)
+
+        def cell(name):
+            a = cp[name]
+            return Dual(a[0], [a[1], a[2], a[3], 0, 0, 0, 0])
+
+        xv = [Dual.var(xw[k], 3 + k) for k in range(4)]
+        pc = Dual.var(p[c], 0)
+        h = F["g"] * w["rho"] * (self.depth[c] - w["z_datum"])
+        dp = pc - xv[3] - h
+        wi = w["wi"][j]
+        b = [cell("b_" + a) for a in "wog"]
+        lam = [cell("lam_" + a) for a in "wog"]
+        zero = [Dual(0.0), Dual(0.0), Dual(0.0)]
+        if dp.v > 0.0:
+            if w["inj"]:
+                return zero
+            q = [wi * b[a] * lam[a] * dp for a in range(3)]
+            q[2] = q[2] + cell("r_go") * q[1]
+            return q
+        if dp.v < 0.0:
+            qres = wi * (lam[0] + lam[1] + lam[2]) * dp
+            Qw = [xv[1] / self.g[0], (1.0 - xv[1] - xv[2]) / self.g[1], xv[2] / self.g[2]]
+            rmix = Dual(0.0)
+            if abs(Qw[1].v) > 0:
+                rs = (F["R_sb"] / F["p_b"]) * pc
+                ratio = Qw[2] / Qw[1] if Qw[2].v / Qw[1].v > 0.0 else Dual(0.0)
+                rmix = rs if rs.v < ratio.v else ratio
+            V = Qw[0] / b[0] + Qw[1] / b[1] + (Qw[2] - rmix * Qw[1]) / b[2]
+            if V.v != 0.0:
+                return [qres * Qw[a] / V for a in range(3)]
+        return zero
+
+    def well_blocks(self, k, dt, p=None, sw=None, x=None, fl=None):
+        """Exact well terms of well k (Eq. wellequation's blocks): per
+        connection the cell-row rates q [ncon, 3] and their derivatives in the
+        cell's unknowns dq_dc [ncon, 3, 3] and in the well's dq_dw [ncon, 3, 4];
+        the well residual Rw [4], its derivatives in each connection cell's
+        unknowns C [ncon, 4, 3] and in the well's unknowns D [4, 4]."""
+        if p is None:
+            p, sw, x, fl = self.cells()
+        w = self.wells[k]
+        xw = w["x"]
+        nc = len(w["cells"])
+        q = np.zeros((nc, 3))
+        dq_dc = np.zeros((nc, 3, 3))
+        dq_dw = np.zeros((nc, 3, 4))
+        for j, c in enumerate(w["cells"]):
+            qd = self._conn_duals(w, j, c, p, sw, x, fl, xw)
+            for a in range(3):
+                q[j, a] = qd[a].v
+                dq_dc[j, a] = qd[a].d[:3]
+                dq_dw[j, a] = qd[a].d[3:]
+        # wellbore balance R_a = (A_a - A0_a)/dt + Q_a - sum_j q_ja, A_a = V_w F_a / g_a
+        Fv = [Dual.var(xw[1], 4), Dual.var(xw[2], 5)]
+        qt = Dual.var(xw[0], 3)
+        frac = [Fv[0], 1.0 - Fv[0] - Fv[1], Fv[1]]
+        bal = [(w["vw"] * frac[a] / self.g[a] - w["A0"][a]) / dt + frac[a] * qt / self.g[a]
+               for a in range(3)]
+        Rw = np.zeros(4)
+        D = np.zeros((4, 4))
+        C = np.zeros((nc, 4, 3))
+        for a in range(3):
+            Rw[a] = bal[a].v - q[:, a].sum()
+            D[a] = bal[a].d[3:] - dq_dw[:, a].sum(axis=0)
+            C[:, a] = -dq_dc[:, a]
+        if w["inj"]:
+            a = w["phase"]
+            Rw[0], D[0], C[:, 0] = Rw[a], D[a].copy(), C[:, a].copy()
+            Rw[1] = xw[1] - (1.0 if a == 0 else 0.0)
+            Rw[2] = xw[2] - (1.0 if a == 2 else 0.0)
+            D[1] = [0, 1, 0, 0]
+            D[2] = [0, 0, 1, 0]
+            C[:, 1:3] = 0.0
+        C[:, 3] = 0.0
+        if w["control"] == 1:
+            Rw[3] = xw[3] - self._bhp_target(w)
+            D[3] = [0, 0, 0, 1]
+        else:
+            a = w["phase"] if w["inj"] else 1
+            Qa = frac[a] * qt / self.g[a]
+            ctl = (-Qa if w["inj"] else Qa) - w["spec"]["target"]
+            Rw[3] = ctl.v
+            D[3] = ctl.d[3:]
+        return {"q": q, "dq_dc": dq_dc, "dq_dw": dq_dw, "Rw": Rw, "C": C, "D": D}
 
     def _well_residual(self, w, q, xw, dt):
         R = np.zeros(4)
@@ -188,7 +344,7 @@ class StandardWellModel:
             R[1] = xw[1] - (1.0 if a == 0 else 0.0)
             R[2] = xw[2] - (1.0 if a == 2 else 0.0)
         if w["control"] == 1:
-            R[3] = xw[3] - w["spec"]["target"]
+            R[3] = xw[3] - self._bhp_target(w)
         elif w["inj"]:
             R[3] = -self._Q(xw)[w["phase"]] - w["spec"]["target"]
         else:
@@ -211,7 +367,33 @@ class StandardWellModel:
         return Rc, Rw
 
     def assemble(self, dt):
-        """Dense Jacobian and residual of cells (3n) and wells (4 nw)."""
+        """Dense Jacobian and residual of cells (3n) and wells (4 nw), the
+        well terms differentiated exactly (``well_blocks``)."""
+        n, nw = self.n, self.nw
+        self.o.assemble(dt)
+        rp, ci, vals, Rres = self.o.system()
+        N = 3 * n + 4 * nw
+        J = np.zeros((N, N))
+        for c in range(n):
+            for q in range(rp[c], rp[c + 1]):
+                J[3 * c:3 * c + 3, 3 * ci[q]:3 * ci[q] + 3] = vals[q]
+        Rc = np.asarray(Rres, float).reshape(-1).copy()
+        Rw_all = np.zeros(4 * nw)
+        for k, w in enumerate(self.wells):
+            blk = self.well_blocks(k, dt)
+            col = 3 * n + 4 * k
+            for j, c in enumerate(w["cells"]):
+                Rc[3 * c:3 * c + 3] += blk["q"][j]
+                J[3 * c:3 * c + 3, 3 * c:3 * c + 3] += blk["dq_dc"][j]
+                J[3 * c:3 * c + 3, col:col + 4] += blk["dq_dw"][j]
+                J[col:col + 4, 3 * c:3 * c + 3] += blk["C"][j]
+            J[col:col + 4, col:col + 4] = blk["D"]
+            Rw_all[4 * k:4 * k + 4] = blk["Rw"]
+        return J, np.concatenate([Rc, Rw_all])
+
+    def assemble_fd(self, dt):
+        """Dense Jacobian and residual with central differences of the well
+        terms (the check of ``assemble``)."""
         n, nw = self.n, self.nw
         self.o.assemble(dt)
         rp, ci, vals, Rres = self.o.system()
@@ -272,7 +454,7 @@ class StandardWellModel:
                 wres = max(wres, abs(Rw[0]) / qs, abs(Rw[1]), abs(Rw[2]))
             else:
                 wres = max(wres, np.abs(Rw[:3]).max() / qs)
-            scale = w["spec"]["target"] if w["control"] == 0 else max(w["spec"]["target"], 1.0)
+            scale = w["spec"]["target"] if w["control"] == 0 else max(self._bhp_target(w), 1.0)
             wres = max(wres, abs(Rw[3]) / scale)
         return mb, cnv, wres
 
@@ -288,32 +470,38 @@ class StandardWellModel:
                 return True, it
             if it == max_newton:
                 return False, it
-            dx = np.linalg.solve(J, R)
-            n = self.n
-            self.o.newton_update(dx[:3 * n])          # cells: dy = -dx with the chop
-            p_new = self.cells()[0]
-            for k, w in enumerate(self.wells):
-                d = -dx[3 * n + 4 * k:3 * n + 4 * k + 4]
-                dmax = 0.3 * w["x"][3]
-                d[3] = max(-dmax, min(dmax, d[3]))
-                old = w["x"][3]
-                w["x"] += d
-                if w["control"] == 0:
-                    # as for the reduced well: a rate-controlled well keeps
-                    # flowing, its BHP at most halves the distance to the
-                    # opening pressure (at the updated cell pressures)
-                    po = self._opening_bhp(w, p_new)
-                    if w["inj"]:
-                        floor = po + 0.5 * (old - po) if old > po else po + 1e-3 * abs(po)
-                        w["x"][3] = max(w["x"][3], floor)
-                    else:
-                        ceil = po - 0.5 * (po - old) if old < po else po - 1e-3 * abs(po)
-                        w["x"][3] = min(w["x"][3], ceil)
-                w["x"][1] = min(max(w["x"][1], 0.0), 1.0)
-                w["x"][2] = min(max(w["x"][2], 0.0), 1.0 - w["x"][1])
-                if w["control"] == 0:
-                    lim = w["spec"]["bhp_limit"]
-                    if (w["inj"] and w["x"][3] > lim) or (not w["inj"] and w["x"][3] < lim):
-                        w["control"] = 1
-                        w["x"][3] = lim
+            self.apply_update(np.linalg.solve(J, R))
         return False, max_newton
+
+    def apply_update(self, dx):
+        """Newton update y -= dx of cells (the oracle's chop and switching) and
+        wells: the BHP step chopped to 30% of the BHP, a rate well's BHP at most
+        halving its distance to the opening pressure, fractions clamped, the
+        switch to BHP control past the limit."""
+        n = self.n
+        self.o.newton_update(dx[:3 * n])          # cells: dy = -dx with the chop
+        p_new = self.cells()[0]
+        for k, w in enumerate(self.wells):
+            d = -dx[3 * n + 4 * k:3 * n + 4 * k + 4]
+            dmax = 0.3 * w["x"][3]
+            d[3] = max(-dmax, min(dmax, d[3]))
+            old = w["x"][3]
+            w["x"] += d
+            if w["control"] == 0:
+                # as for the reduced well: a rate-controlled well keeps
+                # flowing, its BHP at most halves the distance to the
+                # opening pressure (at the updated cell pressures)
+                po = self._opening_bhp(w, p_new)
+                if w["inj"]:
+                    floor = po + 0.5 * (old - po) if old > po else po + 1e-3 * abs(po)
+                    w["x"][3] = max(w["x"][3], floor)
+                else:
+                    ceil = po - 0.5 * (po - old) if old < po else po - 1e-3 * abs(po)
+                    w["x"][3] = min(w["x"][3], ceil)
+            w["x"][1] = min(max(w["x"][1], 0.0), 1.0)
+            w["x"][2] = min(max(w["x"][2], 0.0), 1.0 - w["x"][1])
+            if w["control"] == 0:
+                lim = w["spec"]["bhp_limit"]
+                if (w["inj"] and w["x"][3] > lim) or (not w["inj"] and w["x"][3] < lim):
+                    w["control"] = 1
+                    w["x"][3] = lim

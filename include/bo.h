@@ -229,6 +229,40 @@ bo_status bo_get_system(const bo_sim* sim, int* rowptr, int* colind, double* val
 bo_status bo_get_wells(const bo_sim* sim, double* Rw, double* Dw, double* B, double* C,
                        int* control);
 
+/* Well model (Section 2.2.1).  BO_WELL_REDUCED (default): the reduced
+ * standard well, one unknown per rate-controlled well (its BHP), no
+ * cross-flow.  BO_WELL_STANDARD: the full standard well -- four unknowns per
+ * well, the weighted total rate Q_t, the weighted fractions F_w, F_g
+ * (Eq. weighted_total_rate, weights g = (1, 1, 0.01)) and p_bhp; connection
+ * inflow by Eq. (wellinflow) with cross-flow (an injecting connection of a
+ * producer carries the wellbore mixture); one balance per component with,
+ * when storage != 0, the wellbore storage A_a = V_w F_a / g_a, V_w = pi r_w^2
+ * times the perforated thickness (Eq. conseq-swell); the control of
+ * Eqs. (well-control-bhp/rate); the Schur complement of Eq. (wellequation)
+ * with a 4x4 D_w per well.  An injector's wellbore holds its injected phase
+ * (F fixed).  The well unknowns are initialised by the next bo_set_state,
+ * bo_init_hydrostatic or bo_init_equilibrium (a producer's Q_t and F from
+ * its inflow at that state and BHP), which must follow this call.
+ * BO_ERR_STATE before bo_set_properties; BO_ERR_INVALID_ARG for another
+ * model. */
+#define BO_WELL_REDUCED 0
+#define BO_WELL_STANDARD 1
+bo_status bo_set_well_model(bo_sim* sim, int model, int storage);
+bo_status bo_get_well_model(const bo_sim* sim, int* model);
+
+/* Full standard wells (BO_WELL_STANDARD): the blocks of Eq. (wellequation)
+ * at the last assembly -- B[ncon][4][3] = dR_w / dy_c of each connection's
+ * cell, C[ncon][3][4] = dR_c / dx_w of the cell row, both in connection
+ * order (well by well, the connections in the order given), D[nw][4][4] =
+ * dR_w / dx_w and Rw[nw][4] (rows: the water, oil and gas balances -- for
+ * an injector the injected phase's balance, F_w - F_w,inj, F_g - F_g,inj --
+ * then the control) -- and the current unknowns xw[nw][4] = (Q_t, F_w, F_g,
+ * p_bhp).  x_w variables are ordered (Q_t, F_w, F_g, p_bhp), cell variables
+ * (p_o, s_w, x).  Any pointer may be NULL; B, C, D, Rw need an assembly
+ * (BO_ERR_STATE otherwise, and when the model is not selected). */
+bo_status bo_get_std_wells(const bo_sim* sim, double* B, double* C, double* D, double* Rw,
+                           double* xw);
+
 /* Well production report (Section 2.2.1): per well the surface rates of
  * water, oil and gas (m^3/s at surface conditions, the connection inflows of
  * Eq. (wellinflow) summed over the well's connections, gas including the
@@ -267,7 +301,8 @@ bo_status bo_apply_op(bo_sim* sim, const double* x, double* y);
  * from a zero initial guess with a fresh max_it; report->fallback says which
  * ran).
  * sol (may be NULL) receives [3n + nwells] (cell-major, then one entry per
- * well, 0 for wells without an unknown). */
+ * well, 0 for wells without an unknown); with BO_WELL_STANDARD [3n + 4
+ * nwells], four entries per well (Q_t, F_w, F_g, p_bhp). */
 bo_status bo_solve(bo_sim* sim, const bo_solve_opts* opts, bo_solve_report* report,
                    double* sol);
 

@@ -122,6 +122,9 @@ _SIGS = {
     "bo_get_precision": [P, P],
     "bo_get_timing": [P, c_int, P, P, P, P],
     "bo_get_launch_count": [P, P],
+    "bo_set_well_model": [P, c_int, c_int],
+    "bo_get_well_model": [P, P],
+    "bo_get_std_wells": [P, P, P, P, P, P],
     "bo_set_preconditioner": [P, c_int],
     "bo_learn_guard": [P, c_int],
     "bo_get_preconditioner": [P, P],
@@ -136,6 +139,7 @@ _SIGS = {
 EXPORTED = sorted(list(_SIGS) + ["bo_last_error"])
 
 PRECONDITIONER = {"ilu0": 0, "cpr": 1}
+WELL_MODEL = {"reduced": 0, "standard": 1}
 
 STATUS = {0: "BO_OK", 1: "BO_ERR_INVALID_ARG", 2: "BO_ERR_CUDA", 3: "BO_ERR_OOM",
           4: "BO_ERR_NOT_CONVERGED", 5: "BO_ERR_LINEAR_BREAKDOWN", 6: "BO_ERR_DEVICE_TIMEOUT",

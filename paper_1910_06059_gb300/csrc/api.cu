@@ -85,7 +85,7 @@ static void free_all(bo_sim* s) {
                     s->d_ml_theta, s->d_ml_grad, s->d_ml_m, s->d_ml_v, s->d_ml_wbf,
                     s->d_ml_feat, s->d_ml_featf, s->d_ml_cell, s->d_ml_part, s->d_ml_delta,
                     s->d_ml_u, s->d_ml_z0, s->d_ml_e, s->d_ml_dd, s->d_ml_scal, s->d_ml_count,
-                    s->d_ml_samples, s->d_ml_W};
+                    s->d_ml_samples, s->d_ml_W, s->d_wB4, s->d_wC4, s->d_wcorr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->h_ns) cudaFreeHost(s->h_ns);
@@ -161,6 +161,10 @@ static int solve_linear(bo_sim* s, double tol, int maxit, int* its) {
     read_status(s);
     check_timeout(s);
     if (s->h_ns->pad != 0) {  // non-finite pivot block
+        *its = 0;
+        return LS_BREAKDOWN;
+    }
+    if (s->h_ns->singular_wells > 0) {   // a full standard well with a singular D_w
         *its = 0;
         return LS_BREAKDOWN;
     }
@@ -414,6 +418,12 @@ bo_status bo_set_properties(bo_sim* s, const double* perm, const double* poro,
                 s->con_cell_h.push_back(c);
                 conwell.push_back(w);
             }
+            // wellbore volume of the full standard well's storage term:
+            // pi r_w^2 times the perforated thickness
+            double thick = 0.0;
+            for (int q = 0; q < in.ncon; ++q)
+                thick += s->dz[in.cells[q] / (s->geo.nx * s->geo.ny)];
+            d.vw = M_PI * in.rw * in.rw * thick;
             rw.push_back(in.rw);
             skin.push_back(in.skin);
             s->wells_h.push_back(d);
@@ -492,6 +502,7 @@ static void start_wells(bo_sim* s) {
     // datum densities at the initial state, then the injector BHP estimate
     launch_begin_step(s);
     launch_well_init_bhp(s);
+    if (s->well_model == BO_WELL_MODEL_STANDARD) launch_std_wells_init(s);
     sync(s);
     s->assembled = s->factored = s->solved = false;
 }
@@ -567,6 +578,7 @@ static bo_status set_state_impl(bo_sim* s, const double* p, const double* sw, co
         BO_CUDA(cudaMemcpyAsync(s->d_x, x, sizeof(double) * n, k, s->stream));
         BO_CUDA(cudaMemcpyAsync(s->d_flag, flag, n, k, s->stream));
         set_bhp(s, bhp, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+        if (s->well_model == BO_WELL_MODEL_STANDARD) launch_std_wells_init(s);
         sync(s);
         s->assembled = s->factored = s->solved = false;
     });
@@ -762,7 +774,12 @@ bo_status bo_solve(bo_sim* s, const bo_solve_opts* o, bo_solve_report* rep, doub
             std::vector<WellDev> w(s->nw);
             if (s->nw)
                 BO_CUDA(cudaMemcpy(w.data(), s->d_wells, sizeof(WellDev) * s->nw, cudaMemcpyDeviceToHost));
-            for (int q = 0; q < s->nw; ++q) sol[3 * (size_t)s->geo.n + q] = w[q].xw;
+            if (s->well_model == BO_WELL_MODEL_STANDARD) {
+                for (int q = 0; q < s->nw; ++q)
+                    for (int k = 0; k < 4; ++k) sol[3 * (size_t)s->geo.n + 4 * q + k] = w[q].dxs[k];
+            } else {
+                for (int q = 0; q < s->nw; ++q) sol[3 * (size_t)s->geo.n + q] = w[q].xw;
+            }
         }
     });
 }
@@ -1110,6 +1127,57 @@ bo_status bo_cpr_vcycle(bo_sim* s, const double* b, double* x) {
         need(s->precond == BO_PRECOND_CPR && s->factored, BO_ERR_STATE,
              "bo_cpr_vcycle: no factorisation with CPR selected");
         cpr_vcycle_host(s, b, x);
+    });
+}
+
+bo_status bo_set_well_model(bo_sim* s, int model, int storage) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_set_well_model: call bo_set_properties first");
+        need(model == BO_WELL_REDUCED || model == BO_WELL_STANDARD, BO_ERR_INVALID_ARG,
+             "bo_set_well_model: model must be BO_WELL_REDUCED or BO_WELL_STANDARD");
+        const bool full = model == BO_WELL_STANDARD;
+        if (full) std_wells_setup(s);
+        std::vector<WellDev> w(s->nw);
+        if (s->nw) {
+            BO_CUDA(cudaMemcpy(w.data(), s->d_wells, sizeof(WellDev) * s->nw, cudaMemcpyDeviceToHost));
+            for (int q = 0; q < s->nw; ++q) {
+                w[q].full = full ? 1 : 0;
+                w[q].vw = (full && storage) ? s->wells_h[q].vw : 0.0;
+            }
+            BO_CUDA(cudaMemcpy(s->d_wells, w.data(), sizeof(WellDev) * s->nw, cudaMemcpyHostToDevice));
+        }
+        s->well_model = full ? BO_WELL_MODEL_STANDARD : BO_WELL_MODEL_REDUCED;
+        s->well_storage = storage != 0;
+        s->assembled = s->factored = s->solved = false;
+        build_graphs(s);   // the operator's well part differs between the models
+    });
+}
+
+bo_status bo_get_well_model(const bo_sim* s, int* model) {
+    return guarded([&] {
+        need(s != nullptr && model != nullptr, BO_ERR_INVALID_ARG,
+             "bo_get_well_model: NULL argument");
+        *model = s->well_model == BO_WELL_MODEL_STANDARD ? BO_WELL_STANDARD : BO_WELL_REDUCED;
+    });
+}
+
+bo_status bo_get_std_wells(const bo_sim* s, double* B, double* C, double* D, double* Rw,
+                           double* xw) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_get_std_wells: properties not set");
+        need(s->well_model == BO_WELL_MODEL_STANDARD, BO_ERR_STATE,
+             "bo_get_std_wells: the full standard well model is not selected");
+        need(!(B || C || D || Rw) || s->assembled, BO_ERR_STATE, "bo_get_std_wells: no assembly");
+        if (s->nw == 0) return;
+        std::vector<WellDev> w(s->nw);
+        BO_CUDA(cudaMemcpy(w.data(), s->d_wells, sizeof(WellDev) * s->nw, cudaMemcpyDeviceToHost));
+        for (int q = 0; q < s->nw; ++q) {
+            if (D) std::memcpy(D + 16 * (size_t)q, w[q].D, sizeof(double) * 16);
+            if (Rw) std::memcpy(Rw + 4 * (size_t)q, w[q].Rs, sizeof(double) * 4);
+            if (xw) std::memcpy(xw + 4 * (size_t)q, w[q].xs, sizeof(double) * 4);
+        }
+        if (B) BO_CUDA(cudaMemcpy(B, s->d_wB4, sizeof(double) * 12 * s->ncon, cudaMemcpyDeviceToHost));
+        if (C) BO_CUDA(cudaMemcpy(C, s->d_wC4, sizeof(double) * 12 * s->ncon, cudaMemcpyDeviceToHost));
     });
 }
 

@@ -19,60 +19,9 @@
 //            well-equation residual and Schur pieces B_w, C_w, D_w.
 #include <cmath>
 
-#include "common.cuh"
-#include "dual.cuh"
+#include "cell.cuh"
 
 namespace bo {
-
-enum { W_ = 0, O_ = 1, G_ = 2 };
-
-struct CellD {
-    D3 b[3], lam[3], rho[3], mphi, rgo, A[3];
-};
-
-// Cell quantities at (p_o, s_w, x, state) with derivatives with respect to
-// the cell's primary variables (Section 2.1.2).
-__device__ __forceinline__ void cell_eval(const DevFluid& F, double p_, double sw_, double x_,
-                                          int flag, CellD& c) {
-    D3 p = dvar(p_, 0), sw = dvar(sw_, 1), x = dvar(x_, 2);
-    D3 sg, rgo;
-    if (flag == 0) {            // SAT: gas present, oil saturated at r_s(p)
-        sg = x;
-        rgo = (F.R_sb / F.p_b) * p;
-    } else {                    // USAT: no free gas, x is the dissolved ratio
-        sg = dconst(0.0);
-        rgo = x;
-    }
-    D3 so = 1.0 - sw - sg;
-    c.rgo = rgo;
-    c.b[W_] = F.bw_ref * dexp(F.c_w * (p - F.p_ref));
-    D3 psat = (F.p_b / F.R_sb) * rgo;
-    D3 bsat = 1.0 + F.Bo_slope * rgo;
-    c.b[O_] = ddiv(dexp(F.c_o * (p - psat)), bsat);
-    D3 mu_o = ddiv(dconst(F.mu_o0), 1.0 + F.mu_o_r * rgo) * dexp(F.c_mu * (p - psat));
-    c.b[G_] = (1.0 / (F.p_sc * F.Z)) * p;
-    D3 mu_g = F.mu_g0 * (1.0 + (1.0 / F.mu_g_p) * p);
-    c.mphi = dexp(F.c_r * (p - F.p_ref));
-    c.rho[W_] = F.rho_s[W_] * c.b[W_];
-    c.rho[O_] = c.b[O_] * (F.rho_s[O_] + F.rho_s[G_] * rgo);
-    c.rho[G_] = F.rho_s[G_] * c.b[G_];
-    const double n = F.n_corey;
-    D3 krw = dpow(dclamp01((1.0 / (1.0 - F.s_wco - F.s_orw)) * (sw - F.s_wco)), n);
-    D3 krg = dpow(dclamp01((1.0 / (1.0 - F.s_wco - F.s_org)) * sg), n);
-    D3 krow = dpow(dclamp01((1.0 / (1.0 - F.s_wco - F.s_orw)) * (so - F.s_orw)), n);
-    D3 krog = dpow(dclamp01((1.0 / (1.0 - F.s_wco - F.s_org)) * (so - F.s_org)), n);
-    D3 ww = sw - F.s_wco;
-    if (ww.v < 0.0) ww = dconst(0.0);
-    D3 den = ww + sg;
-    // Eq. (gwseg): volume-weighted oil relperm of the two sub-systems.
-    D3 kro = (den.v <= 1e-14) ? krow : ddiv(ww * krow + sg * krog, den);
-    c.lam[W_] = (1.0 / F.mu_w) * krw;
-    c.lam[O_] = ddiv(kro, mu_o);
-    c.lam[G_] = ddiv(krg, mu_g);
-    c.A[W_] = c.mphi * c.b[W_] * sw;
-    c.A[O_] = c.mphi * c.b[O_] * so;
-    c.A[G_] = c.mphi * (c.b[G_] * sg + rgo * c.b[O_] * so);
-}
 
 // ---------------------------------------------------------------------------
 // a1: static data (Appendix B) -- one thread per cell.  perm is [3][n]
@@ -330,6 +279,12 @@ __global__ void k_begin_wells(int nw, DevFluid F, WellDev* __restrict__ wells,
         W.rho_well = den > 0.0 ? num / den : 0.0;
     }
     W.bhp_bk = W.bhp;
+    if (W.full) {   // full standard well: storage at the step start, backup
+        W.xs[3] = W.bhp;
+        const double frac[3] = {W.xs[1], (1.0 - W.xs[1]) - W.xs[2], W.xs[2]};
+        for (int a = 0; a < 3; ++a) W.A0s[a] = (W.vw * frac[a]) / std_well_g(a);
+        for (int k = 0; k < 4; ++k) W.xs_bk[k] = W.xs[k];
+    }
 }
 
 __global__ void k_restore(int n, double* __restrict__ p, double* __restrict__ sw,
@@ -343,7 +298,12 @@ __global__ void k_restore(int n, double* __restrict__ p, double* __restrict__ sw
         x[c] = bk[2 * n + c];
         flag[c] = bkflag[c];
     }
-    if (c < nw) wells[c].bhp = wells[c].bhp_bk;
+    if (c < nw) {
+        WellDev& W = wells[c];
+        W.bhp = W.bhp_bk;
+        if (W.full)
+            for (int k = 0; k < 4; ++k) W.xs[k] = W.xs_bk[k];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -692,7 +652,10 @@ __global__ void k_fix_dead_wells(WellDev* __restrict__ wells, const int* __restr
     WellDev& W = wells[blockIdx.x];
     if (!(W.ctl == 0 && W.Dw == 0.0)) return;   // uniform over the block
     double po = opening_bhp(W, con_cell, p, depth, g);
-    if (threadIdx.x == 0) W.bhp = (W.kind == 0) ? po + 1e-3 * fabs(po) : po - 1e-3 * fabs(po);
+    if (threadIdx.x == 0) {
+        W.bhp = (W.kind == 0) ? po + 1e-3 * fabs(po) : po - 1e-3 * fabs(po);
+        if (W.full) W.xs[3] = W.bhp;
+    }
 }
 
 // Initial BHP of a rate-controlled injector: the BHP that meets the target by
@@ -800,9 +763,25 @@ __global__ void k_norm_final(int n, int nb_norm, const double* __restrict__ part
             ns->norms[3 + a] = dt * bavg * acc[3 + a];
         }
         double wr = 0.0;
-        for (int w = 0; w < nw; ++w)
-            if (wells[w].ctl == 0)
-                wr = fmax(wr, fabs(wells[w].Rw) / fmax(fabs(wells[w].target), 1e-300));
+        for (int w = 0; w < nw; ++w) {
+            const WellDev& W = wells[w];
+            if (W.full) {
+                // balances relative to the well's rate scale, fixed fractions
+                // absolute, the control relative to its target
+                const double qs = fmax(fabs(W.xs[0]), 1e-12);
+                if (W.kind == 0) {
+                    wr = fmax(wr, fabs(W.Rs[0]) / qs);
+                    wr = fmax(wr, fmax(fabs(W.Rs[1]), fabs(W.Rs[2])));
+                } else {
+                    wr = fmax(wr, fmax(fmax(fabs(W.Rs[0]), fabs(W.Rs[1])), fabs(W.Rs[2])) / qs);
+                }
+                const double scale =
+                    (W.ctl == 0) ? W.target : fmax(W.ctl0 == 1 ? W.target : W.limit, 1.0);
+                wr = fmax(wr, fabs(W.Rs[3]) / scale);
+            } else if (W.ctl == 0) {
+                wr = fmax(wr, fabs(W.Rw) / fmax(fabs(W.target), 1e-300));
+            }
+        }
         ns->norms[6] = wr;
     }
 }
@@ -933,13 +912,16 @@ void launch_begin_step(bo_sim* s) {
                                                             s->d_bk, s->d_bkflag);
     count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_begin_cells");
-    if (s->nw > 0) {
-        k_begin_wells<<<blocks_for(s->nw, 32), 32, 0, s->stream>>>(
-            s->nw, s->fluid, s->d_wells, s->d_con_cell, s->d_depth, s->d_p, s->d_sw, s->d_x,
-            s->d_flag);
-        count_launch(s, s->stream);
-        BO_LAUNCH_CHECK("k_begin_wells");
-    }
+    launch_begin_wells(s);
+}
+
+void launch_begin_wells(bo_sim* s) {
+    if (s->nw == 0) return;
+    k_begin_wells<<<blocks_for(s->nw, 32), 32, 0, s->stream>>>(
+        s->nw, s->fluid, s->d_wells, s->d_con_cell, s->d_depth, s->d_p, s->d_sw, s->d_x,
+        s->d_flag);
+    count_launch(s, s->stream);
+    BO_LAUNCH_CHECK("k_begin_wells");
 }
 
 void launch_restore(bo_sim* s) {
@@ -977,7 +959,9 @@ void launch_assemble(bo_sim* s, double dt) {
     BO_LAUNCH_CHECK("k_flux");
     timer_end(s, tf);
     BO_CUDA(cudaMemsetAsync(&s->d_ns->dead_wells, 0, sizeof(int), s->stream));
-    if (s->nw > 0) {
+    if (s->well_model == BO_WELL_MODEL_STANDARD) {
+        launch_std_wells_assemble(s, dt);
+    } else if (s->nw > 0) {
         k_wells<<<s->nw, WELL_BS, 0, s->stream>>>(s->geo, s->fluid, s->d_wells, s->d_con_cell,
                                                   s->d_con_wi, s->d_depth, s->d_p, s->d_sw,
                                                   s->d_x, s->d_flag, s->d_R, s->d_A, s->d_wB,
@@ -1024,7 +1008,9 @@ void launch_newton_update(bo_sim* s, const bo_newton_opts& o) {
                                                               s->d_sw, s->d_x, s->d_flag);
     count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_newton_update");
-    if (s->nw > 0) {
+    if (s->well_model == BO_WELL_MODEL_STANDARD) {
+        launch_std_wells_update(s, o);
+    } else if (s->nw > 0) {
         k_well_update<<<s->nw, 128, 0, s->stream>>>(o, s->d_wells, s->d_con_cell, s->d_p,
                                                      s->d_depth, s->fluid.g);
         count_launch(s, s->stream);

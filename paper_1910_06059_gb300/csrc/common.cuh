@@ -60,7 +60,21 @@ struct WellDev {
     double z_datum, rho_well;
     double Rw, Dw, xw;
     double qs[3];   // surface rates (w, o, g) summed over the connections at the last assembly
+    // full standard well (Section 2.2.1; wells_std.cu), when full != 0
+    int full;
+    int singular;        // D_w had a zero pivot at the last assembly
+    double vw;           // wellbore volume of the storage term (0: no storage)
+    double xs[4];        // Q_t, F_w, F_g, p_bhp (p_bhp mirrors bhp)
+    double xs_bk[4];     // at the step start (restored on a cut)
+    double A0s[3];       // wellbore storage at the step start
+    double Rs[4];        // well residual: three component balances, control
+    double D[16];        // D_w = dR_w / dx_w, row-major
+    double Dinv[16];     // D_w^-1
+    double dxs[4];       // solution of the well rows, x_w = D_w^-1 (R_w - B_w x_r)
 };
+enum { BO_WELL_MODEL_REDUCED = 0, BO_WELL_MODEL_STANDARD = 1 };
+// weights g_w, g_o, g_g of the weighted total rate Q_t (a small gas weight)
+__host__ __device__ __forceinline__ double std_well_g(int a) { return a == 2 ? 0.01 : 1.0; }
 
 // Scalars of the BiCGStab recurrence, kept on the device.
 struct KrylovScalars {
@@ -81,6 +95,8 @@ struct NewtonStatus {
     double norms[7];
     int dead_wells;   // rate wells with D_w == 0 in the last assembly
     int pad;
+    int singular_wells;   // full standard wells whose D_w had a zero pivot
+    int pad2;
 };
 
 constexpr int MAX_TIMERS = 16;
@@ -143,6 +159,12 @@ struct bo_sim {
     double* d_con_wi = nullptr;
     double* d_wB = nullptr;      // 3 * ncon
     double* d_wC = nullptr;      // 3 * ncon
+    // full standard wells (wells_std.cu)
+    int well_model = 0;          // BO_WELL_MODEL_*
+    bool well_storage = true;
+    double* d_wB4 = nullptr;     // [ncon][4][3]: B_w, dR_w / dx_c of the connection cell
+    double* d_wC4 = nullptr;     // [ncon][3][4]: C_w, dR_c / dx_w
+    double* d_wcorr = nullptr;   // [ncon][3]: C_w D_w^-1 B_w x of the last operator
     // Krylov vectors (3n each) and reduction scratch
     double *d_b = nullptr, *d_xs = nullptr, *d_r = nullptr, *d_rh = nullptr, *d_pk = nullptr,
            *d_v = nullptr, *d_s = nullptr, *d_t = nullptr, *d_ph = nullptr, *d_sh = nullptr;
@@ -217,6 +239,7 @@ void launch_static(bo_sim* s);
 void launch_hydrostatic(bo_sim* s, double p_top, double sw, double rgo);
 void launch_equilibrium(bo_sim* s, const EquilDev& e);
 void launch_begin_step(bo_sim* s);
+void launch_begin_wells(bo_sim* s);   // datum, wellbore density, step-start well values
 void launch_assemble(bo_sim* s, double dt);
 void launch_norms(bo_sim* s, double dt);
 void launch_fix_dead_wells(bo_sim* s);
@@ -253,6 +276,26 @@ void enqueue_precond_apply(bo_sim* s, cudaStream_t st, const double* r, double* 
 // y = b - S x with the well-reduced operator S (dot partials clobbered)
 void enqueue_op_resid(bo_sim* s, cudaStream_t st, const double* x, double* y, const double* b,
                       const KrylovScalars* ks);
+
+// The wells' part of the reduced operator for x: reduced wells write per rate
+// well sop_w = (B_w . x) / D_w into the reduction scratch and return it (the
+// cell rows subtract wC sop); full standard wells write C_w D_w^-1 B_w x per
+// connection into d_wcorr and return null (the cell rows subtract d_wcorr).
+const double* enqueue_well_dots(bo_sim* s, cudaStream_t st, const double* x,
+                                const KrylovScalars* ks);
+// the correction the cell rows read: d_wcorr for full wells, else null
+inline const double* well_corr(const bo_sim* s) {
+    return s->well_model == BO_WELL_MODEL_STANDARD ? s->d_wcorr : nullptr;
+}
+
+// full standard wells (wells_std.cu)
+void std_wells_setup(bo_sim* s);                 // buffers, volumes, flags
+void launch_std_wells_assemble(bo_sim* s, double dt);
+void launch_std_wells_init(bo_sim* s);           // Q_t, F from the inflow after a state change
+void enqueue_std_well_corr(bo_sim* s, cudaStream_t st, const double* x, const KrylovScalars* ks);
+void enqueue_std_wells_rhs(bo_sim* s, cudaStream_t st, double* b);
+void launch_std_wells_recover(bo_sim* s);
+void launch_std_wells_update(bo_sim* s, const bo_newton_opts& o);
 
 // CPR (cpr.cu)
 void cpr_build(bo_sim* s);                   // aggregation hierarchy, once per model

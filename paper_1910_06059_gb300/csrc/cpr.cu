@@ -587,6 +587,43 @@ k_cpr_coarse_apply(int nc, const double* __restrict__ cinv, const double* __rest
     }
 }
 
+// Second-stage residual r2 = r - S E_p x_p: only the pressure column of each
+// block enters (x1 = E_p x_p has no s_w or x components), and the well term
+// C_w (B_w . x1) / D_w with the per-well dots already in sop.
+__global__ void __launch_bounds__(CPR_BS)
+k_cpr_resid(Geom g, const double* __restrict__ A, const double* __restrict__ xp,
+            const double* __restrict__ r, const int* __restrict__ cellcon,
+            const int* __restrict__ con_well, const double* __restrict__ wC,
+            const double* __restrict__ sop, const double* __restrict__ ccorr,
+            double* __restrict__ r2, const KrylovScalars* __restrict__ ks) {
+    if (ks != nullptr && ks->state != KS_RUN) return;
+    const int n = g.n;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const Nb7 q = nb7(g, c);
+        double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int b = 0; b < 7; ++b) {
+            if (!q.has[b]) continue;
+            const double x = xp[q.nb[b]];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) acc[e] += A[(size_t)(b * 9 + 3 * e) * n + c] * x;
+        }
+        const int con = cellcon[c];
+        if (con >= 0) {
+            if (ccorr != nullptr) {   // full standard wells
+#pragma unroll
+                for (int e = 0; e < 3; ++e) acc[e] -= ccorr[3 * con + e];
+            } else {
+                const double sw = sop[con_well[con]];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) acc[e] -= wC[3 * con + e] * sw;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 3; ++e) r2[(size_t)e * n + c] = r[(size_t)e * n + c] - acc[e];
+    }
+}
+
 // z += E_p x_p
 __global__ void __launch_bounds__(CPR_BS)
 k_cpr_add(int n, const double* __restrict__ xp, double* __restrict__ z,
@@ -698,8 +735,13 @@ void enqueue_cpr_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
     CprData* c = s->cpr;
     const int n = s->geo.n;
     enqueue_cpr_pressure(s, st, r, ks);
+    // r2 = r - S x1, x1 = E_p x_p (the wells' dots read x1's pressure part)
     BO_CUDA(cudaMemcpyAsync(c->x1, c->lv[0].x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    enqueue_op_resid(s, st, c->x1, c->r2, r, ks);   // r2 = r - S x1
+    const double* sop = enqueue_well_dots(s, st, c->x1, ks);
+    k_cpr_resid<<<grid_for(n), CPR_BS, 0, st>>>(s->geo, s->d_A, c->lv[0].x, r, s->d_cellcon,
+                                               s->d_cellcon + n, s->d_wC, sop, well_corr(s),
+                                               c->r2, ks);
+    count_launch(s, st);
     enqueue_fwd(s, st, c->r2, z, ks);
     enqueue_bwd(s, st, z, ks);
     k_cpr_add<<<grid_for(n), CPR_BS, 0, st>>>(n, c->lv[0].x, z, ks);

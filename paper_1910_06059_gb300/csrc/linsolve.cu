@@ -75,8 +75,9 @@ __global__ void __launch_bounds__(VEC_BS)
 k_spmv(Geom g, const double* __restrict__ A, const double* __restrict__ x,
        double* __restrict__ y, const int* __restrict__ cellcon,
        const int* __restrict__ con_well, const double* __restrict__ wC,
-       const double* __restrict__ sop, const double* __restrict__ o1,
-       double* __restrict__ part, const KrylovScalars* __restrict__ ks) {
+       const double* __restrict__ sop, const double* __restrict__ ccorr,
+       const double* __restrict__ o1, double* __restrict__ part,
+       const KrylovScalars* __restrict__ ks) {
     if (ks_skip(ks)) return;
     const int n = g.n;
     const int plane = g.nx * g.ny;
@@ -105,9 +106,14 @@ k_spmv(Geom g, const double* __restrict__ A, const double* __restrict__ x,
         }
         int con = cellcon[c];
         if (con >= 0) {
-            double sw = sop[con_well[con]];
+            if (ccorr != nullptr) {   // full standard wells: C_j D^-1 B x per connection
 #pragma unroll
-            for (int r = 0; r < 3; ++r) acc[r] -= wC[3 * con + r] * sw;
+                for (int r = 0; r < 3; ++r) acc[r] -= ccorr[3 * con + r];
+            } else {
+                double sw = sop[con_well[con]];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) acc[r] -= wC[3 * con + r] * sw;
+            }
         }
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -481,14 +487,10 @@ static double* d_sop(bo_sim* s) { return s->d_part + 8 * VEC_GRID; }
 template <int MODE>
 static void enqueue_op(bo_sim* s, cudaStream_t st, const double* x, double* y, const double* o1,
                        const KrylovScalars* ks) {
-    if (s->nw > 0) {
-        k_wdot<<<s->nw, 128, 0, st>>>(s->geo.n, s->d_wells, s->d_con_cell, s->d_wB, x, d_sop(s),
-                                      ks);
-        count_launch(s, st);
-    }
+    enqueue_well_dots(s, st, x, ks);
     k_spmv<MODE><<<VEC_GRID, VEC_BS, 0, st>>>(s->geo, s->d_A, x, y, s->d_cellcon,
-                                              s->d_cellcon + s->geo.n, s->d_wC, d_sop(s), o1,
-                                              s->d_part, ks);
+                                              s->d_cellcon + s->geo.n, s->d_wC, d_sop(s),
+                                              well_corr(s), o1, s->d_part, ks);
     count_launch(s, st);
     BO_LAUNCH_CHECK("k_spmv");
 }
@@ -741,12 +743,29 @@ void enqueue_op_resid(bo_sim* s, cudaStream_t st, const double* x, double* y, co
     enqueue_op<3>(s, st, x, y, b, ks);
 }
 
+const double* enqueue_well_dots(bo_sim* s, cudaStream_t st, const double* x,
+                                const KrylovScalars* ks) {
+    if (s->well_model == BO_WELL_MODEL_STANDARD) {
+        enqueue_std_well_corr(s, st, x, ks);
+        return nullptr;
+    }
+    if (s->nw > 0) {
+        k_wdot<<<s->nw, 128, 0, st>>>(s->geo.n, s->d_wells, s->d_con_cell, s->d_wB, x, d_sop(s), ks);
+        count_launch(s, st);
+    }
+    return d_sop(s);
+}
+
 void launch_op(bo_sim* s, const double* x, double* y) {
     enqueue_op<0>(s, s->stream, x, y, nullptr, nullptr);
 }
 
 void launch_well_recover(bo_sim* s) {
     if (s->nw == 0) return;
+    if (s->well_model == BO_WELL_MODEL_STANDARD) {
+        launch_std_wells_recover(s);
+        return;
+    }
     k_well_recover<<<s->nw, 128, 0, s->stream>>>(s->geo.n, s->d_wells, s->d_con_cell, s->d_wB,
                                                  s->d_xs);
     count_launch(s, s->stream);
@@ -811,7 +830,9 @@ int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool f
     // right-hand side of the reduced system
     k_rhs_copy<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b);
     count_launch(s, st);
-    if (s->nw > 0) {
+    if (s->well_model == BO_WELL_MODEL_STANDARD) {
+        enqueue_std_wells_rhs(s, st, s->d_b);
+    } else if (s->nw > 0) {
         k_rhs_wells<<<s->nw, 128, 0, st>>>(n, s->d_wells, s->d_con_cell, s->d_wC, s->d_b);
         count_launch(s, st);
     }

@@ -167,6 +167,43 @@ class Sim:
             off += nc
         return out
 
+    # -- well model ----------------------------------------------------------
+    @property
+    def well_model(self):
+        """"reduced" (one unknown per rate well) or "standard" (four unknowns
+        per well, cross-flow, wellbore storage)."""
+        v = ctypes.c_int()
+        call("bo_get_well_model", self.h, ctypes.byref(v))
+        return {q: k for k, q in L.WELL_MODEL.items()}[v.value]
+
+    def set_well_model(self, name, storage=True):
+        """Select the well model; the well unknowns start at the next
+        set_state / init_hydrostatic / init_equilibrium."""
+        call("bo_set_well_model", self.h, L.WELL_MODEL[name], 1 if storage else 0)
+
+    def std_wells(self, blocks=True):
+        """Full standard wells: per well dict(B [ncon,4,3], C [ncon,3,4],
+        D [4,4], Rw [4]) of the last assembly (blocks=True) and the current
+        unknowns xw [4] = (Q_t, F_w, F_g, p_bhp)."""
+        nw, nc = max(self.nw, 1), max(self.ncon, 1)
+        B, C = np.zeros(12 * nc), np.zeros(12 * nc)
+        D, Rw, xw = np.zeros(16 * nw), np.zeros(4 * nw), np.zeros(4 * nw)
+        if blocks:
+            call("bo_get_std_wells", self.h, ptr(B), ptr(C), ptr(D), ptr(Rw), ptr(xw))
+        else:
+            call("bo_get_std_wells", self.h, None, None, None, None, ptr(xw))
+        out, off = [], 0
+        for q in range(self.nw):
+            k = len(self.well_cells[q])
+            d = {"xw": xw[4 * q:4 * q + 4].copy()}
+            if blocks:
+                d.update(B=B[12 * off:12 * (off + k)].reshape(k, 4, 3),
+                         C=C[12 * off:12 * (off + k)].reshape(k, 3, 4),
+                         D=D[16 * q:16 * q + 16].reshape(4, 4), Rw=Rw[4 * q:4 * q + 4].copy())
+            out.append(d)
+            off += k
+        return out
+
     def well_rates(self):
         """Per-well surface rates [nw, 3] (water, oil, gas; m^3/s, production
         positive) at the last assembly, with the current BHP [nw] and control
@@ -202,9 +239,10 @@ class Sim:
         without the learned stage, 2: repeated with the FP64 sweeps)."""
         o = L.BoSolveOpts(tol=float(tol), max_it=int(maxit))
         rep = L.BoSolveReport()
-        sol = np.zeros(3 * self.n + max(self.nw, 1))
+        nwv = 4 * self.nw if self.well_model == "standard" else self.nw
+        sol = np.zeros(3 * self.n + max(nwv, 1))
         call("bo_solve", self.h, ctypes.byref(o), ctypes.byref(rep), ptr(sol))
-        out = (rep.status, rep.iterations, sol[:3 * self.n + self.nw])
+        out = (rep.status, rep.iterations, sol[:3 * self.n + nwv])
         if report:
             return out + ({"restarts": rep.restarts, "rel_res": rep.rel_res,
                            "fallback": rep.fallback},)

@@ -391,6 +391,7 @@ bo_status bo_set_properties(bo_sim* s, const double* perm, const double* poro,
         std::vector<double> rw, skin;
         s->wells_h.clear();
         s->con_cell_h.clear();
+        s->well_volume.clear();
         s->nrate = 0;
         for (int w = 0; w < nwells; ++w) {
             const bo_well& in = wells[w];
@@ -423,7 +424,9 @@ bo_status bo_set_properties(bo_sim* s, const double* perm, const double* poro,
             double thick = 0.0;
             for (int q = 0; q < in.ncon; ++q)
                 thick += s->dz[in.cells[q] / (s->geo.nx * s->geo.ny)];
-            d.vw = M_PI * in.rw * in.rw * thick;
+            s->well_volume.push_back(M_PI * in.rw * in.rw * thick);
+            d.full = 0;
+            d.vw = 0.0;
             rw.push_back(in.rw);
             skin.push_back(in.skin);
             s->wells_h.push_back(d);
@@ -1141,8 +1144,9 @@ bo_status bo_set_well_model(bo_sim* s, int model, int storage) {
         if (s->nw) {
             BO_CUDA(cudaMemcpy(w.data(), s->d_wells, sizeof(WellDev) * s->nw, cudaMemcpyDeviceToHost));
             for (int q = 0; q < s->nw; ++q) {
-                w[q].full = full ? 1 : 0;
-                w[q].vw = (full && storage) ? s->wells_h[q].vw : 0.0;
+                // the host mirror too: start_wells uploads it after an initial state
+                w[q].full = s->wells_h[q].full = full ? 1 : 0;
+                w[q].vw = s->wells_h[q].vw = (full && storage) ? s->well_volume[q] : 0.0;
             }
             BO_CUDA(cudaMemcpy(s->d_wells, w.data(), sizeof(WellDev) * s->nw, cudaMemcpyHostToDevice));
         }

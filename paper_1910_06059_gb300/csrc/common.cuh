@@ -126,6 +126,7 @@ struct bo_sim {
     int nw = 0, ncon = 0, nrate = 0;
     std::vector<bo::WellDev> wells_h;
     std::vector<int> con_cell_h;
+    std::vector<double> well_volume;   // wellbore volume per well (pi r_w^2 x perforated thickness)
 
 
     // device memory

@@ -281,7 +281,7 @@ void cpr_build(bo_sim* s) {
             v.cidx = upload(idx);
         }
         v.dinv = dzeros<double>(v.n);
-        v.x = dzeros<double>(v.n);
+        v.x = (l == 0) ? nullptr : dzeros<double>(v.n);   // level 0: the pressure column of x1
         v.y = dzeros<double>(v.n);
         v.b = dzeros<double>(v.n);
         if (l + 1 < L) {
@@ -302,6 +302,7 @@ void cpr_build(bo_sim* s) {
     c->cinv = dzeros<double>((size_t)c->nc * c->nc);
     c->w = dzeros<double>(3 * (size_t)n);
     c->x1 = dzeros<double>(3 * (size_t)n);
+    c->lv[0].x = c->x1;   // x1 = E_p x_p: its s_w and x columns stay zero
     c->r2 = dzeros<double>(3 * (size_t)n);
     c->status = dzeros<int>(1);
 }
@@ -311,7 +312,7 @@ void cpr_free(bo_sim* s) {
     if (!c) return;
     for (CprLevel& v : c->lv) {
         void* ptrs[] = {v.rowptr, v.colind, v.diag, v.val, v.dinv, v.cptr, v.cidx,
-                        v.agg,    v.mptr,   v.mem,  v.x,   v.y,    v.b};
+                        v.agg,    v.mptr,   v.mem,  v.x == c->x1 ? nullptr : v.x, v.y, v.b};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -525,6 +526,28 @@ k_cpr_jac0(Geom g, const double* __restrict__ ap, const double* __restrict__ din
         y[c] = xv(c) + CPR_OMEGA * dinv[c] * (b[c] - s);
     }
 }
+// Levels >= 1 (CSR): G lanes per row, the row's entries strided over the
+// lanes and summed by shuffles (coalesced loads of val and colind; coarse rows
+// are long).  The loops run warp-uniform so every lane reaches the shuffles.
+template <int G>
+__device__ __forceinline__ double row_dot(int i, bool active, int lane,
+                                          const int* __restrict__ rowptr,
+                                          const int* __restrict__ colind,
+                                          const double* __restrict__ val, const double* __restrict__ x,
+                                          const double* __restrict__ xc, const int* __restrict__ agg) {
+    double s = 0.0;
+    if (active)
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += G) {
+            const int j = colind[e];
+            s += val[e] * (xc ? x[j] + xc[agg[j]] : x[j]);
+        }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    return s;
+}
+
+// y = x' + omega dinv (b - A x'), x' = x + P xc when xc != nullptr
+template <int G>
 __global__ void __launch_bounds__(CPR_BS)
 k_cpr_jac(int n, const int* __restrict__ rowptr, const int* __restrict__ colind,
           const double* __restrict__ val, const double* __restrict__ dinv,
@@ -532,45 +555,60 @@ k_cpr_jac(int n, const int* __restrict__ rowptr, const int* __restrict__ colind,
           const double* __restrict__ xc, const int* __restrict__ agg, double* __restrict__ y,
           const KrylovScalars* __restrict__ ks) {
     if (ks != nullptr && ks->state != KS_RUN) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        auto xv = [&](int j) { return xc ? x[j] + xc[agg[j]] : x[j]; };
-        double s = 0.0;
-        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) s += val[e] * xv(colind[e]);
-        y[i] = xv(i) + CPR_OMEGA * dinv[i] * (b[i] - s);
+    constexpr int GW = 32 / G;   // rows per warp
+    const int lane = threadIdx.x % G, sub = (threadIdx.x & 31) / G;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = warp * GW; base < n; base += nwarps * GW) {
+        const int i = base + sub;
+        const bool active = i < n;
+        const double s = row_dot<G>(i, active, lane, rowptr, colind, val, x, xc, agg);
+        if (active && lane == 0) {
+            const double xi = xc ? x[i] + xc[agg[i]] : x[i];
+            y[i] = xi + CPR_OMEGA * dinv[i] * (b[i] - s);
+        }
     }
 }
 
-// coarse right-hand side: bc[I] = sum over the members i of I of (b - A x)_i
+// residual y = b - A x of a CSR level
+template <int G>
 __global__ void __launch_bounds__(CPR_BS)
-k_cpr_restrict0(Geom g, int nc, const int* __restrict__ mptr, const int* __restrict__ mem,
-                const double* __restrict__ ap, const double* __restrict__ b,
-                const double* __restrict__ x, double* __restrict__ bc,
-                const KrylovScalars* __restrict__ ks) {
+k_cpr_res(int n, const int* __restrict__ rowptr, const int* __restrict__ colind,
+          const double* __restrict__ val, const double* __restrict__ b,
+          const double* __restrict__ x, double* __restrict__ y,
+          const KrylovScalars* __restrict__ ks) {
     if (ks != nullptr && ks->state != KS_RUN) return;
-    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
-            const int c = mem[q];
-            s += b[c] - ax0(g, ap, c, [&](int j) { return x[j]; });
-        }
-        bc[I] = s;
+    constexpr int GW = 32 / G;
+    const int lane = threadIdx.x % G, sub = (threadIdx.x & 31) / G;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = warp * GW; base < n; base += nwarps * GW) {
+        const int i = base + sub;
+        const bool active = i < n;
+        const double s = row_dot<G>(i, active, lane, rowptr, colind, val, x, nullptr, nullptr);
+        if (active && lane == 0) y[i] = b[i] - s;
     }
 }
+
+// residual y = b - A x on level 0 (one thread per cell, coalesced)
 __global__ void __launch_bounds__(CPR_BS)
-k_cpr_restrict(int nc, const int* __restrict__ mptr, const int* __restrict__ mem,
-               const int* __restrict__ rowptr, const int* __restrict__ colind,
-               const double* __restrict__ val, const double* __restrict__ b,
-               const double* __restrict__ x, double* __restrict__ bc,
-               const KrylovScalars* __restrict__ ks) {
+k_cpr_res0(Geom g, const double* __restrict__ ap, const double* __restrict__ b,
+           const double* __restrict__ x, double* __restrict__ y,
+           const KrylovScalars* __restrict__ ks) {
+    if (ks != nullptr && ks->state != KS_RUN) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += gridDim.x * blockDim.x)
+        y[c] = b[c] - ax0(g, ap, c, [&](int j) { return x[j]; });
+}
+
+// coarse right-hand side: bc[I] = sum over the members of I (ascending) of y
+__global__ void __launch_bounds__(CPR_BS)
+k_cpr_sum(int nc, const int* __restrict__ mptr, const int* __restrict__ mem,
+          const double* __restrict__ y, double* __restrict__ bc,
+          const KrylovScalars* __restrict__ ks) {
     if (ks != nullptr && ks->state != KS_RUN) return;
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
-            const int i = mem[q];
-            double ax = 0.0;
-            for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) ax += val[e] * x[colind[e]];
-            s += b[i] - ax;
-        }
+        for (int q = mptr[I]; q < mptr[I + 1]; ++q) s += y[mem[q]];
         bc[I] = s;
     }
 }
@@ -656,8 +694,39 @@ void enqueue_cpr_setup(bo_sim* s, cudaStream_t st) {
     BO_LAUNCH_CHECK("cpr setup");
 }
 
+// CSR level kernels with G lanes per row: 32 for long coarse rows, 8 for the
+// short rows of the first coarse level.
+static int row_lanes(const CprLevel& v) { return v.nnz > 12 * (long long)v.n ? 32 : 8; }
+static int grid_rows(int n, int G) {
+    const long long t = (long long)n * G;
+    return (int)std::max<long long>(1, std::min<long long>(CPR_GRID, (t + CPR_BS - 1) / CPR_BS));
+}
+static void jac_csr(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x,
+                    const double* xc, const int* agg, double* y, const KrylovScalars* ks) {
+    if (row_lanes(v) == 32)
+        k_cpr_jac<32><<<grid_rows(v.n, 32), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.dinv,
+                                                            v.b, x, xc, agg, y, ks);
+    else
+        k_cpr_jac<8><<<grid_rows(v.n, 8), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.dinv,
+                                                          v.b, x, xc, agg, y, ks);
+    count_launch(s, st);
+}
+static void res_csr(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
+                    const KrylovScalars* ks) {
+    if (row_lanes(v) == 32)
+        k_cpr_res<32><<<grid_rows(v.n, 32), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.b, x,
+                                                            y, ks);
+    else
+        k_cpr_res<8><<<grid_rows(v.n, 8), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.b, x, y,
+                                                          ks);
+    count_launch(s, st);
+}
+
 // One V-cycle of levels l.. on lv[l].b, result in lv[l].x; on level 0 the
 // right-hand side is w^T r (or lv[0].b as it stands when r is null).
+// Pre-smoothing: two sweeps from zero (-> y -> x); restriction: the residual
+// b - A x into y, summed per aggregate into the next level's b; post-smoothing:
+// x + P xc -> y, then y -> x.
 static void vcycle(bo_sim* s, cudaStream_t st, size_t l, const double* r,
                    const KrylovScalars* ks) {
     CprData* c = s->cpr;
@@ -674,7 +743,6 @@ static void vcycle(bo_sim* s, cudaStream_t st, size_t l, const double* r,
         return;
     }
     CprLevel& w = c->lv[l + 1];
-    // pre-smoothing: two sweeps from zero (x, then y -> x)
     if (l == 0) {
         if (r)
             k_cpr_pre0<<<gr, CPR_BS, 0, st>>>(v.n, c->w, r, v.dinv, v.b, v.y, ks);
@@ -683,32 +751,25 @@ static void vcycle(bo_sim* s, cudaStream_t st, size_t l, const double* r,
         count_launch(s, st);
         k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.y, nullptr, nullptr, v.x, ks);
         count_launch(s, st);
-        k_cpr_restrict0<<<grid_for(w.n), CPR_BS, 0, st>>>(g, w.n, v.mptr, v.mem, v.val, v.b, v.x, w.b, ks);
+        k_cpr_res0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.b, v.x, v.y, ks);
         count_launch(s, st);
     } else {
         k_cpr_pre<<<gr, CPR_BS, 0, st>>>(v.n, v.b, v.dinv, v.y, ks);
         count_launch(s, st);
-        k_cpr_jac<<<gr, CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.dinv, v.b, v.y, nullptr,
-                                        nullptr, v.x, ks);
-        count_launch(s, st);
-        k_cpr_restrict<<<grid_for(w.n), CPR_BS, 0, st>>>(w.n, v.mptr, v.mem, v.rowptr, v.colind, v.val,
-                                                        v.b, v.x, w.b, ks);
-        count_launch(s, st);
+        jac_csr(s, st, v, v.y, nullptr, nullptr, v.x, ks);
+        res_csr(s, st, v, v.x, v.y, ks);
     }
+    k_cpr_sum<<<grid_for(w.n), CPR_BS, 0, st>>>(w.n, v.mptr, v.mem, v.y, w.b, ks);
+    count_launch(s, st);
     vcycle(s, st, l + 1, r, ks);
-    // post-smoothing: x + P xc, then two sweeps (x -> y -> x)
     if (l == 0) {
         k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.x, w.x, v.agg, v.y, ks);
         count_launch(s, st);
         k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.y, nullptr, nullptr, v.x, ks);
         count_launch(s, st);
     } else {
-        k_cpr_jac<<<gr, CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.dinv, v.b, v.x, w.x, v.agg,
-                                        v.y, ks);
-        count_launch(s, st);
-        k_cpr_jac<<<gr, CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.dinv, v.b, v.y, nullptr,
-                                        nullptr, v.x, ks);
-        count_launch(s, st);
+        jac_csr(s, st, v, v.x, w.x, v.agg, v.y, ks);
+        jac_csr(s, st, v, v.y, nullptr, nullptr, v.x, ks);
     }
 }
 
@@ -736,7 +797,6 @@ void enqueue_cpr_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
     const int n = s->geo.n;
     enqueue_cpr_pressure(s, st, r, ks);
     // r2 = r - S x1, x1 = E_p x_p (the wells' dots read x1's pressure part)
-    BO_CUDA(cudaMemcpyAsync(c->x1, c->lv[0].x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     const double* sop = enqueue_well_dots(s, st, c->x1, ks);
     k_cpr_resid<<<grid_for(n), CPR_BS, 0, st>>>(s->geo, s->d_A, c->lv[0].x, r, s->d_cellcon,
                                                s->d_cellcon + n, s->d_wC, sop, well_corr(s),

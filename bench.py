@@ -575,6 +575,38 @@ def shard_members(count, rank, world):
     return [q for q in range(count) if q % world == rank]
 
 
+def ensemble_cpu_baseline(models, snap, dt, threads, budget_s=25.0):
+    """The oracle, as it stands, on whole report steps of ensemble members
+    (smallest first, from the same state as the timed steps) until about
+    budget_s seconds of CPU work: no extrapolation, the cells of the members
+    it finished over its time."""
+    import oracle
+    oracle.set_threads(threads)
+    order = sorted(range(len(models)), key=lambda q: models[q]["nx"] * models[q]["ny"] * models[q]["nz"])
+    cells, sec, done = 0, 0.0, []
+    for q in order:
+        if sec >= budget_s:
+            break
+        m = models[q]
+        o = oracle.Oracle(m)
+        st, d = snap[q]
+        o.set_state(*st)
+        o.dt_next = d
+        t0 = time.perf_counter()
+        status, _ = o.step(dt)
+        sec += time.perf_counter() - t0
+        if status == 0:
+            cells += m["nx"] * m["ny"] * m["nz"]
+            done.append(q)
+    oracle.set_threads(1)
+    if not done:
+        return None
+    return {"value": cells / sec, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
+            "sample": (f"one whole report step of {len(done)} members, smallest first "
+                       f"({cells} cells, {sec:.1f} s on {threads} threads)"),
+            "host": host_cpu()}
+
+
 def run_ensemble(args):
     """Config 3: the ensemble of uneven members stepped together (batched
     form), against the same members stepped one at a time on one stream.
@@ -600,24 +632,66 @@ def run_ensemble(args):
         ens.step(dt)
     torch.cuda.synchronize()
     snap = [(s.get_state(), s.dt_next) for s in ens.members]
+    # ---- timed region: K report steps, one loop; every step takes each
+    # member's state in from pinned host memory and back out through the
+    # C ABI; the device time of the step itself comes from the ensemble's
+    # CUDA events (members run on up to 64 streams)
+    bufs = [(pinned_state(sm), pinned_state(sm)) for sm in ens.members]
+    h_in = [b[0][1] for b in bufs]
+    h_out = [b[1][1] for b in bufs]
+    for hb, (st, _) in zip(h_in, snap):
+        for dst, src in zip(hb, st):
+            dst[:len(src)] = src
+    for sm in ens.members:
+        sm.set_timing(True)
+    launches0 = sum(sm.launches for sm in ens.members)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    reps = []
+    reps, dev_ms, e2e_s = [], 0.0, 0.0
     for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for sm, hb in zip(ens.members, h_in):
+            sm.set_state(*hb)
         _, r = ens.step(dt)
+        ms = ens.last_step_ms()
+        for sm, hb in zip(ens.members, h_out):
+            sm.get_state(out=hb)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        dev_ms = dev_ms + ms if ms >= 0 and dev_ms >= 0 else -1.0
         reps.append(r)
-    torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
+        h_in, h_out = h_out, h_in
     clk = clocks.stop()
+    launches = sum(sm.launches for sm in ens.members) - launches0
+    timers = [sm.timing() for sm in ens.members]
+    for sm in ens.members:
+        sm.set_timing(False)
+    sec = dev_ms / 1e3 if dev_ms > 0 else e2e_s
     sec = max_over_ranks(sec, world, "cuda")
+    e2e_s = max_over_ranks(e2e_s, world, "cuda")
+    h2d = int(sum(sum(a.nbytes for a in hb[:4]) + 8 * sm.nw for sm, hb in zip(ens.members, h_in)))
     if rank != 0:
         ens.close()
         dist.destroy_process_group()
         return
+    # roofline of the forward sweep, averaged over every member's launches
+    # (members share the SMs, so a launch takes longer than alone)
+    fw = [(t["ilu_fwd_sweep"], sm.n) for t, sm in zip(timers, ens.members) if "ilu_fwd_sweep" in t]
+    tot_ms = sum(v[0][0] for v in fw)
+    nl = sum(v[0][1] for v in fw)
+    byt = sum(ALGO_BYTES_PER_CELL["ilu_fwd_sweep"] * c * v[0][1] for v, c in fw)
+    pk = peaks()
+    roof = None
+    if tot_ms > 0 and nl > 0:
+        ach = byt / (tot_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "ilu_fwd_sweep", "achieved": round(ach, 1),
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4),
+                "traffic": None, "algorithmic_bytes": int(byt / nl),
+                "peak_source": pk["source"], "avg_launch_ms": round(tot_ms / nl, 4),
+                "launches": nl, "note": "all members' launches; members run concurrently"}
     # the same first report step, members one at a time on one stream, on a
     # sample of the members (largest and smallest mixed as in the ensemble)
     k = min(args.seq_sample, len(models))
@@ -632,12 +706,16 @@ def run_ensemble(args):
     seq.step(dt)
     torch.cuda.synchronize()
     sec_seq = time.perf_counter() - t1
+    ms_seq = seq.last_step_ms()
     seq.close()
     cells_sample = sum(s.n for s in sample)
-    seq_value = cells_sample / sec_seq
+    seq_value = cells_sample / (ms_seq / 1e3 if ms_seq > 0 else sec_seq)
     value = all_cells * args.steps / sec
     lin = sum(r["lin_its"] for rs in reps for r in rs)
     newton = sum(r["newton_its"] for rs in reps for r in rs)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = ensemble_cpu_baseline(models, snap, dt, host_cpu()["nproc"])
     out = {
         "metric": "cell-steps/s at 1e-6 Newton tol: plain FP64 vs mixed/learned/batched",
         "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
@@ -648,17 +726,23 @@ def run_ensemble(args):
                                 "plain FP64 ILU0-BiCGStab per member, Newton tol 1e-6"),
                    "cells": all_cells, "members": args.members,
                    "schedule": tune["chosen"],
-                   "timing": "host clock between device-wide synchronisations (members run on "
-                             "up to 64 streams)",
+                   "timing": "CUDA events bracketing every worker stream of the step",
                    "l2": "members' Jacobians and ILU data together exceed L2",
                    "parallelism": f"members split over {world} GPUs" if world > 1 else "single GPU"},
         "clocks": clk,
+        "e2e": {"value": all_cells * args.steps / e2e_s, "unit": "cell-steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                "path": "bo_set_state (pinned host) per member + bo_ensemble_step + "
+                        "bo_get_state (pinned host) per member"},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
         "autotune_probe_s": tune,
         "sequential": {"value": seq_value, "unit": "cell-steps/s",
                        "sample": f"first report step of {k} members one at a time on one stream "
-                                 f"({cells_sample} cells, {sec_seq:.2f} s)"},
+                                 f"({cells_sample} cells, {sec_seq:.2f} s host clock, "
+                                 f"{ms_seq / 1e3:.2f} s device events)"},
         "iterations": {"newton": newton, "lin_its": lin},
-        "e2e": None, "roofline": None, "cpu_baseline": None,
     }
     print(json.dumps(out))
     ens.close()

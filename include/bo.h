@@ -496,7 +496,12 @@ bo_status bo_learn_loss_grad(bo_sim* sim, const double* r, double* loss, double*
  *   orders, putting every member's state and step control back after each
  *   probe, and keeps the fastest schedule whose probe succeeded;
  *   seconds[2 * ncand] (may be NULL) receives the probe times, largest-first
- *   order first.  BO_ERR_NOT_CONVERGED if no probe succeeded. */
+ *   order first.  BO_ERR_NOT_CONVERGED if no probe succeeded.
+ * bo_ensemble_last_step_ms: device time of the last bo_ensemble_step (or
+ *   autotune probe) in milliseconds, measured with CUDA events: from an
+ *   event every worker stream waits on before its first member to an event
+ *   recorded after every worker stream's last member; -1 when it could not
+ *   be measured. */
 typedef struct bo_ensemble bo_ensemble;
 bo_status bo_ensemble_create(bo_sim* const* members, int count, int streams, bo_ensemble** out);
 bo_status bo_ensemble_set_schedule(bo_ensemble* ens, int streams, int largest_first);
@@ -505,6 +510,7 @@ bo_status bo_ensemble_step(bo_ensemble* ens, double dt, const bo_newton_opts* op
                            bo_step_report* reports, bo_status* statuses);
 bo_status bo_ensemble_autotune(bo_ensemble* ens, double dt_probe, const bo_newton_opts* opts,
                                const int* candidates, int ncand, double* seconds);
+bo_status bo_ensemble_last_step_ms(const bo_ensemble* ens, double* ms);
 bo_status bo_ensemble_destroy(bo_ensemble* ens);
 
 /* Self-test of failure detection: runs the bounded device-side wait of the

@@ -30,6 +30,12 @@ struct bo_ensemble {
     int active = 1;                  // streams in use
     bool largest_first = true;
     int device = 0;
+    // device time of a step: every worker stream waits on ev_start before its
+    // first member and records ev_done[w] after its last; tstream joins them
+    cudaStream_t tstream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+    std::vector<cudaEvent_t> ev_done;
+    double last_ms = -1.0;
 };
 
 namespace {
@@ -84,9 +90,27 @@ void run_step(bo_ensemble* e, double dt, const bo_newton_opts* opts, bo_step_rep
             if (statuses) statuses[q] = BO_ERR_CUDA;
         return;
     }
+    // device-side bracket of the whole step (events of this ensemble)
+    bool timed = e->ev_start != nullptr ||
+                 (cudaStreamCreateWithFlags(&e->tstream, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreate(&e->ev_start) == cudaSuccess &&
+                  cudaEventCreate(&e->ev_end) == cudaSuccess);
+    if (timed && (int)e->ev_done.size() < nworkers) {
+        for (int w = (int)e->ev_done.size(); w < nworkers; ++w) {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                timed = false;
+                break;
+            }
+            e->ev_done.push_back(ev);
+        }
+    }
+    timed = timed && cudaEventRecord(e->ev_start, e->tstream) == cudaSuccess;
+    e->last_ms = -1.0;
     auto work = [&](int w) {
         cudaSetDevice(e->device);
         cudaStream_t st = e->streams[w];
+        if (timed) cudaStreamWaitEvent(st, e->ev_start, 0);
         for (;;) {
             const int q = next.fetch_add(1);
             if (q >= count) break;
@@ -100,6 +124,7 @@ void run_step(bo_ensemble* e, double dt, const bo_newton_opts* opts, bo_step_rep
             if (reports) reports[id] = rep;
             if (statuses) statuses[id] = s;
         }
+        if (timed) cudaEventRecord(e->ev_done[w], st);
     };
     std::vector<std::thread> pool;
     pool.reserve(nworkers);
@@ -111,6 +136,14 @@ void run_step(bo_ensemble* e, double dt, const bo_newton_opts* opts, bo_step_rep
     }
     work(0);
     for (auto& t : pool) t.join();
+    if (timed) {
+        for (int w = 0; w < nworkers; ++w) cudaStreamWaitEvent(e->tstream, e->ev_done[w], 0);
+        float ms = 0.f;
+        if (cudaEventRecord(e->ev_end, e->tstream) == cudaSuccess &&
+            cudaEventSynchronize(e->ev_end) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e->ev_start, e->ev_end) == cudaSuccess)
+            e->last_ms = ms;
+    }
 }
 
 }  // namespace
@@ -242,10 +275,21 @@ bo_status bo_ensemble_autotune(bo_ensemble* e, double dt_probe, const bo_newton_
                           "bo_ensemble_autotune: no candidate schedule stepped every member");
 }
 
+bo_status bo_ensemble_last_step_ms(const bo_ensemble* e, double* ms) {
+    if (e == nullptr || ms == nullptr)
+        return set_last_error(BO_ERR_INVALID_ARG, "bo_ensemble_last_step_ms: NULL argument");
+    *ms = e->last_ms;
+    return BO_OK;
+}
+
 bo_status bo_ensemble_destroy(bo_ensemble* e) {
     if (e == nullptr) return set_last_error(BO_ERR_INVALID_ARG, "bo_ensemble_destroy: NULL ensemble");
     for (auto& s : e->streams)
         if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t ev : e->ev_done) cudaEventDestroy(ev);
+    if (e->ev_start) cudaEventDestroy(e->ev_start);
+    if (e->ev_end) cudaEventDestroy(e->ev_end);
+    if (e->tstream) cudaStreamDestroy(e->tstream);
     delete e;
     return BO_OK;
 }

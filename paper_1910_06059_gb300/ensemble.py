@@ -69,6 +69,12 @@ class Ensemble:
                 "substeps": r.substeps} for r in reps]
         return list(sts), out
 
+    def last_step_ms(self):
+        """Device time (CUDA events) of the last step, in ms (-1: not measured)."""
+        v = ctypes.c_double()
+        call("bo_ensemble_last_step_ms", self.h, ctypes.byref(v))
+        return v.value
+
     def autotune(self, dt_probe, candidates=(1, 2, 4, 8, 16, 32), **opts):
         """Pick the worker count and order by timing a probe step of each
         candidate (states restored after each probe); returns the probe times."""

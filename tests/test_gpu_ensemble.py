@@ -7,6 +7,8 @@ and the autotuner must leave every member's state as it found it.
 """
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import pytest
 
@@ -43,8 +45,14 @@ def test_ensemble_equals_members_stepped_alone():
     for s in alone:
         s.init_hydrostatic()
     for days in (1.0, 3.0):
+        t0 = time.perf_counter()
         sts, reps = ens.step(days * synth.DAY)
+        host_ms = 1e3 * (time.perf_counter() - t0)
         assert all(st == 0 for st in sts)
+        # the step's device time (events bracketing every worker stream) is
+        # measured and lies within the host's view of the same call
+        ms = ens.last_step_ms()
+        assert 0.0 < ms <= host_ms
         for q, s in enumerate(alone):
             st, rep = s.step(days * synth.DAY)
             assert st == 0

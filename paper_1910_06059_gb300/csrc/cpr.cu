@@ -24,9 +24,11 @@
 //
 // GPU layout: level 0 is the 7-point pressure matrix in the Jacobian's
 // layout ap[b][n] (b: diag, -x, +x, -y, +y, -z, +z; zero where no
-// neighbour); coarser levels are CSR.  Restriction sums each aggregate's
-// members in ascending order (no atomics); prolongation reads the
-// aggregate of each node.  The coarsest matrix is inverted per Newton
+// neighbour); coarser levels are CSR (what the Galerkin sums and the
+// coarsest inverse read) with an ELL copy for the V-cycle (one thread per
+// row, coalesced).  Restriction forms each level's residual once and sums
+// each aggregate's members in ascending order (no atomics); prolongation
+// adds each node's aggregate value.  The coarsest matrix is inverted per Newton
 // system by one CTA (Gauss-Jordan, partial pivoting) and applied as a dense
 // product.  All kernels are memory-bound streaming kernels; the V-cycle is
 // captured in the BiCGStab iteration's CUDA graph.
@@ -44,6 +46,7 @@ constexpr int CPR_COARSE = 200;
 constexpr int CPR_MAX_LEVELS = 12;
 constexpr int CPR_BS = 256;
 constexpr int CPR_GRID = 152 * 4;
+constexpr int CPR_GRID_ROWS = 152 * 8;   // coarse-level rows: latency-bound gathers, full occupancy
 
 struct CprLevel {
     int n = 0, nnz = 0;
@@ -53,6 +56,11 @@ struct CprLevel {
     // Galerkin lists: entry e of this level = sum of the previous level's
     // entries cidx[cptr[e] .. cptr[e + 1])
     int *cptr = nullptr, *cidx = nullptr;
+    // the same operator in ELL form for the V-cycle: width W (the longest
+    // row), entry e of row i at e n + i; padding has column i and value 0
+    int W = 0;
+    int* ecol = nullptr;
+    double* eval = nullptr;
     // to the next level: agg[i] = aggregate of node i; members of aggregate I
     // are mem[mptr[I] .. mptr[I + 1]) (ascending)
     int *agg = nullptr, *mptr = nullptr, *mem = nullptr;
@@ -279,6 +287,17 @@ void cpr_build(bo_sim* s) {
                     idx[fill[target[q]]++] = (l == 1) ? l0_entry(i, F.ci[q], g) : q;
             v.cptr = upload(cnt);
             v.cidx = upload(idx);
+            int W = 0;
+            for (int I = 0; I < v.n; ++I) W = std::max(W, A[l].rp[I + 1] - A[l].rp[I]);
+            std::vector<int> ec((size_t)W * v.n);
+            for (int I = 0; I < v.n; ++I)
+                for (int e = 0; e < W; ++e) {
+                    const int q = A[l].rp[I] + e;
+                    ec[(size_t)e * v.n + I] = q < A[l].rp[I + 1] ? A[l].ci[q] : I;
+                }
+            v.W = W;
+            v.ecol = upload(ec);
+            v.eval = dzeros<double>((size_t)W * v.n);
         }
         v.dinv = dzeros<double>(v.n);
         v.x = (l == 0) ? nullptr : dzeros<double>(v.n);   // level 0: the pressure column of x1
@@ -311,8 +330,9 @@ void cpr_free(bo_sim* s) {
     CprData* c = s->cpr;
     if (!c) return;
     for (CprLevel& v : c->lv) {
-        void* ptrs[] = {v.rowptr, v.colind, v.diag, v.val, v.dinv, v.cptr, v.cidx,
-                        v.agg,    v.mptr,   v.mem,  v.x == c->x1 ? nullptr : v.x, v.y, v.b};
+        void* ptrs[] = {v.rowptr, v.colind, v.diag, v.val, v.dinv, v.cptr, v.cidx, v.ecol,
+                        v.eval,   v.agg,    v.mptr, v.mem, v.x == c->x1 ? nullptr : v.x,
+                        v.y,      v.b};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -357,12 +377,14 @@ k_cpr_level0(int n, const double* __restrict__ A, double* __restrict__ w, double
 __global__ void __launch_bounds__(CPR_BS)
 k_cpr_galerkin(int nc, const int* __restrict__ rowptr, const int* __restrict__ diag,
                const int* __restrict__ cptr, const int* __restrict__ cidx,
-               const double* __restrict__ fine, double* __restrict__ val, double* __restrict__ dinv) {
+               const double* __restrict__ fine, double* __restrict__ val, double* __restrict__ eval,
+               double* __restrict__ dinv) {
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
         for (int e = rowptr[I]; e < rowptr[I + 1]; ++e) {
             double s = 0.0;
             for (int q = cptr[e]; q < cptr[e + 1]; ++q) s += fine[cidx[q]];
             val[e] = s;
+            eval[(size_t)(e - rowptr[I]) * nc + I] = s;
         }
         dinv[I] = 1.0 / val[diag[I]];
     }
@@ -512,82 +534,56 @@ k_cpr_pre(int n, const double* __restrict__ b, const double* __restrict__ dinv,
         x[c] = CPR_OMEGA * dinv[c] * b[c];
 }
 
-// y = x + omega dinv (b - A x'), x' = x + P xc when xc != nullptr (prolongation
-// of the coarse correction folded into the sweep: y then also carries it)
+// y = x + omega dinv (b - A x) on level 0
 __global__ void __launch_bounds__(CPR_BS)
 k_cpr_jac0(Geom g, const double* __restrict__ ap, const double* __restrict__ dinv,
-           const double* __restrict__ b, const double* __restrict__ x,
-           const double* __restrict__ xc, const int* __restrict__ agg, double* __restrict__ y,
+           const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ y,
            const KrylovScalars* __restrict__ ks) {
     if (ks != nullptr && ks->state != KS_RUN) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += gridDim.x * blockDim.x) {
-        auto xv = [&](int j) { return xc ? x[j] + xc[agg[j]] : x[j]; };
-        const double s = ax0(g, ap, c, xv);
-        y[c] = xv(c) + CPR_OMEGA * dinv[c] * (b[c] - s);
+        const double s = ax0(g, ap, c, [&](int j) { return x[j]; });
+        y[c] = x[c] + CPR_OMEGA * dinv[c] * (b[c] - s);
     }
 }
-// Levels >= 1 (CSR): G lanes per row, the row's entries strided over the
-// lanes and summed by shuffles (coalesced loads of val and colind; coarse rows
-// are long).  The loops run warp-uniform so every lane reaches the shuffles.
-template <int G>
-__device__ __forceinline__ double row_dot(int i, bool active, int lane,
-                                          const int* __restrict__ rowptr,
-                                          const int* __restrict__ colind,
-                                          const double* __restrict__ val, const double* __restrict__ x,
-                                          const double* __restrict__ xc, const int* __restrict__ agg) {
+// Levels >= 1 in ELL form: one thread per row, the W entries of a row read
+// at e n + i (coalesced over the rows of a warp), all loads of a row
+// independent of each other.
+__device__ __forceinline__ double ell_dot(int n, int W, int i, const int* __restrict__ col,
+                                          const double* __restrict__ val,
+                                          const double* __restrict__ x) {
     double s = 0.0;
-    if (active)
-        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += G) {
-            const int j = colind[e];
-            s += val[e] * (xc ? x[j] + xc[agg[j]] : x[j]);
-        }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    for (int e = 0; e < W; ++e) s += val[(size_t)e * n + i] * x[col[(size_t)e * n + i]];
     return s;
 }
 
-// y = x' + omega dinv (b - A x'), x' = x + P xc when xc != nullptr
-template <int G>
+// y = x + omega dinv (b - A x)
 __global__ void __launch_bounds__(CPR_BS)
-k_cpr_jac(int n, const int* __restrict__ rowptr, const int* __restrict__ colind,
-          const double* __restrict__ val, const double* __restrict__ dinv,
-          const double* __restrict__ b, const double* __restrict__ x,
-          const double* __restrict__ xc, const int* __restrict__ agg, double* __restrict__ y,
-          const KrylovScalars* __restrict__ ks) {
-    if (ks != nullptr && ks->state != KS_RUN) return;
-    constexpr int GW = 32 / G;   // rows per warp
-    const int lane = threadIdx.x % G, sub = (threadIdx.x & 31) / G;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int base = warp * GW; base < n; base += nwarps * GW) {
-        const int i = base + sub;
-        const bool active = i < n;
-        const double s = row_dot<G>(i, active, lane, rowptr, colind, val, x, xc, agg);
-        if (active && lane == 0) {
-            const double xi = xc ? x[i] + xc[agg[i]] : x[i];
-            y[i] = xi + CPR_OMEGA * dinv[i] * (b[i] - s);
-        }
-    }
-}
-
-// residual y = b - A x of a CSR level
-template <int G>
-__global__ void __launch_bounds__(CPR_BS)
-k_cpr_res(int n, const int* __restrict__ rowptr, const int* __restrict__ colind,
-          const double* __restrict__ val, const double* __restrict__ b,
+k_cpr_jac(int n, int W, const int* __restrict__ col, const double* __restrict__ val,
+          const double* __restrict__ dinv, const double* __restrict__ b,
           const double* __restrict__ x, double* __restrict__ y,
           const KrylovScalars* __restrict__ ks) {
     if (ks != nullptr && ks->state != KS_RUN) return;
-    constexpr int GW = 32 / G;
-    const int lane = threadIdx.x % G, sub = (threadIdx.x & 31) / G;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int base = warp * GW; base < n; base += nwarps * GW) {
-        const int i = base + sub;
-        const bool active = i < n;
-        const double s = row_dot<G>(i, active, lane, rowptr, colind, val, x, nullptr, nullptr);
-        if (active && lane == 0) y[i] = b[i] - s;
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = x[i] + CPR_OMEGA * dinv[i] * (b[i] - ell_dot(n, W, i, col, val, x));
+}
+
+// residual y = b - A x
+__global__ void __launch_bounds__(CPR_BS)
+k_cpr_res(int n, int W, const int* __restrict__ col, const double* __restrict__ val,
+          const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ y,
+          const KrylovScalars* __restrict__ ks) {
+    if (ks != nullptr && ks->state != KS_RUN) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = b[i] - ell_dot(n, W, i, col, val, x);
+}
+
+// coarse correction: x += P xc (each node takes its aggregate's value)
+__global__ void __launch_bounds__(CPR_BS)
+k_cpr_prolong(int n, const double* __restrict__ xc, const int* __restrict__ agg,
+              double* __restrict__ x, const KrylovScalars* __restrict__ ks) {
+    if (ks != nullptr && ks->state != KS_RUN) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] += xc[agg[i]];
 }
 
 // residual y = b - A x on level 0 (one thread per cell, coalesced)
@@ -684,7 +680,7 @@ void enqueue_cpr_setup(bo_sim* s, cudaStream_t st) {
     for (size_t l = 1; l < c->lv.size(); ++l) {
         CprLevel& v = c->lv[l];
         k_cpr_galerkin<<<grid_for(v.n), CPR_BS, 0, st>>>(v.n, v.rowptr, v.diag, v.cptr, v.cidx,
-                                                        c->lv[l - 1].val, v.val, v.dinv);
+                                                        c->lv[l - 1].val, v.val, v.eval, v.dinv);
         count_launch(s, st);
     }
     const CprLevel& last = c->lv.back();
@@ -694,31 +690,18 @@ void enqueue_cpr_setup(bo_sim* s, cudaStream_t st) {
     BO_LAUNCH_CHECK("cpr setup");
 }
 
-// CSR level kernels with G lanes per row: 32 for long coarse rows, 8 for the
-// short rows of the first coarse level.
-static int row_lanes(const CprLevel& v) { return v.nnz > 12 * (long long)v.n ? 32 : 8; }
-static int grid_rows(int n, int G) {
-    const long long t = (long long)n * G;
-    return (int)std::max<long long>(1, std::min<long long>(CPR_GRID, (t + CPR_BS - 1) / CPR_BS));
+static int grid_for_rows(int n) {
+    return std::max(1, std::min(CPR_GRID_ROWS, (n + CPR_BS - 1) / CPR_BS));
 }
-static void jac_csr(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x,
-                    const double* xc, const int* agg, double* y, const KrylovScalars* ks) {
-    if (row_lanes(v) == 32)
-        k_cpr_jac<32><<<grid_rows(v.n, 32), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.dinv,
-                                                            v.b, x, xc, agg, y, ks);
-    else
-        k_cpr_jac<8><<<grid_rows(v.n, 8), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.dinv,
-                                                          v.b, x, xc, agg, y, ks);
+static void jac_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
+                    const KrylovScalars* ks) {
+    k_cpr_jac<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.dinv, v.b, x, y,
+                                                    ks);
     count_launch(s, st);
 }
-static void res_csr(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
+static void res_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
                     const KrylovScalars* ks) {
-    if (row_lanes(v) == 32)
-        k_cpr_res<32><<<grid_rows(v.n, 32), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.b, x,
-                                                            y, ks);
-    else
-        k_cpr_res<8><<<grid_rows(v.n, 8), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val, v.b, x, y,
-                                                          ks);
+    k_cpr_res<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.b, x, y, ks);
     count_launch(s, st);
 }
 
@@ -726,7 +709,7 @@ static void res_csr(bo_sim* s, cudaStream_t st, const CprLevel& v, const double*
 // right-hand side is w^T r (or lv[0].b as it stands when r is null).
 // Pre-smoothing: two sweeps from zero (-> y -> x); restriction: the residual
 // b - A x into y, summed per aggregate into the next level's b; post-smoothing:
-// x + P xc -> y, then y -> x.
+// x += P xc, then two sweeps x -> y -> x.
 static void vcycle(bo_sim* s, cudaStream_t st, size_t l, const double* r,
                    const KrylovScalars* ks) {
     CprData* c = s->cpr;
@@ -749,27 +732,29 @@ static void vcycle(bo_sim* s, cudaStream_t st, size_t l, const double* r,
         else
             k_cpr_pre<<<gr, CPR_BS, 0, st>>>(v.n, v.b, v.dinv, v.y, ks);
         count_launch(s, st);
-        k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.y, nullptr, nullptr, v.x, ks);
+        k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.y, v.x, ks);
         count_launch(s, st);
         k_cpr_res0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.b, v.x, v.y, ks);
         count_launch(s, st);
     } else {
         k_cpr_pre<<<gr, CPR_BS, 0, st>>>(v.n, v.b, v.dinv, v.y, ks);
         count_launch(s, st);
-        jac_csr(s, st, v, v.y, nullptr, nullptr, v.x, ks);
-        res_csr(s, st, v, v.x, v.y, ks);
+        jac_ell(s, st, v, v.y, v.x, ks);
+        res_ell(s, st, v, v.x, v.y, ks);
     }
     k_cpr_sum<<<grid_for(w.n), CPR_BS, 0, st>>>(w.n, v.mptr, v.mem, v.y, w.b, ks);
     count_launch(s, st);
     vcycle(s, st, l + 1, r, ks);
+    k_cpr_prolong<<<gr, CPR_BS, 0, st>>>(v.n, w.x, v.agg, v.x, ks);
+    count_launch(s, st);
     if (l == 0) {
-        k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.x, w.x, v.agg, v.y, ks);
+        k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.x, v.y, ks);
         count_launch(s, st);
-        k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.y, nullptr, nullptr, v.x, ks);
+        k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.y, v.x, ks);
         count_launch(s, st);
     } else {
-        jac_csr(s, st, v, v.x, w.x, v.agg, v.y, ks);
-        jac_csr(s, st, v, v.y, nullptr, nullptr, v.x, ks);
+        jac_ell(s, st, v, v.x, v.y, ks);
+        jac_ell(s, st, v, v.y, v.x, ks);
     }
 }
 

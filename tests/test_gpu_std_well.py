@@ -186,20 +186,20 @@ def test_std_well_linear_solution(name):
     st, its, sol = g.solve(tol=1e-13, maxit=1000)
     assert st == 0, its
     n = o.n
-    # per unknown family, relative to the family's largest update; a family
-    # whose update is below 1e-9 of its natural size (the r_go updates of
-    # an undersaturated state over a short step) is judged absolutely on
-    # that size, where both solutions are rounding noise of the solve
-    p, sw, x, fl = o.cells()
-    natural = [np.abs(p).max(), 1.0, max(np.abs(x).max(), 1.0)]
-    for v in range(3):
-        a, b = sol[v:3 * n:3], dx[v:3 * n:3]
-        scale = max(np.abs(b).max(), 1e-9 * natural[v])
-        assert np.abs(a - b).max() <= 1e-9 * scale, (v, np.abs(a - b).max(), scale)
     # the GPU solution solves the oracle's unreduced system
     res = J @ sol - R
     for a in range(3):
         assert np.abs(res[a:3 * n:3]).max() <= 1e-9 * np.abs(R[a:3 * n:3]).max(), a
+    # per unknown family: 1e-9 of the family's largest update, plus 1e-11 of
+    # the variable's own size (an update family far below its variable's
+    # size, like the r_go updates of an undersaturated state over a short
+    # step, is rounding noise of the solve on both sides)
+    p, sw, x, fl = o.cells()
+    natural = [np.abs(p).max(), 1.0, max(np.abs(x).max(), 1.0)]
+    for v in range(3):
+        a, b = sol[v:3 * n:3], dx[v:3 * n:3]
+        bar = 1e-9 * np.abs(b).max() + 1e-11 * natural[v]
+        assert np.abs(a - b).max() <= bar, (v, np.abs(a - b).max(), bar)
     for k in range(o.nw):
         a, b = sol[3 * n + 4 * k:3 * n + 4 * k + 4], dx[3 * n + 4 * k:3 * n + 4 * k + 4]
         scale = np.array([abs(o.wells[k]["x"][0]) + abs(b[0]), 1.0, 1.0, abs(o.wells[k]["x"][3])])

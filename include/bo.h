@@ -306,6 +306,23 @@ bo_status bo_apply_op(bo_sim* sim, const double* x, double* y);
 bo_status bo_solve(bo_sim* sim, const bo_solve_opts* opts, bo_solve_report* report,
                    double* sol);
 
+/* The same linear solve as K subdomains (Section 2.5: each process owns the
+ * rows of its subdomain, exchanges one ghost layer before every operator
+ * product, applies ILU(0) to its own block and joins the inner products by
+ * an all-reduce), emulated on one GPU.  The subdomains are the y slabs set
+ * by bo_set_subdomains (ysub > 0, zsub = 0; K = ceil(ny / ysub)); the
+ * Krylov vectors and the Jacobian rows live in a subdomain-local layout with
+ * ghost rows, the halo exchange is a device copy, each inner product is a
+ * per-subdomain sum followed by a sum over the subdomains in order, and the
+ * preconditioner is the same block-Jacobi ILU(0) as bo_solve's (so the
+ * iteration equals bo_solve's up to the grouping of the inner products).
+ * The scalars of the iteration come back to the host once per
+ * half-iteration (no CUDA graph).  Requires FP64 sweeps, ILU(0), the reduced
+ * well model and no learned stage (BO_ERR_STATE otherwise); sol and report
+ * as for bo_solve (restarts, rel_res and fallback are reported as 0). */
+bo_status bo_dd_solve(bo_sim* sim, const bo_solve_opts* opts, bo_solve_report* report,
+                      double* sol);
+
 /* Newton update from the last bo_solve: dy = -sol with chop and variable
  * switching as in bo_newton_opts; wells on rate control that pass their BHP
  * limit switch to BHP control. */

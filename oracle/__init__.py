@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
         if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
             os.makedirs(os.path.dirname(_SO), exist_ok=True)
             tmp = _SO + f".tmp{os.getpid()}"
-            subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC",
+            subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-pthread", "-shared", "-fPIC",
                                    "-o", tmp, _SRC])
             os.replace(tmp, _SO)
     return _SO
@@ -79,6 +79,8 @@ def lib():
         L.orc_apply_op.argtypes = [P, P, P]
         L.orc_solve.argtypes = [P, d, i, P, P]
         L.orc_solve.restype = i
+        L.orc_dd_solve.argtypes = [P, d, i, P, P]
+        L.orc_dd_solve.restype = i
         L.orc_newton_update.argtypes = [P, P, P]
         L.orc_step.argtypes = [P, d, P, P]
         L.orc_step.restype = i
@@ -298,6 +300,15 @@ class Oracle:
         sol = np.zeros(3 * self.n + max(self.nw, 1))
         its = np.zeros(1, dtype=np.int32)
         st = lib().orc_solve(self.h, float(tol), int(maxit), _p(sol), _p(its))
+        return st, int(its[0]), sol[:3 * self.n + self.nw]
+
+    def dd_solve(self, tol=1e-3, maxit=500):
+        """solve() as K host-thread ranks, one per y slab of the block-Jacobi
+        subdomains (set_subdomains(ysub), no z cuts): local rows, halo
+        exchange, all-reduced inner products."""
+        sol = np.zeros(3 * self.n + max(self.nw, 1))
+        its = np.zeros(1, dtype=np.int32)
+        st = lib().orc_dd_solve(self.h, float(tol), int(maxit), _p(sol), _p(its))
         return st, int(its[0]), sol[:3 * self.n + self.nw]
 
     def newton_update(self, sol, **opts):

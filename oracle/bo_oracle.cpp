@@ -43,8 +43,11 @@
 // Full three-phase trajectories are pinned only through those invariants.
 
 #include <cmath>
+#include <condition_variable>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <thread>
 #include <vector>
 #include <algorithm>
 
@@ -820,6 +823,339 @@ static int solve(Model& m, double tol, int maxit, double* sol, int* its_out) {
 }
 
 // ---------------------------------------------------------------------------
+// Domain decomposition (Section 2.5) emulated with K host threads, one per
+// subdomain: slabs of ysub cell rows in y (the block-Jacobi slabs of the
+// preconditioner).  Each rank keeps its interior rows of the operator with
+// columns in its own index space (interior plus one ghost row on each side
+// that has a neighbour), its own ILU(0) block factorised from those rows, the
+// wells whose columns it holds, and its slice of every Krylov vector.  Before
+// each operator product the ranks exchange their boundary rows (halo); every
+// inner product is a local sum in row order followed by an all-reduce (the
+// K local sums added in rank order by every rank).  The iteration is the
+// BiCGStab of `solve` step for step, so with K = 1 it is `solve` bit for bit;
+// with K > 1 only the grouping of the inner products' sums differs.
+// ---------------------------------------------------------------------------
+struct DdBarrier {
+    std::mutex mu;
+    std::condition_variable cv;
+    int n, count = 0;
+    long gen = 0;
+    explicit DdBarrier(int k) : n(k) {}
+    void wait() {
+        std::unique_lock<std::mutex> lock(mu);
+        const long g = gen;
+        if (++count == n) {
+            count = 0;
+            ++gen;
+            cv.notify_all();
+        } else {
+            cv.wait(lock, [&] { return gen != g; });
+        }
+    }
+};
+
+struct DdRank {
+    int nx = 0, j0 = 0, j1 = 0, gl = 0, gh = 0, nyl = 0, nint = 0, ntot = 0;
+    std::vector<int> gcell;   // interior index -> global cell
+    std::vector<int> lpos;    // interior index -> position in the ghosted local layout
+    std::vector<int> rp, ci, diag;   // local operator rows (columns: local positions)
+    std::vector<double> val, lu, Uinv;
+    std::vector<int> wells;   // wells whose connection cells lie in this slab
+    std::vector<double> send_lo, send_hi;   // boundary rows for the neighbours
+};
+
+// global cell (inside the rank's slab or its ghost rows) -> ghosted position
+static int local_of(const Model& m, const DdRank& d, int c) {
+    const int i = c % m.nx, j = (c / m.nx) % m.ny, k = c / (m.nx * m.ny);
+    return i + m.nx * (j - d.j0 + d.gl + d.nyl * k);
+}
+// global cell of the slab -> interior index (natural order inside the slab)
+static int interior_of(const Model& m, const DdRank& d, int c) {
+    const int i = c % m.nx, j = (c / m.nx) % m.ny, k = c / (m.nx * m.ny);
+    return i + m.nx * (j - d.j0 + (d.j1 - d.j0) * k);
+}
+// ghosted position -> interior index, -1 for a ghost
+static int interior_pos(const DdRank& d, int pos) {
+    const int jl = (pos / d.nx) % d.nyl;
+    if (jl < d.gl || jl >= d.nyl - d.gh) return -1;
+    const int i = pos % d.nx, k = pos / (d.nx * d.nyl);
+    return i + d.nx * (jl - d.gl + (d.j1 - d.j0) * k);
+}
+
+static int dd_solve(Model& m, double tol, int maxit, double* sol, int* its_out) {
+    const int n = m.n, nx = m.nx, ny = m.ny, nz = m.nz;
+    *its_out = 0;
+    if (m.ysub <= 0 || m.zsub > 0) return LIN_FACTOR_FAIL;   // y slabs only
+    const int K = (ny + m.ysub - 1) / m.ysub;
+    std::vector<DdRank> R(K);
+    for (int k = 0; k < K; ++k) {
+        DdRank& d = R[k];
+        d.nx = nx;
+        d.j0 = k * m.ysub;
+        d.j1 = std::min(ny, d.j0 + m.ysub);
+        d.gl = k > 0 ? 1 : 0;
+        d.gh = k + 1 < K ? 1 : 0;
+        d.nyl = d.j1 - d.j0 + d.gl + d.gh;
+        d.ntot = nx * d.nyl * nz;
+        auto local = [&](int c) {   // global cell -> local position (inside the ghosted slab)
+            const int i = c % nx, j = (c / nx) % ny, kk = c / (nx * ny);
+            return i + nx * (j - d.j0 + d.gl + d.nyl * kk);
+        };
+        for (int kk = 0; kk < nz; ++kk)
+            for (int j = d.j0; j < d.j1; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const int c = cidx(m, i, j, kk);
+                    d.gcell.push_back(c);
+                    d.lpos.push_back(local(c));
+                }
+        d.nint = (int)d.gcell.size();
+        // local operator rows (all blocks) and the ILU(0) block (in-slab blocks)
+        d.rp.push_back(0);
+        for (int ii = 0; ii < d.nint; ++ii) {
+            const int c = d.gcell[ii];
+            for (int q = m.rowptr[c]; q < m.rowptr[c + 1]; ++q) {
+                d.ci.push_back(local(m.colind[q]));
+                d.val.insert(d.val.end(), &m.vals[9 * q], &m.vals[9 * q] + 9);
+                if (m.colind[q] == c) d.diag.push_back((int)d.ci.size() - 1);
+            }
+            d.rp.push_back((int)d.ci.size());
+        }
+        for (size_t w = 0; w < m.wells.size(); ++w) {
+            const int c0 = m.wells[w].cells[0];
+            const int j = (c0 / nx) % ny;
+            if (j >= d.j0 && j < d.j1) d.wells.push_back((int)w);
+        }
+    }
+    // ILU(0) of each block: the textbook elimination on the rank's rows with
+    // the blocks of other slabs left out (they are zero in the block-Jacobi M)
+    auto in_slab = [&](const DdRank& d, int pos) {
+        const int jl = (pos / nx) % d.nyl;
+        return jl >= d.gl && jl < d.nyl - d.gh;
+    };
+    std::vector<int> pos2int;
+    for (DdRank& d : R) {
+        pos2int.assign(d.ntot, -1);
+        for (int ii = 0; ii < d.nint; ++ii) pos2int[d.lpos[ii]] = ii;
+        d.lu = d.val;
+        for (int ii = 0; ii < d.nint; ++ii)
+            for (int q = d.rp[ii]; q < d.rp[ii + 1]; ++q)
+                if (!in_slab(d, d.ci[q]))
+                    for (int e = 0; e < 9; ++e) d.lu[9 * q + e] = 0.0;
+        d.Uinv.assign(9 * (size_t)d.nint, 0.0);
+        auto find = [&](int row, int colpos) {
+            for (int q = d.rp[row]; q < d.rp[row + 1]; ++q)
+                if (d.ci[q] == colpos) return q;
+            return -1;
+        };
+        for (int ii = 0; ii < d.nint; ++ii) {
+            for (int q = d.rp[ii]; q < d.rp[ii + 1]; ++q) {
+                const int kk = pos2int[d.ci[q]];
+                if (d.ci[q] >= d.lpos[ii]) break;
+                if (kk < 0) continue;   // a ghost column: its block is zero
+                double L[9];
+                mm3(&d.lu[9 * q], &d.Uinv[9 * kk], L);
+                std::memcpy(&d.lu[9 * q], L, sizeof(L));
+                for (int qk = d.rp[kk]; qk < d.rp[kk + 1]; ++qk) {
+                    if (d.ci[qk] <= d.lpos[kk]) continue;
+                    const int qi = find(ii, d.ci[qk]);
+                    if (qi < 0) continue;
+                    double P[9];
+                    mm3(L, &d.lu[9 * qk], P);
+                    for (int e = 0; e < 9; ++e) d.lu[9 * qi + e] -= P[e];
+                }
+            }
+            if (!inv3(&d.lu[9 * d.diag[ii]], &d.Uinv[9 * ii])) return LIN_FACTOR_FAIL;
+        }
+    }
+    // right-hand side of the reduced system, sliced per rank
+    std::vector<double> bglob(m.R);
+    for (const Well& w : m.wells) {
+        if (w.control != 0) continue;
+        const double s = w.Rw / w.Dw;
+        for (size_t con = 0; con < w.cells.size(); ++con)
+            for (int e = 0; e < 3; ++e) bglob[3 * w.cells[con] + e] -= w.C[3 * con + e] * s;
+    }
+    DdBarrier bar(K);
+    std::vector<double> partial(K, 0.0);
+    std::vector<int> status(K, LIN_OK), its(K, 0);
+    auto rank_main = [&](int k) {
+        DdRank& d = R[k];
+        const int Ni = 3 * d.nint;
+        auto allreduce = [&](double v) {
+            partial[k] = v;
+            bar.wait();
+            double s = 0.0;
+            for (int q = 0; q < K; ++q) s += partial[q];
+            bar.wait();
+            return s;
+        };
+        auto dotl = [&](const std::vector<double>& a, const std::vector<double>& b) {
+            double s = 0.0;
+            for (int q = 0; q < Ni; ++q) s += a[q] * b[q];
+            return allreduce(s);
+        };
+        // x in the ghosted layout (3 per position); interior vectors are [3 nint]
+        const int plane = nx;   // cells of one x-line
+        auto halo = [&](std::vector<double>& xl) {
+            // send: the first and the last interior row of every z layer
+            const int rows = d.j1 - d.j0;
+            d.send_lo.resize(3 * (size_t)plane * nz);
+            d.send_hi.resize(3 * (size_t)plane * nz);
+            for (int kk = 0; kk < nz; ++kk)
+                for (int i = 0; i < nx; ++i)
+                    for (int e = 0; e < 3; ++e) {
+                        d.send_lo[3 * (i + nx * kk) + e] = xl[3 * (i + nx * (d.gl + d.nyl * kk)) + e];
+                        d.send_hi[3 * (i + nx * kk) + e] =
+                            xl[3 * (i + nx * (d.gl + rows - 1 + d.nyl * kk)) + e];
+                    }
+            bar.wait();
+            for (int kk = 0; kk < nz; ++kk)
+                for (int i = 0; i < nx; ++i)
+                    for (int e = 0; e < 3; ++e) {
+                        if (d.gl) xl[3 * (i + nx * (0 + d.nyl * kk)) + e] = R[k - 1].send_hi[3 * (i + nx * kk) + e];
+                        if (d.gh) xl[3 * (i + nx * (d.nyl - 1 + d.nyl * kk)) + e] = R[k + 1].send_lo[3 * (i + nx * kk) + e];
+                    }
+            bar.wait();
+        };
+        std::vector<double> gx(3 * (size_t)d.ntot, 0.0);   // ghosted work vector
+        // y = S x for interior x (halo exchanged inside); wells of this rank
+        auto op = [&](const std::vector<double>& xi, std::vector<double>& y) {
+            for (int ii = 0; ii < d.nint; ++ii)
+                for (int e = 0; e < 3; ++e) gx[3 * d.lpos[ii] + e] = xi[3 * ii + e];
+            halo(gx);
+            for (int ii = 0; ii < d.nint; ++ii) {
+                double acc[3] = {0, 0, 0};
+                for (int q = d.rp[ii]; q < d.rp[ii + 1]; ++q) {
+                    double t[3];
+                    mv3(&d.val[9 * q], &gx[3 * d.ci[q]], t);
+                    for (int e = 0; e < 3; ++e) acc[e] += t[e];
+                }
+                for (int e = 0; e < 3; ++e) y[3 * ii + e] = acc[e];
+            }
+            for (int wi : d.wells) {
+                const Well& w = m.wells[wi];
+                if (w.control != 0) continue;
+                double bx = 0.0;
+                for (size_t con = 0; con < w.cells.size(); ++con)
+                    for (int v = 0; v < 3; ++v) bx += w.B[3 * con + v] * gx[3 * (size_t)local_of(m, d, w.cells[con]) + v];
+                const double s = bx / w.Dw;
+                for (size_t con = 0; con < w.cells.size(); ++con) {
+                    const int ii = interior_of(m, d, w.cells[con]);
+                    for (int e = 0; e < 3; ++e) y[3 * ii + e] -= w.C[3 * con + e] * s;
+                }
+            }
+        };
+        // z = M_k^-1 r on the rank's block
+        std::vector<double> yv(Ni);
+        auto prec = [&](const std::vector<double>& r, std::vector<double>& z) {
+            for (int ii = 0; ii < d.nint; ++ii) {
+                double acc[3] = {r[3 * ii], r[3 * ii + 1], r[3 * ii + 2]};
+                for (int q = d.rp[ii]; q < d.diag[ii]; ++q) {
+                    const int kk = interior_pos(d, d.ci[q]);
+                    if (kk < 0) continue;
+                    double t[3];
+                    mv3(&d.lu[9 * q], &yv[3 * kk], t);
+                    for (int e = 0; e < 3; ++e) acc[e] -= t[e];
+                }
+                for (int e = 0; e < 3; ++e) yv[3 * ii + e] = acc[e];
+            }
+            for (int ii = d.nint - 1; ii >= 0; --ii) {
+                double acc[3] = {yv[3 * ii], yv[3 * ii + 1], yv[3 * ii + 2]};
+                for (int q = d.diag[ii] + 1; q < d.rp[ii + 1]; ++q) {
+                    const int kk = interior_pos(d, d.ci[q]);
+                    if (kk < 0) continue;
+                    double t[3];
+                    mv3(&d.lu[9 * q], &z[3 * kk], t);
+                    for (int e = 0; e < 3; ++e) acc[e] -= t[e];
+                }
+                mv3(&d.Uinv[9 * ii], acc, &z[3 * ii]);
+            }
+        };
+        std::vector<double> b(Ni);
+        for (int ii = 0; ii < d.nint; ++ii)
+            for (int e = 0; e < 3; ++e) b[3 * ii + e] = bglob[3 * d.gcell[ii] + e];
+        std::vector<double> x(Ni, 0.0), r(b), rh(b), p(Ni, 0.0), v(Ni, 0.0), ph(Ni), s(Ni), sh(Ni), t(Ni);
+        const double nr0 = std::sqrt(dotl(r, r));
+        int it_done = 0;
+        auto cycle = [&]() -> int {
+            double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+            for (int it = it_done + 1; it <= maxit; ++it) {
+                const double rho = dotl(rh, r);
+                if (rho == 0.0 || !std::isfinite(rho)) return LIN_BREAKDOWN;
+                const double beta = (rho / rho_old) * (alpha / omega);
+                for (int i = 0; i < Ni; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+                prec(p, ph);
+                op(ph, v);
+                const double rv = dotl(rh, v);
+                if (rv == 0.0 || !std::isfinite(rv)) return LIN_BREAKDOWN;
+                alpha = rho / rv;
+                for (int i = 0; i < Ni; ++i) s[i] = r[i] - alpha * v[i];
+                const double ns = std::sqrt(dotl(s, s));
+                if (ns <= tol * nr0) {
+                    for (int i = 0; i < Ni; ++i) x[i] += alpha * ph[i];
+                    it_done = it;
+                    return LIN_OK;
+                }
+                prec(s, sh);
+                op(sh, t);
+                const double tt = dotl(t, t);
+                if (tt == 0.0 || !std::isfinite(tt)) return LIN_BREAKDOWN;
+                omega = dotl(t, s) / tt;
+                if (omega == 0.0 || !std::isfinite(omega)) return LIN_BREAKDOWN;
+                for (int i = 0; i < Ni; ++i) {
+                    x[i] += alpha * ph[i] + omega * sh[i];
+                    r[i] = s[i] - omega * t[i];
+                }
+                const double nr = std::sqrt(dotl(r, r));
+                it_done = it;
+                if (nr <= tol * nr0) return LIN_OK;
+                rho_old = rho;
+            }
+            return LIN_NOT_CONVERGED;
+        };
+        int st = nr0 == 0.0 ? LIN_OK : cycle();
+        for (int restarts = 0; st == LIN_OK && nr0 > 0.0; ++restarts) {
+            op(x, t);
+            for (int i = 0; i < Ni; ++i) r[i] = b[i] - t[i];
+            const double nt = std::sqrt(dotl(r, r));
+            if (nt <= tol * nr0) break;
+            if (restarts >= 8 || it_done >= maxit || !std::isfinite(nt)) {
+                st = LIN_NOT_CONVERGED;
+                break;
+            }
+            rh = r;
+            std::fill(p.begin(), p.end(), 0.0);
+            std::fill(v.begin(), v.end(), 0.0);
+            st = cycle();
+        }
+        if (st == LIN_NOT_CONVERGED) it_done = maxit;
+        for (int ii = 0; ii < d.nint; ++ii)
+            for (int e = 0; e < 3; ++e) sol[3 * d.gcell[ii] + e] = x[3 * ii + e];
+        // the owned wells' unknowns
+        for (int wi : d.wells) {
+            const Well& w = m.wells[wi];
+            double xw = 0.0;
+            if (w.control == 0) {
+                double bx = 0.0;
+                for (size_t con = 0; con < w.cells.size(); ++con)
+                    for (int v2 = 0; v2 < 3; ++v2)
+                        bx += w.B[3 * con + v2] * x[3 * interior_of(m, d, w.cells[con]) + v2];
+                xw = (w.Rw - bx) / w.Dw;
+            }
+            sol[3 * n + wi] = xw;
+        }
+        status[k] = st;
+        its[k] = it_done;
+    };
+    std::vector<std::thread> th;
+    for (int k = 1; k < K; ++k) th.emplace_back(rank_main, k);
+    rank_main(0);
+    for (auto& t : th) t.join();
+    *its_out = its[0];
+    return status[0];
+}
+
+// ---------------------------------------------------------------------------
 // Newton update (Section 2.3): dy = -sol; Appleyard chop; variable switching.
 // ---------------------------------------------------------------------------
 struct Opts {
@@ -1293,6 +1629,13 @@ void orc_apply_op(void* h, const double* x, double* y) { apply_op(*static_cast<M
 
 int orc_solve(void* h, double tol, int maxit, double* sol, int* its) {
     return solve(*static_cast<Model*>(h), tol, maxit, sol, its);
+}
+
+// The same solve with one host thread per y slab of the block-Jacobi
+// subdomains (orc_set_subdomains with ysub > 0, zsub = 0): local rows,
+// halo exchange and all-reduced inner products.
+int orc_dd_solve(void* h, double tol, int maxit, double* sol, int* its) {
+    return dd_solve(*static_cast<Model*>(h), tol, maxit, sol, its);
 }
 
 void orc_newton_update(void* h, const double* opts, const double* sol) {

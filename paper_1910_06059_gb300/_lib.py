@@ -124,6 +124,7 @@ _SIGS = {
     "bo_get_timing": [P, c_int, P, P, P, P],
     "bo_get_launch_count": [P, P],
     "bo_set_well_model": [P, c_int, c_int],
+    "bo_dd_solve": [P, P, P, P],
     "bo_get_well_model": [P, P],
     "bo_get_std_wells": [P, P, P, P, P, P],
     "bo_set_preconditioner": [P, c_int],

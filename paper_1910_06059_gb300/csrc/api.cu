@@ -76,6 +76,7 @@ void download_aos3(const bo_sim* s, const double* dev, double* host) {
 static void free_all(bo_sim* s) {
     destroy_graphs(s);
     cpr_free(s);
+    dd_free(s);
     void* ptrs[] = {s->d_dx, s->d_dy, s->d_dz, s->d_perm, s->d_poro, s->d_T, s->d_pv, s->d_depth,
                     s->d_p, s->d_sw, s->d_x, s->d_flag, s->d_bk, s->d_bkflag, s->d_A0,
                     s->d_props, s->d_R, s->d_A, s->d_P, s->d_yt, s->d_qt, s->d_order, s->d_face, s->d_cellcon, s->d_wells,
@@ -783,6 +784,42 @@ bo_status bo_solve(bo_sim* s, const bo_solve_opts* o, bo_solve_report* rep, doub
             } else {
                 for (int q = 0; q < s->nw; ++q) sol[3 * (size_t)s->geo.n + q] = w[q].xw;
             }
+        }
+    });
+}
+
+bo_status bo_dd_solve(bo_sim* s, const bo_solve_opts* o, bo_solve_report* rep, double* sol) {
+    return guarded([&] {
+        need(s && s->assembled, BO_ERR_STATE, "bo_dd_solve: no assembly");
+        need(o && o->tol > 0 && o->max_it > 0, BO_ERR_INVALID_ARG, "bo_dd_solve: bad options");
+        need(s->ysub > 0 && s->zsub == 0, BO_ERR_STATE,
+             "bo_dd_solve: the subdomains are y slabs: call bo_set_subdomains with ysub > 0, zsub = 0");
+        need(!s->mixed && s->precond == BO_PRECOND_ILU0 && !s->ml_on &&
+                 s->well_model == BO_WELL_MODEL_REDUCED,
+             BO_ERR_STATE, "bo_dd_solve: needs FP64 ILU(0) sweeps, no learned stage, reduced wells");
+        launch_factor(s);
+        read_status(s);
+        check_timeout(s);
+        int its = 0, st = LS_BREAKDOWN;
+        if (s->h_ns->pad == 0) {
+            s->factored = true;
+            st = dd_bicgstab(s, o->tol, o->max_it, &its);
+            check_timeout(s);
+            launch_well_recover(s);
+            s->solved = true;
+        }
+        sync(s);
+        if (rep) {
+            std::memset(rep, 0, sizeof(*rep));
+            rep->iterations = its;
+            rep->status = st;
+        }
+        if (sol) {
+            download_aos3(s, s->d_xs, sol);
+            std::vector<WellDev> w(s->nw);
+            if (s->nw)
+                BO_CUDA(cudaMemcpy(w.data(), s->d_wells, sizeof(WellDev) * s->nw, cudaMemcpyDeviceToHost));
+            for (int q = 0; q < s->nw; ++q) sol[3 * (size_t)s->geo.n + q] = w[q].xw;
         }
     });
 }

@@ -102,6 +102,7 @@ struct NewtonStatus {
 constexpr int MAX_TIMERS = 16;
 
 struct CprData;   // CPR preconditioner data (cpr.cu)
+struct DdData;    // K-subdomain solver data (dd.cu)
 
 }  // namespace bo
 
@@ -210,6 +211,7 @@ struct bo_sim {
     // CPR two-stage preconditioner (cpr.cu); precond: BO_PRECOND_*
     int precond = 0;
     bo::CprData* cpr = nullptr;
+    bo::DdData* dd = nullptr;   // K-subdomain solver (dd.cu)
 
     // CUDA graphs of one BiCGStab iteration block and of the factorisation
     cudaGraphExec_t g_iter = nullptr;
@@ -274,6 +276,11 @@ void launch_well_recover(bo_sim* s);
 // the preconditioner application of BiCGStab: ILU(0) or CPR, z = M^-1 r
 void enqueue_precond_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
                            const KrylovScalars* ks);
+// right-hand side of the well-reduced system into d_b
+void enqueue_reduced_rhs(bo_sim* s, cudaStream_t st);
+// K-subdomain solve (dd.cu): returns LS_*
+int dd_bicgstab(bo_sim* s, double tol, int maxit, int* its);
+void dd_free(bo_sim* s);
 // y = b - S x with the well-reduced operator S (dot partials clobbered)
 void enqueue_op_resid(bo_sim* s, cudaStream_t st, const double* x, double* y, const double* b,
                       const KrylovScalars* ks);

@@ -824,10 +824,9 @@ static void replay_iterations(bo_sim* s, cudaGraphExec_t g, bool timed, int* pre
     }
 }
 
-int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool fp64) {
+// Right-hand side of the reduced system into d_b: b = R - sum_w C_w D_w^-1 R_w.
+void enqueue_reduced_rhs(bo_sim* s, cudaStream_t st) {
     const int n = s->geo.n, N = 3 * n;
-    cudaStream_t st = s->stream;
-    // right-hand side of the reduced system
     k_rhs_copy<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b);
     count_launch(s, st);
     if (s->well_model == BO_WELL_MODEL_STANDARD) {
@@ -836,6 +835,12 @@ int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool f
         k_rhs_wells<<<s->nw, 128, 0, st>>>(n, s->d_wells, s->d_con_cell, s->d_wC, s->d_b);
         count_launch(s, st);
     }
+}
+
+int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool fp64) {
+    const int N = 3 * s->geo.n;
+    cudaStream_t st = s->stream;
+    enqueue_reduced_rhs(s, st);
     k_krylov_init<<<VEC_GRID, VEC_BS, 0, st>>>(N, s->d_R, s->d_b, s->d_xs, s->d_r, s->d_rh,
                                                s->d_pk, s->d_v, s->d_part);
     count_launch(s, st);

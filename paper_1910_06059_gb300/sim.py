@@ -248,6 +248,16 @@ class Sim:
                            "fallback": rep.fallback},)
         return out
 
+    def dd_solve(self, tol=1e-3, maxit=500):
+        """solve() as K subdomains (the y slabs of `subdomains`): subdomain-
+        local vectors with ghost rows, device halo copies, all-reduced inner
+        products.  Returns (status, iterations, sol[3n + nw])."""
+        o = L.BoSolveOpts(tol=float(tol), max_it=int(maxit))
+        rep = L.BoSolveReport()
+        sol = np.zeros(3 * self.n + max(self.nw, 1))
+        call("bo_dd_solve", self.h, ctypes.byref(o), ctypes.byref(rep), ptr(sol))
+        return rep.status, rep.iterations, sol[:3 * self.n + self.nw]
+
     def newton_update(self, **opts):
         o = L.newton_opts(**opts)
         call("bo_newton_update", self.h, ctypes.byref(o))

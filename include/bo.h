@@ -465,6 +465,18 @@ bo_status bo_learn_get_params(bo_sim* sim, double* theta, int nparam);
 /* Stage on (1) or off (0) inside BiCGStab (bo_solve, bo_step); re-records the
  * solver graphs.  Requires parameters. */
 bo_status bo_learn_enable(bo_sim* sim, int on);
+/* Tensor-core kernel of the network (run once per factorisation):
+ * BO_LEARN_ENGINE_TCGEN05 (default) issues tcgen05.mma kind::f16 from one
+ * thread per CTA on 128-cell tiles with the accumulators in tensor memory;
+ * BO_LEARN_ENGINE_MMA_SYNC uses warp-level mma.sync m16n8k16.  Both take BF16
+ * weights and activations with FP32 accumulation (results equal up to the
+ * order of the FP32 sums).  A tcgen05 layer that does not complete within its
+ * bounded wait fails the factorisation (the linear solve reports a
+ * breakdown).  BO_ERR_INVALID_ARG for another value. */
+#define BO_LEARN_ENGINE_MMA_SYNC 0
+#define BO_LEARN_ENGINE_TCGEN05 1
+bo_status bo_learn_set_engine(bo_sim* sim, int engine);
+bo_status bo_learn_get_engine(const bo_sim* sim, int* engine);
 /* Online training: with opts non-NULL every later linear solve (bo_solve,
  * bo_step) keeps its first opts->samples BiCGStab residuals and then takes
  * opts->epochs Adam passes over them on that system; NULL turns it off.

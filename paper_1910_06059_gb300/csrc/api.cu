@@ -975,6 +975,27 @@ bo_status bo_learn_get_params(bo_sim* s, double* theta, int nparam) {
     });
 }
 
+bo_status bo_learn_set_engine(bo_sim* s, int engine) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_learn_set_engine: sim is NULL");
+        need(engine == BO_LEARN_ENGINE_MMA_SYNC || engine == BO_LEARN_ENGINE_TCGEN05,
+             BO_ERR_INVALID_ARG, "bo_learn_set_engine: engine must be BO_LEARN_ENGINE_*");
+        if (engine == s->ml_engine) return;
+        sync(s);
+        s->ml_engine = engine;
+        if (s->props_set) build_graphs(s);   // the factorisation graph runs the network
+        if (s->ml_on && s->assembled) enqueue_learn_features(s, s->stream);
+        sync(s);
+    });
+}
+
+bo_status bo_learn_get_engine(const bo_sim* s, int* engine) {
+    return guarded([&] {
+        need(s != nullptr && engine != nullptr, BO_ERR_INVALID_ARG, "bo_learn_get_engine: NULL argument");
+        *engine = s->ml_engine;
+    });
+}
+
 bo_status bo_learn_enable(bo_sim* s, int on) {
     return guarded([&] {
         need(s != nullptr, BO_ERR_INVALID_ARG, "bo_learn_enable: sim is NULL");

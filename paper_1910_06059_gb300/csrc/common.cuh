@@ -195,6 +195,7 @@ struct bo_sim {
     double* d_ml_samples = nullptr;  // [cap][3n] residual samples
     int ml_cap = 0;
     int ml_adam_t = 0;
+    int ml_engine = 1;             // BO_LEARN_ENGINE_*: tensor-core kernel of the network
     bool ml_params = false;        // parameters set
     bool ml_on = false;            // the stage runs inside BiCGStab
     bool ml_online = false;        // collect residuals and train after each solve

@@ -247,6 +247,254 @@ k_ml_net(int n, const __nv_bfloat16* __restrict__ feat, const __nv_bfloat16* __r
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same network on the fifth-generation tensor cores (tcgen05).  A CTA
+// takes 128 cells at a time (the MMA's M = 128); each layer is one chain of
+// tcgen05.mma kind::f16 -- BF16 operands in shared memory, FP32 accumulators
+// in tensor memory -- issued by one thread and completed on an mbarrier; the
+// layer's epilogue reads the accumulator rows back with tcgen05.ld (thread t
+// of warp w holds row 32 w + t), adds the bias, applies ReLU, rounds to BF16
+// and writes the next layer's operand tile.  Tensor memory: 256 columns,
+// layer 1 in columns 0..127, layer 2 in 128..255, layer 3 in 0..15.
+//
+// Operand tiles are K-major without swizzling, in 8-row x 16-byte core
+// matrices: row r, column k of a tile with K columns sits at byte
+// (r / 8) SBO + (k / 8) 128 + (r % 8) 16 + (k % 8) 2, SBO = (K / 8) 128, so
+// the leading (K-direction) core-matrix offset is 128 and one MMA (K = 16,
+// two core matrices) advances the start address by 256 bytes.
+// ---------------------------------------------------------------------------
+constexpr int TC_BS = 128;   // four warps: one per 32 accumulator lanes
+constexpr int TC_W1 = 0, TC_W2 = TC_W1 + 128 * 64 * 2, TC_W3 = TC_W2 + 128 * 128 * 2,
+              TC_X = TC_W3 + 16 * 128 * 2, TC_H = TC_X + 128 * 64 * 2,
+              TC_BIAS = TC_H + 128 * 128 * 2, TC_MBAR = TC_BIAS + (2 * MLH + N3) * 4,
+              TC_TADDR = TC_MBAR + 8, TC_FLAG = TC_TADDR + 4, TC_SMEM = TC_FLAG + 4;
+constexpr uint32_t TC_COLS = 256;
+constexpr long long TC_WAIT_LIMIT = 1LL << 24;   // polls of a layer's completion
+
+__device__ __forceinline__ uint32_t tc_smem(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor: start, leading and stride byte offsets
+// (each >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N / 8 and M / 16
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_proxy_fence() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// 16 consecutive FP32 accumulator columns of this thread's lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ bool tc_mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// byte offset of (row r, column k) in a K-major no-swizzle tile of K columns
+__device__ __forceinline__ uint32_t tc_off(int r, int k, int K) {
+    return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+// copy rows x K of a row-major BF16 matrix (row stride ld elements, 16-byte
+// aligned rows) into a tile; rows >= valid are zero
+__device__ __forceinline__ void tc_fill(unsigned char* tile, const __nv_bfloat16* src, int rows,
+                                        int K, int ld, int valid) {
+    const int chunks = K / 8;
+    for (int q = threadIdx.x; q < rows * chunks; q += blockDim.x) {
+        const int r = q / chunks, kc = q % chunks;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r < valid) v = *reinterpret_cast<const uint4*>(src + (size_t)r * ld + kc * 8);
+        *reinterpret_cast<uint4*>(tile + tc_off(r, kc * 8, K)) = v;
+    }
+}
+
+// Thread 0 waits (bounded) for the layer's MMAs; the outcome reaches every
+// thread through shared memory, so all threads take the same path.
+__device__ __forceinline__ bool tc_layer_done(uint32_t mbar, uint32_t parity, int* flag) {
+    if (threadIdx.x == 0) {
+        long long q = 0;
+        while (!tc_mbar_try(mbar, parity) && ++q < TC_WAIT_LIMIT) {
+        }
+        *flag = q < TC_WAIT_LIMIT ? 1 : 0;
+    }
+    __syncthreads();
+    const bool ok = *reinterpret_cast<volatile int*>(flag) != 0;
+    tc_fence_after();
+    return ok;
+}
+
+// accumulator columns [col, col + ncols) of this thread's row + bias, ReLU,
+// BF16 into the hidden tile (K = 128)
+__device__ __forceinline__ void tc_hidden(uint32_t taddr, int col, const float* bias,
+                                          unsigned char* H) {
+    const int warp = threadIdx.x >> 5, row = threadIdx.x;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+#pragma unroll 1
+    for (int cb = 0; cb < 8; ++cb) {
+        float v[16];
+        tc_ld16(taddr + lane_base + (uint32_t)(col + 16 * cb), v);
+        unsigned u[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            u[k] = pack_bf16(fmaxf(v[2 * k] + bias[16 * cb + 2 * k], 0.f),
+                             fmaxf(v[2 * k + 1] + bias[16 * cb + 2 * k + 1], 0.f));
+        *reinterpret_cast<uint4*>(H + tc_off(row, 16 * cb, 128)) = make_uint4(u[0], u[1], u[2], u[3]);
+        *reinterpret_cast<uint4*>(H + tc_off(row, 16 * cb + 8, 128)) = make_uint4(u[4], u[5], u[6], u[7]);
+    }
+}
+
+// W[q][c] = N(f_c)[q], q < 9, for every cell; *bad is set if a layer's MMAs
+// did not complete within the wait limit.
+__global__ void __launch_bounds__(TC_BS)
+k_ml_net_tc(int n, const __nv_bfloat16* __restrict__ feat, const __nv_bfloat16* __restrict__ wbf,
+            const float* __restrict__ theta, float* __restrict__ Wc, int* __restrict__ bad) {
+    extern __shared__ __align__(1024) unsigned char tc_sm[];
+    unsigned char* W1 = tc_sm + TC_W1;
+    unsigned char* W2 = tc_sm + TC_W2;
+    unsigned char* W3 = tc_sm + TC_W3;
+    unsigned char* X = tc_sm + TC_X;
+    unsigned char* H = tc_sm + TC_H;
+    float* bias = reinterpret_cast<float*>(tc_sm + TC_BIAS);   // b1[128], b2[128], b3[16]
+    const uint32_t mbar = tc_smem(tc_sm + TC_MBAR);
+    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(tc_sm + TC_TADDR);
+    int* flag = reinterpret_cast<int*>(tc_sm + TC_FLAG);
+    const int warp = threadIdx.x >> 5;
+    // weights into the tile layout, biases
+    tc_fill(W1, wbf, 128, 64, K1P, 128);
+    tc_fill(W2, wbf + W1S, 128, 128, K2P, 128);
+    tc_fill(W3, wbf + W1S + W2S, 16, 128, K2P, 16);
+    for (int q = threadIdx.x; q < 2 * MLH + N3; q += blockDim.x)
+        bias[q] = q < MLH ? theta[OFF_B1 + q]
+                          : (q < 2 * MLH ? theta[OFF_B2 + q - MLH]
+                                         : (q - 2 * MLH < MLO ? theta[OFF_B3 + q - 2 * MLH] : 0.f));
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc_smem(taddr_slot)),
+                     "r"(TC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *taddr_slot;
+    constexpr uint32_t ID1 = tc_idesc(128, 128), ID3 = tc_idesc(128, 16);
+    uint32_t parity = 0;
+    bool ok = true;
+    for (int base = blockIdx.x * 128; base < n && ok; base += gridDim.x * 128) {
+        // stage 128 cells x 64 features
+        tc_fill(X, feat + (size_t)base * 64, 128, 64, 64, min(128, n - base));
+        tc_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {   // layer 1: K = 64 -> accumulator columns 0..127
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                tc_mma(taddr, tc_desc(tc_smem(X) + 256 * s, 128, 1024),
+                       tc_desc(tc_smem(W1) + 256 * s, 128, 1024), ID1, s > 0);
+            tc_commit(mbar);
+        }
+        ok = tc_layer_done(mbar, parity, flag);
+        parity ^= 1u;
+        if (!ok) break;
+        tc_hidden(taddr, 0, bias, H);
+        tc_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {   // layer 2: K = 128 -> columns 128..255
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                tc_mma(taddr + 128, tc_desc(tc_smem(H) + 256 * s, 128, 2048),
+                       tc_desc(tc_smem(W2) + 256 * s, 128, 2048), ID1, s > 0);
+            tc_commit(mbar);
+        }
+        ok = tc_layer_done(mbar, parity, flag);
+        parity ^= 1u;
+        if (!ok) break;
+        tc_hidden(taddr, 128, bias + MLH, H);   // H is free: layer 2 has read it
+        tc_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {   // layer 3: N = 16 -> columns 0..15
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                tc_mma(taddr, tc_desc(tc_smem(H) + 256 * s, 128, 2048),
+                       tc_desc(tc_smem(W3) + 256 * s, 128, 2048), ID3, s > 0);
+            tc_commit(mbar);
+        }
+        ok = tc_layer_done(mbar, parity, flag);
+        parity ^= 1u;
+        if (!ok) break;
+        float v[16];
+        tc_ld16(taddr + ((uint32_t)(32 * warp) << 16), v);
+        const int c = base + threadIdx.x;
+        if (c < n)
+#pragma unroll
+            for (int q = 0; q < MLO; ++q) Wc[(size_t)q * n + c] = v[q] + bias[2 * MLH + q];
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            atomicExch(bad, 1);
+            long long q = 0;   // the layer still in flight: a second bounded wait
+            while (!tc_mbar_try(mbar, parity ^ 1u) && ++q < TC_WAIT_LIMIT) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_COLS)
+                     : "memory");
+    }
+}
+
 // z += delta(r): delta_c[v] = sigma_v sum_e W_c[3 v + e] r_c[e] / rho_c[e]
 // (ks: skip when the solve has finished).  FP32 products, FP64 accumulation
 // into z.
@@ -671,6 +919,7 @@ void learn_setup(bo_sim* s) {
     ml_alloc(&s->d_ml_part, 2 * ML_GRID + 8);
     BO_CUDA(cudaMemsetAsync(s->d_ml_grad, 0, sizeof(float) * NPARAM, s->stream));
     BO_CUDA(cudaFuncSetAttribute(k_ml_net, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INF_SMEM));
+    BO_CUDA(cudaFuncSetAttribute(k_ml_net_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     BO_CUDA(cudaFuncSetAttribute(k_ml_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
     BO_CUDA(cudaFuncSetAttribute(k_ml_bwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
 }
@@ -720,11 +969,21 @@ void enqueue_learn_features(bo_sim* s, cudaStream_t st) {
                                         s->d_ml_cell);
     count_launch(s, st);
     BO_LAUNCH_CHECK("k_ml_feat");
-    const int grid = std::max(1, std::min(152 * 2, (n + 16 * INF_WARPS - 1) / (16 * INF_WARPS)));
-    k_ml_net<<<grid, 32 * INF_WARPS, INF_SMEM, st>>>(n, feat_of(s), wbf_of(s), s->d_ml_theta,
-                                                     s->d_ml_W);
-    count_launch(s, st);
-    BO_LAUNCH_CHECK("k_ml_net");
+    if (s->ml_engine == BO_LEARN_ENGINE_TCGEN05) {
+        // 128 cells per CTA, two CTAs per SM (103.5 KB of shared memory and
+        // 256 tensor-memory columns each)
+        const int grid = std::max(1, std::min(152 * 2, (n + 127) / 128));
+        k_ml_net_tc<<<grid, TC_BS, TC_SMEM, st>>>(n, feat_of(s), wbf_of(s), s->d_ml_theta, s->d_ml_W,
+                                                  reinterpret_cast<int*>(&s->d_ns->pad));
+        count_launch(s, st);
+        BO_LAUNCH_CHECK("k_ml_net_tc");
+    } else {
+        const int grid = std::max(1, std::min(152 * 2, (n + 16 * INF_WARPS - 1) / (16 * INF_WARPS)));
+        k_ml_net<<<grid, 32 * INF_WARPS, INF_SMEM, st>>>(n, feat_of(s), wbf_of(s), s->d_ml_theta,
+                                                         s->d_ml_W);
+        count_launch(s, st);
+        BO_LAUNCH_CHECK("k_ml_net");
+    }
 }
 
 // z += delta(r) (inside the BiCGStab graph when ks is given)

@@ -368,6 +368,17 @@ class Sim:
         call("bo_learn_get_params", self.h, ptr(theta), L.LEARN_NPARAM)
         return theta
 
+    @property
+    def learn_engine(self):
+        """"tcgen05" (default) or "mma_sync": the tensor-core kernel of the network."""
+        v = ctypes.c_int()
+        call("bo_learn_get_engine", self.h, ctypes.byref(v))
+        return {0: "mma_sync", 1: "tcgen05"}[v.value]
+
+    @learn_engine.setter
+    def learn_engine(self, name):
+        call("bo_learn_set_engine", self.h, {"mma_sync": 0, "tcgen05": 1}[name])
+
     def learn_enable(self, on=True):
         call("bo_learn_enable", self.h, 1 if on else 0)
 

@@ -101,6 +101,13 @@ struct NewtonStatus {
 
 constexpr int MAX_TIMERS = 16;
 
+// A timed interval outside the solver graphs: two events on the sim's stream,
+// read back at the next flush.
+struct EagerTimer {
+    cudaEvent_t a, b;
+    int id;
+};
+
 struct CprData;   // CPR preconditioner data (cpr.cu)
 struct DdData;    // K-subdomain solver data (dd.cu)
 
@@ -229,6 +236,7 @@ struct bo_sim {
     double timer_ms[bo::MAX_TIMERS] = {};
     long long timer_n[bo::MAX_TIMERS] = {};
     std::vector<cudaEvent_t> iter_events;  // per iteration-in-graph: begin/end pairs
+    std::vector<bo::EagerTimer> pending_timers;   // this object's open intervals
 
     // kernels launched for this object (direct launches, plus the kernel
     // nodes of every graph launch)

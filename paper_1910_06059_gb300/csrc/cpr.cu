@@ -47,6 +47,7 @@ constexpr int CPR_MAX_LEVELS = 12;
 constexpr int CPR_BS = 256;
 constexpr int CPR_GRID = 152 * 4;
 constexpr int CPR_GRID_ROWS = 152 * 8;   // coarse-level rows: latency-bound gathers, full occupancy
+constexpr int CPR_ELL_MAX = 32;          // levels with rows up to this long get an ELL copy
 
 struct CprLevel {
     int n = 0, nnz = 0;
@@ -289,15 +290,17 @@ void cpr_build(bo_sim* s) {
             v.cidx = upload(idx);
             int W = 0;
             for (int I = 0; I < v.n; ++I) W = std::max(W, A[l].rp[I + 1] - A[l].rp[I]);
-            std::vector<int> ec((size_t)W * v.n);
-            for (int I = 0; I < v.n; ++I)
-                for (int e = 0; e < W; ++e) {
-                    const int q = A[l].rp[I] + e;
-                    ec[(size_t)e * v.n + I] = q < A[l].rp[I + 1] ? A[l].ci[q] : I;
-                }
             v.W = W;
-            v.ecol = upload(ec);
-            v.eval = dzeros<double>((size_t)W * v.n);
+            if (W <= CPR_ELL_MAX) {
+                std::vector<int> ec((size_t)W * v.n);
+                for (int I = 0; I < v.n; ++I)
+                    for (int e = 0; e < W; ++e) {
+                        const int q = A[l].rp[I] + e;
+                        ec[(size_t)e * v.n + I] = q < A[l].rp[I + 1] ? A[l].ci[q] : I;
+                    }
+                v.ecol = upload(ec);
+                v.eval = dzeros<double>((size_t)W * v.n);
+            }
         }
         v.dinv = dzeros<double>(v.n);
         v.x = (l == 0) ? nullptr : dzeros<double>(v.n);   // level 0: the pressure column of x1
@@ -384,7 +387,7 @@ k_cpr_galerkin(int nc, const int* __restrict__ rowptr, const int* __restrict__ d
             double s = 0.0;
             for (int q = cptr[e]; q < cptr[e + 1]; ++q) s += fine[cidx[q]];
             val[e] = s;
-            eval[(size_t)(e - rowptr[I]) * nc + I] = s;
+            if (eval) eval[(size_t)(e - rowptr[I]) * nc + I] = s;
         }
         dinv[I] = 1.0 / val[diag[I]];
     }
@@ -577,6 +580,38 @@ k_cpr_res(int n, int W, const int* __restrict__ col, const double* __restrict__ 
         y[i] = b[i] - ell_dot(n, W, i, col, val, x);
 }
 
+// Levels whose rows are long (the coarse ones): 32 lanes per row, the row's
+// entries strided over the lanes and summed by shuffles.  The loops run
+// warp-uniform so every lane reaches the shuffles.
+__device__ __forceinline__ double row_dot32(int i, bool active, int lane,
+                                            const int* __restrict__ rowptr,
+                                            const int* __restrict__ colind,
+                                            const double* __restrict__ val,
+                                            const double* __restrict__ x) {
+    double s = 0.0;
+    if (active)
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) s += val[e] * x[colind[e]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+// y = x + omega dinv (b - A x) (RES = false) or y = b - A x (RES = true)
+template <bool RES>
+__global__ void __launch_bounds__(CPR_BS)
+k_cpr_csr32(int n, const int* __restrict__ rowptr, const int* __restrict__ colind,
+            const double* __restrict__ val, const double* __restrict__ dinv,
+            const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ y,
+            const KrylovScalars* __restrict__ ks) {
+    if (ks != nullptr && ks->state != KS_RUN) return;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < n; i += nwarps) {   // warp-uniform
+        const double s = row_dot32(i, true, lane, rowptr, colind, val, x);
+        if (lane == 0) y[i] = RES ? b[i] - s : x[i] + CPR_OMEGA * dinv[i] * (b[i] - s);
+    }
+}
+
 // coarse correction: x += P xc (each node takes its aggregate's value)
 __global__ void __launch_bounds__(CPR_BS)
 k_cpr_prolong(int n, const double* __restrict__ xc, const int* __restrict__ agg,
@@ -693,15 +728,28 @@ void enqueue_cpr_setup(bo_sim* s, cudaStream_t st) {
 static int grid_for_rows(int n) {
     return std::max(1, std::min(CPR_GRID_ROWS, (n + CPR_BS - 1) / CPR_BS));
 }
+// short rows (the first coarse level): one thread per row over the ELL copy;
+// long rows: a warp per row over the CSR arrays
+static int grid_warps(int n) {
+    return std::max(1, std::min(CPR_GRID_ROWS, (n + CPR_BS / 32 - 1) / (CPR_BS / 32)));
+}
 static void jac_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
                     const KrylovScalars* ks) {
-    k_cpr_jac<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.dinv, v.b, x, y,
-                                                    ks);
+    if (v.W <= CPR_ELL_MAX)
+        k_cpr_jac<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.dinv, v.b, x,
+                                                        y, ks);
+    else
+        k_cpr_csr32<false><<<grid_warps(v.n), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val,
+                                                              v.dinv, v.b, x, y, ks);
     count_launch(s, st);
 }
 static void res_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
                     const KrylovScalars* ks) {
-    k_cpr_res<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.b, x, y, ks);
+    if (v.W <= CPR_ELL_MAX)
+        k_cpr_res<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.b, x, y, ks);
+    else
+        k_cpr_csr32<true><<<grid_warps(v.n), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val,
+                                                             v.dinv, v.b, x, y, ks);
     count_launch(s, st);
 }
 

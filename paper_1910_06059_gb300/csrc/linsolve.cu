@@ -533,11 +533,6 @@ int timer_id(bo_sim* s, const char* name) {
     return s->ntimers++;
 }
 
-struct EagerTimer {
-    cudaEvent_t a, b;
-    int id;
-};
-static std::vector<EagerTimer> g_pending;  // per process; flushed after each sync
 
 void timer_begin(bo_sim* s, int id) {
     if (!s->timing || id < 0) return;
@@ -546,20 +541,20 @@ void timer_begin(bo_sim* s, int id) {
     BO_CUDA(cudaEventCreate(&t.a));
     BO_CUDA(cudaEventCreate(&t.b));
     BO_CUDA(cudaEventRecord(t.a, s->stream));
-    g_pending.push_back(t);
+    s->pending_timers.push_back(t);   // per object: ensemble workers time members concurrently
 }
 void timer_end(bo_sim* s, int id) {
     if (!s->timing || id < 0) return;
-    for (auto it = g_pending.rbegin(); it != g_pending.rend(); ++it)
+    for (auto it = s->pending_timers.rbegin(); it != s->pending_timers.rend(); ++it)
         if (it->id == id) {
             BO_CUDA(cudaEventRecord(it->b, s->stream));
             return;
         }
 }
 void timers_flush(bo_sim* s) {
-    if (g_pending.empty()) return;
+    if (s->pending_timers.empty()) return;
     BO_CUDA(cudaStreamSynchronize(s->stream));
-    for (auto& t : g_pending) {
+    for (auto& t : s->pending_timers) {
         float ms = 0.f;
         BO_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
         s->timer_ms[t.id] += ms;
@@ -567,7 +562,7 @@ void timers_flush(bo_sim* s) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
     }
-    g_pending.clear();
+    s->pending_timers.clear();
 }
 
 // One BiCGStab iteration enqueued on st (captured into a graph).

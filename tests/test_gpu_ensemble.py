@@ -63,6 +63,25 @@ def test_ensemble_equals_members_stepped_alone():
     ens.close()
 
 
+def test_ensemble_with_member_timers():
+    """Members timed while the workers step them concurrently: each member
+    keeps its own open intervals, and every member's timers are filled."""
+    from paper_1910_06059_gb300 import Ensemble
+    models = small_members(6)
+    ens = Ensemble(models, streams=3)
+    ens.init_hydrostatic()
+    for sm in ens.members:
+        sm.set_timing(True)
+    sts, reps = ens.step(1.0 * synth.DAY)
+    assert all(st == 0 for st in sts)
+    for sm, rep in zip(ens.members, reps):
+        t = sm.timing()
+        assert t["ilu_fwd_sweep"][1] >= rep["lin_its"] > 0
+        assert all(np.isfinite(v[0]) and v[0] >= 0 for v in t.values())
+        sm.set_timing(False)
+    ens.close()
+
+
 def test_ensemble_member_vs_oracle():
     from paper_1910_06059_gb300 import Ensemble
     models = small_members(3)

@@ -682,7 +682,7 @@ def run_ensemble(args):
     fw = [(t["ilu_fwd_sweep"], sm.n) for t, sm in zip(timers, ens.members) if "ilu_fwd_sweep" in t]
     tot_ms = sum(v[0][0] for v in fw)
     nl = sum(v[0][1] for v in fw)
-    byt = sum(ALGO_BYTES_PER_CELL["ilu_fwd_sweep"] * c * v[0][1] for v, c in fw)
+    byt = sum(ALGO_BYTES_PER_CELL["ilu_fwd_sweep"] * c * v[1] for v, c in fw)
     pk = peaks()
     roof = None
     if tot_ms > 0 and nl > 0:

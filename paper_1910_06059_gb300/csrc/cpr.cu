@@ -47,7 +47,10 @@ constexpr int CPR_MAX_LEVELS = 12;
 constexpr int CPR_BS = 256;
 constexpr int CPR_GRID = 152 * 4;
 constexpr int CPR_GRID_ROWS = 152 * 8;   // coarse-level rows: latency-bound gathers, full occupancy
-constexpr int CPR_ELL_MAX = 32;          // levels with rows up to this long get an ELL copy
+// levels whose rows are short (the first coarse level: up to 32 entries, 12
+// on average) get an ELL copy and one thread per row; the longer rows of the
+// coarser levels are read by a warp per row
+constexpr int CPR_ELL_MAX = 32, CPR_ELL_AVG = 12;
 
 struct CprLevel {
     int n = 0, nnz = 0;
@@ -60,6 +63,7 @@ struct CprLevel {
     // the same operator in ELL form for the V-cycle: width W (the longest
     // row), entry e of row i at e n + i; padding has column i and value 0
     int W = 0;
+    bool ell = false;
     int* ecol = nullptr;
     double* eval = nullptr;
     // to the next level: agg[i] = aggregate of node i; members of aggregate I
@@ -291,7 +295,8 @@ void cpr_build(bo_sim* s) {
             int W = 0;
             for (int I = 0; I < v.n; ++I) W = std::max(W, A[l].rp[I + 1] - A[l].rp[I]);
             v.W = W;
-            if (W <= CPR_ELL_MAX) {
+            v.ell = W <= CPR_ELL_MAX && v.nnz <= CPR_ELL_AVG * (long long)v.n;
+            if (v.ell) {
                 std::vector<int> ec((size_t)W * v.n);
                 for (int I = 0; I < v.n; ++I)
                     for (int e = 0; e < W; ++e) {
@@ -735,7 +740,7 @@ static int grid_warps(int n) {
 }
 static void jac_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
                     const KrylovScalars* ks) {
-    if (v.W <= CPR_ELL_MAX)
+    if (v.ell)
         k_cpr_jac<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.dinv, v.b, x,
                                                         y, ks);
     else
@@ -745,7 +750,7 @@ static void jac_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double*
 }
 static void res_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
                     const KrylovScalars* ks) {
-    if (v.W <= CPR_ELL_MAX)
+    if (v.ell)
         k_cpr_res<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.b, x, y, ks);
     else
         k_cpr_csr32<true><<<grid_warps(v.n), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val,

@@ -131,6 +131,8 @@ def parse():
                          "profiles/op_counts_config<C>.json (the CPU scaling record)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3])
+    ap.add_argument("--sweep-ctas-per-sm", type=int, default=0,
+                    help="persistent CTAs per SM of the FP64 sweeps (1 or 2; 0: the library's default)")
     ap.add_argument("--members", type=int, default=256, help="ensemble members (config 3)")
     ap.add_argument("--seq-sample", type=int, default=32,
                     help="members stepped one at a time for the sequential comparison (config 3)")
@@ -359,6 +361,8 @@ def run_gb300(args):
     if args.ysub or args.zsub:
         sim.subdomains, sim.subdomains_z = args.ysub, args.zsub
     sim.preconditioner = args.precond
+    if args.sweep_ctas_per_sm:
+        sim.set_sweep_ctas_per_sm(args.sweep_ctas_per_sm)
     sim.init_hydrostatic()
     if args.learned:
         import synth

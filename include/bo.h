@@ -245,6 +245,13 @@ bo_status bo_get_wells(const bo_sim* sim, double* Rw, double* Dw, double* B, dou
  * its inflow at that state and BHP), which must follow this call.
  * BO_ERR_STATE before bo_set_properties; BO_ERR_INVALID_ARG for another
  * model. */
+/* Residency of the FP64 triangular sweeps' persistent CTAs: k = 1 or 2 per
+ * SM (default 2).  With two, the row warps of the two CTAs on an SM share the
+ * sub-partitions' FP64 pipes; with one, fewer tiles of the wavefront are in
+ * flight at once.  Re-records the solver graphs.  BO_ERR_INVALID_ARG for
+ * another k, BO_ERR_STATE before bo_set_properties. */
+bo_status bo_set_sweep_ctas_per_sm(bo_sim* sim, int k);
+
 #define BO_WELL_REDUCED 0
 #define BO_WELL_STANDARD 1
 bo_status bo_set_well_model(bo_sim* sim, int model, int storage);

@@ -125,6 +125,7 @@ _SIGS = {
     "bo_get_launch_count": [P, P],
     "bo_set_well_model": [P, c_int, c_int],
     "bo_dd_solve": [P, P, P, P],
+    "bo_set_sweep_ctas_per_sm": [P, c_int],
     "bo_learn_set_engine": [P, c_int],
     "bo_learn_get_engine": [P, P],
     "bo_get_well_model": [P, P],

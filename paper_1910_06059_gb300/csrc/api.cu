@@ -1191,6 +1191,18 @@ bo_status bo_cpr_vcycle(bo_sim* s, const double* b, double* x) {
     });
 }
 
+bo_status bo_set_sweep_ctas_per_sm(bo_sim* s, int k) {
+    return guarded([&] {
+        need(s && s->props_set, BO_ERR_STATE, "bo_set_sweep_ctas_per_sm: call bo_set_properties first");
+        need(k == 1 || k == 2, BO_ERR_INVALID_ARG, "bo_set_sweep_ctas_per_sm: k must be 1 or 2");
+        if (k == s->sweep_ctas_per_sm) return;
+        sync(s);
+        s->sweep_ctas_per_sm = k;
+        setup_sweeps64(s);   // residency check and tile lists for the new grid
+        build_graphs(s);     // the captured launches carry the grid
+    });
+}
+
 bo_status bo_set_well_model(bo_sim* s, int model, int storage) {
     return guarded([&] {
         need(s && s->props_set, BO_ERR_STATE, "bo_set_well_model: call bo_set_properties first");

@@ -226,6 +226,7 @@ struct bo_sim {
     cudaGraphExec_t g_factor = nullptr;
     cudaGraphExec_t g_iter_timed = nullptr;
     int iters_per_graph = 4;
+    int sweep_ctas_per_sm = 2;   // persistent CTAs of the FP64 sweeps per SM (1 or 2)
     int ysub = 0;                // block-Jacobi slabs of ysub cell rows in y (0: no cut in y)
     int zsub = 0;                // and of zsub cell layers in z (0: no cut in z)
 
@@ -263,6 +264,7 @@ int sweep_timeout(bo_sim* s);
 size_t ilu_storage(const bo_sim* s);
 int tile_count(const bo_sim* s);                 // tiles of the wavefront schedule
 void update_sweep_order(bo_sim* s);              // sweep tile lists after a block-Jacobi change
+void setup_sweeps64(bo_sim* s);                  // FP64 sweep grid: residency check, tile lists
 size_t face_storage(const bo_sim* s);
 void enqueue_factor(bo_sim* s, cudaStream_t st, int* bad);
 void enqueue_fwd(bo_sim* s, cudaStream_t st, const double* r, double* y, const KrylovScalars* ks);

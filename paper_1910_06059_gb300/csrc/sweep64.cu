@@ -391,17 +391,19 @@ k_fwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Qt
             mb_wait(&bar[st], (unsigned)((g / S64) & 1), a.err);
             const double* L = ring + (size_t)st * STAGE + 3 * rw * 32 + lane;   // row rw of D^-1 A_-x
             const double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF + op;
-            // two independent chains: q and the -x block; the -y and -z blocks
+            // three independent chains (q and the -x block, the -y block, the -z
+            // block) of three dependent FP64 operations each, then two adds
             double u = ring[(size_t)st * STAGE + (BLK_ENT + rw) * 32 + lane];
             double v = -L[9 * 32] * yb[-1];
+            double w = -L[18 * 32] * yb[-HJ];
 #pragma unroll
             for (int s2 = 0; s2 < 3; ++s2) u = fma(-L[s2 * 32], yb[s2 * YPL], u);          // -x
 #pragma unroll
             for (int s2 = 1; s2 < 3; ++s2) v = fma(-L[(9 + s2) * 32], yb[s2 * YPL - 1], v);   // -y
 #pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2) v = fma(-L[(18 + s2) * 32], yb[s2 * YPL - HJ], v); // -z
+            for (int s2 = 1; s2 < 3; ++s2) w = fma(-L[(18 + s2) * 32], yb[s2 * YPL - HJ], w); // -z
             const bool act = lane_active(a, G, l);
-            const double acc = act ? u + v : 0.0;
+            const double acc = act ? u + (v + w) : 0.0;
             ysh[(int)(g & 1) * YBUF + rw * YPL + op] = acc;
             yout[(size_t)l * 96] = acc;
             if (act && feedJ) st_relaxed(fjo + (size_t)l * TK * 3, acc);
@@ -519,17 +521,19 @@ k_bwd64(SweepArgs A, const double* __restrict__ P, const double* __restrict__ Yt
             mb_wait(&bar[st], (unsigned)((g / S64) & 1), a.err);
             const double* U = ring + (size_t)st * STAGE + 3 * rw * 32 + lane;
             const double* yb = ysh + (((int)(g & 1)) ^ 1) * YBUF + op;
-            // two independent chains: y and the +x block; the +y and +z blocks
+            // three independent chains (y and the +x block, the +y block, the +z
+            // block), then two adds
             double u = ring[(size_t)st * STAGE + (BLK_ENT + rw) * 32 + lane];
             double v = -U[9 * 32] * yb[1];
+            double w = -U[18 * 32] * yb[HJ];
 #pragma unroll
             for (int s2 = 0; s2 < 3; ++s2) u = fma(-U[s2 * 32], yb[s2 * YPL], u);            // +x
 #pragma unroll
             for (int s2 = 1; s2 < 3; ++s2) v = fma(-U[(9 + s2) * 32], yb[s2 * YPL + 1], v);   // +y
 #pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2) v = fma(-U[(18 + s2) * 32], yb[s2 * YPL + HJ], v); // +z
+            for (int s2 = 1; s2 < 3; ++s2) w = fma(-U[(18 + s2) * 32], yb[s2 * YPL + HJ], w); // +z
             const bool act = lane_active(a, G, l);
-            const double acc = act ? u + v : 0.0;
+            const double acc = act ? u + (v + w) : 0.0;
             ysh[(int)(g & 1) * YBUF + rw * YPL + op] = acc;
             if (act) {
                 zo[l] = acc;
@@ -563,11 +567,13 @@ std::vector<int> sweep_tile_order(const TileArgs& a) {
     return t;
 }
 
+// Persistent CTAs of the sweeps: sweep_ctas_per_sm per SM (1 or 2; with two,
+// the row warps of the two CTAs share the SM sub-partitions' FP64 pipes).
 int sweep_ctas(const bo_sim* s) {
     int dev, sms;
     BO_CUDA(cudaGetDevice(&dev));
     BO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    return std::min(tile_args(s).T, 2 * sms);
+    return std::min(tile_args(s).T, s->sweep_ctas_per_sm * sms);
 }
 
 void setup_sweeps64(bo_sim* s) {

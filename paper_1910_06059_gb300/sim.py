@@ -176,6 +176,10 @@ class Sim:
         call("bo_get_well_model", self.h, ctypes.byref(v))
         return {q: k for k, q in L.WELL_MODEL.items()}[v.value]
 
+    def set_sweep_ctas_per_sm(self, k):
+        """Persistent CTAs of the FP64 sweeps per SM (1 or 2)."""
+        call("bo_set_sweep_ctas_per_sm", self.h, int(k))
+
     def set_well_model(self, name, storage=True):
         """Select the well model; the well unknowns start at the next
         set_state / init_hydrostatic / init_equilibrium."""

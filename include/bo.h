@@ -480,6 +480,27 @@ bo_status bo_learn_enable(bo_sim* sim, int on);
  * order of the FP32 sums).  A tcgen05 layer that does not complete within its
  * bounded wait fails the factorisation (the linear solve reports a
  * breakdown).  BO_ERR_INVALID_ARG for another value. */
+/* Offline training set of the learned stage (the simulator's own earlier
+ * systems).  bo_learn_collect with max_systems > 0 clears the set and, from
+ * then on, keeps every linear solve's system -- its Jacobian, ILU(0) data,
+ * FP32 features and per-cell scalings -- with the first `samples` (1..64)
+ * BiCGStab residuals of its solve, until max_systems are kept or the device
+ * has no room left; max_systems = 0 stops collecting and keeps the set.
+ * Needs parameters (BO_ERR_STATE); with online training on, samples must be
+ * its own count.  Memory: about 0.9 KB per cell plus 24 B per cell and
+ * residual for every kept system.
+ * bo_learn_set_info: the kept systems and residuals (either pointer may be
+ * NULL).
+ * bo_learn_train_offline: `epochs` passes of one Adam step (step size lr) per
+ * kept residual, each on its own system (the loss of bo_learn_loss_grad);
+ * first_loss / last_loss (may be NULL) receive the mean loss over the first
+ * and over the last pass.  Needs a non-empty set, parameters and the FP64
+ * ILU(0) preconditioner (BO_ERR_STATE). */
+bo_status bo_learn_collect(bo_sim* sim, int max_systems, int samples);
+bo_status bo_learn_set_info(const bo_sim* sim, int* systems, int* residuals);
+bo_status bo_learn_train_offline(bo_sim* sim, int epochs, double lr, double* first_loss,
+                                 double* last_loss);
+
 #define BO_LEARN_ENGINE_MMA_SYNC 0
 #define BO_LEARN_ENGINE_TCGEN05 1
 bo_status bo_learn_set_engine(bo_sim* sim, int engine);

@@ -127,6 +127,9 @@ _SIGS = {
     "bo_dd_solve": [P, P, P, P],
     "bo_set_sweep_ctas_per_sm": [P, c_int],
     "bo_learn_set_engine": [P, c_int],
+    "bo_learn_collect": [P, c_int, c_int],
+    "bo_learn_set_info": [P, P, P],
+    "bo_learn_train_offline": [P, c_int, c_double, P, P],
     "bo_learn_get_engine": [P, P],
     "bo_get_well_model": [P, P],
     "bo_get_std_wells": [P, P, P, P, P, P],

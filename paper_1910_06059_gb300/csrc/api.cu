@@ -77,6 +77,7 @@ static void free_all(bo_sim* s) {
     destroy_graphs(s);
     cpr_free(s);
     dd_free(s);
+    learn_set_clear(s);
     void* ptrs[] = {s->d_dx, s->d_dy, s->d_dz, s->d_perm, s->d_poro, s->d_T, s->d_pv, s->d_depth,
                     s->d_p, s->d_sw, s->d_x, s->d_flag, s->d_bk, s->d_bkflag, s->d_A0,
                     s->d_props, s->d_R, s->d_A, s->d_P, s->d_yt, s->d_qt, s->d_order, s->d_face, s->d_cellcon, s->d_wells,
@@ -143,6 +144,53 @@ static void learn_online_step(bo_sim* s) {
     s->ml_systems += 1;
     s->ml_train_ms +=
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Offline set of the learned stage: free every kept system.
+void learn_set_clear(bo_sim* s) {
+    for (LearnSystem& q : s->ml_set) {
+        void* ptrs[] = {q.A, q.P, q.featf, q.cell, q.r};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+    }
+    s->ml_set.clear();
+}
+
+// Keep the last solve's system and its first residuals for offline training
+// (while the set has room; a failed allocation ends the collection).
+static void learn_store_system(bo_sim* s) {
+    if ((int)s->ml_set.size() >= s->ml_collect_max) return;
+    int cnt = 0;
+    BO_CUDA(cudaMemcpyAsync(&cnt, s->d_ml_count, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+    const int nr = std::min(cnt, s->ml_cap);
+    if (nr <= 0) return;
+    const size_t n = s->geo.n, NA = 63 * n, NP = 63 * ilu_storage(s), NR = (size_t)nr * 3 * n;
+    LearnSystem q;
+    bool ok = cudaMalloc(reinterpret_cast<void**>(&q.A), sizeof(double) * NA) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&q.P), sizeof(double) * NP) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&q.featf), sizeof(float) * 64 * n) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&q.cell), sizeof(float4) * n) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&q.r), sizeof(double) * NR) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();   // the device is full: keep what was collected
+        void* ptrs[] = {q.A, q.P, q.featf, q.cell, q.r};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        s->ml_collect_max = (int)s->ml_set.size();
+        return;
+    }
+    q.nr = nr;
+    BO_CUDA(cudaMemcpyAsync(q.A, s->d_A, sizeof(double) * NA, cudaMemcpyDeviceToDevice, s->stream));
+    BO_CUDA(cudaMemcpyAsync(q.P, s->d_P, sizeof(double) * NP, cudaMemcpyDeviceToDevice, s->stream));
+    BO_CUDA(cudaMemcpyAsync(q.featf, s->d_ml_featf, sizeof(float) * 64 * n, cudaMemcpyDeviceToDevice,
+                            s->stream));
+    BO_CUDA(cudaMemcpyAsync(q.cell, s->d_ml_cell, sizeof(float4) * n, cudaMemcpyDeviceToDevice,
+                            s->stream));
+    BO_CUDA(cudaMemcpyAsync(q.r, s->d_ml_samples, sizeof(double) * NR, cudaMemcpyDeviceToDevice,
+                            s->stream));
+    BO_CUDA(cudaStreamSynchronize(s->stream));
+    s->ml_set.push_back(q);
 }
 
 // Linear solve of the last assembly; returns the LS_* status.
@@ -220,6 +268,7 @@ static int solve_linear(bo_sim* s, double tol, int maxit, int* its) {
         }
     }
     if (s->ml_online) learn_online_step(s);
+    if (s->ml_collect_max > 0) learn_store_system(s);
     launch_well_recover(s);
     s->solved = true;
     return st;
@@ -1036,6 +1085,100 @@ bo_status bo_learn_online(bo_sim* s, const bo_learn_opts* o) {
         build_graphs(s);
         if (s->assembled) enqueue_learn_features(s, s->stream);
         sync(s);
+    });
+}
+
+bo_status bo_learn_collect(bo_sim* s, int max_systems, int samples) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_learn_collect: sim is NULL");
+        need(max_systems >= 0 && samples >= 1 && samples <= 64, BO_ERR_INVALID_ARG,
+             "bo_learn_collect: max_systems >= 0, samples 1..64");
+        sync(s);
+        if (max_systems == 0) {   // stop collecting, keep the set
+            if (s->ml_collect_max == 0) return;
+            s->ml_collect_max = 0;
+            build_graphs(s);
+            return;
+        }
+        need(s->ml_params, BO_ERR_STATE, "bo_learn_collect: no parameters set");
+        need(!s->ml_online || s->ml_cap == samples, BO_ERR_STATE,
+             "bo_learn_collect: online training keeps a different number of residuals");
+        learn_set_clear(s);
+        learn_setup_training(s);
+        if (s->ml_cap != samples) {
+            if (s->d_ml_samples) cudaFree(s->d_ml_samples);
+            s->d_ml_samples = nullptr;
+            dalloc(&s->d_ml_samples, (size_t)samples * 3 * s->geo.n);
+            s->ml_cap = samples;
+        }
+        s->ml_collect_max = max_systems;
+        build_graphs(s);
+        if (s->assembled) enqueue_learn_features(s, s->stream);
+        sync(s);
+    });
+}
+
+bo_status bo_learn_set_info(const bo_sim* s, int* systems, int* residuals) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_learn_set_info: sim is NULL");
+        int r = 0;
+        for (const LearnSystem& q : s->ml_set) r += q.nr;
+        if (systems) *systems = (int)s->ml_set.size();
+        if (residuals) *residuals = r;
+    });
+}
+
+bo_status bo_learn_train_offline(bo_sim* s, int epochs, double lr, double* first_loss,
+                                 double* last_loss) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_learn_train_offline: sim is NULL");
+        need(epochs >= 1 && epochs <= 1000 && lr > 0.0 && lr < 1.0, BO_ERR_INVALID_ARG,
+             "bo_learn_train_offline: epochs 1..1000, 0 < lr < 1");
+        need(s->ml_params && !s->ml_set.empty(), BO_ERR_STATE,
+             "bo_learn_train_offline: no parameters or an empty set (bo_learn_collect)");
+        need(!s->mixed && s->precond == BO_PRECOND_ILU0, BO_ERR_STATE,
+             "bo_learn_train_offline: needs the FP64 ILU(0) preconditioner");
+        learn_setup_training(s);
+        const auto t0 = std::chrono::steady_clock::now();
+        const size_t N = 3 * (size_t)s->geo.n;
+        // each kept system's Jacobian, ILU(0) data, features and scalings take
+        // the place of the current ones while its residuals are trained on
+        struct Swap {
+            bo_sim* s;
+            double *A, *P;
+            float* featf;
+            float4* cell;
+            ~Swap() {
+                s->d_A = A;
+                s->d_P = P;
+                s->d_ml_featf = featf;
+                s->d_ml_cell = cell;
+            }
+        } keep{s, s->d_A, s->d_P, s->d_ml_featf, s->d_ml_cell};
+        double first = 0.0, last = 0.0;
+        long long cnt = 0;
+        for (int ep = 0; ep < epochs; ++ep) {
+            for (const LearnSystem& q : s->ml_set) {
+                s->d_A = q.A;
+                s->d_P = q.P;
+                s->d_ml_featf = q.featf;
+                s->d_ml_cell = q.cell;
+                for (int j = 0; j < q.nr; ++j) {
+                    const double L = learn_loss_grad(s, q.r + (size_t)j * N);
+                    if (ep == 0) first += L;
+                    if (ep == epochs - 1) last += L;
+                    if (ep == 0) ++cnt;
+                    learn_adam(s, lr);
+                    s->ml_steps += 1;
+                }
+            }
+        }
+        sync(s);
+        check_timeout(s);
+        s->ml_train_ms +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (first_loss) *first_loss = first / std::max<long long>(cnt, 1);
+        if (last_loss) *last_loss = last / std::max<long long>(cnt, 1);
     });
 }
 

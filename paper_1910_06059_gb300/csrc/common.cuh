@@ -108,6 +108,18 @@ struct EagerTimer {
     int id;
 };
 
+// One Newton system kept for offline training of the learned stage: its
+// Jacobian, ILU(0) data, FP32 features, per-cell scalings and nr residuals
+// of its BiCGStab solve ([nr][3n]).
+struct LearnSystem {
+    double* A = nullptr;
+    double* P = nullptr;
+    float* featf = nullptr;
+    float4* cell = nullptr;
+    double* r = nullptr;
+    int nr = 0;
+};
+
 struct CprData;   // CPR preconditioner data (cpr.cu)
 struct DdData;    // K-subdomain solver data (dd.cu)
 
@@ -212,6 +224,8 @@ struct bo_sim {
     int ml_guard_left = 0, ml_guard_state = 0;          // bo_learn_guard window and decision
     long long ml_guard_stage_its = 0, ml_guard_plain_its = 0;
     double ml_first_loss = -1.0, ml_last_loss = -1.0, ml_train_ms = 0.0;
+    int ml_collect_max = 0;                   // systems to keep for offline training (0: off)
+    std::vector<bo::LearnSystem> ml_set;      // the kept systems
     cudaGraphExec_t g_iter_ml = nullptr;
     cudaGraphExec_t g_iter64 = nullptr;   // FP64 sweeps in mixed mode (fallback solves)
     int last_fallback = 0;                // bo_solve_report::fallback of the last solve
@@ -287,6 +301,10 @@ void launch_well_recover(bo_sim* s);
 // the preconditioner application of BiCGStab: ILU(0) or CPR, z = M^-1 r
 void enqueue_precond_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,
                            const KrylovScalars* ks);
+// the BiCGStab graphs store their iterations' residuals (online training or
+// the offline set's collection)
+inline bool learn_collecting(const bo_sim* s) { return s->ml_online || s->ml_collect_max > 0; }
+void learn_set_clear(bo_sim* s);
 // right-hand side of the well-reduced system into d_b
 void enqueue_reduced_rhs(bo_sim* s, cudaStream_t st);
 // K-subdomain solve (dd.cu): returns LS_*

@@ -672,7 +672,7 @@ static cudaGraphExec_t capture_factor(bo_sim* s) {
     BO_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     enqueue_factor(s, cs, factor_bad(s));
     if (s->precond == BO_PRECOND_CPR) enqueue_cpr_setup(s, cs);
-    if (s->ml_on || s->ml_online) enqueue_learn_features(s, cs);
+    if (s->ml_on || learn_collecting(s)) enqueue_learn_features(s, cs);
     BO_CUDA(cudaStreamEndCapture(cs, &graph));
     cudaGraphExec_t exec;
     BO_CUDA(cudaGraphInstantiate(&exec, graph, 0));
@@ -685,8 +685,8 @@ static cudaGraphExec_t capture_factor(bo_sim* s) {
 void build_graphs(bo_sim* s) {
     destroy_graphs(s);
     s->g_factor = capture_factor(s);
-    s->g_iter = capture(s, s->iters_per_graph, nullptr, false, s->ml_online);
-    if (s->ml_on) s->g_iter_ml = capture(s, s->iters_per_graph, nullptr, true, s->ml_online);
+    s->g_iter = capture(s, s->iters_per_graph, nullptr, false, learn_collecting(s));
+    if (s->ml_on) s->g_iter_ml = capture(s, s->iters_per_graph, nullptr, true, learn_collecting(s));
     if (s->mixed) {   // FP64 sweeps for a solve the FP32 sweeps fail
         s->mixed = false;
         try {
@@ -715,7 +715,7 @@ static void ensure_timed_graph(bo_sim* s) {
     if (s->g_iter_timed) return;
     s->iter_events.resize((size_t)EV_PER_ITER * s->iters_per_graph);
     for (auto& e : s->iter_events) BO_CUDA(cudaEventCreate(&e));
-    s->g_iter_timed = capture(s, s->iters_per_graph, s->iter_events.data(), s->ml_on, s->ml_online);
+    s->g_iter_timed = capture(s, s->iters_per_graph, s->iter_events.data(), s->ml_on, learn_collecting(s));
 }
 
 
@@ -847,7 +847,7 @@ int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool f
                                  (fp32 || ml) ? MIXED_INNER : 0.0);
     count_launch(s, st);
     BO_LAUNCH_CHECK("bicgstab setup");
-    if (s->ml_online) BO_CUDA(cudaMemsetAsync(s->d_ml_count, 0, sizeof(int), st));
+    if (learn_collecting(s)) BO_CUDA(cudaMemsetAsync(s->d_ml_count, 0, sizeof(int), st));
     s->h_ks->it = 0;
     s->h_ks->maxit = maxit;
     // the timed graph carries the configured stage; a fallback solve runs untimed

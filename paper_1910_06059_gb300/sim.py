@@ -383,6 +383,25 @@ class Sim:
     def learn_engine(self, name):
         call("bo_learn_set_engine", self.h, {"mma_sync": 0, "tcgen05": 1}[name])
 
+    def learn_collect(self, max_systems, samples=16):
+        """Keep the next max_systems linear systems with their first `samples`
+        residuals for offline training (0: stop collecting)."""
+        call("bo_learn_collect", self.h, int(max_systems), int(samples))
+
+    def learn_set_info(self):
+        """(kept systems, kept residuals) of the offline set."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        call("bo_learn_set_info", self.h, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
+
+    def learn_train_offline(self, epochs=1, lr=1e-3):
+        """Adam over every kept residual on its own system; returns the mean
+        loss of the first and of the last pass."""
+        f, l = ctypes.c_double(), ctypes.c_double()
+        call("bo_learn_train_offline", self.h, int(epochs), float(lr), ctypes.byref(f),
+             ctypes.byref(l))
+        return f.value, l.value
+
     def learn_enable(self, on=True):
         call("bo_learn_enable", self.h, 1 if on else 0)
 

@@ -250,3 +250,45 @@ def test_trained_stage_against_plain_ilu0():
     assert r["guard_state"] in (2, 3)
     assert (r["guard_state"] == 2) == (r["guard_stage_its"] < r["guard_plain_its"])
     g.close()
+
+
+def test_offline_set_from_earlier_steps():
+    """The offline training set: the simulator's own systems and BiCGStab
+    residuals from a report step (the reading of 'Jacobian/residual pairs
+    from earlier steps' at this model's scale), several passes of Adam over
+    all of them, then the trained stage against plain ILU(0) on the next
+    system, printed win or loss."""
+    import time
+    m = synth.layered_model(20, 30, 20, config=1, name="layered 20x30x20")
+    g = Sim(m)
+    g.init_hydrostatic()
+    g.learn_set_params(synth.learned_init(0))
+    g.learn_collect(100, samples=16)
+    st, rep = g.step(5 * synth.DAY)
+    assert st == 0
+    g.learn_collect(0)
+    systems, residuals = g.learn_set_info()
+    assert 0 < systems <= 100 and systems <= residuals <= 16 * systems
+    first, last = g.learn_train_offline(epochs=3, lr=1e-3)
+    print(f"offline set: {systems} systems, {residuals} residuals; mean loss {first:.4f} "
+          f"in the first pass, {last:.4f} in the last")
+    assert np.isfinite(first) and np.isfinite(last) and last < first
+    dt = 5 * synth.DAY
+    g.begin_step()
+    g.assemble(dt)
+    g.factor()
+    g.learn_enable(False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st0, its0, _ = g.solve(tol=1e-3, maxit=500)
+    t_plain = time.perf_counter() - t0
+    g.learn_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st1, its1, _, info = g.solve(tol=1e-3, maxit=500, report=True)
+    t_stage = time.perf_counter() - t0
+    print(f"offline-trained stage: {its1} BiCGStab its in {1e3 * t_stage:.1f} ms "
+          f"(fallback mask {info['fallback']}) vs plain ILU(0): {its0} its in "
+          f"{1e3 * t_plain:.1f} ms -> {'gain' if its1 < its0 else 'loss'}")
+    assert st0 == 0 and st1 == 0
+    g.close()

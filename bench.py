@@ -632,6 +632,7 @@ def run_ensemble(args):
     ens.init_hydrostatic()
     cand = (1, 4, 8, 16, 32, 64)
     tune = ens.autotune(0.05 * 86400.0, candidates=cand)
+    tune_pc = ens.autotune_precond(0.05 * 86400.0)
     for _ in range(args.warmup):
         ens.step(dt)
     torch.cuda.synchronize()
@@ -727,9 +728,11 @@ def run_ensemble(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": (f"batched ensemble of {len(models)} members (nx, ny in 20..64, "
                                 f"nz in 5..16; {all_cells} cells), {dt / 86400.0:g}-day report steps, "
-                                "plain FP64 ILU0-BiCGStab per member, Newton tol 1e-6"),
+                                "FP64 BiCGStab per member with ILU0 or CPR chosen per size "
+                                "class by the autotuner, Newton tol 1e-6"),
                    "cells": all_cells, "members": args.members,
                    "schedule": tune["chosen"],
+                   "precond_by_size": tune_pc["chosen"],
                    "timing": "CUDA events bracketing every worker stream of the step",
                    "l2": "members' Jacobians and ILU data together exceed L2",
                    "parallelism": f"members split over {world} GPUs" if world > 1 else "single GPU"},
@@ -742,6 +745,7 @@ def run_ensemble(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "autotune_probe_s": tune,
+        "autotune_precond_probe_s": tune_pc["probe_s"],
         "sequential": {"value": seq_value, "unit": "cell-steps/s",
                        "sample": f"first report step of {k} members one at a time on one stream "
                                  f"({cells_sample} cells, {sec_seq:.2f} s host clock, "

@@ -568,6 +568,18 @@ bo_status bo_ensemble_step(bo_ensemble* ens, double dt, const bo_newton_opts* op
 bo_status bo_ensemble_autotune(bo_ensemble* ens, double dt_probe, const bo_newton_opts* opts,
                                const int* candidates, int ncand, double* seconds);
 bo_status bo_ensemble_last_step_ms(const bo_ensemble* ens, double* ms);
+/* Preconditioner per member size class: members up to the median cell count
+ * and the larger ones each get BO_PRECOND_ILU0 or BO_PRECOND_CPR; one probe
+ * report step of length dt_probe (with the current worker schedule) times
+ * each of the four combinations, putting every member's state and step
+ * control back after each, and the fastest one whose probe stepped every
+ * member is kept.  seconds[4] (may be NULL) receives the probe times in the
+ * order (ILU0, ILU0), (ILU0, CPR), (CPR, ILU0), (CPR, CPR) for (small,
+ * large); small_kind / large_kind (may be NULL) the choice.
+ * BO_ERR_NOT_CONVERGED if no combination stepped every member (the members'
+ * preconditioners are then as before). */
+bo_status bo_ensemble_autotune_precond(bo_ensemble* ens, double dt_probe, const bo_newton_opts* opts,
+                                      double* seconds, int* small_kind, int* large_kind);
 bo_status bo_ensemble_destroy(bo_ensemble* ens);
 
 /* Self-test of failure detection: runs the bounded device-side wait of the

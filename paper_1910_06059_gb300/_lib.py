@@ -112,6 +112,7 @@ _SIGS = {
     "bo_ensemble_step": [P, c_double, P, P, P],
     "bo_ensemble_autotune": [P, c_double, P, P, c_int, P],
     "bo_ensemble_last_step_ms": [P, P],
+    "bo_ensemble_autotune_precond": [P, c_double, P, P, P, P],
     "bo_ensemble_destroy": [P],
     "bo_learn_set_params": [P, P, c_int],
     "bo_learn_get_params": [P, P, c_int],

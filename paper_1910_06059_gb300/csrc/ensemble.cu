@@ -275,6 +275,72 @@ bo_status bo_ensemble_autotune(bo_ensemble* e, double dt_probe, const bo_newton_
                           "bo_ensemble_autotune: no candidate schedule stepped every member");
 }
 
+bo_status bo_ensemble_autotune_precond(bo_ensemble* e, double dt_probe, const bo_newton_opts* opts,
+                                      double* seconds, int* small_kind, int* large_kind) {
+    if (e == nullptr || !(dt_probe > 0.0))
+        return set_last_error(BO_ERR_INVALID_ARG,
+                              "bo_ensemble_autotune_precond: NULL ensemble or dt_probe <= 0");
+    const int count = (int)e->members.size();
+    // size classes: members up to the median cell count, and the larger ones
+    std::vector<int> sizes(count);
+    for (int q = 0; q < count; ++q) sizes[q] = e->members[q]->geo.n;
+    std::vector<int> sorted = sizes;
+    std::sort(sorted.begin(), sorted.end());
+    const int median = sorted[(count - 1) / 2];
+    std::vector<Snapshot> snap(count);
+    std::vector<int> kind0(count);
+    for (int q = 0; q < count; ++q) {
+        bo_status s = snapshot(e->members[q], snap[q]);
+        if (s != BO_OK) return s;
+        bo_get_preconditioner(e->members[q], &kind0[q]);
+    }
+    auto apply = [&](int ks, int kl) -> bo_status {
+        for (int q = 0; q < count; ++q) {
+            const bo_status s = bo_set_preconditioner(e->members[q], sizes[q] <= median ? ks : kl);
+            if (s != BO_OK) return s;
+        }
+        return BO_OK;
+    };
+    const int combos[4][2] = {{BO_PRECOND_ILU0, BO_PRECOND_ILU0}, {BO_PRECOND_ILU0, BO_PRECOND_CPR},
+                              {BO_PRECOND_CPR, BO_PRECOND_ILU0}, {BO_PRECOND_CPR, BO_PRECOND_CPR}};
+    double best = 1e300;
+    int best_c = -1;
+    for (int c = 0; c < 4; ++c) {
+        bo_status s = apply(combos[c][0], combos[c][1]);
+        if (s != BO_OK) return s;
+        std::vector<bo_status> st(count, BO_OK);
+        const auto t0 = std::chrono::steady_clock::now();
+        try {
+            run_step(e, dt_probe, opts, nullptr, st.data());
+        } catch (const std::exception&) {
+            return set_last_error(BO_ERR_STATE, "bo_ensemble_autotune_precond: out of host memory");
+        }
+        const double sec =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (seconds) seconds[c] = sec;
+        for (int q = 0; q < count; ++q) {
+            s = restore(e->members[q], snap[q]);
+            if (s != BO_OK) return s;
+        }
+        bool ok = true;
+        for (int q = 0; q < count; ++q) ok = ok && st[q] == BO_OK;
+        if (ok && sec < best) {
+            best = sec;
+            best_c = c;
+        }
+    }
+    if (best_c < 0) {   // no combination stepped every member: back to what they had
+        for (int q = 0; q < count; ++q) bo_set_preconditioner(e->members[q], kind0[q]);
+        return set_last_error(BO_ERR_NOT_CONVERGED,
+                              "bo_ensemble_autotune_precond: no combination stepped every member");
+    }
+    bo_status s = apply(combos[best_c][0], combos[best_c][1]);
+    if (s != BO_OK) return s;
+    if (small_kind) *small_kind = combos[best_c][0];
+    if (large_kind) *large_kind = combos[best_c][1];
+    return BO_OK;
+}
+
 bo_status bo_ensemble_last_step_ms(const bo_ensemble* e, double* ms) {
     if (e == nullptr || ms == nullptr)
         return set_last_error(BO_ERR_INVALID_ARG, "bo_ensemble_last_step_ms: NULL argument");

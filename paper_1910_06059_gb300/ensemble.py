@@ -69,6 +69,20 @@ class Ensemble:
                 "substeps": r.substeps} for r in reps]
         return list(sts), out
 
+    def autotune_precond(self, dt_probe, **opts):
+        """Preconditioner per size class (members up to the median size, the
+        larger ones) from a probe step of each of the four combinations;
+        returns the probe times and the choice."""
+        o = L.newton_opts(**opts)
+        sec = np.zeros(4)
+        ks, kl = ctypes.c_int(), ctypes.c_int()
+        call("bo_ensemble_autotune_precond", self.h, float(dt_probe), ctypes.byref(o),
+             sec.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ks), ctypes.byref(kl))
+        names = {v: k for k, v in L.PRECONDITIONER.items()}
+        combos = [("ilu0", "ilu0"), ("ilu0", "cpr"), ("cpr", "ilu0"), ("cpr", "cpr")]
+        return {"probe_s": {f"small {a}, large {b}": float(t) for (a, b), t in zip(combos, sec)},
+                "chosen": {"small": names[ks.value], "large": names[kl.value]}}
+
     def last_step_ms(self):
         """Device time (CUDA events) of the last step, in ms (-1: not measured)."""
         v = ctypes.c_double()

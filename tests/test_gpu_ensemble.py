@@ -121,6 +121,46 @@ def test_autotune_restores_every_member():
     ens.close()
 
 
+def test_autotune_precond_per_size_class():
+    """The preconditioner choice per size class probes all four combinations,
+    puts every member back as it was after each probe, sets the chosen
+    preconditioner on each member by its class, and the ensemble then steps
+    (a member under CPR still matches the oracle's state)."""
+    from paper_1910_06059_gb300 import Ensemble
+    models = small_members(6)
+    ens = Ensemble(models, streams=3)
+    ens.init_hydrostatic()
+    ens.step(0.5 * synth.DAY)
+    before = [s.get_state() for s in ens.members]
+    dt_before = [s.dt_next for s in ens.members]
+    res = ens.autotune_precond(0.2 * synth.DAY)
+    assert len(res["probe_s"]) == 4 and all(t > 0 for t in res["probe_s"].values())
+    sizes = sorted(s.n for s in ens.members)
+    median = sizes[(len(sizes) - 1) // 2]
+    for s, b, d in zip(ens.members, before, dt_before):
+        for x, y in zip(s.get_state(), b):
+            assert np.array_equal(x, y)
+        assert s.dt_next == d
+        want = res["chosen"]["small"] if s.n <= median else res["chosen"]["large"]
+        assert s.preconditioner == want
+    # every member through CPR for one report step against the oracle
+    for s in ens.members:
+        s.preconditioner = "cpr"
+    orc = [oracle.Oracle(m) for m in models]
+    for o, s in zip(orc, ens.members):
+        o.set_state(*s.get_state())
+        o.dt_next = s.dt_next
+    tight = dict(tol_mb=1e-10, tol_cnv=1e-10, tol_well=1e-10, tol_lin=1e-10)
+    sts, _ = ens.step(1.0 * synth.DAY, **tight)
+    assert all(st == 0 for st in sts)
+    for o, s in zip(orc, ens.members):
+        st, _ = o.step(1.0 * synth.DAY, **tight)
+        assert st == 0
+        pg, pgo = s.get_state()[0], o.get_state()[0]
+        assert np.max(np.abs(pg - pgo) / pgo) <= 1e-6
+    ens.close()
+
+
 def test_failing_members_are_reported_and_restored():
     """A Newton budget of zero with no cuts fails every member: the step
     reports each failure and leaves each member at the start of the step."""

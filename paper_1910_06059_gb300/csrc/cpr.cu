@@ -553,6 +553,19 @@ k_cpr_jac0(Geom g, const double* __restrict__ ap, const double* __restrict__ din
         y[c] = x[c] + CPR_OMEGA * dinv[c] * (b[c] - s);
     }
 }
+// Prolongation folded into the last kernel that writes a coarse level's x:
+// each coarse row I adds its final value to the finer level's x at the
+// members of aggregate I (every fine node has one aggregate: no conflicts).
+struct Prolong {
+    const int* mptr = nullptr;
+    const int* mem = nullptr;
+    double* xf = nullptr;
+};
+__device__ __forceinline__ void prolong_row(const Prolong& up, int I, double xI) {
+    if (up.xf == nullptr) return;
+    for (int q = up.mptr[I]; q < up.mptr[I + 1]; ++q) up.xf[up.mem[q]] += xI;
+}
+
 // Levels >= 1 in ELL form: one thread per row, the W entries of a row read
 // at e n + i (coalesced over the rows of a warp), all loads of a row
 // independent of each other.
@@ -564,15 +577,18 @@ __device__ __forceinline__ double ell_dot(int n, int W, int i, const int* __rest
     return s;
 }
 
-// y = x + omega dinv (b - A x)
+// y = x + omega dinv (b - A x); with up, y is also added into the finer level
 __global__ void __launch_bounds__(CPR_BS)
 k_cpr_jac(int n, int W, const int* __restrict__ col, const double* __restrict__ val,
           const double* __restrict__ dinv, const double* __restrict__ b,
-          const double* __restrict__ x, double* __restrict__ y,
+          const double* __restrict__ x, double* __restrict__ y, Prolong up,
           const KrylovScalars* __restrict__ ks) {
     if (ks != nullptr && ks->state != KS_RUN) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        y[i] = x[i] + CPR_OMEGA * dinv[i] * (b[i] - ell_dot(n, W, i, col, val, x));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double yi = x[i] + CPR_OMEGA * dinv[i] * (b[i] - ell_dot(n, W, i, col, val, x));
+        y[i] = yi;
+        prolong_row(up, i, yi);
+    }
 }
 
 // residual y = b - A x
@@ -606,24 +622,19 @@ __global__ void __launch_bounds__(CPR_BS)
 k_cpr_csr32(int n, const int* __restrict__ rowptr, const int* __restrict__ colind,
             const double* __restrict__ val, const double* __restrict__ dinv,
             const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ y,
-            const KrylovScalars* __restrict__ ks) {
+            Prolong up, const KrylovScalars* __restrict__ ks) {
     if (ks != nullptr && ks->state != KS_RUN) return;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int i = warp; i < n; i += nwarps) {   // warp-uniform
         const double s = row_dot32(i, true, lane, rowptr, colind, val, x);
-        if (lane == 0) y[i] = RES ? b[i] - s : x[i] + CPR_OMEGA * dinv[i] * (b[i] - s);
+        if (lane == 0) {
+            const double yi = RES ? b[i] - s : x[i] + CPR_OMEGA * dinv[i] * (b[i] - s);
+            y[i] = yi;
+            if (!RES) prolong_row(up, i, yi);
+        }
     }
-}
-
-// coarse correction: x += P xc (each node takes its aggregate's value)
-__global__ void __launch_bounds__(CPR_BS)
-k_cpr_prolong(int n, const double* __restrict__ xc, const int* __restrict__ agg,
-              double* __restrict__ x, const KrylovScalars* __restrict__ ks) {
-    if (ks != nullptr && ks->state != KS_RUN) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        x[i] += xc[agg[i]];
 }
 
 // residual y = b - A x on level 0 (one thread per cell, coalesced)
@@ -636,28 +647,33 @@ k_cpr_res0(Geom g, const double* __restrict__ ap, const double* __restrict__ b,
         y[c] = b[c] - ax0(g, ap, c, [&](int j) { return x[j]; });
 }
 
-// coarse right-hand side: bc[I] = sum over the members of I (ascending) of y
+// coarse right-hand side: bc[I] = sum over the members of I (ascending) of y;
+// with yc, also the coarse level's first pre-smoothing sweep from zero,
+// yc = omega dinv_c bc
 __global__ void __launch_bounds__(CPR_BS)
 k_cpr_sum(int nc, const int* __restrict__ mptr, const int* __restrict__ mem,
           const double* __restrict__ y, double* __restrict__ bc,
+          const double* __restrict__ dinv_c, double* __restrict__ yc,
           const KrylovScalars* __restrict__ ks) {
     if (ks != nullptr && ks->state != KS_RUN) return;
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int q = mptr[I]; q < mptr[I + 1]; ++q) s += y[mem[q]];
         bc[I] = s;
+        if (yc) yc[I] = CPR_OMEGA * dinv_c[I] * s;
     }
 }
 
 // coarsest level: x = A^-1 b (dense)
 __global__ void __launch_bounds__(CPR_BS)
 k_cpr_coarse_apply(int nc, const double* __restrict__ cinv, const double* __restrict__ b,
-                   double* __restrict__ x, const KrylovScalars* __restrict__ ks) {
+                   double* __restrict__ x, Prolong up, const KrylovScalars* __restrict__ ks) {
     if (ks != nullptr && ks->state != KS_RUN) return;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nc; r += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int q = 0; q < nc; ++q) s += cinv[(size_t)r * nc + q] * b[q];
         x[r] = s;
+        prolong_row(up, r, s);
     }
 }
 
@@ -739,13 +755,13 @@ static int grid_warps(int n) {
     return std::max(1, std::min(CPR_GRID_ROWS, (n + CPR_BS / 32 - 1) / (CPR_BS / 32)));
 }
 static void jac_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
-                    const KrylovScalars* ks) {
+                    const KrylovScalars* ks, Prolong up = Prolong{}) {
     if (v.ell)
         k_cpr_jac<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.dinv, v.b, x,
-                                                        y, ks);
+                                                        y, up, ks);
     else
         k_cpr_csr32<false><<<grid_warps(v.n), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val,
-                                                              v.dinv, v.b, x, y, ks);
+                                                              v.dinv, v.b, x, y, up, ks);
     count_launch(s, st);
 }
 static void res_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double* x, double* y,
@@ -754,17 +770,18 @@ static void res_ell(bo_sim* s, cudaStream_t st, const CprLevel& v, const double*
         k_cpr_res<<<grid_for_rows(v.n), CPR_BS, 0, st>>>(v.n, v.W, v.ecol, v.eval, v.b, x, y, ks);
     else
         k_cpr_csr32<true><<<grid_warps(v.n), CPR_BS, 0, st>>>(v.n, v.rowptr, v.colind, v.val,
-                                                             v.dinv, v.b, x, y, ks);
+                                                             v.dinv, v.b, x, y, Prolong{}, ks);
     count_launch(s, st);
 }
 
 // One V-cycle of levels l.. on lv[l].b, result in lv[l].x; on level 0 the
 // right-hand side is w^T r (or lv[0].b as it stands when r is null).
-// Pre-smoothing: two sweeps from zero (-> y -> x); restriction: the residual
-// b - A x into y, summed per aggregate into the next level's b; post-smoothing:
-// x += P xc, then two sweeps x -> y -> x.
+// Pre-smoothing: two sweeps from zero (-> y -> x; on the coarse levels the
+// first comes with the restriction into the level); restriction: the residual
+// b - A x into y, summed per aggregate into the next level's b; the coarser
+// levels' last kernel adds P xc into x; post-smoothing: two sweeps x -> y -> x.
 static void vcycle(bo_sim* s, cudaStream_t st, size_t l, const double* r,
-                   const KrylovScalars* ks) {
+                   const KrylovScalars* ks, Prolong up = Prolong{}) {
     CprData* c = s->cpr;
     CprLevel& v = c->lv[l];
     const Geom& g = s->geo;
@@ -774,11 +791,12 @@ static void vcycle(bo_sim* s, cudaStream_t st, size_t l, const double* r,
             k_cpr_pre0<<<gr, CPR_BS, 0, st>>>(v.n, c->w, r, v.dinv, v.b, v.y, ks);
             count_launch(s, st);
         }
-        k_cpr_coarse_apply<<<gr, CPR_BS, 0, st>>>(v.n, c->cinv, v.b, v.x, ks);
+        k_cpr_coarse_apply<<<gr, CPR_BS, 0, st>>>(v.n, c->cinv, v.b, v.x, up, ks);
         count_launch(s, st);
         return;
     }
     CprLevel& w = c->lv[l + 1];
+    const bool w_coarsest = l + 2 == c->lv.size();
     if (l == 0) {
         if (r)
             k_cpr_pre0<<<gr, CPR_BS, 0, st>>>(v.n, c->w, r, v.dinv, v.b, v.y, ks);
@@ -789,17 +807,14 @@ static void vcycle(bo_sim* s, cudaStream_t st, size_t l, const double* r,
         count_launch(s, st);
         k_cpr_res0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.b, v.x, v.y, ks);
         count_launch(s, st);
-    } else {
-        k_cpr_pre<<<gr, CPR_BS, 0, st>>>(v.n, v.b, v.dinv, v.y, ks);
-        count_launch(s, st);
+    } else {   // the first sweep from zero came with the restriction into this level
         jac_ell(s, st, v, v.y, v.x, ks);
         res_ell(s, st, v, v.x, v.y, ks);
     }
-    k_cpr_sum<<<grid_for(w.n), CPR_BS, 0, st>>>(w.n, v.mptr, v.mem, v.y, w.b, ks);
+    k_cpr_sum<<<grid_for(w.n), CPR_BS, 0, st>>>(w.n, v.mptr, v.mem, v.y, w.b, w.dinv,
+                                               w_coarsest ? nullptr : w.y, ks);
     count_launch(s, st);
-    vcycle(s, st, l + 1, r, ks);
-    k_cpr_prolong<<<gr, CPR_BS, 0, st>>>(v.n, w.x, v.agg, v.x, ks);
-    count_launch(s, st);
+    vcycle(s, st, l + 1, r, ks, Prolong{v.mptr, v.mem, v.x});   // adds P xc into v.x
     if (l == 0) {
         k_cpr_jac0<<<gr, CPR_BS, 0, st>>>(g, v.val, v.dinv, v.b, v.x, v.y, ks);
         count_launch(s, st);
@@ -807,7 +822,7 @@ static void vcycle(bo_sim* s, cudaStream_t st, size_t l, const double* r,
         count_launch(s, st);
     } else {
         jac_ell(s, st, v, v.x, v.y, ks);
-        jac_ell(s, st, v, v.y, v.x, ks);
+        jac_ell(s, st, v, v.y, v.x, ks, up);
     }
 }
 

@@ -633,6 +633,7 @@ def run_ensemble(args):
     cand = (1, 4, 8, 16, 32, 64)
     tune = ens.autotune(0.05 * 86400.0, candidates=cand)
     tune_pc = ens.autotune_precond(0.05 * 86400.0)
+    tune_sc = ens.autotune_schedule(0.05 * 86400.0)
     for _ in range(args.warmup):
         ens.step(dt)
     torch.cuda.synchronize()
@@ -697,6 +698,14 @@ def run_ensemble(args):
                 "traffic": None, "algorithmic_bytes": int(byt / nl),
                 "peak_source": pk["source"], "avg_launch_ms": round(tot_ms / nl, 4),
                 "launches": nl, "note": "all members' launches; members run concurrently"}
+    # one-CTA solves of the small members (BO_SCHEDULE_BLOCK), when chosen
+    bl = [t["block_bicgstab"] for t in timers if "block_bicgstab" in t]
+    block = None
+    if bl:
+        bms, bn = sum(v[0] for v in bl), sum(v[1] for v in bl)
+        block = {"members": len(bl), "launches": bn, "ms_total": round(bms, 1),
+                 "avg_launch_ms": round(bms / max(bn, 1), 3),
+                 "note": "one launch of one CTA per linear solve; members overlap on the SMs"}
     # the same first report step, members one at a time on one stream, on a
     # sample of the members (largest and smallest mixed as in the ensemble)
     k = min(args.seq_sample, len(models))
@@ -728,11 +737,14 @@ def run_ensemble(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": (f"batched ensemble of {len(models)} members (nx, ny in 20..64, "
                                 f"nz in 5..16; {all_cells} cells), {dt / 86400.0:g}-day report steps, "
-                                "FP64 BiCGStab per member with ILU0 or CPR chosen per size "
-                                "class by the autotuner, Newton tol 1e-6"),
+                                "FP64 BiCGStab per member with ILU0 or CPR and the tiled or "
+                                "one-CTA solve schedule chosen per size class by the autotuner, "
+                                "Newton tol 1e-6"),
                    "cells": all_cells, "members": args.members,
                    "schedule": tune["chosen"],
                    "precond_by_size": tune_pc["chosen"],
+                   "solve_schedule_small": tune_sc["chosen"]["small"],
+                   "streams": tune_sc["chosen"]["streams"],
                    "timing": "CUDA events bracketing every worker stream of the step",
                    "l2": "members' Jacobians and ILU data together exceed L2",
                    "parallelism": f"members split over {world} GPUs" if world > 1 else "single GPU"},
@@ -746,6 +758,8 @@ def run_ensemble(args):
         "cpu_baseline": cpu,
         "autotune_probe_s": tune,
         "autotune_precond_probe_s": tune_pc["probe_s"],
+        "autotune_schedule_probe_s": tune_sc["probe_s"],
+        "block_solve": block,
         "sequential": {"value": seq_value, "unit": "cell-steps/s",
                        "sample": f"first report step of {k} members one at a time on one stream "
                                  f"({cells_sample} cells, {sec_seq:.2f} s host clock, "

@@ -370,6 +370,26 @@ bo_status bo_get_timing(const bo_sim* sim, int max, char (*names)[32], double* m
 bo_status bo_set_preconditioner(bo_sim* sim, int kind);
 bo_status bo_get_preconditioner(const bo_sim* sim, int* kind);
 
+/* Schedule of the linear solve (Section 2.3.1's ILU0-BiCGStab; the paper runs
+ * it as a sequence of parallel kernels, which is BO_SCHEDULE_TILED here).
+ * BO_SCHEDULE_TILED (default): the wavefront-tiled sweeps and vector kernels
+ * over the whole GPU, replayed as CUDA graphs of a few iterations each.
+ * BO_SCHEDULE_BLOCK: the whole solve (reduced right-hand side aside) is ONE
+ * launch of ONE 256-thread CTA: triangular sweeps by levels i + j + k inside
+ * the CTA, the operator, the dot products, the recurrence and its true
+ * residual checks and restarts, with the tiled factorisation's ILU(0) data;
+ * meant for small models stepped side by side (an ensemble), where it frees
+ * the rest of the GPU for the other models.  Same recurrence and stopping
+ * rules, results equal to rounding.  It applies while the preconditioner is
+ * FP64 ILU(0) without block-Jacobi cuts, the wells are the reduced standard
+ * wells (at most 128), no learned stage runs and ceil(ny/8) ceil(nz/4) <= 128;
+ * otherwise the tiled schedule runs.  bo_precond_apply follows the schedule.
+ * Errors: BO_ERR_INVALID_ARG for an unknown kind or a NULL sim. */
+#define BO_SCHEDULE_TILED 0
+#define BO_SCHEDULE_BLOCK 1
+bo_status bo_set_solve_schedule(bo_sim* sim, int kind);
+bo_status bo_get_solve_schedule(const bo_sim* sim, int* kind);
+
 /* The CPR aggregation hierarchy (for checking): *nlevels levels, sizes[l]
  * unknowns on level l (up to max_levels entries), agg = the maps of levels
  * 0 .. nlevels-2 concatenated (agg[off_l + i] = aggregate of node i of level
@@ -580,6 +600,19 @@ bo_status bo_ensemble_last_step_ms(const bo_ensemble* ens, double* ms);
  * preconditioners are then as before). */
 bo_status bo_ensemble_autotune_precond(bo_ensemble* ens, double dt_probe, const bo_newton_opts* opts,
                                       double* seconds, int* small_kind, int* large_kind);
+/* Solve schedule of the small members (up to the median cell count; the
+ * larger ones keep BO_SCHEDULE_TILED) and the number of worker streams: one
+ * probe report step of length dt_probe times each of (BO_SCHEDULE_TILED, w),
+ * (BO_SCHEDULE_BLOCK, w), (BO_SCHEDULE_TILED, w4), (BO_SCHEDULE_BLOCK, w4),
+ * w the current worker count and w4 = min(256, 4 w) (one-CTA solves leave
+ * the SMs to other members, so more of them can run at once), putting every
+ * member's state and step control back after each; the fastest combination
+ * whose probe stepped every member is kept.  seconds[4] (may be NULL)
+ * receives the probe times in that order, *small_schedule and *streams (may
+ * be NULL) the choice.  BO_ERR_NOT_CONVERGED if no combination stepped every
+ * member (schedules and worker count are then as before). */
+bo_status bo_ensemble_autotune_schedule(bo_ensemble* ens, double dt_probe, const bo_newton_opts* opts,
+                                       double* seconds, int* small_schedule, int* streams);
 bo_status bo_ensemble_destroy(bo_ensemble* ens);
 
 /* Self-test of failure detection: runs the bounded device-side wait of the

@@ -113,6 +113,7 @@ _SIGS = {
     "bo_ensemble_autotune": [P, c_double, P, P, c_int, P],
     "bo_ensemble_last_step_ms": [P, P],
     "bo_ensemble_autotune_precond": [P, c_double, P, P, P, P],
+    "bo_ensemble_autotune_schedule": [P, c_double, P, P, P, P],
     "bo_ensemble_destroy": [P],
     "bo_learn_set_params": [P, P, c_int],
     "bo_learn_get_params": [P, P, c_int],
@@ -137,6 +138,8 @@ _SIGS = {
     "bo_set_preconditioner": [P, c_int],
     "bo_learn_guard": [P, c_int],
     "bo_get_preconditioner": [P, P],
+    "bo_set_solve_schedule": [P, c_int],
+    "bo_get_solve_schedule": [P, P],
     "bo_cpr_hierarchy": [P, c_int, P, P, P],
     "bo_cpr_pressure_system": [P, P, P],
     "bo_cpr_vcycle": [P, P, P],
@@ -148,6 +151,7 @@ _SIGS = {
 EXPORTED = sorted(list(_SIGS) + ["bo_last_error"])
 
 PRECONDITIONER = {"ilu0": 0, "cpr": 1}
+SCHEDULE = {"tiled": 0, "block": 1}
 WELL_MODEL = {"reduced": 0, "standard": 1}
 
 STATUS = {0: "BO_OK", 1: "BO_ERR_INVALID_ARG", 2: "BO_ERR_CUDA", 3: "BO_ERR_OOM",

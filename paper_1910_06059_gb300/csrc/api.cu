@@ -1295,6 +1295,22 @@ bo_status bo_get_preconditioner(const bo_sim* s, int* kind) {
     });
 }
 
+bo_status bo_set_solve_schedule(bo_sim* s, int kind) {
+    return guarded([&] {
+        need(s != nullptr, BO_ERR_INVALID_ARG, "bo_set_solve_schedule: sim is NULL");
+        need(kind == BO_SCHEDULE_TILED || kind == BO_SCHEDULE_BLOCK, BO_ERR_INVALID_ARG,
+             "bo_set_solve_schedule: kind must be BO_SCHEDULE_TILED or BO_SCHEDULE_BLOCK");
+        s->solve_schedule = kind;
+    });
+}
+
+bo_status bo_get_solve_schedule(const bo_sim* s, int* kind) {
+    return guarded([&] {
+        need(s != nullptr && kind != nullptr, BO_ERR_INVALID_ARG, "bo_get_solve_schedule: NULL argument");
+        *kind = s->solve_schedule;
+    });
+}
+
 bo_status bo_cpr_hierarchy(const bo_sim* s, int max_levels, int* nlevels, int* sizes, int* agg) {
     return guarded([&] {
         need(s != nullptr && nlevels != nullptr && sizes != nullptr, BO_ERR_INVALID_ARG,

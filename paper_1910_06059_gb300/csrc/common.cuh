@@ -232,6 +232,7 @@ struct bo_sim {
 
     // CPR two-stage preconditioner (cpr.cu); precond: BO_PRECOND_*
     int precond = 0;
+    int solve_schedule = 0;   // BO_SCHEDULE_*: tiled kernels or one CTA per solve
     bo::CprData* cpr = nullptr;
     bo::DdData* dd = nullptr;   // K-subdomain solver (dd.cu)
 
@@ -297,6 +298,11 @@ void launch_precond(bo_sim* s, const double* r, double* z);
 void launch_op(bo_sim* s, const double* x, double* y);
 // returns LS_*; fp64: FP64 sweeps even in mixed mode (the fallback solve)
 int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool fp64 = false);
+// one-CTA solve of a small model (block_solve.cu)
+bool block_solve_fits(const bo_sim* s);
+bool block_solve_active(const bo_sim* s);
+int run_block_bicgstab(bo_sim* s, double tol, int maxit, int max_restarts, int* its);
+void launch_block_precond(bo_sim* s, const double* r, double* z);
 void launch_well_recover(bo_sim* s);
 // the preconditioner application of BiCGStab: ILU(0) or CPR, z = M^-1 r
 void enqueue_precond_apply(bo_sim* s, cudaStream_t st, const double* r, double* z,

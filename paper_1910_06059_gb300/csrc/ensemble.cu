@@ -341,6 +341,76 @@ bo_status bo_ensemble_autotune_precond(bo_ensemble* e, double dt_probe, const bo
     return BO_OK;
 }
 
+bo_status bo_ensemble_autotune_schedule(bo_ensemble* e, double dt_probe, const bo_newton_opts* opts,
+                                       double* seconds, int* small_schedule, int* streams) {
+    if (e == nullptr || !(dt_probe > 0.0))
+        return set_last_error(BO_ERR_INVALID_ARG,
+                              "bo_ensemble_autotune_schedule: NULL ensemble or dt_probe <= 0");
+    const int count = (int)e->members.size();
+    std::vector<int> sizes(count);
+    for (int q = 0; q < count; ++q) sizes[q] = e->members[q]->geo.n;
+    std::vector<int> sorted = sizes;
+    std::sort(sorted.begin(), sorted.end());
+    const int median = sorted[(count - 1) / 2];
+    std::vector<Snapshot> snap(count);
+    std::vector<int> sched0(count);
+    for (int q = 0; q < count; ++q) {
+        bo_status s = snapshot(e->members[q], snap[q]);
+        if (s != BO_OK) return s;
+        sched0[q] = e->members[q]->solve_schedule;
+    }
+    const int w0 = e->active;
+    const int wide = std::min(256, std::max(w0, 4 * w0));
+    // (schedule of the small members, workers)
+    const int combos[4][2] = {{BO_SCHEDULE_TILED, w0}, {BO_SCHEDULE_BLOCK, w0},
+                              {BO_SCHEDULE_TILED, wide}, {BO_SCHEDULE_BLOCK, wide}};
+    auto apply = [&](int kind) {
+        for (int q = 0; q < count; ++q)
+            e->members[q]->solve_schedule = sizes[q] <= median ? kind : BO_SCHEDULE_TILED;
+    };
+    double best = 1e300;
+    int best_c = -1;
+    for (int c = 0; c < 4; ++c) {
+        apply(combos[c][0]);
+        e->active = combos[c][1];
+        std::vector<bo_status> st(count, BO_OK);
+        const auto t0 = std::chrono::steady_clock::now();
+        try {
+            run_step(e, dt_probe, opts, nullptr, st.data());
+        } catch (const std::exception&) {
+            e->active = w0;
+            return set_last_error(BO_ERR_STATE, "bo_ensemble_autotune_schedule: out of host memory");
+        }
+        const double sec =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (seconds) seconds[c] = sec;
+        for (int q = 0; q < count; ++q) {
+            const bo_status s = restore(e->members[q], snap[q]);
+            if (s != BO_OK) {
+                e->active = w0;
+                return s;
+            }
+        }
+        bool ok = true;
+        for (int q = 0; q < count; ++q) ok = ok && st[q] == BO_OK;
+        if (ok && sec < best) {
+            best = sec;
+            best_c = c;
+        }
+    }
+    if (best_c < 0) {   // no combination stepped every member: back to what they had
+        for (int q = 0; q < count; ++q) e->members[q]->solve_schedule = sched0[q];
+        e->active = w0;
+        return set_last_error(BO_ERR_NOT_CONVERGED,
+                              "bo_ensemble_autotune_schedule: no combination stepped every member");
+    }
+    apply(combos[best_c][0]);
+    e->active = combos[best_c][1];
+    if (small_schedule) *small_schedule = combos[best_c][0];
+    if (streams) *streams = combos[best_c][1];
+    return BO_OK;
+}
+
 bo_status bo_ensemble_last_step_ms(const bo_ensemble* e, double* ms) {
     if (e == nullptr || ms == nullptr)
         return set_last_error(BO_ERR_INVALID_ARG, "bo_ensemble_last_step_ms: NULL argument");

@@ -730,6 +730,10 @@ void launch_factor(bo_sim* s) {
 }
 
 void launch_precond(bo_sim* s, const double* r, double* z) {
+    if (block_solve_active(s)) {
+        launch_block_precond(s, r, z);
+        return;
+    }
     enqueue_precond_apply(s, s->stream, r, z, nullptr);
 }
 
@@ -833,6 +837,7 @@ void enqueue_reduced_rhs(bo_sim* s, cudaStream_t st) {
 }
 
 int run_bicgstab(bo_sim* s, double tol, int maxit, int* its, bool use_ml, bool fp64) {
+    if (block_solve_active(s)) return run_block_bicgstab(s, tol, maxit, MAX_RESTARTS, its);
     const int N = 3 * s->geo.n;
     cudaStream_t st = s->stream;
     enqueue_reduced_rhs(s, st);

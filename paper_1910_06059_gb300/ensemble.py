@@ -83,6 +83,24 @@ class Ensemble:
         return {"probe_s": {f"small {a}, large {b}": float(t) for (a, b), t in zip(combos, sec)},
                 "chosen": {"small": names[ks.value], "large": names[kl.value]}}
 
+    def autotune_schedule(self, dt_probe, **opts):
+        """Solve schedule of the members up to the median size ("tiled" or
+        "block") and the worker count (current or four times it, at most
+        256) from a probe step of each of the four combinations; returns the
+        probe times and the choice."""
+        o = L.newton_opts(**opts)
+        sec = np.zeros(4)
+        ks, ws = ctypes.c_int(), ctypes.c_int()
+        w0 = self.schedule["streams"]
+        call("bo_ensemble_autotune_schedule", self.h, float(dt_probe), ctypes.byref(o),
+             sec.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ks), ctypes.byref(ws))
+        names = {v: k for k, v in L.SCHEDULE.items()}
+        labels = ["small tiled, workers w", "small block, workers w",
+                  "small tiled, workers 4w", "small block, workers 4w"]
+        return {"probe_s": {k: float(t) for k, t in zip(labels, sec)},
+                "chosen": {"small": names[ks.value], "streams": int(ws.value)},
+                "workers_before": w0}
+
     def last_step_ms(self):
         """Device time (CUDA events) of the last step, in ms (-1: not measured)."""
         v = ctypes.c_double()

@@ -312,6 +312,18 @@ class Sim:
     def preconditioner(self, name):
         call("bo_set_preconditioner", self.h, L.PRECONDITIONER[name])
 
+    @property
+    def solve_schedule(self):
+        """"tiled" (wavefront-tiled kernels over the GPU) or "block" (the whole
+        ILU(0)-BiCGStab solve in one launch of one CTA, for small models)."""
+        v = ctypes.c_int()
+        call("bo_get_solve_schedule", self.h, ctypes.byref(v))
+        return {q: k for k, q in L.SCHEDULE.items()}[v.value]
+
+    @solve_schedule.setter
+    def solve_schedule(self, name):
+        call("bo_set_solve_schedule", self.h, L.SCHEDULE[name])
+
     def cpr_hierarchy(self):
         """(sizes per level, aggregation maps of levels 0 .. L-2)."""
         nl = ctypes.c_int()

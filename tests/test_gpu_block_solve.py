@@ -119,17 +119,23 @@ def test_block_solve_equals_tiled_solve_to_rounding():
     # the tiled schedule's solution test)
     m, g, o = _pair("ragged_33x17x9", seed=3)
     g.assemble(0.1 * synth.DAY)
-    # both solve to a 1e-12 relative residual: their difference is bounded by
-    # the condition number times that, as for the oracle comparison
+    # Both solve to a 1e-12 relative residual.  Two such solutions differ by
+    # up to the condition number times that (measured here: 2.6e-9 of the
+    # family maximum on this system), so what must agree is that each solves
+    # the oracle's unreduced system; the solutions themselves agree to 1e-7.
+    o.assemble(0.1 * synth.DAY)
     stb, itb, solb, rep_b = g.solve(tol=1e-12, maxit=500, report=True)
     g.solve_schedule = "tiled"
     stt, itt, solt, rep_t = g.solve(tol=1e-12, maxit=500, report=True)
     assert stb == stt == 0, (stb, itb, rep_b, stt, itt, rep_t)
     assert abs(itb - itt) <= max(2, 0.05 * itt)
-    n = o.n
-    for v in range(3):
-        assert vec_close(solb[v:3 * n:3], solt[v:3 * n:3]) <= 1e-9
     assert rep_b["rel_res"] <= 1e-12 and rep_t["rel_res"] <= 1e-12
+    n = o.n
+    scale = np.abs(o.system()[3]).max()
+    for sol in (solb, solt):
+        assert np.max(np.abs(o.residual_check(sol)[:3 * n])) <= 1e-9 * scale
+    for v in range(3):
+        assert vec_close(solb[v:3 * n:3], solt[v:3 * n:3]) <= 1e-7
 
 
 def test_block_iteration_limit_and_status():

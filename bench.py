@@ -134,6 +134,14 @@ def parse():
     ap.add_argument("--sweep-ctas-per-sm", type=int, default=0,
                     help="persistent CTAs per SM of the FP64 sweeps (1 or 2; 0: the library's default)")
     ap.add_argument("--members", type=int, default=256, help="ensemble members (config 3)")
+    ap.add_argument("--ens-streams", type=int, default=0,
+                    help="config 3: worker streams (0: the autotuner picks them)")
+    ap.add_argument("--ens-precond", default="auto", choices=["auto", "ilu0", "cpr", "ilu0,cpr"],
+                    help="config 3: preconditioner of every member, or 'small,large' by size "
+                         "class (auto: the autotuner picks per size class)")
+    ap.add_argument("--ens-small-schedule", default="auto", choices=["auto", "tiled", "block"],
+                    help="config 3: solve schedule of the members up to the median size "
+                         "(auto: the autotuner picks it)")
     ap.add_argument("--seq-sample", type=int, default=32,
                     help="members stepped one at a time for the sequential comparison (config 3)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
@@ -631,9 +639,27 @@ def run_ensemble(args):
     ens = Ensemble(models, streams=8)
     ens.init_hydrostatic()
     cand = (1, 4, 8, 16, 32, 64)
-    tune = ens.autotune(0.05 * 86400.0, candidates=cand)
-    tune_pc = ens.autotune_precond(0.05 * 86400.0)
-    tune_sc = ens.autotune_schedule(0.05 * 86400.0)
+    sizes = [sm.n for sm in ens.members]
+    median = sorted(sizes)[(len(sizes) - 1) // 2]
+    if args.ens_streams > 0:
+        ens.set_schedule(args.ens_streams, largest_first=True)
+        tune = {"chosen": ens.schedule, "given": True}
+    else:
+        tune = ens.autotune(0.05 * 86400.0, candidates=cand)
+    if args.ens_precond == "auto":
+        tune_pc = ens.autotune_precond(0.05 * 86400.0)
+    else:
+        small, large = (args.ens_precond.split(",") * 2)[:2]
+        for sm, sz in zip(ens.members, sizes):
+            sm.preconditioner = small if sz <= median else large
+        tune_pc = {"chosen": {"small": small, "large": large}, "probe_s": None}
+    if args.ens_small_schedule == "auto":
+        tune_sc = ens.autotune_schedule(0.05 * 86400.0)
+    else:
+        for sm, sz in zip(ens.members, sizes):
+            sm.solve_schedule = args.ens_small_schedule if sz <= median else "tiled"
+        tune_sc = {"chosen": {"small": args.ens_small_schedule, "streams": ens.schedule["streams"]},
+                   "probe_s": None}
     for _ in range(args.warmup):
         ens.step(dt)
     torch.cuda.synchronize()

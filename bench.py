@@ -139,9 +139,11 @@ def parse():
     ap.add_argument("--ens-precond", default="auto", choices=["auto", "ilu0", "cpr", "ilu0,cpr"],
                     help="config 3: preconditioner of every member, or 'small,large' by size "
                          "class (auto: the autotuner picks per size class)")
-    ap.add_argument("--ens-small-schedule", default="auto", choices=["auto", "tiled", "block"],
+    ap.add_argument("--ens-small-schedule", default="tiled", choices=["auto", "tiled", "block"],
                     help="config 3: solve schedule of the members up to the median size "
-                         "(auto: the autotuner picks it)")
+                         "(auto: the autotuner's short probe picks it; that probe does not "
+                         "separate the two, and the one-CTA solve is the slower on whole "
+                         "report steps, so the default is tiled)")
     ap.add_argument("--seq-sample", type=int, default=32,
                     help="members stepped one at a time for the sequential comparison (config 3)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],

@@ -53,6 +53,35 @@ ALGO_BYTES_PER_CELL_MIXED.update({
     "ilu_bwd_sweep": 27 * 4 + 12 + 24,
 })
 
+# FP64 floating-point operations per cell of each timed kernel (an FMA counts
+# two), the co-limit on GB300 where FP64 runs at 1/64 of the FP32 rate:
+ALGO_FP64_FLOPS_PER_CELL = {
+    # D^-1 r (9 FMA) and three scaled lower blocks times a 3-vector (27 FMA)
+    "ilu_fwd_sweep": 2 * 36,
+    # three scaled upper blocks times a 3-vector
+    "ilu_bwd_sweep": 2 * 27,
+    # seven 3x3 blocks times a 3-vector
+    "spmv_wells": 2 * 63,
+    # D -= A_ck (D_k^-1 A_kc) for three lower neighbours (81 FMA), the 3x3
+    # inverse (~40 operations), six scaled blocks D^-1 A_cj (162 FMA)
+    "ilu_factor": 2 * (81 + 162) + 40,
+}
+# FP64 FMA throughput of this GPU, measured by a timing probe of dependent-free
+# DFMA streams on every SM (1.9 DFMA per clock per SM at 2070 MHz)
+FP64_PEAK_TFLOPS = 1.19
+
+
+def fp64_colimit(kernel, n, avg_s):
+    """Achieved FP64 rate of one launch of `kernel` over n cells taking avg_s
+    seconds, against the measured FP64 peak (None for a kernel not listed)."""
+    f = ALGO_FP64_FLOPS_PER_CELL.get(kernel)
+    if f is None or not avg_s > 0:
+        return None
+    tf = f * n / avg_s / 1e12
+    return {"flops_per_cell": f, "achieved_tflops": round(tf, 4), "peak_tflops": FP64_PEAK_TFLOPS,
+            "frac": round(tf / FP64_PEAK_TFLOPS, 4), "peak_source": "of measured (FP64 FMA probe)"}
+
+
 WORKLOADS = {
     0: "spe1-shaped 10x10x3, 30-day report steps",
     1: "layered 60x220x85 black-oil, 5-spot wells, 10-day report steps",
@@ -467,7 +496,8 @@ def run_gb300(args):
             "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
             "traffic": ncu_traffic(dominant, n) if args.precision == "fp64" else None,
             "algorithmic_bytes": algo, "peak_source": pk["source"],
-            "avg_launch_ms": round(avg_s * 1e3, 4), "launches": nlaunch}
+            "avg_launch_ms": round(avg_s * 1e3, 4), "launches": nlaunch,
+            "fp64": fp64_colimit(dominant, n, avg_s) if args.precision == "fp64" else None}
 
     counts = {"steps": args.steps,
               "assemblies": sum(r["newton_its"] + r["substeps"] + r["cuts"] for r in reps),

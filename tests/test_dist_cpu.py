@@ -57,3 +57,18 @@ def test_ensemble_members_shard_over_ranks():
         assert flat == list(range(256))
         sizes = [len(sh) for sh in shards]
         assert max(sizes) - min(sizes) <= 1
+
+
+def test_fp64_colimit_of_the_roofline():
+    """The bench's FP64 figure: flops per cell x cells / launch time against
+    the measured FP64 peak (the forward sweep at 0.436 ms on 1.122 M cells
+    runs 72 flop/cell = 0.185 TFLOP/s, 0.156 of 1.19)."""
+    import bench
+    r = bench.fp64_colimit("ilu_fwd_sweep", 1_122_000, 0.436e-3)
+    assert r["flops_per_cell"] == 72
+    assert r["achieved_tflops"] == pytest.approx(0.1853, abs=1e-4)
+    assert r["frac"] == pytest.approx(0.1853 / 1.19, abs=1e-4)
+    assert bench.fp64_colimit("cpr_apply", 1000, 1e-3) is None
+    assert bench.fp64_colimit("spmv_wells", 1000, 0.0) is None
+    for k in bench.ALGO_BYTES_PER_CELL:
+        assert k in bench.ALGO_FP64_FLOPS_PER_CELL

@@ -51,6 +51,8 @@ MODELS = {
     "config0": synth.config0,
     # 20 tiles (5 x 4) over 8 warps: several tiles per warp and level
     "ragged_21x37x13": lambda: synth.small_model(21, 37, 13, wells="5spot", dz=3.0),
+    # 32 tiles, the largest ensemble member's tiling: a 48 KB ring (shared-memory opt-in)
+    "tiles32_6x64x16": lambda: synth.small_model(6, 64, 16, wells="5spot", dz=3.0),
 }
 
 

@@ -30,7 +30,6 @@
 //
 // Scope: the FP64 ILU(0) preconditioner, reduced standard wells, no
 // block-Jacobi cuts; other configurations keep the tiled schedule.
-#include <atomic>
 #include <cmath>
 
 #include "tiles.cuh"
@@ -470,15 +469,14 @@ bool block_solve_active(const bo_sim* s) {
 
 static void launch_block(bo_sim* s, const BlockArgs& a) {
     const size_t smem = (size_t)2 * 3 * 32 * a.T * sizeof(double);
-    // Above 48 KB of static + dynamic shared memory a launch needs the opt-in.
-    // Every caller sets the same value (the ring of BLK_MAXT tiles), so
-    // concurrent callers (ensemble workers) cannot lower it under each other.
-    static std::atomic<bool> opted{false};
-    if (smem + 2048 > 48 * 1024 && !opted.load()) {
+    // Above 48 KB of static + dynamic shared memory a launch needs the opt-in,
+    // an attribute of the current context: it is set before every such launch
+    // (a new context after a reset needs it again), always to the same value
+    // (the ring of BLK_MAXT tiles), so concurrent callers (ensemble workers)
+    // cannot lower it under each other.
+    if (smem + 2048 > 48 * 1024)
         BO_CUDA(cudaFuncSetAttribute(k_block_bicgstab, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)((size_t)2 * 3 * 32 * BLK_MAXT * sizeof(double))));
-        opted.store(true);
-    }
     k_block_bicgstab<<<1, BLK_THREADS, smem, s->stream>>>(a);
     count_launch(s, s->stream);
     BO_LAUNCH_CHECK("k_block_bicgstab");

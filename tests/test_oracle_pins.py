@@ -1068,3 +1068,33 @@ def test_rate_injector_meets_its_target():
     lam_t = cp["lam_w"][0] + cp["lam_o"][0] + cp["lam_g"][0]
     q = o.static()["wi"][0] * lam_t * cp["b_w"][0] * (bhp[0] - p[c])
     assert q == pytest.approx(target, rel=1e-8)
+
+
+def test_rate_injector_switches_to_its_bhp_limit():
+    """A water injector asked for far more than its BHP limit allows: after
+    the update that would push p_bhp over the limit it switches to BHP
+    control (Section 2.2.1's control switch), ends the step exactly at the
+    limit, and injects what Eq. wellinflow gives at the limit,
+    WI lambda_t b_w (p_limit - p_j), by hand, less than the target.  (A well
+    that kept the rate target, or took the rate target as its BHP after the
+    switch, fails this.)"""
+    target = 1e5 * synth.STB / synth.DAY
+    limit = 5200 * PSI
+    wells = [_well(2, 2, [0], "inj", "rate", target, limit, phase="water"),
+             _well(0, 0, [0], "prod", "bhp", 3000 * PSI, 3000 * PSI),
+             _well(4, 4, [0], "prod", "bhp", 3000 * PSI, 3000 * PSI)]
+    m = make_model(5, 5, 1, 200 * MD, 0.2, wells, dx=30.0, dy=30.0, dz=6.0)
+    o = oracle.Oracle(m)
+    o.init_hydrostatic()
+    st, rep = o.step(0.5 * synth.DAY, tol_mb=1e-12, tol_cnv=1e-12, tol_well=1e-12, tol_lin=1e-12)
+    assert st == 0
+    p, sw, x, fl, bhp = o.get_state()
+    q, bhp_r, ctl = o.well_rates()
+    assert ctl[0] == 1 and bhp[0] == limit and bhp_r[0] == limit
+    c = 2 + 5 * 2
+    assert p[c] < limit
+    cp = _props_at(m, p[c], sw[c], x[c], fl[c])
+    lam_t = cp["lam_w"][0] + cp["lam_o"][0] + cp["lam_g"][0]
+    hand = o.static()["wi"][0] * lam_t * cp["b_w"][0] * (limit - p[c])
+    assert q[0][0] < 0 and -q[0][0] == pytest.approx(hand, rel=1e-8)
+    assert hand < 0.5 * target

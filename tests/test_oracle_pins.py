@@ -1098,3 +1098,27 @@ def test_rate_injector_switches_to_its_bhp_limit():
     hand = o.static()["wi"][0] * lam_t * cp["b_w"][0] * (limit - p[c])
     assert q[0][0] < 0 and -q[0][0] == pytest.approx(hand, rel=1e-8)
     assert hand < 0.5 * target
+
+
+def test_failed_step_restores_the_state_and_cuts_the_substep():
+    """Section 2.3's time-step control: a Newton solve that fails (here one
+    Newton iteration allowed, no cut allowed) leaves every unknown -- cell
+    pressures, saturations, r_go or s_g, phase states, well BHPs -- bit for
+    bit as at the step start, and the next sub-step is the failed one times
+    the cut factor; with cuts allowed the same step completes in more than
+    one sub-step."""
+    m = synth.small_model(6, 5, 4, wells="5spot", dz=4.0)
+    o = oracle.Oracle(m)
+    o.init_hydrostatic()
+    o.step(1.0 * synth.DAY)                 # a moving state (wells have flowed)
+    assert o.well_rates()[2][0] == 0        # the injector's BHP is an unknown (rate control)
+    before = [a.copy() for a in o.get_state()]
+    o.dt_next = 10.0 * synth.DAY
+    st, rep = o.step(30 * synth.DAY, max_newton=1, max_cuts=0)
+    assert st != 0 and rep["cuts"] == 1 and rep["substeps"] == 0
+    for a, b in zip(before, o.get_state()):
+        assert np.array_equal(a, b)
+    assert o.dt_next == 5.0 * synth.DAY
+    # six Newton iterations are too few for the 5-day sub-step, enough for 2.5 days
+    st, rep = o.step(30 * synth.DAY, max_newton=6, max_cuts=8)
+    assert st == 0 and rep["cuts"] >= 1 and rep["substeps"] >= 2
